@@ -1,0 +1,320 @@
+"""Benchmark of the electrokinetic LB-MD step on GB300.
+
+Workload (default): the translocation pore, 64 x 64 x 128 D3Q19 lattice,
+membrane z = 60..67 with a cylindrical pore of radius 4, 1:1 salt 0.005,
+E_z = 5e-3, a 32-bead FENE+WCA chain threaded through the pore, FP32
+populations, Poisson by red-black Chebyshev SOR to relative residual 1e-8.
+A step is one whole time step (charge, Poisson, beads, fused LB update).
+
+Metric: species-MLUPS = lattice nodes x 3 species x steps / s / 1e6, plus
+steps/s; the fused LB kernel is reported against the HBM roofline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own independent replica (the path
+has no data exchange between replicas), timing is the max over ranks and the
+value is the aggregate over all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EK-LB-MD steps/s & species-MLUPS vs HBM roofline; learned vs plain Poisson"
+UNIT = "species-MLUPS"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def lb_algorithmic_bytes(wl, store_bytes):
+    """Bytes one fused-LB launch must move at minimum: per fluid node 57
+    populations read and written, the link word and the potential (8 B, the
+    6 neighbours come from cache); per wall node the link word."""
+    nf = int((wl.solid == 0).sum())
+    ns = wl.n_nodes - nf
+    return nf * (2 * 57 * store_bytes + 4 + 8) + ns * 4
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload_for(name, rank=0):
+    from paper_1710_09421_gb300 import workloads as W
+    if name == "pore":
+        wl = W.config_pore_fp32()
+    elif name == "slit":
+        wl = W.config_slit_fp64().replace(precision="f32", poisson_tol=1e-8)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if rank:
+        wl = wl.replace(seed=wl.seed + 1000 * rank)  # independent replica per rank
+    return wl
+
+
+def cpu_baseline(wl, budget_s=20.0):
+    """The oracle, as it stands, on all host cores, over a bounded number of
+    steps of the same workload; returns species-MLUPS."""
+    import oracle
+    cores = os.cpu_count() or 1
+    ref = oracle.Sim(wl, threads=cores)
+    ref.step(1)  # first step includes the cold Poisson start
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        ref.step(1)
+        n += 1
+        if time.perf_counter() - t0 > budget_s or n >= 50:
+            break
+    dt = time.perf_counter() - t0
+    v = wl.n_nodes * 3 * n / dt / 1e6
+    return {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} oracle steps (after 1 warm-up step) of the {wl.name} workload, "
+                      f"FP64, {cores} threads, {dt:.1f} s",
+            "steps_per_s": round(n / dt, 4)}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return
+    wl = workload_for(args.workload)
+    import oracle
+    cores = os.cpu_count() or 1
+    ref = oracle.Sim(wl, threads=cores)
+    ref.step(max(1, min(args.warmup, 2)))
+    budget = 90.0
+    t0 = time.perf_counter()
+    n = 0
+    while n < args.steps:
+        ref.step(1)
+        n += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    value = wl.n_nodes * 3 * n / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": n, "warmup": max(1, min(args.warmup, 2)),
+        "ms_per_step": round(1e3 * dt / n, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "nodes": wl.n_nodes, "species": 3, "beads": wl.n_beads,
+                   "poisson_tol": wl.poisson_tol},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} of {args.steps} requested steps (time-capped at "
+                                   f"{budget:.0f} s) on the full lattice"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    world, rank, local = dist_setup(args)
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    import paper_1710_09421_gb300 as E
+
+    E.load()
+    wl = workload_for(args.workload, rank)
+    stream = torch.cuda.Stream()
+    sraw = stream.cuda_stream
+    store = {"f32": 4, "f64": 8, "bf16": 2, "fp16": 2}[args.precision]
+
+    # ---- device-resident timed run
+    sim = E.Simulation(wl, precision=args.precision, stream=sraw)
+    for _ in range(args.warmup):
+        sim.step(1)
+    sim.set_timing(True)
+    st0 = sim.stats()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        rc = sim.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    st1 = sim.stats()
+    ms_max = max_over_ranks(ms, world)
+    launches = st1["launches"] - st0["launches"]
+    ph = st1["ms_phase"]
+    iters = st1["poisson_iters"]
+    sim.close()
+
+    node_steps = wl.n_nodes * args.steps * world
+    value = node_steps * 3 / (ms_max / 1e3) / 1e6
+    steps_per_s = args.steps * world / (ms_max / 1e3)
+    lb_ms = ph["lb"] / args.steps
+    lb_bytes = lb_algorithmic_bytes(wl, store)
+    hbm, peak_kind = peaks()
+    achieved = lb_bytes / (lb_ms / 1e3) / 1e9
+
+    # ---- end to end through the public API: host inputs in, fields out
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    sim2 = E.Simulation(wl, precision=args.precision, stream=sraw)
+    sim2.step(e2e_steps)
+    F = sim2.fields(("n", "j", "phi", "R", "V"))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    sim2.close()
+    e2e_s = max_over_ranks(t1 - t0, world)
+    h2d = wl.n_nodes * (1 + 3 * 8) + (wl.n_beads * (3 + 3 + 1) * 8)
+    if wl.surface_charge is not None:
+        h2d += wl.n_nodes * 8
+    d2h = wl.n_nodes * (3 + 9 + 1) * 8 + wl.n_beads * 6 * 8
+    e2e_val = wl.n_nodes * e2e_steps * world * 3 / e2e_s / 1e6
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "f64": "f64", "bf16": "bf16-storage/f32", "fp16": "fp16-storage/f32"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": wl.name, "nodes": wl.n_nodes, "species": 3, "beads": wl.n_beads,
+                   "precision": args.precision, "poisson_tol": wl.poisson_tol,
+                   "l2": "inputs larger than L2 (populations 2 x %.0f MB)" % (
+                       wl.n_nodes * 57 * store / 1e6)},
+        "steps_per_s": round(steps_per_s, 3),
+        "poisson_sweeps_last_step": iters,
+        "phase_ms_per_step": {k: round(v / args.steps, 5) for k, v in ph.items()},
+        "roofline": {"kernel": "lb_fused_kernel", "bound": "hbm", "achieved": round(achieved, 1),
+                     "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                     "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": lb_bytes,
+                     "avg_launch_ms": round(lb_ms, 5)},
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+        "e2e": {"value": round(e2e_val, 3), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d / e2e_steps), "d2h_bytes_per_step": int(d2h / e2e_steps),
+                "what": "create from host arrays + beads + %d steps + all fields to host" % e2e_steps},
+        "status": rc,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget)
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pore")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16", "fp16"])
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

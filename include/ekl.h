@@ -1,0 +1,187 @@
+/*
+ * ekl.h -- C ABI of the GB300 electrokinetic lattice-Boltzmann / MD step.
+ *
+ * The library advances the method of Datar, Fyta, Marini Bettolo Marconi and
+ * Melchionna (arXiv:1710.09421): a ternary mixture (solvent, cation, anion)
+ * on a D3Q19 lattice (Sec. II.C), the Poisson equation for the potential
+ * (Eq. 3), and a bead-spring polyelectrolyte in Langevin dynamics (Sec. II.B)
+ * coupled to the fluid by frictional drag through a trilinear interpolation
+ * kernel (Sec. II.C, algorithm).  The caller states the problem as the paper
+ * does (Sec. II.C: geometry, boundary conditions, temperature and all fluid
+ * and molecular parameters are inputs) and drives it with these calls:
+ *
+ *   ekl_create      -> grid, wall map, surface charge, species, solver knobs
+ *   ekl_set_beads   -> bead positions, velocities, charges, chain ids
+ *   ekl_step        -> advance n lattice time steps on the GPU
+ *   ekl_get_fields  -> densities, currents, potential, bead state to the host
+ *   ekl_get_stats   -> FP64 totals, Poisson iterations / residual, status
+ *   ekl_destroy
+ *
+ * Units: lattice units, dx = dt = 1, m = 1, v_T^2 = 1/3, k_B T = m v_T^2 = 1/3
+ * (Sec. II.C).  The reduced potential phi = e psi / k_B T solves
+ * lap(phi) = -4 pi l_B rho_e with rho_e in proton charges per node (Eqs. 2-3);
+ * E_app is in k_B T / (e dx); wall surface charge in e per wall node.
+ *
+ * Layout: node id = x + nx (y + ny z); host arrays are row-major [nz][ny][nx];
+ * species 0 = solvent, 1 = cation, 2 = anion.
+ *
+ * Ownership: every input array is copied during the call; the caller keeps
+ * it.  Output pointers are caller-allocated HOST memory.  Device memory is
+ * owned by the handle (allocated with cudaMalloc, or through the allocator
+ * installed with ekl_set_allocator).
+ *
+ * Errors: every call returns EKL_OK (0), a positive warning bit set or a
+ * negative error code; ekl_last_error() returns a message for the calling
+ * thread.  A failed ekl_create leaves nothing allocated.  A step that fails
+ * with EKL_ERR_UNSTABLE / EKL_ERR_BEAD stops the step loop; the populations
+ * of the failing step are already written, so the state is the failed one.
+ */
+#ifndef EKL_H
+#define EKL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define EKL_OK 0
+#define EKL_WARN_NOCONV 1      /* Poisson hit poisson_max_iter before the tolerance */
+#define EKL_WARN_CFL 2         /* |z grad phi| >= 1 somewhere: the stability bound of Sec. III */
+#define EKL_ERR_ARG (-1)       /* bad sizes, odd periodic extent, null required pointer */
+#define EKL_ERR_ALLOC (-2)     /* device allocation failed */
+#define EKL_ERR_UNSTABLE (-3)  /* non-finite or non-positive species density */
+#define EKL_ERR_BEAD (-4)      /* bead inside walls / outside the box / FENE bond broken */
+#define EKL_ERR_TIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define EKL_ERR_CUDA (-6)      /* a CUDA runtime call failed */
+
+/* storage precision of the populations */
+#define EKL_F64 0      /* FP64 populations, FP64 arithmetic (the oracle's arithmetic) */
+#define EKL_F32 1      /* FP32 deviations from w_p n_ref, FP32 arithmetic */
+#define EKL_BF16DEV 2  /* BF16 deviations, FP32 arithmetic */
+#define EKL_FP16DEV 3  /* FP16 deviations, FP32 arithmetic */
+
+/* flags */
+#define EKL_EQ_BARYCENTRIC 1   /* f_eq and S use the barycentric velocity (printed Eq. 10) */
+#define EKL_GAMMA_LITERAL 2    /* bead drag gamma^a = xi for every species (literal Sec. II.B) */
+#define EKL_NO_BEAD_NOISE 4    /* no Langevin noise on the beads */
+
+#define EKL_BOND_FENE 0
+#define EKL_BOND_HARMONIC 1
+
+typedef struct ekl_handle ekl_handle;
+
+/* Problem statement (Sec. II.C: "geometry, boundary conditions, temperature,
+ * timesteps and all fluid and molecular parameters are given as input").
+ * Pointers are host pointers, read during ekl_create only. */
+typedef struct ekl_params {
+    int32_t nx, ny, nz;           /* lattice extents, each >= 2 */
+    int32_t periodic[3];          /* 1 = periodic axis (extent must be even: red-black) */
+    const uint8_t *solid;         /* [nz][ny][nx], 1 = wall node; required */
+    const double *surface_charge; /* [nz][ny][nx] e per wall node, or NULL (Sec. II.A) */
+    const double *n_init;         /* [3][nz][ny][nx] initial densities, or NULL = n_ref */
+    int32_t valence[3];           /* z^a (Sec. II.A); solvent 0 */
+    double diffusivity[3];        /* D^a -> omega_drag = v_T^2 / D^a (Eq. 6); <= 0: use D^1 */
+    double tau[3];                /* BGK relaxation time per species (Eq. 12: omega = 1/tau) */
+    double n_ref[3];              /* reference densities (deviation storage baseline) */
+    double body_force[3][3];      /* Phi_ext^a per particle (Eq. 5) */
+    double bjerrum;               /* l_B in lattice units */
+    double E_app[3];              /* applied field, k_B T / (e dx) */
+    double poisson_tol;           /* stop when ||r||_2 <= tol ||b||_2 */
+    int32_t poisson_max_iter;     /* cap on red+black sweeps per step */
+    int32_t poisson_check_every;  /* test the residual every k sweeps (>= 1) */
+    int32_t poisson_fixed_iter;   /* > 0: exactly this many sweeps, no test */
+    double rho_jacobi;            /* Jacobi spectral radius for Chebyshev omega; <= 0: box default */
+    int32_t md_substeps;          /* MD sub-steps per LB step (Sec. II.B), >= 1 */
+    double bead_xi;               /* total bead friction xi (Sec. II.B gamma) */
+    double bead_mass;             /* bead mass M */
+    int32_t bond_kind;            /* EKL_BOND_FENE or EKL_BOND_HARMONIC (Eq. 9c) */
+    double bond_k, bond_r0, bond_l0;           /* spring constant, FENE R0, harmonic rest length */
+    double wca_eps, wca_sigma, wall_eps, wall_sigma; /* WCA bead-bead (Eq. 9a), bead-wall */
+    uint64_t seed;                /* Philox key of the bead noise */
+    double bead_kT;               /* bead thermostat temperature (Eq. 8) */
+    int32_t flags;                /* EKL_EQ_BARYCENTRIC | EKL_GAMMA_LITERAL | EKL_NO_BEAD_NOISE */
+    int32_t precision;            /* EKL_F64 / EKL_F32 / EKL_BF16DEV / EKL_FP16DEV */
+} ekl_params;
+
+typedef struct ekl_stats {
+    double mass[3];          /* FP64 per-species total of the last step's densities */
+    int64_t step;            /* completed steps */
+    int32_t poisson_iters;   /* sweeps of the last step */
+    int32_t status;          /* accumulated warning bits of the last ekl_step */
+    double poisson_res;      /* ||r|| / ||b|| of the last step */
+    double ms_phase[6];      /* per-phase GPU time (ms) accumulated while timing is on:
+                                bead bin, charge, Poisson, bead MD, LB, other */
+    int64_t launches;        /* kernels launched by the library since creation */
+} ekl_stats;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  Must be
+ * installed before ekl_create; NULL restores cudaMalloc/cudaFree.  `stream`
+ * is the handle's stream as a cudaStream_t. */
+typedef void *(*ekl_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*ekl_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+int ekl_set_allocator(ekl_alloc_fn alloc, ekl_free_fn free_fn, void *ctx);
+
+/* Create a simulation on the current CUDA device.  `stream` is a
+ * cudaStream_t (NULL = the legacy default stream) on which every later call
+ * of this handle is ordered.  Builds the wall link table, the wall-charge
+ * source, and the initial populations w_p n_init (placed as the
+ * post-collision state of step -1).  Errors: EKL_ERR_ARG, EKL_ERR_ALLOC,
+ * EKL_ERR_CUDA; *out is NULL on error. */
+int ekl_create(const ekl_params *params, void *stream, ekl_handle **out);
+
+/* Replace the beads (Sec. II.B): positions R[n][3], velocities V[n][3] (NULL =
+ * zero), charges q[n] (e), chain ids chain[n] (NULL = one chain; consecutive
+ * beads with equal ids are bonded).  n <= 1024.  Errors: EKL_ERR_ARG. */
+int ekl_set_beads(ekl_handle *h, int32_t n, const double *R, const double *V,
+                  const double *q, const int32_t *chain);
+
+/* Advance nsteps time steps (Sec. II.C algorithm): charge density, Poisson,
+ * bead interpolation + MD + spreading, fused pull-collide-stream.  Work is
+ * queued on the handle's stream; the call synchronises once at the end to
+ * read the status word.  Returns EKL_OK, warning bits, or an error. */
+int ekl_step(ekl_handle *h, int32_t nsteps);
+
+/* Queue nsteps steps without synchronising (status is read by the next
+ * ekl_step / ekl_get_stats). */
+int ekl_step_async(ekl_handle *h, int32_t nsteps);
+
+/* Copy fields to host memory (any pointer may be NULL):
+ *   n_out[3][N]     species densities n^a of the current populations (Eq. 15)
+ *   j_out[3][3][N]  bare currents sum_p c_p f_p (Eq. 16)
+ *   phi_out[N]      potential of the last step, fluid mean removed, 0 on walls
+ *   R_out, V_out    bead positions / velocities [nb][3] */
+int ekl_get_fields(ekl_handle *h, double *n_out, double *j_out, double *phi_out,
+                   double *R_out, double *V_out);
+
+/* Checkpoint: post-collision populations as FP64 f values [3][19][N] and the
+ * raw potential [N] (no gauge shift), plus the step counter. */
+int ekl_get_state(ekl_handle *h, double *fstar, double *phi, int64_t *step);
+int ekl_set_state(ekl_handle *h, const double *fstar, const double *phi, int64_t step);
+
+int ekl_get_stats(ekl_handle *h, ekl_stats *out);
+
+/* Per-phase CUDA-event timing of later steps (adds one event pair per phase). */
+int ekl_set_timing(ekl_handle *h, int32_t on);
+
+/* Link table as built on the device: bit p (1..18) set when x - c_p is a wall
+ * node or lies beyond a closed face, bit 31 on wall nodes. mask_out[N]. */
+int ekl_get_link_mask(ekl_handle *h, uint32_t *mask_out);
+
+/* Lattice table of the library: c[19][3], w[19], opp[19] (host memory). */
+void ekl_lattice(int32_t *c, double *w, int32_t *opp);
+
+void ekl_destroy(ekl_handle *h);
+
+/* Message of the last error on this thread ("" if none). */
+const char *ekl_last_error(void);
+
+int64_t ekl_sizeof_params(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EKL_H */

@@ -1,0 +1,679 @@
+// C ABI of the library: handle life cycle, argument checks, geometry set-up,
+// dispatch to the per-precision step implementations, host transfers.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "ekl_dev.cuh"
+
+using namespace ekl;
+
+struct ekl_handle {
+    Ctx c;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+ekl_alloc_fn g_alloc = nullptr;
+ekl_free_fn g_free = nullptr;
+void *g_alloc_ctx = nullptr;
+
+int fail(int code, const char *msg)
+{
+    snprintf(g_err, sizeof g_err, "%s", msg);
+    return code;
+}
+
+int fail_cuda(cudaError_t e, const char *where)
+{
+    snprintf(g_err, sizeof g_err, "%s: %s", where, cudaGetErrorString(e));
+    return EKL_ERR_CUDA;
+}
+
+struct PrecOps {
+    int (*init)(Ctx &, const double *);
+    int (*run)(Ctx &, int);
+    int (*fields)(Ctx &, double *, double *, double *);
+    int (*get_state)(Ctx &, double *, double *);
+    int (*set_state)(Ctx &, const double *, const double *);
+    int (*pois_blocks)();
+};
+
+const PrecOps &ops(int prec)
+{
+    static const PrecOps t[4] = {
+        {init_populations_f64, run_steps_f64, get_fields_f64, get_state_f64, set_state_f64, pois_blocks_f64},
+        {init_populations_f32, run_steps_f32, get_fields_f32, get_state_f32, set_state_f32, pois_blocks_f32},
+        {init_populations_bf16, run_steps_bf16, get_fields_bf16, get_state_bf16, set_state_bf16, pois_blocks_bf16},
+        {init_populations_fp16, run_steps_fp16, get_fields_fp16, get_state_fp16, set_state_fp16, pois_blocks_fp16},
+    };
+    return t[prec];
+}
+
+// Link bits of every node (integer work, bit-exact against the oracle):
+// bit p set when x - c_p is a wall node or beyond a closed face; bit 31 on walls.
+__global__ void mask_kernel(Grid3 g, int px, int py, int pz, const uint8_t *__restrict__ solid,
+                            uint32_t *__restrict__ mask)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    if (solid[i]) {
+        mask[i] = SOLID_BIT;
+        return;
+    }
+    int x, y, z;
+    coords_of(g, i, x, y, z);
+    uint32_t m = 0;
+#pragma unroll
+    for (int p = 1; p < Q; p++) {
+        int X = x - cx_(p), Y = y - cy_(p), Z = z - cz_(p);
+        bool in = true;
+        if (X < 0 || X >= g.nx) {
+            if (px) X = (X + g.nx) % g.nx;
+            else in = false;
+        }
+        if (Y < 0 || Y >= g.ny) {
+            if (py) Y = (Y + g.ny) % g.ny;
+            else in = false;
+        }
+        if (Z < 0 || Z >= g.nz) {
+            if (pz) Z = (Z + g.nz) % g.nz;
+            else in = false;
+        }
+        if (!in || solid[(long long)X + (long long)g.nx * (Y + (long long)g.ny * Z)]) m |= 1u << p;
+    }
+    mask[i] = m;
+}
+
+void release(Ctx &c)
+{
+    size_t rs = real_size(c.prec);
+    dev_free(c, c.f[0], 0);
+    dev_free(c, c.f[1], 0);
+    dev_free(c, c.mask, 0);
+    dev_free(c, c.wall_share, 0);
+    dev_free(c, c.src_wall, 0);
+    dev_free(c, c.rho, 0);
+    dev_free(c, c.b, 0);
+    dev_free(c, c.phi, 0);
+    dev_free(c, c.part_charge, 0);
+    dev_free(c, c.part_mass, 0);
+    dev_free(c, c.part_pois, 0);
+    dev_free(c, c.barrier, 0);
+    dev_free(c, c.status, 0);
+    dev_free(c, c.pois_iters, 0);
+    dev_free(c, c.pois_res, 0);
+    dev_free(c, c.R, 0);
+    dev_free(c, c.V, 0);
+    dev_free(c, c.q, 0);
+    dev_free(c, c.chain, 0);
+    dev_free(c, c.patch_count, 0);
+    dev_free(c, c.patch_node, 0);
+    dev_free(c, c.patch_q, 0);
+    dev_free(c, c.patch_f, 0);
+    dev_free(c, c.patch_mom, 0);
+    dev_free(c, c.entry_slot, 0);
+    dev_free(c, c.sorted_entry, 0);
+    dev_free(c, c.slot_first, 0);
+    dev_free(c, c.entry_w, 0);
+    (void)rs;
+    for (int k = 0; k < 2 * PH_COUNT; k++)
+        if (c.ev[k]) cudaEventDestroy(c.ev[k]);
+    for (int k = 0; k < c.tcap; k++) cudaEventDestroy(c.tpool[k]);
+    free(c.tpool);
+    free(c.tphase);
+}
+
+int status_to_code(int st)
+{
+    if (st & ST_TIMEOUT) return fail(EKL_ERR_TIMEOUT, "a device-side wait timed out");
+    if (st & ST_UNSTABLE) return fail(EKL_ERR_UNSTABLE, "non-finite or non-positive species density");
+    if (st & ST_BEAD) return fail(EKL_ERR_BEAD, "bead in a wall, outside the box, or FENE bond broken");
+    int w = 0;
+    if (st & ST_NOCONV) w |= EKL_WARN_NOCONV;
+    if (st & ST_CFL) w |= EKL_WARN_CFL;
+    return w;
+}
+
+}  // namespace
+
+namespace ekl {
+
+void timing_record(Ctx &c, int phase, int begin)
+{
+    if (c.tused + 1 > c.tcap) {
+        int ncap = c.tcap ? 2 * c.tcap : 256;
+        cudaEvent_t *np = (cudaEvent_t *)realloc(c.tpool, ncap * sizeof(cudaEvent_t));
+        int *nph = (int *)realloc(c.tphase, ncap * sizeof(int));
+        if (!np || !nph) {
+            if (np) c.tpool = np;
+            if (nph) c.tphase = nph;
+            return;
+        }
+        c.tpool = np;
+        c.tphase = nph;
+        for (int k = c.tcap; k < ncap; k++) cudaEventCreate(&c.tpool[k]);
+        c.tcap = ncap;
+    }
+    cudaEventRecord(c.tpool[c.tused], c.stream);
+    c.tphase[c.tused] = begin ? phase : -1 - phase;
+    c.tused++;
+}
+
+// call after the stream has been synchronised
+void timing_flush(Ctx &c)
+{
+    for (int k = 0; k + 1 < c.tused; k++) {
+        if (c.tphase[k] >= 0 && c.tphase[k + 1] == -1 - c.tphase[k]) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c.tpool[k], c.tpool[k + 1]) == cudaSuccess)
+                c.ms_phase[c.tphase[k]] += ms;
+            k++;
+        }
+    }
+    c.tused = 0;
+}
+
+size_t real_size(int prec) { return prec == EKL_F64 ? 8 : 4; }
+size_t store_size(int prec) { return prec == EKL_F64 ? 8 : (prec == EKL_F32 ? 4 : 2); }
+size_t phi_size(int prec) { return 8; }
+
+void *dev_alloc(Ctx &c, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (g_alloc) return g_alloc(bytes, (void *)c.stream, g_alloc_ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    return p;
+}
+
+void dev_free(Ctx &c, void *p, size_t bytes)
+{
+    if (!p) return;
+    if (g_free) g_free(p, bytes, (void *)c.stream, g_alloc_ctx);
+    else cudaFree(p);
+}
+
+}  // namespace ekl
+
+extern "C" {
+
+int ekl_set_allocator(ekl_alloc_fn alloc, ekl_free_fn free_fn, void *ctx)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return fail(EKL_ERR_ARG, "allocator and free must both be set");
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_ctx = ctx;
+    return EKL_OK;
+}
+
+int64_t ekl_sizeof_params(void) { return (int64_t)sizeof(ekl_params); }
+
+const char *ekl_last_error(void) { return g_err; }
+
+void ekl_lattice(int32_t *c, double *w, int32_t *opp)
+{
+    for (int p = 0; p < Q; p++) {
+        c[3 * p] = cx_(p);
+        c[3 * p + 1] = cy_(p);
+        c[3 * p + 2] = cz_(p);
+        w[p] = w_(p);
+        opp[p] = opp_(p);
+    }
+}
+
+int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
+{
+    g_err[0] = 0;
+    if (!out) return fail(EKL_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!P || !P->solid) return fail(EKL_ERR_ARG, "params or solid map is null");
+    if (P->nx < 2 || P->ny < 2 || P->nz < 2) return fail(EKL_ERR_ARG, "every extent must be >= 2");
+    int L[3] = {P->nx, P->ny, P->nz};
+    for (int a = 0; a < 3; a++)
+        if (P->periodic[a] && (L[a] & 1)) return fail(EKL_ERR_ARG, "periodic extents must be even (red-black ordering)");
+    if (P->precision < EKL_F64 || P->precision > EKL_FP16DEV) return fail(EKL_ERR_ARG, "unknown precision");
+    for (int s = 0; s < NS; s++)
+        if (!(P->tau[s] > 0.5)) return fail(EKL_ERR_ARG, "tau must exceed 1/2");
+    if (!(P->diffusivity[1] > 0.0)) return fail(EKL_ERR_ARG, "cation diffusivity must be positive");
+    long long N = (long long)P->nx * P->ny * P->nz;
+    if (N > (1ll << 31) / 64) return fail(EKL_ERR_ARG, "lattice too large for 32-bit patch ids");
+
+    ekl_handle *h = new (std::nothrow) ekl_handle();
+    if (!h) return fail(EKL_ERR_ALLOC, "host allocation failed");
+    Ctx &c = h->c;
+    memset(&c, 0, sizeof(Ctx));
+    c.P = *P;
+    c.P.solid = nullptr;
+    c.P.surface_charge = nullptr;
+    c.P.n_init = nullptr;
+    c.nx = P->nx;
+    c.ny = P->ny;
+    c.nz = P->nz;
+    for (int a = 0; a < 3; a++) c.per[a] = P->periodic[a] ? 1 : 0;
+    c.N = N;
+    c.prec = P->precision;
+    c.stream = (cudaStream_t)stream;
+    cudaGetDevice(&c.device);
+    cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device);
+    if (c.P.md_substeps < 1) c.P.md_substeps = 1;
+    if (c.P.poisson_check_every < 1) c.P.poisson_check_every = 1;
+
+    // constants, each as the oracle's formula states it
+    const double VT2 = 1.0 / 3.0;
+    c.c4 = 4.0 * M_PI * P->bjerrum;
+    for (int s = 0; s < NS; s++) {
+        double D = P->diffusivity[s] > 0.0 ? P->diffusivity[s] : P->diffusivity[1];
+        c.wd[s] = VT2 / D;
+        c.om[s] = 1.0 / P->tau[s];
+    }
+    if (P->rho_jacobi > 0.0) {
+        c.rJ = P->rho_jacobi;
+    } else {
+        double th = 1e30;
+        for (int a = 0; a < 3; a++) {
+            double t = (c.per[a] ? 2.0 : 1.0) * M_PI / L[a];
+            if (t < th) th = t;
+        }
+        c.rJ = (2.0 + cos(th)) / 3.0;
+    }
+
+    // geometry on the host: fluid count, wall charge shares
+    const uint8_t *solid = P->solid;
+    long long nf = 0;
+    for (long long i = 0; i < N; i++) nf += solid[i] ? 0 : 1;
+    c.n_fluid = nf;
+    bool charged = false;
+    if (P->surface_charge)
+        for (long long i = 0; i < N; i++)
+            if (solid[i] && P->surface_charge[i] != 0.0) charged = true;
+    std::vector<double> share, src;
+    if (charged) {
+        share.assign(N, 0.0);
+        src.assign(N, 0.0);
+        const int F[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+        auto nid = [&](int x, int y, int z, bool &in) -> long long {
+            int q[3] = {x, y, z};
+            in = true;
+            for (int a = 0; a < 3; a++) {
+                if (c.per[a]) {
+                    q[a] %= L[a];
+                    if (q[a] < 0) q[a] += L[a];
+                } else if (q[a] < 0 || q[a] >= L[a]) {
+                    in = false;
+                }
+            }
+            return in ? (long long)q[0] + (long long)L[0] * (q[1] + (long long)L[1] * q[2]) : -1;
+        };
+        for (long long w = 0; w < N; w++) {
+            if (!solid[w] || P->surface_charge[w] == 0.0) continue;
+            int x = (int)(w % L[0]), y = (int)((w / L[0]) % L[1]), z = (int)(w / ((long long)L[0] * L[1]));
+            int k = 0;
+            for (int f = 0; f < 6; f++) {
+                bool in;
+                long long j = nid(x + F[f][0], y + F[f][1], z + F[f][2], in);
+                if (in && !solid[j]) k++;
+            }
+            if (k > 0) share[w] = P->surface_charge[w] / k;
+        }
+        for (long long i = 0; i < N; i++) {
+            if (solid[i]) continue;
+            int x = (int)(i % L[0]), y = (int)((i / L[0]) % L[1]), z = (int)(i / ((long long)L[0] * L[1]));
+            double acc = 0.0;
+            for (int f = 0; f < 6; f++) {
+                bool in;
+                long long j = nid(x + F[f][0], y + F[f][1], z + F[f][2], in);
+                if (in && solid[j]) acc += share[j];
+            }
+            src[i] = acc;
+        }
+    }
+
+    // device buffers
+    const size_t rs = real_size(c.prec), ss = store_size(c.prec), ps = phi_size(c.prec);
+    c.charge_blocks = (int)((N + CHARGE_THREADS - 1) / CHARGE_THREADS);
+    c.lb_blocks = (int)((N + LB_THREADS - 1) / LB_THREADS);
+    int occ = ops(c.prec).pois_blocks();
+    if (occ < 1) {
+        delete h;
+        return fail(EKL_ERR_CUDA, "Poisson kernel cannot be resident");
+    }
+    c.pois_blocks = c.num_sms * (occ < 2 ? occ : 2);
+    bool okall = true;
+    auto A = [&](size_t bytes) {
+        void *p = dev_alloc(c, bytes);
+        if (!p) okall = false;
+        return p;
+    };
+    c.f[0] = A((size_t)NS * Q * N * ss);
+    c.f[1] = A((size_t)NS * Q * N * ss);
+    c.mask = (uint32_t *)A(N * 4);
+    if (charged) {
+        c.wall_share = A(N * rs);
+        c.src_wall = A(N * rs);
+    }
+    c.rho = A(N * rs);
+    c.b = A(N * ps);
+    c.phi = A(N * ps);
+    c.part_charge = (double *)A(c.charge_blocks * sizeof(double));
+    c.part_mass = (double *)A((size_t)c.lb_blocks * NS * sizeof(double));
+    c.part_pois = (double *)A((2 * (size_t)c.pois_blocks + 1) * sizeof(double));
+    c.barrier = (unsigned *)A(4 * sizeof(unsigned));
+    c.status = (int *)A(sizeof(int));
+    c.pois_iters = (int *)A(sizeof(int));
+    c.pois_res = (double *)A(sizeof(double));
+    c.patch_count = (int *)A(sizeof(int));
+    c.patch_node = (int *)A(MAX_ENTRIES * sizeof(int));
+    c.patch_q = A(MAX_ENTRIES * rs);
+    c.patch_f = A((size_t)(MAX_ENTRIES + MAX_BEADS) * 9 * rs);
+    c.patch_mom = A((size_t)MAX_ENTRIES * 15 * rs);
+    c.entry_slot = (int *)A(MAX_ENTRIES * sizeof(int));
+    c.sorted_entry = (int *)A(MAX_ENTRIES * sizeof(int));
+    c.slot_first = (int *)A((MAX_ENTRIES + 1) * sizeof(int));
+    c.entry_w = A(MAX_ENTRIES * rs);
+    c.R = A(MAX_BEADS * 3 * rs);
+    c.V = A(MAX_BEADS * 3 * rs);
+    c.q = A(MAX_BEADS * rs);
+    c.chain = (int *)A(MAX_BEADS * sizeof(int));
+    if (!okall) {
+        release(c);
+        delete h;
+        return fail(EKL_ERR_ALLOC, "device allocation failed");
+    }
+    for (int k = 0; k < 2 * PH_COUNT; k++) cudaEventCreate(&c.ev[k]);
+
+    int rc = EKL_OK;
+    uint8_t *d_solid = nullptr;
+    double *d_n = nullptr;
+    cudaError_t e = cudaSuccess;
+    do {
+        d_solid = (uint8_t *)dev_alloc(c, N);
+        if (!d_solid) { rc = fail(EKL_ERR_ALLOC, "device allocation failed"); break; }
+        e = cudaMemcpyAsync(d_solid, solid, N, cudaMemcpyHostToDevice, c.stream);
+        if (e != cudaSuccess) { rc = fail_cuda(e, "upload solid"); break; }
+        mask_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c.stream>>>(Grid3{c.nx, c.ny, c.nz, N}, c.per[0], c.per[1], c.per[2], d_solid, c.mask);
+        c.launches++;
+        if (charged) {
+            if (c.prec == EKL_F64) {
+                cudaMemcpyAsync(c.wall_share, share.data(), N * 8, cudaMemcpyHostToDevice, c.stream);
+                cudaMemcpyAsync(c.src_wall, src.data(), N * 8, cudaMemcpyHostToDevice, c.stream);
+            } else {
+                std::vector<float> a(N), b(N);
+                for (long long i = 0; i < N; i++) {
+                    a[i] = (float)share[i];
+                    b[i] = (float)src[i];
+                }
+                cudaMemcpyAsync(c.wall_share, a.data(), N * 4, cudaMemcpyHostToDevice, c.stream);
+                cudaMemcpyAsync(c.src_wall, b.data(), N * 4, cudaMemcpyHostToDevice, c.stream);
+                cudaStreamSynchronize(c.stream);
+            }
+        }
+        if (P->n_init) {
+            d_n = (double *)dev_alloc(c, (size_t)NS * N * 8);
+            if (!d_n) { rc = fail(EKL_ERR_ALLOC, "device allocation failed"); break; }
+            e = cudaMemcpyAsync(d_n, P->n_init, (size_t)NS * N * 8, cudaMemcpyHostToDevice, c.stream);
+            if (e != cudaSuccess) { rc = fail_cuda(e, "upload n_init"); break; }
+        }
+        rc = ops(c.prec).init(c, d_n);
+        if (rc != EKL_OK) { fail(rc, "init kernel failed"); break; }
+        cudaMemsetAsync(c.phi, 0, N * ps, c.stream);
+        cudaMemsetAsync(c.patch_count, 0, sizeof(int), c.stream);
+        cudaMemsetAsync(c.status, 0, sizeof(int), c.stream);
+        cudaMemsetAsync(c.pois_iters, 0, sizeof(int), c.stream);
+        cudaMemsetAsync(c.pois_res, 0, sizeof(double), c.stream);
+        double nfd = (double)nf;
+        cudaMemcpyAsync(c.part_pois + 2 * (size_t)c.pois_blocks, &nfd, sizeof(double), cudaMemcpyHostToDevice, c.stream);
+        e = cudaStreamSynchronize(c.stream);
+        if (e != cudaSuccess) { rc = fail_cuda(e, "create"); break; }
+    } while (0);
+    dev_free(c, d_solid, N);
+    dev_free(c, d_n, 0);
+    if (rc != EKL_OK) {
+        release(c);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return EKL_OK;
+}
+
+int ekl_set_beads(ekl_handle *h, int32_t n, const double *R, const double *V, const double *q,
+                  const int32_t *chain)
+{
+    if (!h) return fail(EKL_ERR_ARG, "null handle");
+    if (n < 0 || n > MAX_BEADS) return fail(EKL_ERR_ARG, "bead count out of range (max 256)");
+    if (n > 0 && (!R || !q)) return fail(EKL_ERR_ARG, "positions and charges are required");
+    Ctx &c = h->c;
+    for (int b = 0; b < n; b++)
+        for (int a = 0; a < 3; a++) {
+            double L = a == 0 ? c.nx : (a == 1 ? c.ny : c.nz);
+            double r = R[3 * b + a];
+            if (!(r >= 0.0 && r < L)) return fail(EKL_ERR_ARG, "bead position outside [0, L)");
+        }
+    std::vector<double> Rd(3 * (size_t)n), Vd(3 * (size_t)n, 0.0), qd(n);
+    std::vector<int> ch(n, 0);
+    for (int k = 0; k < 3 * n; k++) {
+        Rd[k] = R[k];
+        if (V) Vd[k] = V[k];
+    }
+    for (int k = 0; k < n; k++) {
+        qd[k] = q[k];
+        if (chain) ch[k] = chain[k];
+    }
+    cudaError_t e;
+    if (c.prec == EKL_F64) {
+        e = cudaMemcpyAsync(c.R, Rd.data(), 3 * (size_t)n * 8, cudaMemcpyHostToDevice, c.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c.V, Vd.data(), 3 * (size_t)n * 8, cudaMemcpyHostToDevice, c.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c.q, qd.data(), (size_t)n * 8, cudaMemcpyHostToDevice, c.stream);
+    } else {
+        std::vector<float> Rf(Rd.begin(), Rd.end()), Vf(Vd.begin(), Vd.end()), qf(qd.begin(), qd.end());
+        e = cudaMemcpyAsync(c.R, Rf.data(), 3 * (size_t)n * 4, cudaMemcpyHostToDevice, c.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c.V, Vf.data(), 3 * (size_t)n * 4, cudaMemcpyHostToDevice, c.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c.q, qf.data(), (size_t)n * 4, cudaMemcpyHostToDevice, c.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.chain, ch.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess && n == 0) e = cudaMemsetAsync(c.patch_count, 0, sizeof(int), c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return fail_cuda(e, "set_beads");
+    c.nb = n;
+    return EKL_OK;
+}
+
+int ekl_step_async(ekl_handle *h, int32_t nsteps)
+{
+    if (!h) return fail(EKL_ERR_ARG, "null handle");
+    if (nsteps < 0) return fail(EKL_ERR_ARG, "negative step count");
+    int rc = ops(h->c.prec).run(h->c, nsteps);
+    if (rc != EKL_OK) return fail(rc, "kernel launch failed");
+    return EKL_OK;
+}
+
+int ekl_step(ekl_handle *h, int32_t nsteps)
+{
+    if (!h) return fail(EKL_ERR_ARG, "null handle");
+    Ctx &c = h->c;
+    cudaMemsetAsync(c.status, 0, sizeof(int), c.stream);
+    int rc = ekl_step_async(h, nsteps);
+    if (rc != EKL_OK) return rc;
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, c.status, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return fail_cuda(e, "step");
+    timing_flush(c);
+    c.last_status = st;
+    return status_to_code(st);
+}
+
+int ekl_get_fields(ekl_handle *h, double *n_out, double *j_out, double *phi_out, double *R_out,
+                   double *V_out)
+{
+    if (!h) return fail(EKL_ERR_ARG, "null handle");
+    Ctx &c = h->c;
+    const long long N = c.N;
+    double *dn = n_out ? (double *)dev_alloc(c, (size_t)NS * N * 8) : nullptr;
+    double *dj = j_out ? (double *)dev_alloc(c, (size_t)NS * 3 * N * 8) : nullptr;
+    double *dp = phi_out ? (double *)dev_alloc(c, (size_t)N * 8) : nullptr;
+    if ((n_out && !dn) || (j_out && !dj) || (phi_out && !dp)) {
+        dev_free(c, dn, 0);
+        dev_free(c, dj, 0);
+        dev_free(c, dp, 0);
+        return fail(EKL_ERR_ALLOC, "device allocation failed");
+    }
+    int rc = ops(c.prec).fields(c, dn, dj, dp);
+    cudaError_t e = cudaSuccess;
+    if (rc == EKL_OK) {
+        if (dn) e = cudaMemcpyAsync(n_out, dn, (size_t)NS * N * 8, cudaMemcpyDeviceToHost, c.stream);
+        if (e == cudaSuccess && dj) e = cudaMemcpyAsync(j_out, dj, (size_t)NS * 3 * N * 8, cudaMemcpyDeviceToHost, c.stream);
+        if (e == cudaSuccess && dp) e = cudaMemcpyAsync(phi_out, dp, (size_t)N * 8, cudaMemcpyDeviceToHost, c.stream);
+        if (c.nb > 0 && e == cudaSuccess && (R_out || V_out)) {
+            size_t bytes = 3 * (size_t)c.nb * real_size(c.prec);
+            std::vector<char> r(bytes), v(bytes);
+            e = cudaMemcpyAsync(r.data(), c.R, bytes, cudaMemcpyDeviceToHost, c.stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(v.data(), c.V, bytes, cudaMemcpyDeviceToHost, c.stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+            for (int k = 0; k < 3 * c.nb && e == cudaSuccess; k++) {
+                double rv, vv;
+                if (c.prec == EKL_F64) {
+                    rv = ((double *)r.data())[k];
+                    vv = ((double *)v.data())[k];
+                } else {
+                    rv = ((float *)r.data())[k];
+                    vv = ((float *)v.data())[k];
+                }
+                if (R_out) R_out[k] = rv;
+                if (V_out) V_out[k] = vv;
+            }
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    }
+    dev_free(c, dn, 0);
+    dev_free(c, dj, 0);
+    dev_free(c, dp, 0);
+    if (rc != EKL_OK) return fail(rc, "fields kernel failed");
+    if (e != cudaSuccess) return fail_cuda(e, "get_fields");
+    if (phi_out) {
+        // gauge: remove the fluid mean, summed in node order
+        std::vector<uint32_t> m(N);
+        e = cudaMemcpy(m.data(), c.mask, N * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail_cuda(e, "get_fields mask");
+        double sum = 0.0;
+        long long nf = 0;
+        for (long long i = 0; i < N; i++)
+            if (!(m[i] & SOLID_BIT)) {
+                sum += phi_out[i];
+                nf++;
+            }
+        double mean = nf ? sum / nf : 0.0;
+        for (long long i = 0; i < N; i++) phi_out[i] = (m[i] & SOLID_BIT) ? 0.0 : phi_out[i] - mean;
+    }
+    return EKL_OK;
+}
+
+int ekl_get_state(ekl_handle *h, double *fstar, double *phi, int64_t *step)
+{
+    if (!h) return fail(EKL_ERR_ARG, "null handle");
+    Ctx &c = h->c;
+    double *df = fstar ? (double *)dev_alloc(c, (size_t)NS * Q * c.N * 8) : nullptr;
+    double *dp = phi ? (double *)dev_alloc(c, (size_t)c.N * 8) : nullptr;
+    if ((fstar && !df) || (phi && !dp)) {
+        dev_free(c, df, 0);
+        dev_free(c, dp, 0);
+        return fail(EKL_ERR_ALLOC, "device allocation failed");
+    }
+    int rc = ops(c.prec).get_state(c, df ? df : nullptr, dp);
+    cudaError_t e = cudaSuccess;
+    if (rc == EKL_OK && df) e = cudaMemcpyAsync(fstar, df, (size_t)NS * Q * c.N * 8, cudaMemcpyDeviceToHost, c.stream);
+    if (rc == EKL_OK && e == cudaSuccess && dp) e = cudaMemcpyAsync(phi, dp, (size_t)c.N * 8, cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    dev_free(c, df, 0);
+    dev_free(c, dp, 0);
+    if (rc != EKL_OK) return fail(rc, "state kernel failed");
+    if (e != cudaSuccess) return fail_cuda(e, "get_state");
+    if (step) *step = c.step;
+    return EKL_OK;
+}
+
+int ekl_set_state(ekl_handle *h, const double *fstar, const double *phi, int64_t step)
+{
+    if (!h || !fstar) return fail(EKL_ERR_ARG, "null handle or populations");
+    Ctx &c = h->c;
+    double *df = (double *)dev_alloc(c, (size_t)NS * Q * c.N * 8);
+    double *dp = phi ? (double *)dev_alloc(c, (size_t)c.N * 8) : nullptr;
+    if (!df || (phi && !dp)) {
+        dev_free(c, df, 0);
+        dev_free(c, dp, 0);
+        return fail(EKL_ERR_ALLOC, "device allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(df, fstar, (size_t)NS * Q * c.N * 8, cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess && dp) e = cudaMemcpyAsync(dp, phi, (size_t)c.N * 8, cudaMemcpyHostToDevice, c.stream);
+    int rc = e == cudaSuccess ? ops(c.prec).set_state(c, df, dp) : EKL_ERR_CUDA;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    dev_free(c, df, 0);
+    dev_free(c, dp, 0);
+    if (rc != EKL_OK || e != cudaSuccess) return fail_cuda(e, "set_state");
+    c.step = step;
+    return EKL_OK;
+}
+
+int ekl_get_stats(ekl_handle *h, ekl_stats *out)
+{
+    if (!h || !out) return fail(EKL_ERR_ARG, "null argument");
+    Ctx &c = h->c;
+    std::vector<double> pm((size_t)c.lb_blocks * NS);
+    int it = 0;
+    double res = 0;
+    cudaError_t e = cudaMemcpyAsync(pm.data(), c.part_mass, pm.size() * 8, cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&it, c.pois_iters, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&res, c.pois_res, sizeof(double), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return fail_cuda(e, "get_stats");
+    timing_flush(c);
+    memset(out, 0, sizeof(*out));
+    for (int s = 0; s < NS; s++) {
+        double t = 0;
+        for (int b = 0; b < c.lb_blocks; b++) t += pm[(size_t)b * NS + s];
+        out->mass[s] = t;
+    }
+    out->step = c.step;
+    out->poisson_iters = it;
+    out->poisson_res = res;
+    out->status = c.last_status;
+    for (int k = 0; k < PH_COUNT; k++) out->ms_phase[k] = c.ms_phase[k];
+    out->launches = c.launches;
+    return EKL_OK;
+}
+
+int ekl_set_timing(ekl_handle *h, int32_t on)
+{
+    if (!h) return fail(EKL_ERR_ARG, "null handle");
+    cudaStreamSynchronize(h->c.stream);
+    timing_flush(h->c);
+    h->c.timing = on ? 1 : 0;
+    for (int k = 0; k < PH_COUNT; k++) h->c.ms_phase[k] = 0.0;
+    return EKL_OK;
+}
+
+int ekl_get_link_mask(ekl_handle *h, uint32_t *mask_out)
+{
+    if (!h || !mask_out) return fail(EKL_ERR_ARG, "null argument");
+    cudaError_t e = cudaMemcpyAsync(mask_out, h->c.mask, h->c.N * 4, cudaMemcpyDeviceToHost, h->c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->c.stream);
+    if (e != cudaSuccess) return fail_cuda(e, "get_link_mask");
+    return EKL_OK;
+}
+
+void ekl_destroy(ekl_handle *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->c.stream);
+    release(h->c);
+    delete h;
+}
+
+}  // extern "C"

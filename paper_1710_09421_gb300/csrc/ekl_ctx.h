@@ -1,0 +1,135 @@
+// Host-side state of one simulation handle (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ekl.h"
+
+namespace ekl {
+
+constexpr int Q = 19;
+constexpr int NS = 3;
+constexpr int MAX_BEADS = 256;
+constexpr int MAX_ENTRIES = 8 * MAX_BEADS;
+constexpr int LB_THREADS = 256;
+constexpr int CHARGE_THREADS = 256;
+constexpr int POIS_THREADS = 512;
+constexpr int BEAD_THREADS = 256;
+// fixed-point scale of the potential in the reduced-precision paths: 2^40
+constexpr double PHI_SCALE = 1099511627776.0;
+constexpr double PHI_INV = 1.0 / 1099511627776.0;
+
+// status bits written by kernels (mapped to return codes on the host)
+constexpr int ST_NOCONV = 1;
+constexpr int ST_CFL = 2;
+constexpr int ST_UNSTABLE = 4;
+constexpr int ST_BEAD = 8;
+constexpr int ST_TIMEOUT = 16;
+
+enum Phase { PH_BIN = 0, PH_CHARGE, PH_POISSON, PH_MD, PH_LB, PH_OTHER, PH_COUNT };
+
+struct Ctx {
+    ekl_params P;  // copy; pointer members cleared
+    int nx, ny, nz;
+    int per[3];
+    long long N;
+    long long n_fluid;
+    int prec;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+
+    // constants (FP64, derived exactly as the paper's formulas state)
+    double c4;        // 4 pi l_B
+    double wd[NS];    // omega_drag = v_T^2 / D
+    double om[NS];    // 1 / tau
+    double rJ;        // Jacobi spectral radius of the Chebyshev schedule
+
+    // device buffers
+    void *f[2];
+    int cur;
+    uint32_t *mask;
+    void *wall_share;  // Real[N] (wall node's charge per fluid face) or null
+    void *src_wall;    // Real[N] (wall charge moved onto fluid nodes) or null
+    void *rho;         // Real[N]
+    void *b;           // PhiT[N]
+    void *phi;         // PhiT[N]
+    double *part_charge;  // [charge blocks]
+    double *part_mass;    // [lb blocks][3]
+    double *part_pois;    // [poisson blocks][2]
+    unsigned *barrier;    // {count, generation, abort}
+    int *status;          // device status word
+    int *pois_iters;      // last step's sweep count
+    double *pois_res;     // last step's relative residual
+    int charge_blocks;
+    int lb_blocks;
+    int pois_blocks;
+
+    // beads
+    int nb;
+    void *R, *V, *q;      // Real[nb*3], Real[nb*3], Real[nb]
+    int *chain;           // [nb]
+    int *patch_count;     // [1]
+    int *patch_node;      // [MAX_ENTRIES]
+    void *patch_q;        // Real[MAX_ENTRIES]
+    void *patch_f;        // Real[MAX_ENTRIES][9]
+    void *patch_mom;      // Real[MAX_ENTRIES][15] scratch: n[3], u[9], grad[3]
+    int *entry_slot;      // [MAX_ENTRIES]
+    int *sorted_entry;    // [MAX_ENTRIES]
+    int *slot_first;      // [MAX_ENTRIES + 1]
+    void *entry_w;        // Real[MAX_ENTRIES]
+
+    // timing / accounting
+    int timing;
+    cudaEvent_t ev[2 * PH_COUNT];
+    cudaEvent_t *tpool;   // event pairs recorded around phases while timing is on
+    int *tphase;
+    int tcap, tused;
+    double ms_phase[PH_COUNT];
+    long long launches;
+    long long step;
+    int last_status;
+};
+
+// deferred phase timing: record now, accumulate after the next synchronisation
+void timing_record(Ctx &c, int phase, int begin);
+void timing_flush(Ctx &c);
+
+// allocation through the installed allocator
+void *dev_alloc(Ctx &c, size_t bytes);
+void dev_free(Ctx &c, void *p, size_t bytes);
+
+// per-precision entry points (defined in the instantiation units)
+int init_populations_f64(Ctx &c, const double *d_n_init);
+int run_steps_f64(Ctx &c, int nsteps);
+int get_fields_f64(Ctx &c, double *d_n, double *d_j, double *d_phi);
+int get_state_f64(Ctx &c, double *d_f, double *d_phi);
+int set_state_f64(Ctx &c, const double *d_f, const double *d_phi);
+int pois_blocks_f64();
+
+int init_populations_f32(Ctx &c, const double *d_n_init);
+int run_steps_f32(Ctx &c, int nsteps);
+int get_fields_f32(Ctx &c, double *d_n, double *d_j, double *d_phi);
+int get_state_f32(Ctx &c, double *d_f, double *d_phi);
+int set_state_f32(Ctx &c, const double *d_f, const double *d_phi);
+int pois_blocks_f32();
+
+int init_populations_bf16(Ctx &c, const double *d_n_init);
+int run_steps_bf16(Ctx &c, int nsteps);
+int get_fields_bf16(Ctx &c, double *d_n, double *d_j, double *d_phi);
+int get_state_bf16(Ctx &c, double *d_f, double *d_phi);
+int set_state_bf16(Ctx &c, const double *d_f, const double *d_phi);
+int pois_blocks_bf16();
+
+int init_populations_fp16(Ctx &c, const double *d_n_init);
+int run_steps_fp16(Ctx &c, int nsteps);
+int get_fields_fp16(Ctx &c, double *d_n, double *d_j, double *d_phi);
+int get_state_fp16(Ctx &c, double *d_f, double *d_phi);
+int set_state_fp16(Ctx &c, const double *d_f, const double *d_phi);
+int pois_blocks_fp16();
+
+size_t real_size(int prec);
+size_t store_size(int prec);
+size_t phi_size(int prec);
+
+}  // namespace ekl

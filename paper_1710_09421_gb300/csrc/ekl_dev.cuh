@@ -1,0 +1,256 @@
+// Device-side building blocks shared by the kernels of the library:
+// D3Q19 table, storage conversions, neighbour indexing, Philox-4x32-10,
+// bounded grid barrier, warp reductions.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ekl_ctx.h"
+
+namespace ekl {
+
+// D3Q19 velocity set (Sec. II.C): rest, +-x, +-y, +-z, then the xy, xz and
+// yz diagonals, each velocity followed by its opposite.
+__host__ __device__ constexpr int cx_(int p)
+{
+    constexpr int t[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[p];
+}
+__host__ __device__ constexpr int cy_(int p)
+{
+    constexpr int t[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[p];
+}
+__host__ __device__ constexpr int cz_(int p)
+{
+    constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[p];
+}
+__host__ __device__ constexpr int opp_(int p) { return p == 0 ? 0 : ((p & 1) ? p + 1 : p - 1); }
+// weights 1/3, 1/18 (|c| = 1), 1/36 (|c| = sqrt 2)
+__host__ __device__ constexpr double w_(int p)
+{
+    return p == 0 ? 1.0 / 3.0 : (p <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+constexpr uint32_t SOLID_BIT = 0x80000000u;
+
+// ---------------------------------------------------------------- storage
+template <typename S> struct Store;
+template <> struct Store<double> {
+    __device__ static double ld(const double *p) { return __ldg(p); }
+    __device__ static void st(double *p, double v) { *p = v; }
+};
+template <> struct Store<float> {
+    __device__ static float ld(const float *p) { return __ldg(p); }
+    __device__ static void st(float *p, float v) { *p = v; }
+};
+template <> struct Store<__nv_bfloat16> {
+    __device__ static float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    __device__ static void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <> struct Store<__half> {
+    __device__ static float ld(const __half *p) { return __half2float(__ldg(p)); }
+    __device__ static void st(__half *p, float v) { *p = __float2half_rn(v); }
+};
+
+// ---------------------------------------------------------------- potential
+// FP64 path: phi stored as double.  Reduced-precision paths: phi stored as a
+// signed 64-bit fixed-point number with 40 fractional bits, so that the
+// 7-point residual is computed exactly in integer arithmetic.
+template <typename PhiT> struct PhiOps;
+template <> struct PhiOps<double> {
+    __device__ static double diff(double a, double b) { return a - b; }  // as real
+};
+template <> struct PhiOps<long long> {
+    __device__ static float diff(long long a, long long b)
+    {
+        return __ll2float_rn(a - b) * (float)PHI_INV;
+    }
+};
+
+// ---------------------------------------------------------------- indexing
+struct Grid3 {
+    int nx, ny, nz;
+    long long N;
+};
+
+__device__ __forceinline__ void coords_of(const Grid3 &g, long long i, int &x, int &y, int &z)
+{
+    long long r = i / g.nx;
+    x = (int)(i - r * g.nx);
+    z = (int)(r / g.ny);
+    y = (int)(r - (long long)z * g.ny);
+}
+
+// Neighbour offsets for the pull x - c_p: X[cx + 1] = {x+1, x, x-1}.  Indices
+// wrap on every axis; on a closed axis the wrapped neighbour is never read
+// because the link bit of that direction is set.
+struct Nbr {
+    int X[3];
+    long long Y[3];
+    long long Z[3];
+    __device__ __forceinline__ long long pull(int p) const
+    {
+        return (long long)X[cx_(p) + 1] + Y[cy_(p) + 1] + Z[cz_(p) + 1];
+    }
+};
+
+__device__ __forceinline__ Nbr make_nbr(const Grid3 &g, int x, int y, int z)
+{
+    Nbr n;
+    int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+    int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+    int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+    long long sxy = (long long)g.nx * g.ny;
+    n.X[0] = xp; n.X[1] = x; n.X[2] = xm;
+    n.Y[0] = (long long)yp * g.nx; n.Y[1] = (long long)y * g.nx; n.Y[2] = (long long)ym * g.nx;
+    n.Z[0] = zp * sxy; n.Z[1] = z * sxy; n.Z[2] = zm * sxy;
+    return n;
+}
+
+// face neighbours (-x, +x, -y, +y, -z, +z) are the pulls of p = 1..6
+__device__ __forceinline__ long long face_idx(const Nbr &n, int f)
+{
+    // face f is the node x + e_f; pull p gives x - c_p: -x face = p1, +x = p2, ...
+    return n.pull(f + 1);
+}
+
+// ---------------------------------------------------------------- Philox
+// Philox-4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
+// multiplies, key bumped by the Weyl increments between rounds.
+__host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+#ifdef __CUDA_ARCH__
+        uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+#else
+        uint64_t p0 = (uint64_t)0xD2511F53u * c[0], p1 = (uint64_t)0xCD9E8D57u * c[2];
+        uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
+#endif
+        uint32_t n0 = hi1 ^ c[1] ^ k0;
+        uint32_t n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+// zero-mean unit-variance variate sqrt(3)(2U - 1), U = (x + 1/2) / 2^32
+template <typename R> __device__ __forceinline__ R unit_variate(uint32_t x);
+template <> __device__ __forceinline__ double unit_variate<double>(uint32_t x)
+{
+    double t = ((double)(2.0 * (double)x + 1.0) - 4294967296.0) * (1.0 / 4294967296.0);
+    return 1.7320508075688772 * t;
+}
+template <> __device__ __forceinline__ float unit_variate<float>(uint32_t x)
+{
+    // exact: 2x + 1 - 2^32 is an odd integer below 2^33 in magnitude
+    float t = (float)((int64_t)(2ull * x + 1ull) - 4294967296ll) * (1.0f / 4294967296.0f);
+    return 1.7320508f * t;
+}
+
+// ---------------------------------------------------------------- sync
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch with a bounded wait: a block that
+// waits more than ~2 s raises ST_TIMEOUT and the abort word; every waiter
+// also leaves as soon as the abort word is set.  Returns false on abort.
+// bar[0] = arrival count, bar[1] = generation, bar[2] = abort.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, int *status)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned gen = ld_acquire(&bar[1]);
+        __threadfence();
+        unsigned arrived = atomicAdd(&bar[0], 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            uint64_t t0 = globaltimer_ns();
+            unsigned spins = 0;
+            while (ld_acquire(&bar[1]) == gen) {
+                if (ld_acquire(&bar[2])) {
+                    ok = 0;
+                    break;
+                }
+                if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > 2000000000ull) {
+                    atomicOr(status, ST_TIMEOUT);
+                    atomicExch(&bar[2], 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(20);
+            }
+        }
+        if (ld_acquire(&bar[2])) ok = 0;
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum (fixed shuffle tree, fixed warp order); result valid
+// in thread 0.  `sh` must hold blockDim.x / 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < nw; k++) t += sh[k];
+    }
+    return t;
+}
+
+// lower bound of `key` in sorted a[0..n)
+__device__ __forceinline__ int lower_bound_i(const int *a, int n, long long key)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((long long)a[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+}  // namespace ekl

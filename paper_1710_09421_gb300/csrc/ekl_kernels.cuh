@@ -1,0 +1,944 @@
+// Kernels of one electrokinetic LB-MD time step (Sec. II.C algorithm):
+//   bead_bin   : bead -> node stencils, deterministic patch list, bead charge
+//   charge     : ion densities pulled from the post-collision state, charge
+//                density (Eq. 2) with wall and bead charge, FP64 block sums
+//   poisson    : persistent red-black Chebyshev SOR for Eq. 3, FP64 residual
+//   bead_md    : fluid -> bead interpolation, Langevin sub-steps (Eqs. 7-9),
+//                bead drag spread back to the patch nodes
+//   lb_fused   : pull-stream with bounce-back + moments + forces (Eqs. 5-6)
+//                + BGK collision with forcing (Eqs. 10, 12, 13), one pass
+// Template parameters: S = population storage type, R = arithmetic type,
+// DEV = populations stored as deviations from w_p n_ref, PhiT = potential
+// storage (double, or 64-bit fixed point).
+#pragma once
+#include <cooperative_groups.h>
+
+#include "ekl_dev.cuh"
+
+namespace ekl {
+
+template <typename R> struct Consts {
+    static constexpr R KT = R(1.0) / R(3.0);
+    static constexpr R VT2 = R(1.0) / R(3.0);
+};
+
+// ============================================================== arguments
+template <typename S, typename R, typename PhiT> struct StepArgs {
+    Grid3 g;
+    int per[3];
+    const uint32_t *__restrict__ mask;
+    const S *__restrict__ fin;  // post-collision populations of the previous step
+    S *__restrict__ fout;       // post-collision populations of this step
+    PhiT *phi;
+    PhiT *b;
+    R *rho;
+    const R *__restrict__ wall_share;  // null when no wall carries charge
+    const R *__restrict__ src_wall;
+    R n_ref[NS];
+    R zv[NS];        // valences as reals
+    R wd[NS];        // omega_drag
+    R om[NS];        // 1 / tau
+    R body[NS][3];
+    R E[3];
+    R c4;            // 4 pi l_B
+    int flags;
+    // bead patch
+    const int *patch_count;
+    const int *patch_node;
+    const R *patch_q;
+    const R *patch_f;
+    // reductions / status
+    double *part_charge;
+    double *part_mass;
+    double *part_pois;
+    unsigned *barrier;
+    int *status;
+    int *pois_iters;
+    double *pois_res;
+    // Poisson controls
+    double tol;
+    int max_iter, check_every, fixed_iter;
+    double rJ;
+    int nblocks_charge;
+};
+
+// pull of the 19 populations of species s at node i (bounce-back on set bits)
+template <typename S, typename R>
+__device__ __forceinline__ void pull19(const S *__restrict__ f, long long N, int s, long long i,
+                                       uint32_t m, const Nbr &nb, R v[Q])
+{
+#pragma unroll
+    for (int p = 0; p < Q; p++) {
+        long long src = ((m >> p) & 1u) ? ((long long)(s * Q + opp_(p)) * N + i)
+                                        : ((long long)(s * Q + p) * N + nb.pull(p));
+        v[p] = (R)Store<S>::ld(f + src);
+    }
+}
+
+// ------------------------------------------------------------ node gradient
+// Central differences of phi; a wall (or closed-box) face neighbour takes the
+// Neumann ghost value phi_i + 4 pi l_B sigma_face (Sec. II.A boundary condition).
+template <typename R, typename PhiT>
+__device__ __forceinline__ void node_gradient(const PhiT *phi, const R *wall_share, R c4,
+                                              long long i, uint32_t m, const Nbr &nb,
+                                              const int out_lo[3], const int out_hi[3], R g[3])
+{
+    PhiT pi = phi[i];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        int fm = 2 * a, fp = 2 * a + 1;  // minus and plus faces
+        bool sm = (m >> (fm + 1)) & 1u, sp = (m >> (fp + 1)) & 1u;
+        long long jm = face_idx(nb, fm), jp = face_idx(nb, fp);
+        // a face beyond a closed box side is a wall without charge
+        const R *wsm = out_lo[a] ? nullptr : wall_share;
+        const R *wsp = out_hi[a] ? nullptr : wall_share;
+        if constexpr (sizeof(PhiT) == 8 && ((PhiT)0.5) != 0) {
+            // FP64: the ghost value enters the difference exactly as written
+            double vm = sm ? (double)pi + (wsm ? (double)c4 * (double)wsm[jm] : 0.0)
+                           : (double)phi[jm];
+            double vp = sp ? (double)pi + (wsp ? (double)c4 * (double)wsp[jp] : 0.0)
+                           : (double)phi[jp];
+            g[a] = (R)((vp - vm) * 0.5);
+        } else {
+            PhiT vm = sm ? pi : phi[jm];
+            PhiT vp = sp ? pi : phi[jp];
+            R d = (R)PhiOps<PhiT>::diff(vp, vm) * R(0.5);
+            if (sp && wsp) d += R(0.5) * c4 * wsp[jp];
+            if (sm && wsm) d -= R(0.5) * c4 * wsm[jm];
+            g[a] = d;
+        }
+    }
+}
+
+// which faces of node (x, y, z) lie beyond a closed box side
+__device__ __forceinline__ void closed_faces(const Grid3 &g, const int per[3], int x, int y, int z,
+                                             int lo[3], int hi[3])
+{
+    lo[0] = !per[0] && x == 0; hi[0] = !per[0] && x == g.nx - 1;
+    lo[1] = !per[1] && y == 0; hi[1] = !per[1] && y == g.ny - 1;
+    lo[2] = !per[2] && z == 0; hi[2] = !per[2] && z == g.nz - 1;
+}
+
+// ============================================================== init
+template <typename S, typename R, bool DEV>
+__global__ void init_kernel(Grid3 g, const uint32_t *__restrict__ mask,
+                            const double *__restrict__ n_init, S *__restrict__ f, R n0, R n1, R n2)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    bool solid = mask[i] & SOLID_BIT;
+    R nref[NS] = {n0, n1, n2};
+    for (int s = 0; s < NS; s++) {
+        double n = solid ? 0.0 : (n_init ? n_init[(long long)s * g.N + i] : (double)nref[s]);
+#pragma unroll
+        for (int p = 0; p < Q; p++) {
+            double v;
+            if (solid) v = 0.0;
+            else if (DEV) v = w_(p) * (n - (double)nref[s]);
+            else v = w_(p) * n;
+            Store<S>::st(f + (long long)(s * Q + p) * g.N + i, (R)v);
+        }
+    }
+}
+
+// ============================================================== charge
+// rho_i = sum_a z^a n^a + wall charge + bead charge (Eq. 2), n^a pulled from
+// the post-collision state (the streamed densities of this step, Eq. 15).
+template <typename S, typename R, typename PhiT, bool DEV>
+__global__ void __launch_bounds__(CHARGE_THREADS) charge_kernel(StepArgs<S, R, PhiT> a)
+{
+    __shared__ double sh[CHARGE_THREADS / 32];
+    __shared__ int plo, phi_;
+    const Grid3 g = a.g;
+    long long i0 = blockIdx.x * (long long)blockDim.x;
+    long long i = i0 + threadIdx.x;
+    if (threadIdx.x == 0) {
+        int pc = *a.patch_count;
+        plo = lower_bound_i(a.patch_node, pc, i0);
+        phi_ = lower_bound_i(a.patch_node, pc, i0 + blockDim.x);
+    }
+    __syncthreads();
+    double mine = 0.0;
+    if (i < g.N) {
+        uint32_t m = a.mask[i];
+        R rho = R(0);
+        if (!(m & SOLID_BIT)) {
+            int x, y, z;
+            coords_of(g, i, x, y, z);
+            Nbr nb = make_nbr(g, x, y, z);
+            R r = R(0);
+            r += a.zv[0] * R(0);  // solvent carries no charge
+            for (int s = 1; s < NS; s++) {
+                R v[Q];
+                pull19<S, R>(a.fin, g.N, s, i, m, nb, v);
+                R n = R(0);
+#pragma unroll
+                for (int p = 0; p < Q; p++) n += v[p];
+                if (DEV) n = a.n_ref[s] + n;
+                r += a.zv[s] * n;
+            }
+            rho = r + (a.src_wall ? a.src_wall[i] : R(0));
+            for (int k = plo; k < phi_; k++)
+                if (a.patch_node[k] == i) rho = rho + a.patch_q[k];
+            mine = (double)rho;
+        }
+        a.rho[i] = rho;
+    }
+    double t = block_sum(mine, sh);
+    if (threadIdx.x == 0) a.part_charge[blockIdx.x] = t;
+}
+
+// ============================================================== Poisson
+// Red-black successive over-relaxation with Chebyshev acceleration on the
+// 7-point fluid-only finite-volume Laplacian (Eq. 3; Sec. II.C):
+//   r_i = b_i + sum_{fluid faces j} phi_j - deg_i phi_i,  phi_i += omega r_i / deg_i
+//   omega: 1, 1/(1 - rJ^2/2), then 1/(1 - rJ^2 omega / 4) per half sweep.
+// One persistent cooperative launch runs the source set-up, every sweep and
+// every convergence test; the residual norm is accumulated from the nodes'
+// residuals as they are updated, in FP64, and all blocks reach the same
+// decision from the same block partials summed in the same order.
+template <typename PhiT> struct PoisUpd;
+template <> struct PoisUpd<double> {
+    __device__ static double resid(double acc, int deg, double pi) { return acc - deg * pi; }
+    __device__ static double apply(double pi, double omega, double r, int deg)
+    {
+        return pi + omega * r / deg;
+    }
+    typedef double acc_t;
+    __device__ static double r2(double r) { return r * r; }
+};
+template <> struct PoisUpd<long long> {
+    __device__ static long long resid(long long acc, int deg, long long pi) { return acc - deg * pi; }
+    __device__ static long long apply(long long pi, double omega, long long r, int deg)
+    {
+        float d = (float)omega * __ll2float_rn(r) / (float)deg;
+        return pi + __float2ll_rn(d);
+    }
+    typedef float acc_t;
+    __device__ static float r2(long long r)
+    {
+        float v = __ll2float_rn(r) * (float)PHI_INV;
+        return v * v;
+    }
+};
+
+template <typename S, typename R, typename PhiT>
+__global__ void __launch_bounds__(POIS_THREADS) poisson_kernel(StepArgs<S, R, PhiT> a)
+{
+    __shared__ double sh[POIS_THREADS / 32];
+    const Grid3 g = a.g;
+    const unsigned nblk = gridDim.x;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long nthr = (long long)nblk * blockDim.x;
+    // --- source: subtract the mean charge over fluid nodes (neutralisation)
+    double csum = 0.0;
+    for (int k = 0; k < a.nblocks_charge; k++) csum += a.part_charge[k];
+    // number of fluid nodes is carried in part_pois[2*nblk] by the host
+    const double nfl = a.part_pois[2 * nblk];
+    const double mean = nfl > 0 ? csum / nfl : 0.0;
+    double bl = 0.0;
+    for (long long i = tid; i < g.N; i += nthr) {
+        uint32_t m = a.mask[i];
+        PhiT bv;
+        if (m & SOLID_BIT) {
+            bv = (PhiT)0;
+        } else if constexpr (((PhiT)0.5) != 0) {
+            double v = (double)a.c4 * ((double)a.rho[i] - mean);
+            bv = (PhiT)v;
+            bl += v * v;
+        } else {
+            double v = (double)a.c4 * ((double)a.rho[i] - mean);
+            bv = __double2ll_rn(v * PHI_SCALE);
+            double q = (double)bv * PHI_INV;
+            bl += q * q;
+        }
+        __stcg(a.b + i, bv);
+    }
+    double t = block_sum(bl, sh);
+    if (threadIdx.x == 0) a.part_pois[blockIdx.x] = t;
+    if (!grid_barrier(a.barrier, nblk, a.status)) return;
+    double bn2 = 0.0;
+    for (unsigned k = 0; k < nblk; k++) bn2 += __ldcg(a.part_pois + k);
+    const double bnorm = sqrt(bn2);
+    const int limit = a.fixed_iter > 0 ? a.fixed_iter : a.max_iter;
+    if (a.fixed_iter <= 0 && bnorm == 0.0) {
+        if (tid == 0) {
+            *a.pois_iters = 0;
+            *a.pois_res = 0.0;
+        }
+        return;
+    }
+    const double rJ = a.rJ;
+    double omega = 1.0;
+    const int hx = (g.nx + 1) >> 1;
+    const long long nhalf = (long long)hx * g.ny * g.nz;
+    int it = 0, converged = 0;
+    double r2tot = 0.0;
+    for (it = 0; it < limit; it++) {
+        typename PoisUpd<PhiT>::acc_t r2 = 0;
+        for (int colour = 0; colour < 2; colour++) {
+            for (long long h = tid; h < nhalf; h += nthr) {
+                long long row = h / hx;
+                int xh = (int)(h - row * hx);
+                int z = (int)(row / g.ny);
+                int y = (int)(row - (long long)z * g.ny);
+                int x = 2 * xh + ((colour + y + z) & 1);
+                if (x >= g.nx) continue;
+                long long i = (long long)x + (long long)g.nx * row;
+                uint32_t m = a.mask[i];
+                if (m & SOLID_BIT) continue;
+                Nbr nb = make_nbr(g, x, y, z);
+                PhiT acc = __ldcg(a.b + i);
+                int deg = 0;
+#pragma unroll
+                for (int f = 0; f < 6; f++) {
+                    if (!((m >> (f + 1)) & 1u)) {
+                        acc += __ldcg(a.phi + face_idx(nb, f));
+                        deg++;
+                    }
+                }
+                if (deg == 0) continue;
+                PhiT pi = __ldcg(a.phi + i);
+                PhiT r = PoisUpd<PhiT>::resid(acc, deg, pi);
+                __stcg(a.phi + i, PoisUpd<PhiT>::apply(pi, omega, r, deg));
+                r2 += PoisUpd<PhiT>::r2(r);
+            }
+            if (it == 0 && colour == 0) omega = 1.0 / (1.0 - 0.5 * rJ * rJ);
+            else omega = 1.0 / (1.0 - 0.25 * rJ * rJ * omega);
+            if (colour == 1) {
+                double tb = block_sum((double)r2, sh);
+                if (threadIdx.x == 0) a.part_pois[blockIdx.x] = tb;
+            }
+            if (!grid_barrier(a.barrier, nblk, a.status)) return;
+        }
+        r2tot = 0.0;
+        for (unsigned k = 0; k < nblk; k++) r2tot += __ldcg(a.part_pois + k);
+        if (a.fixed_iter <= 0 && ((it + 1) % a.check_every) == 0 && sqrt(r2tot) <= a.tol * bnorm) {
+            converged = 1;
+            it++;
+            break;
+        }
+    }
+    if (tid == 0) {
+        *a.pois_iters = it;
+        *a.pois_res = sqrt(r2tot) / bnorm;
+        if (a.fixed_iter <= 0 && !converged) atomicOr(a.status, ST_NOCONV);
+    }
+}
+
+// ============================================================== beads
+template <typename R> struct BeadArgs {
+    Grid3 g;
+    int per[3];
+    const uint32_t *__restrict__ mask;
+    int nb;
+    R *Rb, *Vb;
+    const R *qb;
+    const int *chain;
+    int *patch_count;
+    int *patch_node;
+    R *patch_q;
+    R *patch_f;
+    R *patch_mom;
+    int *entry_slot;
+    R *entry_w;
+    int *sorted_entry;
+    int *slot_first;
+    int *status;
+};
+
+// Trilinear weights of the 8 nodes around a bead, wall nodes weighted zero
+// and the rest renormalised (the interpolation kernel of Sec. II.C).
+// Slot order k = ox + 2 oy + 4 oz.  Returns false when all 8 are wall.
+template <typename R>
+__device__ bool bead_stencil(const Grid3 &g, const int per[3], const uint32_t *mask, const R Rb[3],
+                             long long nodes[8], R w[8])
+{
+    int base[3];
+    R fr[3];
+    int dims[3] = {g.nx, g.ny, g.nz};
+    for (int c = 0; c < 3; c++)
+        if (!(fabs(Rb[c]) < R(1e6))) return false;  // non-finite or absurd position
+    for (int c = 0; c < 3; c++) {
+        R fl = floor(Rb[c]);
+        base[c] = (int)fl;
+        fr[c] = Rb[c] - fl;
+    }
+    R W = R(0);
+    for (int k = 0; k < 8; k++) {
+        int o[3] = {k & 1, (k >> 1) & 1, (k >> 2) & 1};
+        R wk = R(1);
+        for (int c = 0; c < 3; c++) wk *= o[c] ? fr[c] : R(1) - fr[c];
+        int q[3];
+        bool in = true;
+        for (int c = 0; c < 3; c++) {
+            int v = base[c] + o[c];
+            if (per[c]) {
+                v %= dims[c];
+                if (v < 0) v += dims[c];
+            } else if (v < 0 || v >= dims[c]) {
+                in = false;
+            }
+            q[c] = v;
+        }
+        long long id = in ? (long long)q[0] + (long long)g.nx * (q[1] + (long long)g.ny * q[2]) : -1;
+        bool fl = in && !(mask[id] & SOLID_BIT);
+        nodes[k] = id;
+        w[k] = fl ? wk : R(0);
+        W += w[k];
+    }
+    if (!(W > R(0))) return false;
+    for (int k = 0; k < 8; k++) w[k] = w[k] / W;
+    return true;
+}
+
+// One block: stencils of all beads, entries sorted by (node, bead) with a
+// bitonic sort in shared memory, unique nodes -> patch slots (ascending node
+// id), the sorted entry list with each slot's first position, and the bead
+// charge per slot summed in bead order.
+template <typename R> __global__ void __launch_bounds__(BEAD_THREADS) bead_bin_kernel(BeadArgs<R> a)
+{
+    __shared__ unsigned long long key[MAX_ENTRIES];
+    __shared__ int flag[MAX_ENTRIES];
+    const int ne = a.nb * 8;
+    int npow = 1;
+    while (npow < ne) npow <<= 1;
+    for (int b = threadIdx.x; b < a.nb; b += blockDim.x) {
+        R Rb[3] = {a.Rb[3 * b], a.Rb[3 * b + 1], a.Rb[3 * b + 2]};
+        long long nd[8];
+        R w[8];
+        bool ok = bead_stencil<R>(a.g, a.per, a.mask, Rb, nd, w);
+        if (!ok) atomicOr(a.status, ST_BEAD);
+        for (int k = 0; k < 8; k++) {
+            int e = b * 8 + k;
+            a.entry_w[e] = ok ? w[k] : R(0);
+            bool use = ok && nd[k] >= 0 && !(a.mask[nd[k]] & SOLID_BIT);
+            key[e] = use ? (((unsigned long long)nd[k] << 20) | (unsigned)e) : ~0ull;
+        }
+    }
+    for (int e = ne + threadIdx.x; e < npow; e += blockDim.x) key[e] = ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= npow; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < npow; t += blockDim.x) {
+                int ixj = t ^ j;
+                if (ixj > t) {
+                    unsigned long long u = key[t], v = key[ixj];
+                    bool up = (t & k) == 0;
+                    if ((u > v) == up) {
+                        key[t] = v;
+                        key[ixj] = u;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < npow; t += blockDim.x) {
+        unsigned long long u = key[t];
+        flag[t] = (u != ~0ull) && (t == 0 || (key[t - 1] >> 20) != (u >> 20));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = 0, nvalid = 0;
+        for (int t = 0; t < npow; t++) {
+            if (key[t] == ~0ull) {
+                flag[t] = -1;
+                continue;
+            }
+            nvalid++;
+            if (flag[t]) {
+                a.slot_first[c] = t;
+                c++;
+            }
+            flag[t] = c - 1;
+        }
+        a.slot_first[c] = nvalid;
+        *a.patch_count = c;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ne; t += blockDim.x) a.entry_slot[t] = -1;
+    __syncthreads();
+    for (int t = threadIdx.x; t < npow; t += blockDim.x) {
+        unsigned long long u = key[t];
+        if (u == ~0ull) continue;
+        int e = (int)(u & 0xFFFFFu);
+        a.entry_slot[e] = flag[t];
+        a.sorted_entry[t] = e;
+        if (t == 0 || (key[t - 1] >> 20) != (u >> 20)) a.patch_node[flag[t]] = (int)(u >> 20);
+    }
+    __syncthreads();
+    const int pc = *a.patch_count;
+    for (int k = threadIdx.x; k < pc; k += blockDim.x) {
+        R acc = R(0);
+        for (int t = a.slot_first[k]; t < a.slot_first[k + 1]; t++) {
+            int e = a.sorted_entry[t];
+            R w = a.entry_w[e];
+            if (w != R(0)) acc += a.qb[e >> 3] * w;
+        }
+        a.patch_q[k] = acc;
+    }
+}
+
+template <typename R>
+__device__ void wca_add(R eps, R sig, const R d[3], R F[3])
+{
+    R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    // 2^(1/3) sigma^2 is the squared WCA cut-off
+    R rc2 = (R)1.2599210498948732 * sig * sig;
+    if (r2 >= rc2) return;
+    R sr2 = sig * sig / r2;
+    R sr6 = sr2 * sr2 * sr2;
+    R mag = R(24) * eps * (R(2) * sr6 * sr6 - sr6) / r2;
+    for (int c = 0; c < 3; c++) F[c] += mag * d[c];
+}
+
+template <typename R> __device__ void min_image(const Grid3 &g, const int per[3], R d[3])
+{
+    R L[3] = {(R)g.nx, (R)g.ny, (R)g.nz};
+    for (int c = 0; c < 3; c++)
+        if (per[c]) d[c] -= L[c] * rint(d[c] / L[c]);
+}
+
+template <typename S, typename R, typename PhiT, bool DEV> struct MdArgs {
+    StepArgs<S, R, PhiT> s;
+    BeadArgs<R> b;
+    int md_substeps;
+    R xi, mass, bead_kT;
+    int bond_kind;
+    R bond_k, bond_r0, bond_l0, wca_eps, wca_sigma, wall_eps, wall_sigma;
+    uint32_t key0, key1;
+    long long step;
+};
+
+// Conservative force on bead b: bond with b-1 and b+1 (Eq. 9c, FENE option),
+// WCA against every other bead except bonded neighbours when the bond is
+// harmonic (Eq. 9a), WCA against wall nodes within the cut-off.
+template <typename S, typename R, typename PhiT, bool DEV>
+__device__ bool bead_force(const MdArgs<S, R, PhiT, DEV> &A, const R *Rs, int b, R F[3])
+{
+    const Grid3 &g = A.b.g;
+    const int nb = A.b.nb;
+    F[0] = F[1] = F[2] = R(0);
+    bool ok = true;
+    for (int side = 0; side < 2; side++) {
+        int lo = side == 0 ? b - 1 : b;  // pair (lo, lo+1)
+        if (lo < 0 || lo + 1 >= nb) continue;
+        if (A.b.chain[lo] != A.b.chain[lo + 1]) continue;
+        R d[3];
+        for (int c = 0; c < 3; c++) d[c] = Rs[3 * lo + c] - Rs[3 * (lo + 1) + c];
+        min_image<R>(g, A.b.per, d);
+        R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        R fac;
+        if (A.bond_kind == EKL_BOND_FENE) {
+            R x = r2 / (A.bond_r0 * A.bond_r0);
+            if (!(x < R(1))) ok = false;
+            fac = -A.bond_k / (R(1) - x);
+        } else {
+            R r = sqrt(r2);
+            fac = -A.bond_k * (r - A.bond_l0) / r;
+        }
+        for (int c = 0; c < 3; c++) {
+            if (side == 0) F[c] -= fac * d[c];  // b is the second bead of the pair
+            else F[c] += fac * d[c];
+        }
+    }
+    for (int c2 = 0; c2 < nb; c2++) {
+        if (c2 == b) continue;
+        int lo = c2 < b ? c2 : b, hi = c2 < b ? b : c2;
+        if (A.bond_kind == EKL_BOND_HARMONIC && A.b.chain[lo] == A.b.chain[hi] && hi - lo <= 1)
+            continue;
+        R d[3];
+        for (int c = 0; c < 3; c++) d[c] = Rs[3 * lo + c] - Rs[3 * hi + c];
+        min_image<R>(g, A.b.per, d);
+        R Fp[3] = {R(0), R(0), R(0)};
+        wca_add<R>(A.wca_eps, A.wca_sigma, d, Fp);
+        for (int c = 0; c < 3; c++) {
+            if (c2 < b) F[c] -= Fp[c];
+            else F[c] += Fp[c];
+        }
+    }
+    const R rc = (R)1.122462048309373 * A.wall_sigma;  // 2^(1/6) sigma
+    for (int c = 0; c < 3; c++)
+        if (!(fabs(Rs[3 * b + c]) < R(1e6)) || !(rc < R(16))) return false;  // keeps the wall scan bounded
+    int lo[3], hi[3];
+    for (int c = 0; c < 3; c++) {
+        lo[c] = (int)floor(Rs[3 * b + c] - rc);
+        hi[c] = (int)floor(Rs[3 * b + c] + rc) + 1;
+    }
+    int dims[3] = {g.nx, g.ny, g.nz};
+    for (int z = lo[2]; z <= hi[2]; z++)
+        for (int y = lo[1]; y <= hi[1]; y++)
+            for (int x = lo[0]; x <= hi[0]; x++) {
+                int q[3] = {x, y, z};
+                bool in = true;
+                for (int c = 0; c < 3; c++) {
+                    if (A.b.per[c]) {
+                        q[c] %= dims[c];
+                        if (q[c] < 0) q[c] += dims[c];
+                    } else if (q[c] < 0 || q[c] >= dims[c]) {
+                        in = false;
+                    }
+                }
+                if (!in) continue;
+                long long id = (long long)q[0] + (long long)g.nx * (q[1] + (long long)g.ny * q[2]);
+                if (!(A.b.mask[id] & SOLID_BIT)) continue;
+                R d[3] = {Rs[3 * b] - (R)x, Rs[3 * b + 1] - (R)y, Rs[3 * b + 2] - (R)z};
+                wca_add<R>(A.wall_eps, A.wall_sigma, d, F);
+            }
+    return ok;
+}
+
+// One block: moments and field at the patch nodes, interpolation to beads,
+// md_substeps Langevin sub-steps with implicit friction, spreading of the
+// sub-step-averaged drag g^a_i = -gamma^a (u^a(R_i) - V_i) as a force per
+// particle on the patch nodes.  Readings as in the oracle: gamma^a = xi n^a/n
+// (or xi), fluid/field held at R(t) over the sub-steps, R(t) weights both ways.
+template <typename S, typename R, typename PhiT, bool DEV>
+__global__ void __launch_bounds__(BEAD_THREADS) bead_md_kernel(MdArgs<S, R, PhiT, DEV> A)
+{
+    const StepArgs<S, R, PhiT> &a = A.s;
+    const BeadArgs<R> &B = A.b;
+    const Grid3 g = a.g;
+    const int nb = B.nb;
+    const int pc = *B.patch_count;
+    __shared__ R Rs[3 * MAX_BEADS];
+    // moments at the patch nodes
+    for (int k = threadIdx.x; k < pc; k += blockDim.x) {
+        long long i = B.patch_node[k];
+        uint32_t m = a.mask[i];
+        int x, y, z;
+        coords_of(g, i, x, y, z);
+        Nbr nbr = make_nbr(g, x, y, z);
+        R *out = B.patch_mom + (long long)k * 15;
+        for (int s = 0; s < NS; s++) {
+            R v[Q];
+            pull19<S, R>(a.fin, g.N, s, i, m, nbr, v);
+            R n = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+            for (int p = 0; p < Q; p++) {
+                n += v[p];
+                if (cx_(p) == 1) jx += v[p];
+                if (cx_(p) == -1) jx -= v[p];
+                if (cy_(p) == 1) jy += v[p];
+                if (cy_(p) == -1) jy -= v[p];
+                if (cz_(p) == 1) jz += v[p];
+                if (cz_(p) == -1) jz -= v[p];
+            }
+            if (DEV) n = a.n_ref[s] + n;
+            out[s] = n;
+            out[3 + 3 * s + 0] = jx / n;
+            out[3 + 3 * s + 1] = jy / n;
+            out[3 + 3 * s + 2] = jz / n;
+        }
+        R gr[3];
+        int olo[3], ohi[3];
+        closed_faces(g, a.per, x, y, z, olo, ohi);
+        node_gradient<R, PhiT>(a.phi, a.wall_share, a.c4, i, m, nbr, olo, ohi, gr);
+        out[12] = gr[0];
+        out[13] = gr[1];
+        out[14] = gr[2];
+    }
+    for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) Rs[t] = B.Rb[t];
+    __syncthreads();
+    // interpolation (every bead owned by one thread)
+    const int b = threadIdx.x;
+    R nR[NS] = {R(0), R(0), R(0)}, uR[NS][3], gR[3] = {R(0), R(0), R(0)}, gam[NS];
+    R V[3] = {R(0), R(0), R(0)}, gacc[NS][3];
+    bool active = b < nb;
+    if (active) {
+        for (int s = 0; s < NS; s++)
+            for (int c = 0; c < 3; c++) {
+                uR[s][c] = R(0);
+                gacc[s][c] = R(0);
+            }
+        for (int k = 0; k < 8; k++) {
+            R w = B.entry_w[b * 8 + k];
+            if (w == R(0)) continue;
+            int slot = B.entry_slot[b * 8 + k];
+            const R *mo = B.patch_mom + (long long)slot * 15;
+            for (int s = 0; s < NS; s++) {
+                nR[s] += w * mo[s];
+                for (int c = 0; c < 3; c++) uR[s][c] += w * mo[3 + 3 * s + c];
+            }
+            for (int c = 0; c < 3; c++) gR[c] += w * mo[12 + c];
+        }
+        R ntot = nR[0] + nR[1] + nR[2];
+        for (int s = 0; s < NS; s++)
+            gam[s] = (a.flags & EKL_GAMMA_LITERAL) ? A.xi : A.xi * nR[s] / ntot;
+        R qb = B.qb[b];
+        for (int c = 0; c < 3; c++) {
+            V[c] = B.Vb[3 * b + c];
+            if (fabs(qb * gR[c]) >= R(1)) atomicOr(a.status, ST_CFL);
+        }
+    }
+    const int nsub = A.md_substeps;
+    const R dt = R(1) / (R)nsub;
+    const bool noise = A.bead_kT > R(0) && !(a.flags & EKL_NO_BEAD_NOISE);
+    for (int sub = 0; sub < nsub; sub++) {
+        R F[3] = {R(0), R(0), R(0)};
+        if (active) {
+            if (!bead_force<S, R, PhiT, DEV>(A, Rs, b, F)) atomicOr(a.status, ST_BEAD);
+        }
+        __syncthreads();  // all forces read Rs before it moves
+        if (active) {
+            R xi_[3] = {R(0), R(0), R(0)};
+            if (noise) {
+                uint32_t ctr[4] = {(uint32_t)b, (uint32_t)sub | (1u << 24), (uint32_t)A.step,
+                                   (uint32_t)((uint64_t)A.step >> 32)};
+                philox4x32_10(ctr, A.key0, A.key1);
+                for (int c = 0; c < 3; c++) xi_[c] = unit_variate<R>(ctr[c]);
+            }
+            R gtot = gam[0] + gam[1] + gam[2];
+            R amp = noise ? sqrt(R(2) * gtot * A.bead_kT / dt) : R(0);
+            R qb = B.qb[b];
+            for (int c = 0; c < 3; c++) {
+                R Fe = -qb * Consts<R>::KT * gR[c] + qb * Consts<R>::KT * a.E[c];
+                R num = A.mass * V[c] / dt;
+                for (int s = 0; s < NS; s++) num += gam[s] * uR[s][c];
+                num += F[c] + Fe + amp * xi_[c];
+                R Vn = num / (A.mass / dt + gtot);
+                for (int s = 0; s < NS; s++) gacc[s][c] += dt * (-gam[s] * (uR[s][c] - Vn));
+                V[c] = Vn;
+            }
+            R L[3] = {(R)g.nx, (R)g.ny, (R)g.nz};
+            for (int c = 0; c < 3; c++) {
+                R r = Rs[3 * b + c] + dt * V[c];
+                if (B.per[c]) {
+                    if (r < R(0)) r += L[c];
+                    else if (r >= L[c]) r -= L[c];
+                }
+                Rs[3 * b + c] = r;
+            }
+        }
+        __syncthreads();
+    }
+    if (active) {
+        for (int c = 0; c < 3; c++) {
+            B.Rb[3 * b + c] = Rs[3 * b + c];
+            B.Vb[3 * b + c] = V[c];
+        }
+    }
+    // per-bead sub-step-averaged drag, then per slot in bead order
+    R *gbuf = B.patch_f + (long long)MAX_ENTRIES * 9;
+    if (active)
+        for (int s = 0; s < NS; s++)
+            for (int c = 0; c < 3; c++) gbuf[b * 9 + 3 * s + c] = gacc[s][c];
+    __syncthreads();
+    for (int k = threadIdx.x; k < pc; k += blockDim.x) {
+        R acc[9];
+        for (int t = 0; t < 9; t++) acc[t] = R(0);
+        for (int t = B.slot_first[k]; t < B.slot_first[k + 1]; t++) {
+            int e = B.sorted_entry[t];
+            R w = B.entry_w[e];
+            if (w == R(0)) continue;
+            int bb = e >> 3;
+            for (int u = 0; u < 9; u++) acc[u] += gbuf[bb * 9 + u] * w;
+        }
+        const R *mo = B.patch_mom + (long long)k * 15;
+        for (int s = 0; s < NS; s++)
+            for (int c = 0; c < 3; c++) {
+                R v = acc[3 * s + c];
+                B.patch_f[(long long)k * 9 + 3 * s + c] = v != R(0) ? v / mo[s] : R(0);
+            }
+    }
+}
+
+// ============================================================== fused LB
+// Per fluid node: pull the 3 x 19 populations (halfway bounce-back on set
+// link bits), moments (Eqs. 15-16), force per particle (Eq. 5: external,
+// field -z k_B T grad phi + z k_B T E, bead drag, and the friction of Eq. 6
+// evaluated at the half-force velocities by the closed form below), BGK
+// relaxation to f_eq(n, u^a*) (Eq. 10) plus (1 - omega/2) S (Eq. 13), store.
+//   a^a = j^a/n^a + G^a/2, h^a = omega_d^a/2,
+//   u* = sum n a/(1+h) / sum n/(1+h), u^a* = (a^a + h^a u*)/(1+h^a),
+//   Phi^a = G^a - omega_d^a (u^a* - u*).
+template <typename S, typename R, typename PhiT, bool DEV>
+__global__ void __launch_bounds__(LB_THREADS) lb_fused_kernel(StepArgs<S, R, PhiT> a)
+{
+    __shared__ double sh[LB_THREADS / 32];
+    __shared__ int plo, phi_;
+    const Grid3 g = a.g;
+    const long long i0 = blockIdx.x * (long long)blockDim.x;
+    const long long i = i0 + threadIdx.x;
+    if (threadIdx.x == 0) {
+        int pc = *a.patch_count;
+        plo = lower_bound_i(a.patch_node, pc, i0);
+        phi_ = lower_bound_i(a.patch_node, pc, i0 + blockDim.x);
+    }
+    __syncthreads();
+    double msum[NS] = {0.0, 0.0, 0.0};
+    int bad = 0, cfl = 0;
+    if (i < g.N) {
+        const uint32_t m = a.mask[i];
+        if (!(m & SOLID_BIT)) {
+            int x, y, z;
+            coords_of(g, i, x, y, z);
+            const Nbr nb = make_nbr(g, x, y, z);
+            R f[NS][Q];
+#pragma unroll
+            for (int s = 0; s < NS; s++) pull19<S, R>(a.fin, g.N, s, i, m, nb, f[s]);
+            R gphi[3];
+            int olo[3], ohi[3];
+            closed_faces(g, a.per, x, y, z, olo, ohi);
+            node_gradient<R, PhiT>(a.phi, a.wall_share, a.c4, i, m, nb, olo, ohi, gphi);
+            for (int c = 0; c < 3; c++)
+                if (fabs(gphi[c]) >= R(1)) cfl = 1;
+            int slot = -1;
+            for (int k = plo; k < phi_; k++)
+                if (a.patch_node[k] == i) slot = k;
+            R n[NS], dn[NS], av[NS][3], G[NS][3], h[NS];
+#pragma unroll
+            for (int s = 0; s < NS; s++) {
+                R nn = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+                for (int p = 0; p < Q; p++) {
+                    R v = f[s][p];
+                    nn += v;
+                    if (cx_(p) == 1) jx += v;
+                    if (cx_(p) == -1) jx -= v;
+                    if (cy_(p) == 1) jy += v;
+                    if (cy_(p) == -1) jy -= v;
+                    if (cz_(p) == 1) jz += v;
+                    if (cz_(p) == -1) jz -= v;
+                }
+                dn[s] = nn;
+                n[s] = DEV ? a.n_ref[s] + nn : nn;
+                if (!(n[s] > R(0)) || !isfinite(n[s])) bad = 1;
+                msum[s] = (double)n[s];
+                h[s] = R(0.5) * a.wd[s];
+                R j[3] = {jx, jy, jz};
+                for (int c = 0; c < 3; c++) {
+                    R zk = a.zv[s] * Consts<R>::KT;
+                    R Gc = a.body[s][c] - zk * gphi[c] + zk * a.E[c];
+                    if (slot >= 0) Gc = Gc + a.patch_f[(long long)slot * 9 + 3 * s + c];
+                    G[s][c] = Gc;
+                    av[s][c] = j[c] / n[s] + R(0.5) * Gc;
+                }
+            }
+            R num[3] = {R(0), R(0), R(0)}, den = R(0), us[3];
+#pragma unroll
+            for (int s = 0; s < NS; s++) {
+                den += n[s] / (R(1) + h[s]);
+                for (int c = 0; c < 3; c++) num[c] += n[s] * av[s][c] / (R(1) + h[s]);
+            }
+            for (int c = 0; c < 3; c++) us[c] = num[c] / den;
+#pragma unroll
+            for (int s = 0; s < NS; s++) {
+                R ue[3], Ph[3];
+                for (int c = 0; c < 3; c++) {
+                    R ua = (av[s][c] + h[s] * us[c]) / (R(1) + h[s]);
+                    Ph[c] = G[s][c] - a.wd[s] * (ua - us[c]);
+                    ue[c] = (a.flags & EKL_EQ_BARYCENTRIC) ? us[c] : ua;
+                }
+                const R om = a.om[s];
+                const R u2 = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
+                const R Fu = Ph[0] * ue[0] + Ph[1] * ue[1] + Ph[2] * ue[2];
+                const R cS = R(1) - R(0.5) * om;
+                S *out = a.fout + (long long)(s * Q) * g.N + i;
+#pragma unroll
+                for (int p = 0; p < Q; p++) {
+                    const R cu = (R)cx_(p) * ue[0] + (R)cy_(p) * ue[1] + (R)cz_(p) * ue[2];
+                    const R cF = (R)cx_(p) * Ph[0] + (R)cy_(p) * Ph[1] + (R)cz_(p) * Ph[2];
+                    const R w = (R)w_(p);
+                    R fs;
+                    if constexpr (!DEV) {
+                        const R VT2 = Consts<R>::VT2;
+                        R feq = w * n[s] * (R(1) + cu / VT2 + (cu * cu - VT2 * u2) / (R(2) * VT2 * VT2));
+                        R Sp = w * n[s] * (cF / VT2 + (cu * cF - VT2 * Fu) / (VT2 * VT2));
+                        fs = f[s][p] - om * (f[s][p] - feq) + cS * Sp;
+                    } else {
+                        // deviation form: s_eq = f_eq - w n_ref
+                        R poly = R(3) * cu + R(4.5) * cu * cu - R(1.5) * u2;
+                        R seq = w * (dn[s] + n[s] * poly);
+                        R Sp = w * n[s] * (R(3) * cF + R(9) * cu * cF - R(3) * Fu);
+                        fs = f[s][p] - om * (f[s][p] - seq) + cS * Sp;
+                    }
+                    Store<S>::st(out + (long long)p * g.N, fs);
+                }
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(a.status, ST_UNSTABLE);
+    if (__any_sync(0xffffffffu, cfl) && (threadIdx.x & 31) == 0) atomicOr(a.status, ST_CFL);
+    for (int s = 0; s < NS; s++) {
+        double t = block_sum(msum[s], sh);
+        if (threadIdx.x == 0) a.part_mass[blockIdx.x * NS + s] = t;
+    }
+}
+
+// ============================================================== outputs
+template <typename S, typename R, typename PhiT, bool DEV>
+__global__ void fields_kernel(StepArgs<S, R, PhiT> a, double *n_out, double *j_out, double *phi_out)
+{
+    const Grid3 g = a.g;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    uint32_t m = a.mask[i];
+    bool solid = m & SOLID_BIT;
+    int x, y, z;
+    coords_of(g, i, x, y, z);
+    Nbr nb = make_nbr(g, x, y, z);
+    for (int s = 0; s < NS; s++) {
+        double n = 0, jx = 0, jy = 0, jz = 0;
+        if (!solid) {
+            R v[Q];
+            pull19<S, R>(a.fin, g.N, s, i, m, nb, v);
+            R nn = R(0), ax = R(0), ay = R(0), az = R(0);
+#pragma unroll
+            for (int p = 0; p < Q; p++) {
+                nn += v[p];
+                if (cx_(p) == 1) ax += v[p];
+                if (cx_(p) == -1) ax -= v[p];
+                if (cy_(p) == 1) ay += v[p];
+                if (cy_(p) == -1) ay -= v[p];
+                if (cz_(p) == 1) az += v[p];
+                if (cz_(p) == -1) az -= v[p];
+            }
+            n = DEV ? (double)a.n_ref[s] + (double)nn : (double)nn;
+            jx = ax; jy = ay; jz = az;
+        }
+        if (n_out) n_out[(long long)s * g.N + i] = n;
+        if (j_out) {
+            j_out[((long long)s * 3 + 0) * g.N + i] = jx;
+            j_out[((long long)s * 3 + 1) * g.N + i] = jy;
+            j_out[((long long)s * 3 + 2) * g.N + i] = jz;
+        }
+    }
+    if (phi_out) {
+        double v;
+        if constexpr (((PhiT)0.5) != 0) v = (double)a.phi[i];
+        else v = (double)a.phi[i] * PHI_INV;
+        phi_out[i] = solid ? 0.0 : v;
+    }
+}
+
+template <typename S, typename R, typename PhiT, bool DEV>
+__global__ void state_kernel(StepArgs<S, R, PhiT> a, double *f_io, double *phi_io, int to_host)
+{
+    const Grid3 g = a.g;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    bool solid = a.mask[i] & SOLID_BIT;
+    for (int s = 0; s < NS; s++)
+        for (int p = 0; p < Q; p++) {
+            long long k = (long long)(s * Q + p) * g.N + i;
+            double off = DEV ? w_(p) * (double)a.n_ref[s] : 0.0;
+            if (to_host) {
+                f_io[k] = solid ? 0.0 : (double)Store<S>::ld((const S *)a.fin + k) + off;
+            } else {
+                Store<S>::st((S *)a.fin + k, (R)(solid ? 0.0 : f_io[k] - off));
+            }
+        }
+    if (phi_io) {
+        if (to_host) {
+            if constexpr (((PhiT)0.5) != 0) phi_io[i] = (double)a.phi[i];
+            else phi_io[i] = (double)a.phi[i] * PHI_INV;
+        } else {
+            if constexpr (((PhiT)0.5) != 0) a.phi[i] = (PhiT)phi_io[i];
+            else a.phi[i] = __double2ll_rn(phi_io[i] * PHI_SCALE);
+        }
+    }
+}
+
+}  // namespace ekl
