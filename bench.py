@@ -131,7 +131,7 @@ def barrier(world):
         dist.barrier()
 
 
-def workload_for(name, rank=0):
+def workload_for(name, rank=0, args=None):
     from paper_1710_09421_gb300 import workloads as W
     if name == "pore":
         wl = W.config_pore_fp32()
@@ -141,6 +141,10 @@ def workload_for(name, rank=0):
         raise SystemExit(f"unknown workload {name}")
     if rank:
         wl = wl.replace(seed=wl.seed + 1000 * rank)  # independent replica per rank
+    if args is not None and args.rho_jacobi > 0:
+        wl = wl.replace(rho_jacobi=args.rho_jacobi)
+    if args is not None and args.check_every > 0:
+        wl = wl.replace(poisson_check_every=args.check_every)
     return wl
 
 
@@ -170,7 +174,7 @@ def run_reference(args):
     world, rank, local = dist_setup(args)
     if rank != 0:
         return
-    wl = workload_for(args.workload)
+    wl = workload_for(args.workload, 0, args)
     import oracle
     cores = os.cpu_count() or 1
     ref = oracle.Sim(wl, threads=cores)
@@ -210,7 +214,7 @@ def run_ours(args):
     import paper_1710_09421_gb300 as E
 
     E.load()
-    wl = workload_for(args.workload, rank)
+    wl = workload_for(args.workload, rank, args)
     stream = torch.cuda.Stream()
     sraw = stream.cuda_stream
     store = {"f32": 4, "f64": 8, "bf16": 2, "fp16": 2}[args.precision]
@@ -306,6 +310,10 @@ def main():
     ap.add_argument("--workload", default="pore")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16", "fp16"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--rho-jacobi", type=float, default=0.0,
+                    help="Chebyshev spectral radius (0: library default)")
+    ap.add_argument("--check-every", type=int, default=0,
+                    help="Poisson residual test interval (0: workload default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

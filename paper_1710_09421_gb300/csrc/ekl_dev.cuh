@@ -241,6 +241,22 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return t;
 }
 
+// Sum of n per-block partials, identical in every block: warp 0 reads them
+// (lane l takes l, l+32, ...), reduces with a fixed shuffle tree and
+// broadcasts through shared memory.  Every thread of the block must call it.
+__device__ __forceinline__ double sum_partials(const double *p, int n, double *sh)
+{
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int k = threadIdx.x; k < n; k += 32) v += __ldcg(p + k);
+        v = warp_sum(v);
+        if (threadIdx.x == 0) sh[0] = v;
+    }
+    __syncthreads();
+    return sh[0];
+}
+
 // lower bound of `key` in sorted a[0..n)
 __device__ __forceinline__ int lower_bound_i(const int *a, int n, long long key)
 {

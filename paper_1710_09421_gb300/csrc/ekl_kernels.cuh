@@ -230,9 +230,9 @@ __global__ void __launch_bounds__(POIS_THREADS) poisson_kernel(StepArgs<S, R, Ph
     const unsigned nblk = gridDim.x;
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long nthr = (long long)nblk * blockDim.x;
+    __shared__ double bc[1];
     // --- source: subtract the mean charge over fluid nodes (neutralisation)
-    double csum = 0.0;
-    for (int k = 0; k < a.nblocks_charge; k++) csum += a.part_charge[k];
+    const double csum = sum_partials(a.part_charge, a.nblocks_charge, bc);
     // number of fluid nodes is carried in part_pois[2*nblk] by the host
     const double nfl = a.part_pois[2 * nblk];
     const double mean = nfl > 0 ? csum / nfl : 0.0;
@@ -257,8 +257,7 @@ __global__ void __launch_bounds__(POIS_THREADS) poisson_kernel(StepArgs<S, R, Ph
     double t = block_sum(bl, sh);
     if (threadIdx.x == 0) a.part_pois[blockIdx.x] = t;
     if (!grid_barrier(a.barrier, nblk, a.status)) return;
-    double bn2 = 0.0;
-    for (unsigned k = 0; k < nblk; k++) bn2 += __ldcg(a.part_pois + k);
+    const double bn2 = sum_partials(a.part_pois, (int)nblk, bc);
     const double bnorm = sqrt(bn2);
     const int limit = a.fixed_iter > 0 ? a.fixed_iter : a.max_iter;
     if (a.fixed_iter <= 0 && bnorm == 0.0) {
@@ -311,9 +310,9 @@ __global__ void __launch_bounds__(POIS_THREADS) poisson_kernel(StepArgs<S, R, Ph
             }
             if (!grid_barrier(a.barrier, nblk, a.status)) return;
         }
-        r2tot = 0.0;
-        for (unsigned k = 0; k < nblk; k++) r2tot += __ldcg(a.part_pois + k);
-        if (a.fixed_iter <= 0 && ((it + 1) % a.check_every) == 0 && sqrt(r2tot) <= a.tol * bnorm) {
+        const bool test = a.fixed_iter <= 0 && ((it + 1) % a.check_every) == 0;
+        if (test || it + 1 == limit) r2tot = sum_partials(a.part_pois, (int)nblk, bc);
+        if (test && sqrt(r2tot) <= a.tol * bnorm) {
             converged = 1;
             it++;
             break;
@@ -514,8 +513,15 @@ template <typename S, typename R, typename PhiT, bool DEV> struct MdArgs {
 // Conservative force on bead b: bond with b-1 and b+1 (Eq. 9c, FENE option),
 // WCA against every other bead except bonded neighbours when the bond is
 // harmonic (Eq. 9a), WCA against wall nodes within the cut-off.
+// Solid flags of a WALL_BOX^3 block of nodes around each bead, cached in
+// shared memory for the sub-steps (bit (z*WALL_BOX + y)*WALL_BOX + x of the
+// bead's words, origin org).
+constexpr int WALL_BOX = 6;
+constexpr int WALL_WORDS = (WALL_BOX * WALL_BOX * WALL_BOX + 31) / 32;
+
 template <typename S, typename R, typename PhiT, bool DEV>
-__device__ bool bead_force(const MdArgs<S, R, PhiT, DEV> &A, const R *Rs, int b, R F[3])
+__device__ bool bead_force(const MdArgs<S, R, PhiT, DEV> &A, const R *Rs, int b, R F[3],
+                           const int *org, const uint32_t *bits)
 {
     const Grid3 &g = A.b.g;
     const int nb = A.b.nb;
@@ -581,8 +587,16 @@ __device__ bool bead_force(const MdArgs<S, R, PhiT, DEV> &A, const R *Rs, int b,
                     }
                 }
                 if (!in) continue;
-                long long id = (long long)q[0] + (long long)g.nx * (q[1] + (long long)g.ny * q[2]);
-                if (!(A.b.mask[id] & SOLID_BIT)) continue;
+                int ox = x - org[0], oy = y - org[1], oz = z - org[2];
+                bool solid;
+                if (ox >= 0 && ox < WALL_BOX && oy >= 0 && oy < WALL_BOX && oz >= 0 && oz < WALL_BOX) {
+                    int bit = (oz * WALL_BOX + oy) * WALL_BOX + ox;
+                    solid = (bits[bit >> 5] >> (bit & 31)) & 1u;
+                } else {
+                    long long id = (long long)q[0] + (long long)g.nx * (q[1] + (long long)g.ny * q[2]);
+                    solid = A.b.mask[id] & SOLID_BIT;
+                }
+                if (!solid) continue;
                 R d[3] = {Rs[3 * b] - (R)x, Rs[3 * b + 1] - (R)y, Rs[3 * b + 2] - (R)z};
                 wca_add<R>(A.wall_eps, A.wall_sigma, d, F);
             }
@@ -640,6 +654,35 @@ __global__ void __launch_bounds__(BEAD_THREADS) bead_md_kernel(MdArgs<S, R, PhiT
         out[14] = gr[2];
     }
     for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) Rs[t] = B.Rb[t];
+    __shared__ int worg[3 * MAX_BEADS];
+    __shared__ uint32_t wbits[WALL_WORDS * MAX_BEADS];
+    for (int t = threadIdx.x; t < WALL_WORDS * nb; t += blockDim.x) wbits[t] = 0u;
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
+        R r = Rs[t];
+        worg[t] = fabs(r) < R(1e6) ? (int)floor(r) - WALL_BOX / 2 + 1 : 0;
+    }
+    __syncthreads();
+    {
+        const int dims[3] = {g.nx, g.ny, g.nz};
+        const int cells = WALL_BOX * WALL_BOX * WALL_BOX;
+        for (int t = threadIdx.x; t < nb * cells; t += blockDim.x) {
+            int bb = t / cells, cell = t - bb * cells;
+            int ox = cell % WALL_BOX, oy = (cell / WALL_BOX) % WALL_BOX, oz = cell / (WALL_BOX * WALL_BOX);
+            int q[3] = {worg[3 * bb] + ox, worg[3 * bb + 1] + oy, worg[3 * bb + 2] + oz};
+            bool in = true;
+            for (int c = 0; c < 3; c++) {
+                if (B.per[c]) {
+                    q[c] %= dims[c];
+                    if (q[c] < 0) q[c] += dims[c];
+                } else if (q[c] < 0 || q[c] >= dims[c]) {
+                    in = false;
+                }
+            }
+            if (in && (a.mask[(long long)q[0] + (long long)g.nx * (q[1] + (long long)g.ny * q[2])] & SOLID_BIT))
+                atomicOr(&wbits[bb * WALL_WORDS + (cell >> 5)], 1u << (cell & 31));
+        }
+    }
     __syncthreads();
     // interpolation (every bead owned by one thread)
     const int b = threadIdx.x;
@@ -678,7 +721,8 @@ __global__ void __launch_bounds__(BEAD_THREADS) bead_md_kernel(MdArgs<S, R, PhiT
     for (int sub = 0; sub < nsub; sub++) {
         R F[3] = {R(0), R(0), R(0)};
         if (active) {
-            if (!bead_force<S, R, PhiT, DEV>(A, Rs, b, F)) atomicOr(a.status, ST_BEAD);
+            if (!bead_force<S, R, PhiT, DEV>(A, Rs, b, F, &worg[3 * b], &wbits[b * WALL_WORDS]))
+                atomicOr(a.status, ST_BEAD);
         }
         __syncthreads();  // all forces read Rs before it moves
         if (active) {
@@ -754,7 +798,7 @@ __global__ void __launch_bounds__(BEAD_THREADS) bead_md_kernel(MdArgs<S, R, PhiT
 //   u* = sum n a/(1+h) / sum n/(1+h), u^a* = (a^a + h^a u*)/(1+h^a),
 //   Phi^a = G^a - omega_d^a (u^a* - u*).
 template <typename S, typename R, typename PhiT, bool DEV>
-__global__ void __launch_bounds__(LB_THREADS) lb_fused_kernel(StepArgs<S, R, PhiT> a)
+__global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 2 : 1) lb_fused_kernel(StepArgs<S, R, PhiT> a)
 {
     __shared__ double sh[LB_THREADS / 32];
     __shared__ int plo, phi_;

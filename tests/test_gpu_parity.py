@@ -84,17 +84,29 @@ def test_fp64_closed_box_odd_extent_no_beads():
     assert all(v < TOL64 for v in errs.values()), errs
 
 
+# The FP32 tests run the same number of SOR sweeps on both sides: two
+# solves stopped independently at a relative residual tol differ in phi by up
+# to cond(L) * tol, which is not an FP32 effect.
 def test_fp32_small_pore_1000_steps():
     wl = W.small_pore(nx=20, ny=16, nz=24, membrane=(10, 13), radius=3.0, n_beads=4,
-                      precision="f32")
+                      precision="f32").replace(poisson_fixed_iter=60)
     errs, sg, so = _compare(wl, 1000, TOL32, precision="f32", check_beads=False)
     assert errs["n"] < TOL32 and errs["u"] < TOL32, errs
 
 
 def test_fp32_charged_slit_fixed_point_poisson():
-    wl = W.charged_slit(nx=16, ny=16, nz=16, n_beads=4).replace(poisson_tol=1e-8)
+    wl = W.charged_slit(nx=16, ny=16, nz=16, n_beads=4).replace(poisson_fixed_iter=80)
     errs, sg, so = _compare(wl, 100, TOL32, precision="f32", check_beads=False)
     assert errs["n"] < TOL32 and errs["u"] < TOL32 and errs["phi"] < TOL32, errs
+
+
+def test_fp32_tolerance_stopping_bounded_by_solver_tolerance():
+    """With the tolerance-based stop the FP32 path stays within a small
+    multiple of the Poisson tolerance effect (reported, loose bound)."""
+    wl = W.small_pore(nx=20, ny=16, nz=24, membrane=(10, 13), radius=3.0, n_beads=4,
+                      precision="f32").replace(poisson_tol=1e-10)
+    errs, sg, so = _compare(wl, 200, TOL32, precision="f32", check_beads=False)
+    assert errs["n"] < TOL32 and errs["u"] < 1e-4, errs
 
 
 def test_mass_conservation_fp32():
@@ -145,7 +157,7 @@ def test_full_size_pore_one_step_against_oracle():
     """At the benchmark size (64x64x128, N=32, FP32): run the GPU 30 steps,
     hand its state to the oracle, advance both one step and compare every
     node."""
-    wl = W.config_pore_fp32()
+    wl = W.config_pore_fp32().replace(poisson_fixed_iter=400)
     sim = E.Simulation(wl)
     assert sim.step(30) >= 0
     f, phi, st = sim.get_state()
