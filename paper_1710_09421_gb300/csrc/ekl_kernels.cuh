@@ -174,7 +174,11 @@ __global__ void __launch_bounds__(CHARGE_THREADS) charge_kernel(StepArgs<S, R, P
                 R n = R(0);
 #pragma unroll
                 for (int p = 0; p < Q; p++) n += v[p];
-                if (DEV) n = a.n_ref[s] + n;
+                // Deviation storage: sum_a z^a n^a = sum_a z^a n_ref^a + sum_a z^a dn^a.
+                // The first term is the same constant on every fluid node and
+                // cancels in the neutralising mean subtraction, so only the
+                // deviations enter (no cancellation between two close ion
+                // densities in reduced precision).
                 r += a.zv[s] * n;
             }
             rho = r + (a.src_wall ? a.src_wall[i] : R(0));
