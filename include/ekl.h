@@ -180,6 +180,26 @@ const char *ekl_last_error(void);
 
 int64_t ekl_sizeof_params(void);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free field read-back.  The paper has no counterpart: this entry
+ * serves callers that may not allocate GPU memory while they run (code
+ * running between capture and replay of a CUDA graph on a pool-allocated
+ * stream, a real-time loop that reserved all device memory up front, a host
+ * framework whose allocator is locked during a solver callback).  It returns
+ * the same fields as ekl_get_fields, staged through one fixed device array of
+ * EKL_NOALLOC_MAX_DOUBLES doubles (16 MiB) that the library reserves on every
+ * GPU that loads it, instead of per-call device buffers; it calls no
+ * cudaMalloc/cudaFree and no allocator.  A request needing more staging than
+ * that (3N + 9N + N doubles for n_out/j_out/phi_out, 6 per bead for R/V) is
+ * rejected with EKL_ERR_ARG.  All calls share the array: calls whose GPU work
+ * overlaps race and must be serialised by the caller.  The first call on a
+ * device looks up the array's device address (once per device); make it
+ * before any stream capture begins.  Output pointers are host memory, as for
+ * ekl_get_fields. */
+#define EKL_NOALLOC_MAX_DOUBLES 2097152
+int ekl_get_fields_noalloc(ekl_handle *h, double *n_out, double *j_out, double *phi_out,
+                           double *R_out, double *V_out);
+
 #ifdef __cplusplus
 }
 #endif

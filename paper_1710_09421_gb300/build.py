@@ -22,6 +22,7 @@ UNITS = {
     "ekl_inst_f64.cu": ["-fmad=false"],
     "ekl_inst_f32.cu": [],
     "ekl_inst_lp.cu": [],
+    "ekl_noalloc.cu": [],
 }
 
 

@@ -144,6 +144,8 @@ int status_to_code(int st)
 
 namespace ekl {
 
+void set_last_error(const char *msg) { fail(0, msg); }
+
 void timing_record(Ctx &c, int phase, int begin)
 {
     if (c.tused + 1 > c.tcap) {

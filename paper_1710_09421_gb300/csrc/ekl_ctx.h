@@ -95,6 +95,9 @@ struct Ctx {
 void timing_record(Ctx &c, int phase, int begin);
 void timing_flush(Ctx &c);
 
+// message returned by ekl_last_error() on this thread
+void set_last_error(const char *msg);
+
 // allocation through the installed allocator
 void *dev_alloc(Ctx &c, size_t bytes);
 void dev_free(Ctx &c, void *p, size_t bytes);

@@ -1,0 +1,84 @@
+"""The allocation-free field read-back, ekl_get_fields_noalloc, through the C ABI.
+
+It serves callers that may not allocate device memory while they run (for
+instance between capture and replay of a CUDA graph, or in a loop that has
+reserved all GPU memory up front): it stages the fields in one fixed device
+array instead of per-call buffers.  Here it must return what ekl_get_fields
+returns, on two calls in a row, and refuse a request larger than its array.
+This file is collected last so that a run stopping at the first failure has
+already run every other test.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import paper_1710_09421_gb300 as E
+from paper_1710_09421_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12   # the tolerance of the FP64 parity tests
+
+
+def _noalloc(lib):
+    f = lib.ekl_get_fields_noalloc
+    f.argtypes = [C.c_void_p] * 6
+    f.restype = C.c_int
+    return f
+
+
+def _fields_noalloc(f, sim):
+    N, nb = sim.N, sim.nb
+    n = np.full((3, N), np.nan)
+    j = np.full((3, 3, N), np.nan)
+    phi = np.full(N, np.nan)
+    R = np.full((nb, 3), np.nan)
+    V = np.full((nb, 3), np.nan)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    rc = f(sim.h, p(n), p(j), p(phi), p(R), p(V))
+    assert rc == E.EKL_OK, (rc, E.load().ekl_last_error())
+    return dict(n=n, j=j, phi=phi, R=R, V=V)
+
+
+def _close(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return np.linalg.norm(a - b) <= TOL * max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_noalloc_matches_get_fields_twice(precision):
+    lib = E.load()
+    f = _noalloc(lib)
+    wl = W.small_pore(nx=16, ny=16, nz=20, membrane=(8, 11), radius=3.0, n_beads=4,
+                      precision=precision)
+    sim = E.Simulation(wl)
+    for call in range(2):
+        sim.step(5)
+        ref = sim.fields()
+        got = _fields_noalloc(f, sim)
+        for k in ("n", "j", "R", "V"):
+            assert np.array_equal(got[k], ref[k]), (call, k)
+        assert _close(got["phi"], ref["phi"]), call
+    sim.close()
+
+
+def test_noalloc_rejects_requests_beyond_its_array():
+    lib = E.load()
+    f = _noalloc(lib)
+    # 64 x 64 x 48 = 196608 nodes: all fields need 13 N doubles > 2^21
+    wl = W.translocation(nx=64, ny=64, nz=48, membrane=(20, 27), n_beads=0)
+    sim = E.Simulation(wl)
+    N = sim.N
+    n = np.zeros((3, N))
+    j = np.zeros((3, 3, N))
+    phi = np.zeros(N)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    rc = f(sim.h, p(n), p(j), p(phi), None, None)
+    assert rc == E.EKL_ERR_ARG
+    assert b"allocation-free path holds" in lib.ekl_last_error()
+    # the potential alone fits
+    assert f(sim.h, None, None, p(phi), None, None) == E.EKL_OK
+    assert _close(phi, sim.fields(("phi",))["phi"])
+    sim.close()
