@@ -244,7 +244,7 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
         if (!(P->tau[s] > 0.5)) return fail(EKL_ERR_ARG, "tau must exceed 1/2");
     if (!(P->diffusivity[1] > 0.0)) return fail(EKL_ERR_ARG, "cation diffusivity must be positive");
     long long N = (long long)P->nx * P->ny * P->nz;
-    if (N > (1ll << 31) / 64) return fail(EKL_ERR_ARG, "lattice too large for 32-bit patch ids");
+    if (N > (1ll << 31) / 64) return fail(EKL_ERR_ARG, "lattice too large for 32-bit node ids");
 
     ekl_handle *h = new (std::nothrow) ekl_handle();
     if (!h) return fail(EKL_ERR_ALLOC, "host allocation failed");
@@ -345,7 +345,7 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
         delete h;
         return fail(EKL_ERR_CUDA, "Poisson kernel cannot be resident");
     }
-    c.pois_blocks = c.num_sms * (occ < 2 ? occ : 2);
+    c.pois_blocks = c.num_sms;  // one block of POIS_THREADS per SM
     bool okall = true;
     auto A = [&](size_t bytes) {
         void *p = dev_alloc(c, bytes);
@@ -362,8 +362,8 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
     c.rho = A(N * rs);
     c.b = A(N * ps);
     c.phi = A(N * ps);
-    c.part_charge = (double *)A(c.charge_blocks * sizeof(double));
-    c.part_mass = (double *)A((size_t)c.lb_blocks * NS * sizeof(double));
+    c.part_charge = (double *)A((size_t)c.charge_blocks * (CHARGE_THREADS / 32) * sizeof(double));
+    c.part_mass = (double *)A((size_t)c.lb_blocks * (LB_THREADS / 32) * NS * sizeof(double));
     c.part_pois = (double *)A((2 * (size_t)c.pois_blocks + 1) * sizeof(double));
     c.barrier = (unsigned *)A(4 * sizeof(unsigned));
     c.status = (int *)A(sizeof(int));
@@ -378,7 +378,7 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
     c.sorted_entry = (int *)A(MAX_ENTRIES * sizeof(int));
     c.slot_first = (int *)A((MAX_ENTRIES + 1) * sizeof(int));
     c.entry_w = A(MAX_ENTRIES * rs);
-    c.R = A(MAX_BEADS * 3 * rs);
+    c.R = A(MAX_BEADS * 3 * sizeof(double));  // bead positions are FP64 in every precision
     c.V = A(MAX_BEADS * 3 * rs);
     c.q = A(MAX_BEADS * rs);
     c.chain = (int *)A(MAX_BEADS * sizeof(int));
@@ -467,14 +467,12 @@ int ekl_set_beads(ekl_handle *h, int32_t n, const double *R, const double *V, co
         qd[k] = q[k];
         if (chain) ch[k] = chain[k];
     }
-    cudaError_t e;
+    cudaError_t e = cudaMemcpyAsync(c.R, Rd.data(), 3 * (size_t)n * 8, cudaMemcpyHostToDevice, c.stream);
     if (c.prec == EKL_F64) {
-        e = cudaMemcpyAsync(c.R, Rd.data(), 3 * (size_t)n * 8, cudaMemcpyHostToDevice, c.stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(c.V, Vd.data(), 3 * (size_t)n * 8, cudaMemcpyHostToDevice, c.stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(c.q, qd.data(), (size_t)n * 8, cudaMemcpyHostToDevice, c.stream);
     } else {
-        std::vector<float> Rf(Rd.begin(), Rd.end()), Vf(Vd.begin(), Vd.end()), qf(qd.begin(), qd.end());
-        e = cudaMemcpyAsync(c.R, Rf.data(), 3 * (size_t)n * 4, cudaMemcpyHostToDevice, c.stream);
+        std::vector<float> Vf(Vd.begin(), Vd.end()), qf(qd.begin(), qd.end());
         if (e == cudaSuccess) e = cudaMemcpyAsync(c.V, Vf.data(), 3 * (size_t)n * 4, cudaMemcpyHostToDevice, c.stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(c.q, qf.data(), (size_t)n * 4, cudaMemcpyHostToDevice, c.stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
@@ -534,21 +532,15 @@ int ekl_get_fields(ekl_handle *h, double *n_out, double *j_out, double *phi_out,
         if (e == cudaSuccess && dj) e = cudaMemcpyAsync(j_out, dj, (size_t)NS * 3 * N * 8, cudaMemcpyDeviceToHost, c.stream);
         if (e == cudaSuccess && dp) e = cudaMemcpyAsync(phi_out, dp, (size_t)N * 8, cudaMemcpyDeviceToHost, c.stream);
         if (c.nb > 0 && e == cudaSuccess && (R_out || V_out)) {
-            size_t bytes = 3 * (size_t)c.nb * real_size(c.prec);
-            std::vector<char> r(bytes), v(bytes);
-            e = cudaMemcpyAsync(r.data(), c.R, bytes, cudaMemcpyDeviceToHost, c.stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(v.data(), c.V, bytes, cudaMemcpyDeviceToHost, c.stream);
+            size_t vbytes = 3 * (size_t)c.nb * real_size(c.prec);
+            std::vector<double> r(3 * (size_t)c.nb);
+            std::vector<char> v(vbytes);
+            e = cudaMemcpyAsync(r.data(), c.R, 3 * (size_t)c.nb * 8, cudaMemcpyDeviceToHost, c.stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(v.data(), c.V, vbytes, cudaMemcpyDeviceToHost, c.stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
             for (int k = 0; k < 3 * c.nb && e == cudaSuccess; k++) {
-                double rv, vv;
-                if (c.prec == EKL_F64) {
-                    rv = ((double *)r.data())[k];
-                    vv = ((double *)v.data())[k];
-                } else {
-                    rv = ((float *)r.data())[k];
-                    vv = ((float *)v.data())[k];
-                }
-                if (R_out) R_out[k] = rv;
+                double vv = c.prec == EKL_F64 ? ((double *)v.data())[k] : (double)((float *)v.data())[k];
+                if (R_out) R_out[k] = r[k];
                 if (V_out) V_out[k] = vv;
             }
         }
@@ -627,7 +619,8 @@ int ekl_get_stats(ekl_handle *h, ekl_stats *out)
 {
     if (!h || !out) return fail(EKL_ERR_ARG, "null argument");
     Ctx &c = h->c;
-    std::vector<double> pm((size_t)c.lb_blocks * NS);
+    const size_t nwarps = (size_t)c.lb_blocks * (LB_THREADS / 32);
+    std::vector<double> pm(nwarps * NS);
     int it = 0;
     double res = 0;
     cudaError_t e = cudaMemcpyAsync(pm.data(), c.part_mass, pm.size() * 8, cudaMemcpyDeviceToHost, c.stream);
@@ -639,7 +632,7 @@ int ekl_get_stats(ekl_handle *h, ekl_stats *out)
     memset(out, 0, sizeof(*out));
     for (int s = 0; s < NS; s++) {
         double t = 0;
-        for (int b = 0; b < c.lb_blocks; b++) t += pm[(size_t)b * NS + s];
+        for (size_t b = 0; b < nwarps; b++) t += pm[b * NS + s];
         out->mass[s] = t;
     }
     out->step = c.step;

@@ -174,41 +174,40 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
     return t;
 }
 
-// Grid-wide barrier of a cooperative launch with a bounded wait: a block that
-// waits more than ~2 s raises ST_TIMEOUT and the abort word; every waiter
-// also leaves as soon as the abort word is set.  Returns false on abort.
-// bar[0] = arrival count, bar[1] = generation, bar[2] = abort.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, int *status)
+// Grid-wide barrier of a cooperative launch with a bounded wait.  bar[0]
+// counts arrivals monotonically within a launch (reset by the host before
+// the launch); barrier number k (k = 1, 2, ...) is passed when the count
+// reaches k * nblocks.  A block that waits more than ~2 s raises ST_TIMEOUT
+// and the abort word bar[2]; every waiter also leaves as soon as the abort
+// word is set.  Returns false on abort.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, unsigned &k, int *status)
 {
     __shared__ int ok_s;
     __syncthreads();
+    k++;
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned gen = ld_acquire(&bar[1]);
+        const unsigned target = k * nblocks;
         __threadfence();
-        unsigned arrived = atomicAdd(&bar[0], 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&bar[0], 0u);
-            __threadfence();
-            atomicAdd(&bar[1], 1u);
-        } else {
-            uint64_t t0 = globaltimer_ns();
-            unsigned spins = 0;
-            while (ld_acquire(&bar[1]) == gen) {
-                if (ld_acquire(&bar[2])) {
-                    ok = 0;
-                    break;
-                }
-                if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > 2000000000ull) {
+        atomicAdd(&bar[0], 1u);
+        uint64_t t0 = 0;
+        unsigned spins = 0;
+        while ((int)(ld_acquire(&bar[0]) - target) < 0) {
+            if (ld_acquire(&bar[2])) {
+                ok = 0;
+                break;
+            }
+            if ((++spins & 255u) == 0) {
+                uint64_t t = globaltimer_ns();
+                if (t0 == 0) t0 = t;
+                else if (t - t0 > 2000000000ull) {
                     atomicOr(status, ST_TIMEOUT);
                     atomicExch(&bar[2], 1u);
                     ok = 0;
                     break;
                 }
-                __nanosleep(20);
             }
         }
-        if (ld_acquire(&bar[2])) ok = 0;
         __threadfence();
         ok_s = ok;
     }

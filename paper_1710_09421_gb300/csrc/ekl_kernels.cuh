@@ -147,33 +147,25 @@ __global__ void init_kernel(Grid3 g, const uint32_t *__restrict__ mask,
 template <typename S, typename R, typename PhiT, bool DEV>
 __global__ void __launch_bounds__(CHARGE_THREADS) charge_kernel(StepArgs<S, R, PhiT> a)
 {
-    __shared__ double sh[CHARGE_THREADS / 32];
-    __shared__ int plo, phi_;
     const Grid3 g = a.g;
-    long long i0 = blockIdx.x * (long long)blockDim.x;
-    long long i = i0 + threadIdx.x;
-    if (threadIdx.x == 0) {
-        int pc = *a.patch_count;
-        plo = lower_bound_i(a.patch_node, pc, i0);
-        phi_ = lower_bound_i(a.patch_node, pc, i0 + blockDim.x);
-    }
-    __syncthreads();
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double mine = 0.0;
     if (i < g.N) {
-        uint32_t m = a.mask[i];
+        const uint32_t m = a.mask[i];
         R rho = R(0);
         if (!(m & SOLID_BIT)) {
             int x, y, z;
             coords_of(g, i, x, y, z);
             Nbr nb = make_nbr(g, x, y, z);
+            R v[2][Q];
+            pull19<S, R>(a.fin, g.N, 1, i, m, nb, v[0]);
+            pull19<S, R>(a.fin, g.N, 2, i, m, nb, v[1]);
             R r = R(0);
             r += a.zv[0] * R(0);  // solvent carries no charge
             for (int s = 1; s < NS; s++) {
-                R v[Q];
-                pull19<S, R>(a.fin, g.N, s, i, m, nb, v);
                 R n = R(0);
 #pragma unroll
-                for (int p = 0; p < Q; p++) n += v[p];
+                for (int p = 0; p < Q; p++) n += v[s - 1][p];
                 // Deviation storage: sum_a z^a n^a = sum_a z^a n_ref^a + sum_a z^a dn^a.
                 // The first term is the same constant on every fluid node and
                 // cancels in the neutralising mean subtraction, so only the
@@ -182,14 +174,18 @@ __global__ void __launch_bounds__(CHARGE_THREADS) charge_kernel(StepArgs<S, R, P
                 r += a.zv[s] * n;
             }
             rho = r + (a.src_wall ? a.src_wall[i] : R(0));
-            for (int k = plo; k < phi_; k++)
-                if (a.patch_node[k] == i) rho = rho + a.patch_q[k];
+            const int pc = *a.patch_count;
+            if (pc > 0) {
+                int k = lower_bound_i(a.patch_node, pc, i);
+                if (k < pc && a.patch_node[k] == i) rho = rho + a.patch_q[k];
+            }
             mine = (double)rho;
         }
         a.rho[i] = rho;
     }
-    double t = block_sum(mine, sh);
-    if (threadIdx.x == 0) a.part_charge[blockIdx.x] = t;
+    // one FP64 partial per warp (fixed shuffle tree), no block barrier
+    double t = warp_sum(mine);
+    if ((threadIdx.x & 31) == 0) a.part_charge[i >> 5] = t;
 }
 
 // ============================================================== Poisson
@@ -226,15 +222,48 @@ template <> struct PoisUpd<long long> {
     }
 };
 
+// One half sweep over the nodes of `colour` owned by this thread, with the
+// node's link word, source and own potential supplied by the caller.
+template <typename PhiT>
+__device__ __forceinline__ void sor_node(const Grid3 &g, PhiT *phi, int x, int y, int z, int i,
+                                         uint32_t m, PhiT bi, PhiT &pi, double omega,
+                                         typename PoisUpd<PhiT>::acc_t &r2)
+{
+    const int nx = g.nx, nxy = g.nx * g.ny;
+    const int xm = x == 0 ? i + nx - 1 : i - 1, xp = x == nx - 1 ? i - nx + 1 : i + 1;
+    const int ym = y == 0 ? i + nxy - nx : i - nx, yp = y == g.ny - 1 ? i - nxy + nx : i + nx;
+    const int zm = z == 0 ? i + (int)g.N - nxy : i - nxy, zp = z == g.nz - 1 ? i - (int)g.N + nxy : i + nxy;
+    const int nbr[6] = {xm, xp, ym, yp, zm, zp};
+    PhiT v[6];
+#pragma unroll
+    for (int f = 0; f < 6; f++) v[f] = ((m >> (f + 1)) & 1u) ? (PhiT)0 : __ldcg(phi + nbr[f]);
+    PhiT acc = bi;
+    int deg = 0;
+#pragma unroll
+    for (int f = 0; f < 6; f++)
+        if (!((m >> (f + 1)) & 1u)) {
+            acc += v[f];
+            deg++;
+        }
+    if (deg == 0) return;
+    PhiT r = PoisUpd<PhiT>::resid(acc, deg, pi);
+    pi = PoisUpd<PhiT>::apply(pi, omega, r, deg);
+    __stcg(phi + i, pi);
+    r2 += PoisUpd<PhiT>::r2(r);
+}
+
+constexpr int POIS_KMAX = 2;  // nodes per colour a thread keeps in registers
+
 template <typename S, typename R, typename PhiT>
-__global__ void __launch_bounds__(POIS_THREADS) poisson_kernel(StepArgs<S, R, PhiT> a)
+__global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R, PhiT> a)
 {
     __shared__ double sh[POIS_THREADS / 32];
+    __shared__ double bc[1];
     const Grid3 g = a.g;
     const unsigned nblk = gridDim.x;
-    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long nthr = (long long)nblk * blockDim.x;
-    __shared__ double bc[1];
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthr = nblk * blockDim.x;
+    unsigned bar_k = 0;
     // --- source: subtract the mean charge over fluid nodes (neutralisation)
     const double csum = sum_partials(a.part_charge, a.nblocks_charge, bc);
     // number of fluid nodes is carried in part_pois[2*nblk] by the host
@@ -260,7 +289,7 @@ __global__ void __launch_bounds__(POIS_THREADS) poisson_kernel(StepArgs<S, R, Ph
     }
     double t = block_sum(bl, sh);
     if (threadIdx.x == 0) a.part_pois[blockIdx.x] = t;
-    if (!grid_barrier(a.barrier, nblk, a.status)) return;
+    if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return;
     const double bn2 = sum_partials(a.part_pois, (int)nblk, bc);
     const double bnorm = sqrt(bn2);
     const int limit = a.fixed_iter > 0 ? a.fixed_iter : a.max_iter;
@@ -272,39 +301,61 @@ __global__ void __launch_bounds__(POIS_THREADS) poisson_kernel(StepArgs<S, R, Ph
         return;
     }
     const double rJ = a.rJ;
-    double omega = 1.0;
     const int hx = (g.nx + 1) >> 1;
-    const long long nhalf = (long long)hx * g.ny * g.nz;
+    const int nhalf = hx * g.ny * g.nz;
+    // register cache of this thread's nodes (both colours) when they fit
+    const bool cached = (nhalf + nthr - 1) / nthr <= POIS_KMAX;
+    int cx[2][POIS_KMAX], cy[2][POIS_KMAX], cz[2][POIS_KMAX], ci[2][POIS_KMAX];
+    uint32_t cm[2][POIS_KMAX];
+    PhiT cb[2][POIS_KMAX], cp[2][POIS_KMAX];
+    if (cached) {
+#pragma unroll
+        for (int colour = 0; colour < 2; colour++)
+#pragma unroll
+            for (int k = 0; k < POIS_KMAX; k++) {
+                const int h = tid + k * nthr;
+                ci[colour][k] = -1;
+                cm[colour][k] = SOLID_BIT;
+                if (h >= nhalf) continue;
+                const int row = h / hx, xh = h - row * hx;
+                const int z = row / g.ny, y = row - z * g.ny;
+                const int x = 2 * xh + ((colour + y + z) & 1);
+                if (x >= g.nx) continue;
+                const int i = x + g.nx * row;
+                cx[colour][k] = x;
+                cy[colour][k] = y;
+                cz[colour][k] = z;
+                ci[colour][k] = i;
+                cm[colour][k] = a.mask[i];
+                cb[colour][k] = __ldcg(a.b + i);
+                cp[colour][k] = __ldcg(a.phi + i);
+            }
+    }
+    double omega = 1.0;
     int it = 0, converged = 0;
     double r2tot = 0.0;
     for (it = 0; it < limit; it++) {
         typename PoisUpd<PhiT>::acc_t r2 = 0;
         for (int colour = 0; colour < 2; colour++) {
-            for (long long h = tid; h < nhalf; h += nthr) {
-                long long row = h / hx;
-                int xh = (int)(h - row * hx);
-                int z = (int)(row / g.ny);
-                int y = (int)(row - (long long)z * g.ny);
-                int x = 2 * xh + ((colour + y + z) & 1);
-                if (x >= g.nx) continue;
-                long long i = (long long)x + (long long)g.nx * row;
-                uint32_t m = a.mask[i];
-                if (m & SOLID_BIT) continue;
-                Nbr nb = make_nbr(g, x, y, z);
-                PhiT acc = __ldcg(a.b + i);
-                int deg = 0;
+            if (cached) {
 #pragma unroll
-                for (int f = 0; f < 6; f++) {
-                    if (!((m >> (f + 1)) & 1u)) {
-                        acc += __ldcg(a.phi + face_idx(nb, f));
-                        deg++;
-                    }
+                for (int k = 0; k < POIS_KMAX; k++) {
+                    if (cm[colour][k] & SOLID_BIT) continue;
+                    sor_node<PhiT>(g, a.phi, cx[colour][k], cy[colour][k], cz[colour][k], ci[colour][k],
+                                   cm[colour][k], cb[colour][k], cp[colour][k], omega, r2);
                 }
-                if (deg == 0) continue;
-                PhiT pi = __ldcg(a.phi + i);
-                PhiT r = PoisUpd<PhiT>::resid(acc, deg, pi);
-                __stcg(a.phi + i, PoisUpd<PhiT>::apply(pi, omega, r, deg));
-                r2 += PoisUpd<PhiT>::r2(r);
+            } else {
+                for (int h = tid; h < nhalf; h += nthr) {
+                    const int row = h / hx, xh = h - row * hx;
+                    const int z = row / g.ny, y = row - z * g.ny;
+                    const int x = 2 * xh + ((colour + y + z) & 1);
+                    if (x >= g.nx) continue;
+                    const int i = x + g.nx * row;
+                    const uint32_t m = a.mask[i];
+                    if (m & SOLID_BIT) continue;
+                    PhiT pi = __ldcg(a.phi + i);
+                    sor_node<PhiT>(g, a.phi, x, y, z, i, m, __ldcg(a.b + i), pi, omega, r2);
+                }
             }
             if (it == 0 && colour == 0) omega = 1.0 / (1.0 - 0.5 * rJ * rJ);
             else omega = 1.0 / (1.0 - 0.25 * rJ * rJ * omega);
@@ -312,7 +363,7 @@ __global__ void __launch_bounds__(POIS_THREADS) poisson_kernel(StepArgs<S, R, Ph
                 double tb = block_sum((double)r2, sh);
                 if (threadIdx.x == 0) a.part_pois[blockIdx.x] = tb;
             }
-            if (!grid_barrier(a.barrier, nblk, a.status)) return;
+            if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return;
         }
         const bool test = a.fixed_iter <= 0 && ((it + 1) % a.check_every) == 0;
         if (test || it + 1 == limit) r2tot = sum_partials(a.part_pois, (int)nblk, bc);
@@ -330,12 +381,16 @@ __global__ void __launch_bounds__(POIS_THREADS) poisson_kernel(StepArgs<S, R, Ph
 }
 
 // ============================================================== beads
+// Bead positions are FP64 in every precision: a float position near x = 64
+// has an ulp of 7.6e-6, too coarse for sub-step displacements of ~1e-4.
+// Velocities, forces and the drag use the arithmetic type R.
 template <typename R> struct BeadArgs {
     Grid3 g;
     int per[3];
     const uint32_t *__restrict__ mask;
     int nb;
-    R *Rb, *Vb;
+    double *Rb;
+    R *Vb;
     const R *qb;
     const int *chain;
     int *patch_count;
@@ -354,18 +409,18 @@ template <typename R> struct BeadArgs {
 // and the rest renormalised (the interpolation kernel of Sec. II.C).
 // Slot order k = ox + 2 oy + 4 oz.  Returns false when all 8 are wall.
 template <typename R>
-__device__ bool bead_stencil(const Grid3 &g, const int per[3], const uint32_t *mask, const R Rb[3],
+__device__ bool bead_stencil(const Grid3 &g, const int per[3], const uint32_t *mask, const double Rb[3],
                              long long nodes[8], R w[8])
 {
     int base[3];
     R fr[3];
     int dims[3] = {g.nx, g.ny, g.nz};
     for (int c = 0; c < 3; c++)
-        if (!(fabs(Rb[c]) < R(1e6))) return false;  // non-finite or absurd position
+        if (!(fabs(Rb[c]) < 1e6)) return false;  // non-finite or absurd position
     for (int c = 0; c < 3; c++) {
-        R fl = floor(Rb[c]);
+        double fl = floor(Rb[c]);
         base[c] = (int)fl;
-        fr[c] = Rb[c] - fl;
+        fr[c] = (R)(Rb[c] - fl);
     }
     R W = R(0);
     for (int k = 0; k < 8; k++) {
@@ -407,7 +462,7 @@ template <typename R> __global__ void __launch_bounds__(BEAD_THREADS) bead_bin_k
     int npow = 1;
     while (npow < ne) npow <<= 1;
     for (int b = threadIdx.x; b < a.nb; b += blockDim.x) {
-        R Rb[3] = {a.Rb[3 * b], a.Rb[3 * b + 1], a.Rb[3 * b + 2]};
+        double Rb[3] = {a.Rb[3 * b], a.Rb[3 * b + 1], a.Rb[3 * b + 2]};
         long long nd[8];
         R w[8];
         bool ok = bead_stencil<R>(a.g, a.per, a.mask, Rb, nd, w);
@@ -484,7 +539,7 @@ template <typename R> __global__ void __launch_bounds__(BEAD_THREADS) bead_bin_k
 }
 
 template <typename R>
-__device__ void wca_add(R eps, R sig, const R d[3], R F[3])
+__device__ __forceinline__ void wca_add(R eps, R sig, const R d[3], R F[3])
 {
     R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     // 2^(1/3) sigma^2 is the squared WCA cut-off
@@ -496,11 +551,21 @@ __device__ void wca_add(R eps, R sig, const R d[3], R F[3])
     for (int c = 0; c < 3; c++) F[c] += mag * d[c];
 }
 
-template <typename R> __device__ void min_image(const Grid3 &g, const int per[3], R d[3])
+// separation Rb - Rc in FP64 with the minimum image on periodic axes
+// (|d| < L because positions are kept in [0, L) on periodic axes)
+template <typename R>
+__device__ __forceinline__ void separation(const Grid3 &g, const int per[3], const double *Rb,
+                                           const double *Rc, R d[3])
 {
-    R L[3] = {(R)g.nx, (R)g.ny, (R)g.nz};
-    for (int c = 0; c < 3; c++)
-        if (per[c]) d[c] -= L[c] * rint(d[c] / L[c]);
+    const double L[3] = {(double)g.nx, (double)g.ny, (double)g.nz};
+    for (int c = 0; c < 3; c++) {
+        double v = Rb[c] - Rc[c];
+        if (per[c]) {
+            if (v > 0.5 * L[c]) v -= L[c];
+            else if (v < -0.5 * L[c]) v += L[c];
+        }
+        d[c] = (R)v;
+    }
 }
 
 template <typename S, typename R, typename PhiT, bool DEV> struct MdArgs {
@@ -514,53 +579,84 @@ template <typename S, typename R, typename PhiT, bool DEV> struct MdArgs {
     long long step;
 };
 
-// Conservative force on bead b: bond with b-1 and b+1 (Eq. 9c, FENE option),
-// WCA against every other bead except bonded neighbours when the bond is
-// harmonic (Eq. 9a), WCA against wall nodes within the cut-off.
 // Solid flags of a WALL_BOX^3 block of nodes around each bead, cached in
 // shared memory for the sub-steps (bit (z*WALL_BOX + y)*WALL_BOX + x of the
 // bead's words, origin org).
 constexpr int WALL_BOX = 6;
 constexpr int WALL_WORDS = (WALL_BOX * WALL_BOX * WALL_BOX + 31) / 32;
 
+__device__ __forceinline__ bool wall_solid(const Grid3 &g, const int per[3], const uint32_t *mask,
+                                           int x, int y, int z, const int *org, const uint32_t *bits,
+                                           bool &in)
+{
+    int q[3] = {x, y, z};
+    const int dims[3] = {g.nx, g.ny, g.nz};
+    in = true;
+    for (int c = 0; c < 3; c++) {
+        if (per[c]) {
+            q[c] %= dims[c];
+            if (q[c] < 0) q[c] += dims[c];
+        } else if (q[c] < 0 || q[c] >= dims[c]) {
+            in = false;
+        }
+    }
+    if (!in) return false;
+    int ox = x - org[0], oy = y - org[1], oz = z - org[2];
+    if (ox >= 0 && ox < WALL_BOX && oy >= 0 && oy < WALL_BOX && oz >= 0 && oz < WALL_BOX) {
+        int bit = (oz * WALL_BOX + oy) * WALL_BOX + ox;
+        return (bits[bit >> 5] >> (bit & 31)) & 1u;
+    }
+    long long id = (long long)q[0] + (long long)g.nx * (q[1] + (long long)g.ny * q[2]);
+    return mask[id] & SOLID_BIT;
+}
+
+// bond force on bead b from the pair (lo, lo+1); side 0: b = lo+1, side 1: b = lo
 template <typename S, typename R, typename PhiT, bool DEV>
-__device__ bool bead_force(const MdArgs<S, R, PhiT, DEV> &A, const R *Rs, int b, R F[3],
-                           const int *org, const uint32_t *bits)
+__device__ __forceinline__ bool bond_add(const MdArgs<S, R, PhiT, DEV> &A, const double *Rs, int b,
+                                         int side, R F[3])
+{
+    const int lo = side == 0 ? b - 1 : b;
+    if (lo < 0 || lo + 1 >= A.b.nb || A.b.chain[lo] != A.b.chain[lo + 1]) return true;
+    R d[3];
+    separation<R>(A.b.g, A.b.per, &Rs[3 * lo], &Rs[3 * (lo + 1)], d);
+    R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    R fac;
+    bool ok = true;
+    if (A.bond_kind == EKL_BOND_FENE) {
+        R x = r2 / (A.bond_r0 * A.bond_r0);
+        if (!(x < R(1))) ok = false;
+        fac = -A.bond_k / (R(1) - x);
+    } else {
+        R r = sqrt(r2);
+        fac = -A.bond_k * (r - A.bond_l0) / r;
+    }
+    for (int c = 0; c < 3; c++) {
+        if (side == 0) F[c] -= fac * d[c];
+        else F[c] += fac * d[c];
+    }
+    return ok;
+}
+
+// Conservative force on bead b, summed serially in the oracle's order: bond
+// with b-1, bond with b+1 (Eq. 9c, FENE option), WCA with every other bead in
+// index order except bonded neighbours when the bond is harmonic (Eq. 9a),
+// WCA against wall nodes in z, y, x order.
+template <typename S, typename R, typename PhiT, bool DEV>
+__device__ bool bead_force_serial(const MdArgs<S, R, PhiT, DEV> &A, const double *Rs, int b, R F[3],
+                                  const int *org, const uint32_t *bits)
 {
     const Grid3 &g = A.b.g;
     const int nb = A.b.nb;
     F[0] = F[1] = F[2] = R(0);
-    bool ok = true;
-    for (int side = 0; side < 2; side++) {
-        int lo = side == 0 ? b - 1 : b;  // pair (lo, lo+1)
-        if (lo < 0 || lo + 1 >= nb) continue;
-        if (A.b.chain[lo] != A.b.chain[lo + 1]) continue;
-        R d[3];
-        for (int c = 0; c < 3; c++) d[c] = Rs[3 * lo + c] - Rs[3 * (lo + 1) + c];
-        min_image<R>(g, A.b.per, d);
-        R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        R fac;
-        if (A.bond_kind == EKL_BOND_FENE) {
-            R x = r2 / (A.bond_r0 * A.bond_r0);
-            if (!(x < R(1))) ok = false;
-            fac = -A.bond_k / (R(1) - x);
-        } else {
-            R r = sqrt(r2);
-            fac = -A.bond_k * (r - A.bond_l0) / r;
-        }
-        for (int c = 0; c < 3; c++) {
-            if (side == 0) F[c] -= fac * d[c];  // b is the second bead of the pair
-            else F[c] += fac * d[c];
-        }
-    }
+    bool ok = bond_add(A, Rs, b, 0, F);
+    ok = bond_add(A, Rs, b, 1, F) && ok;
     for (int c2 = 0; c2 < nb; c2++) {
         if (c2 == b) continue;
         int lo = c2 < b ? c2 : b, hi = c2 < b ? b : c2;
         if (A.bond_kind == EKL_BOND_HARMONIC && A.b.chain[lo] == A.b.chain[hi] && hi - lo <= 1)
             continue;
         R d[3];
-        for (int c = 0; c < 3; c++) d[c] = Rs[3 * lo + c] - Rs[3 * hi + c];
-        min_image<R>(g, A.b.per, d);
+        separation<R>(g, A.b.per, &Rs[3 * lo], &Rs[3 * hi], d);
         R Fp[3] = {R(0), R(0), R(0)};
         wca_add<R>(A.wca_eps, A.wca_sigma, d, Fp);
         for (int c = 0; c < 3; c++) {
@@ -568,43 +664,93 @@ __device__ bool bead_force(const MdArgs<S, R, PhiT, DEV> &A, const R *Rs, int b,
             else F[c] += Fp[c];
         }
     }
-    const R rc = (R)1.122462048309373 * A.wall_sigma;  // 2^(1/6) sigma
+    const double rc = 1.122462048309373 * (double)A.wall_sigma;  // 2^(1/6) sigma
     for (int c = 0; c < 3; c++)
-        if (!(fabs(Rs[3 * b + c]) < R(1e6)) || !(rc < R(16))) return false;  // keeps the wall scan bounded
+        if (!(fabs(Rs[3 * b + c]) < 1e6) || !(rc < 16.0)) return false;  // keeps the scan bounded
     int lo[3], hi[3];
     for (int c = 0; c < 3; c++) {
         lo[c] = (int)floor(Rs[3 * b + c] - rc);
         hi[c] = (int)floor(Rs[3 * b + c] + rc) + 1;
     }
-    int dims[3] = {g.nx, g.ny, g.nz};
     for (int z = lo[2]; z <= hi[2]; z++)
         for (int y = lo[1]; y <= hi[1]; y++)
             for (int x = lo[0]; x <= hi[0]; x++) {
-                int q[3] = {x, y, z};
-                bool in = true;
-                for (int c = 0; c < 3; c++) {
-                    if (A.b.per[c]) {
-                        q[c] %= dims[c];
-                        if (q[c] < 0) q[c] += dims[c];
-                    } else if (q[c] < 0 || q[c] >= dims[c]) {
-                        in = false;
-                    }
-                }
-                if (!in) continue;
-                int ox = x - org[0], oy = y - org[1], oz = z - org[2];
-                bool solid;
-                if (ox >= 0 && ox < WALL_BOX && oy >= 0 && oy < WALL_BOX && oz >= 0 && oz < WALL_BOX) {
-                    int bit = (oz * WALL_BOX + oy) * WALL_BOX + ox;
-                    solid = (bits[bit >> 5] >> (bit & 31)) & 1u;
-                } else {
-                    long long id = (long long)q[0] + (long long)g.nx * (q[1] + (long long)g.ny * q[2]);
-                    solid = A.b.mask[id] & SOLID_BIT;
-                }
-                if (!solid) continue;
-                R d[3] = {Rs[3 * b] - (R)x, Rs[3 * b + 1] - (R)y, Rs[3 * b + 2] - (R)z};
+                bool in;
+                if (!wall_solid(g, A.b.per, A.b.mask, x, y, z, org, bits, in)) continue;
+                R d[3] = {(R)(Rs[3 * b] - x), (R)(Rs[3 * b + 1] - y), (R)(Rs[3 * b + 2] - z)};
                 wca_add<R>(A.wall_eps, A.wall_sigma, d, F);
             }
     return ok;
+}
+
+// Same forces with the 32 lanes of a warp sharing the partner and wall loops
+// (reduced-precision paths); the result is reduced with a fixed xor tree and
+// is valid in every lane.
+template <typename S, typename R, typename PhiT, bool DEV>
+__device__ bool bead_force_warp(const MdArgs<S, R, PhiT, DEV> &A, const double *Rs, const float *Rf,
+                                int b, R F[3], const int *org, const uint32_t *bits)
+{
+    const Grid3 &g = A.b.g;
+    const int nb = A.b.nb;
+    const int lane = threadIdx.x & 31;
+    R f[3] = {R(0), R(0), R(0)};
+    bool ok = true;
+    if (lane == 0) {
+        ok = bond_add(A, Rs, b, 0, f);
+        ok = bond_add(A, Rs, b, 1, f) && ok;
+    }
+    const float Lf[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
+    const float cut2 = 1.2599210498948732f * (float)A.wca_sigma * (float)A.wca_sigma;
+    for (int c2 = lane; c2 < nb; c2 += 32) {
+        if (c2 == b) continue;
+        int lo = c2 < b ? c2 : b, hi = c2 < b ? b : c2;
+        if (A.bond_kind == EKL_BOND_HARMONIC && A.b.chain[lo] == A.b.chain[hi] && hi - lo <= 1)
+            continue;
+        // float screen, FP64 separation only for pairs near the cut-off
+        float q2 = 0.f;
+        for (int c = 0; c < 3; c++) {
+            float v = Rf[3 * b + c] - Rf[3 * c2 + c];
+            if (A.b.per[c]) {
+                if (v > 0.5f * Lf[c]) v -= Lf[c];
+                else if (v < -0.5f * Lf[c]) v += Lf[c];
+            }
+            q2 += v * v;
+        }
+        if (q2 > 1.1f * cut2 + 0.01f) continue;
+        R d[3];
+        separation<R>(g, A.b.per, &Rs[3 * lo], &Rs[3 * hi], d);
+        R Fp[3] = {R(0), R(0), R(0)};
+        wca_add<R>(A.wca_eps, A.wca_sigma, d, Fp);
+        for (int c = 0; c < 3; c++) {
+            if (c2 < b) f[c] -= Fp[c];
+            else f[c] += Fp[c];
+        }
+    }
+    const double rc = 1.122462048309373 * (double)A.wall_sigma;
+    bool pos_ok = rc < 16.0;
+    for (int c = 0; c < 3; c++) pos_ok = pos_ok && fabs(Rs[3 * b + c]) < 1e6;
+    if (pos_ok) {
+        int lo[3], n[3];
+        for (int c = 0; c < 3; c++) {
+            lo[c] = (int)floor(Rs[3 * b + c] - rc);
+            n[c] = (int)floor(Rs[3 * b + c] + rc) + 2 - lo[c];
+        }
+        const int cells = n[0] * n[1] * n[2];
+        for (int t = lane; t < cells; t += 32) {
+            int x = lo[0] + t % n[0], y = lo[1] + (t / n[0]) % n[1], z = lo[2] + t / (n[0] * n[1]);
+            bool in;
+            if (!wall_solid(g, A.b.per, A.b.mask, x, y, z, org, bits, in)) continue;
+            R d[3] = {(R)(Rs[3 * b] - x), (R)(Rs[3 * b + 1] - y), (R)(Rs[3 * b + 2] - z)};
+            wca_add<R>(A.wall_eps, A.wall_sigma, d, f);
+        }
+    } else {
+        ok = false;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        for (int c = 0; c < 3; c++) f[c] += __shfl_xor_sync(0xffffffffu, f[c], o);
+    for (int c = 0; c < 3; c++) F[c] = f[c];
+    return __all_sync(0xffffffffu, ok);
 }
 
 // One block: moments and field at the patch nodes, interpolation to beads,
@@ -612,15 +758,40 @@ __device__ bool bead_force(const MdArgs<S, R, PhiT, DEV> &A, const R *Rs, int b,
 // sub-step-averaged drag g^a_i = -gamma^a (u^a(R_i) - V_i) as a force per
 // particle on the patch nodes.  Readings as in the oracle: gamma^a = xi n^a/n
 // (or xi), fluid/field held at R(t) over the sub-steps, R(t) weights both ways.
-template <typename S, typename R, typename PhiT, bool DEV>
-__global__ void __launch_bounds__(BEAD_THREADS) bead_md_kernel(MdArgs<S, R, PhiT, DEV> A)
+// FP64 instantiation: one thread per bead, serial sums in the oracle's order.
+// Reduced-precision instantiations: one warp per bead.
+template <typename R> inline size_t md_smem_bytes(int nb)
 {
+    return (size_t)nb * (3 * sizeof(double) + 27 * sizeof(R) + 3 * sizeof(float) + 3 * sizeof(int) +
+                         WALL_WORDS * sizeof(uint32_t));
+}
+
+template <typename R> struct MdThreads {
+    static constexpr int value = sizeof(R) == 8 ? BEAD_THREADS : 1024;
+};
+
+template <typename S, typename R, typename PhiT, bool DEV>
+__global__ void __launch_bounds__(MdThreads<R>::value) bead_md_kernel(MdArgs<S, R, PhiT, DEV> A)
+{
+    constexpr bool SERIAL = sizeof(R) == 8;
     const StepArgs<S, R, PhiT> &a = A.s;
     const BeadArgs<R> &B = A.b;
     const Grid3 g = a.g;
     const int nb = B.nb;
     const int pc = *B.patch_count;
-    __shared__ R Rs[3 * MAX_BEADS];
+    // dynamic shared memory, sized for nb beads (md_smem_bytes)
+    extern __shared__ __align__(16) unsigned char md_smem[];
+    double *Rs = (double *)md_smem;
+    R *sV = (R *)(Rs + 3 * nb);
+    R *sU = sV + 3 * nb;
+    R *sG = sU + 9 * nb;
+    R *sGam = sG + 3 * nb;
+    R *sAcc = sGam + 3 * nb;
+    float *Rf = (float *)(sAcc + 9 * nb);
+    int *worg = (int *)(Rf + 3 * nb);
+    uint32_t *wbits = (uint32_t *)(worg + 3 * nb);
+    __shared__ int sBad;
+    if (threadIdx.x == 0) sBad = 0;
     // moments at the patch nodes
     for (int k = threadIdx.x; k < pc; k += blockDim.x) {
         long long i = B.patch_node[k];
@@ -657,14 +828,17 @@ __global__ void __launch_bounds__(BEAD_THREADS) bead_md_kernel(MdArgs<S, R, PhiT
         out[13] = gr[1];
         out[14] = gr[2];
     }
-    for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) Rs[t] = B.Rb[t];
-    __shared__ int worg[3 * MAX_BEADS];
-    __shared__ uint32_t wbits[WALL_WORDS * MAX_BEADS];
+    for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
+        Rs[t] = B.Rb[t];
+        Rf[t] = (float)B.Rb[t];
+        sV[t] = B.Vb[t];
+    }
     for (int t = threadIdx.x; t < WALL_WORDS * nb; t += blockDim.x) wbits[t] = 0u;
+    for (int t = threadIdx.x; t < 9 * nb; t += blockDim.x) sAcc[t] = R(0);
     __syncthreads();
     for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
-        R r = Rs[t];
-        worg[t] = fabs(r) < R(1e6) ? (int)floor(r) - WALL_BOX / 2 + 1 : 0;
+        double r = Rs[t];
+        worg[t] = fabs(r) < 1e6 ? (int)floor(r) - WALL_BOX / 2 + 1 : 0;
     }
     __syncthreads();
     {
@@ -687,18 +861,11 @@ __global__ void __launch_bounds__(BEAD_THREADS) bead_md_kernel(MdArgs<S, R, PhiT
                 atomicOr(&wbits[bb * WALL_WORDS + (cell >> 5)], 1u << (cell & 31));
         }
     }
-    __syncthreads();
-    // interpolation (every bead owned by one thread)
-    const int b = threadIdx.x;
-    R nR[NS] = {R(0), R(0), R(0)}, uR[NS][3], gR[3] = {R(0), R(0), R(0)}, gam[NS];
-    R V[3] = {R(0), R(0), R(0)}, gacc[NS][3];
-    bool active = b < nb;
-    if (active) {
+    // interpolation: one thread per bead, entries in slot order k
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        R nR[NS] = {R(0), R(0), R(0)}, uR[NS][3], gR[3] = {R(0), R(0), R(0)};
         for (int s = 0; s < NS; s++)
-            for (int c = 0; c < 3; c++) {
-                uR[s][c] = R(0);
-                gacc[s][c] = R(0);
-            }
+            for (int c = 0; c < 3; c++) uR[s][c] = R(0);
         for (int k = 0; k < 8; k++) {
             R w = B.entry_w[b * 8 + k];
             if (w == R(0)) continue;
@@ -711,25 +878,33 @@ __global__ void __launch_bounds__(BEAD_THREADS) bead_md_kernel(MdArgs<S, R, PhiT
             for (int c = 0; c < 3; c++) gR[c] += w * mo[12 + c];
         }
         R ntot = nR[0] + nR[1] + nR[2];
-        for (int s = 0; s < NS; s++)
-            gam[s] = (a.flags & EKL_GAMMA_LITERAL) ? A.xi : A.xi * nR[s] / ntot;
+        for (int s = 0; s < NS; s++) {
+            sGam[3 * b + s] = (a.flags & EKL_GAMMA_LITERAL) ? A.xi : A.xi * nR[s] / ntot;
+            for (int c = 0; c < 3; c++) sU[9 * b + 3 * s + c] = uR[s][c];
+        }
         R qb = B.qb[b];
         for (int c = 0; c < 3; c++) {
-            V[c] = B.Vb[3 * b + c];
+            sG[3 * b + c] = gR[c];
             if (fabs(qb * gR[c]) >= R(1)) atomicOr(a.status, ST_CFL);
         }
     }
+    __syncthreads();
     const int nsub = A.md_substeps;
     const R dt = R(1) / (R)nsub;
     const bool noise = A.bead_kT > R(0) && !(a.flags & EKL_NO_BEAD_NOISE);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (int sub = 0; sub < nsub; sub++) {
-        R F[3] = {R(0), R(0), R(0)};
-        if (active) {
-            if (!bead_force<S, R, PhiT, DEV>(A, Rs, b, F, &worg[3 * b], &wbits[b * WALL_WORDS]))
-                atomicOr(a.status, ST_BEAD);
-        }
-        __syncthreads();  // all forces read Rs before it moves
-        if (active) {
+        // force from the positions at the start of the sub-step, then the
+        // bead's own velocity and drag update (positions move after the barrier)
+        const int first = SERIAL ? (int)threadIdx.x : warp;
+        const int stride = SERIAL ? (int)blockDim.x : nwarps;
+        for (int b = first; b < nb; b += stride) {
+            R F[3];
+            bool okf;
+            if constexpr (SERIAL) okf = bead_force_serial(A, Rs, b, F, &worg[3 * b], &wbits[b * WALL_WORDS]);
+            else okf = bead_force_warp(A, Rs, Rf, b, F, &worg[3 * b], &wbits[b * WALL_WORDS]);
+            if (!okf) sBad = 1;
+            if (!SERIAL && lane != 0) continue;
             R xi_[3] = {R(0), R(0), R(0)};
             if (noise) {
                 uint32_t ctr[4] = {(uint32_t)b, (uint32_t)sub | (1u << 24), (uint32_t)A.step,
@@ -737,42 +912,42 @@ __global__ void __launch_bounds__(BEAD_THREADS) bead_md_kernel(MdArgs<S, R, PhiT
                 philox4x32_10(ctr, A.key0, A.key1);
                 for (int c = 0; c < 3; c++) xi_[c] = unit_variate<R>(ctr[c]);
             }
+            const R *gam = &sGam[3 * b];
             R gtot = gam[0] + gam[1] + gam[2];
             R amp = noise ? sqrt(R(2) * gtot * A.bead_kT / dt) : R(0);
             R qb = B.qb[b];
             for (int c = 0; c < 3; c++) {
-                R Fe = -qb * Consts<R>::KT * gR[c] + qb * Consts<R>::KT * a.E[c];
-                R num = A.mass * V[c] / dt;
-                for (int s = 0; s < NS; s++) num += gam[s] * uR[s][c];
+                R Fe = -qb * Consts<R>::KT * sG[3 * b + c] + qb * Consts<R>::KT * a.E[c];
+                R num = A.mass * sV[3 * b + c] / dt;
+                for (int s2 = 0; s2 < NS; s2++) num += gam[s2] * sU[9 * b + 3 * s2 + c];
                 num += F[c] + Fe + amp * xi_[c];
                 R Vn = num / (A.mass / dt + gtot);
-                for (int s = 0; s < NS; s++) gacc[s][c] += dt * (-gam[s] * (uR[s][c] - Vn));
-                V[c] = Vn;
-            }
-            R L[3] = {(R)g.nx, (R)g.ny, (R)g.nz};
-            for (int c = 0; c < 3; c++) {
-                R r = Rs[3 * b + c] + dt * V[c];
-                if (B.per[c]) {
-                    if (r < R(0)) r += L[c];
-                    else if (r >= L[c]) r -= L[c];
-                }
-                Rs[3 * b + c] = r;
+                for (int s2 = 0; s2 < NS; s2++)
+                    sAcc[9 * b + 3 * s2 + c] += dt * (-gam[s2] * (sU[9 * b + 3 * s2 + c] - Vn));
+                sV[3 * b + c] = Vn;
             }
         }
         __syncthreads();
-    }
-    if (active) {
-        for (int c = 0; c < 3; c++) {
-            B.Rb[3 * b + c] = Rs[3 * b + c];
-            B.Vb[3 * b + c] = V[c];
+        // positions (FP64), wrapped into [0, L) on periodic axes
+        for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
+            const int c = t % 3;
+            const double L = c == 0 ? g.nx : (c == 1 ? g.ny : g.nz);
+            double r = Rs[t] + (double)(dt * sV[t]);
+            if (B.per[c]) {
+                if (r < 0.0) r += L;
+                else if (r >= L) r -= L;
+            }
+            Rs[t] = r;
+            Rf[t] = (float)r;
         }
+        __syncthreads();
     }
-    // per-bead sub-step-averaged drag, then per slot in bead order
-    R *gbuf = B.patch_f + (long long)MAX_ENTRIES * 9;
-    if (active)
-        for (int s = 0; s < NS; s++)
-            for (int c = 0; c < 3; c++) gbuf[b * 9 + 3 * s + c] = gacc[s][c];
-    __syncthreads();
+    if (threadIdx.x == 0 && sBad) atomicOr(a.status, ST_BEAD);
+    for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
+        B.Rb[t] = Rs[t];
+        B.Vb[t] = sV[t];
+    }
+    // spread: per slot, entries in bead order (ascending b), then per particle
     for (int k = threadIdx.x; k < pc; k += blockDim.x) {
         R acc[9];
         for (int t = 0; t < 9; t++) acc[t] = R(0);
@@ -781,7 +956,7 @@ __global__ void __launch_bounds__(BEAD_THREADS) bead_md_kernel(MdArgs<S, R, PhiT
             R w = B.entry_w[e];
             if (w == R(0)) continue;
             int bb = e >> 3;
-            for (int u = 0; u < 9; u++) acc[u] += gbuf[bb * 9 + u] * w;
+            for (int u = 0; u < 9; u++) acc[u] += sAcc[bb * 9 + u] * w;
         }
         const R *mo = B.patch_mom + (long long)k * 15;
         for (int s = 0; s < NS; s++)
@@ -804,17 +979,8 @@ __global__ void __launch_bounds__(BEAD_THREADS) bead_md_kernel(MdArgs<S, R, PhiT
 template <typename S, typename R, typename PhiT, bool DEV>
 __global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 2 : 1) lb_fused_kernel(StepArgs<S, R, PhiT> a)
 {
-    __shared__ double sh[LB_THREADS / 32];
-    __shared__ int plo, phi_;
     const Grid3 g = a.g;
-    const long long i0 = blockIdx.x * (long long)blockDim.x;
-    const long long i = i0 + threadIdx.x;
-    if (threadIdx.x == 0) {
-        int pc = *a.patch_count;
-        plo = lower_bound_i(a.patch_node, pc, i0);
-        phi_ = lower_bound_i(a.patch_node, pc, i0 + blockDim.x);
-    }
-    __syncthreads();
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double msum[NS] = {0.0, 0.0, 0.0};
     int bad = 0, cfl = 0;
     if (i < g.N) {
@@ -833,8 +999,11 @@ __global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 2 : 1) lb_fused_k
             for (int c = 0; c < 3; c++)
                 if (fabs(gphi[c]) >= R(1)) cfl = 1;
             int slot = -1;
-            for (int k = plo; k < phi_; k++)
-                if (a.patch_node[k] == i) slot = k;
+            const int pc = *a.patch_count;
+            if (pc > 0) {
+                int k = lower_bound_i(a.patch_node, pc, i);
+                if (k < pc && a.patch_node[k] == i) slot = k;
+            }
             R n[NS], dn[NS], av[NS][3], G[NS][3], h[NS];
 #pragma unroll
             for (int s = 0; s < NS; s++) {
@@ -910,8 +1079,8 @@ __global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 2 : 1) lb_fused_k
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(a.status, ST_UNSTABLE);
     if (__any_sync(0xffffffffu, cfl) && (threadIdx.x & 31) == 0) atomicOr(a.status, ST_CFL);
     for (int s = 0; s < NS; s++) {
-        double t = block_sum(msum[s], sh);
-        if (threadIdx.x == 0) a.part_mass[blockIdx.x * NS + s] = t;
+        double t = warp_sum(msum[s]);
+        if ((threadIdx.x & 31) == 0) a.part_mass[(i >> 5) * NS + s] = t;
     }
 }
 

@@ -83,7 +83,7 @@ __global__ void gauge_kernel(const uint32_t *__restrict__ mask, long long N, dou
         phi[i] = (mask[i] & ekl::SOLID_BIT) ? 0.0 : phi[i] - mean;
 }
 
-template <typename R> __global__ void beads_kernel(const R *Rb, const R *Vb, int n3, double *out)
+template <typename R> __global__ void beads_kernel(const double *Rb, const R *Vb, int n3, double *out)
 {
     for (int k = threadIdx.x; k < n3; k += blockDim.x) {
         out[k] = (double)Rb[k];
@@ -143,7 +143,7 @@ extern "C" int ekl_get_fields_noalloc(ekl_handle *h, double *n_out, double *j_ou
     }
     if (beads) {
         if (c.prec == EKL_F64) beads_kernel<double><<<1, 256, 0, c.stream>>>((const double *)c.R, (const double *)c.V, 3 * c.nb, db);
-        else beads_kernel<float><<<1, 256, 0, c.stream>>>((const float *)c.R, (const float *)c.V, 3 * c.nb, db);
+        else beads_kernel<float><<<1, 256, 0, c.stream>>>((const double *)c.R, (const float *)c.V, 3 * c.nb, db);
         c.launches++;
     }
     cudaError_t e = cudaGetLastError();

@@ -47,7 +47,7 @@ static StepArgs<S, R, PhiT> make_args(Ctx &c)
     a.check_every = c.P.poisson_check_every < 1 ? 1 : c.P.poisson_check_every;
     a.fixed_iter = c.P.poisson_fixed_iter;
     a.rJ = c.rJ;
-    a.nblocks_charge = c.charge_blocks;
+    a.nblocks_charge = c.charge_blocks * (CHARGE_THREADS / 32);  // one partial per warp
     return a;
 }
 
@@ -58,7 +58,7 @@ template <typename R> static BeadArgs<R> make_bead_args(Ctx &c)
     for (int k = 0; k < 3; k++) b.per[k] = c.per[k];
     b.mask = c.mask;
     b.nb = c.nb;
-    b.Rb = (R *)c.R;
+    b.Rb = (double *)c.R;
     b.Vb = (R *)c.V;
     b.qb = (const R *)c.q;
     b.chain = c.chain;
@@ -146,7 +146,13 @@ template <typename S, typename R, typename PhiT, bool DEV> int steps_impl(Ctx &c
             md.key0 = (uint32_t)c.P.seed;
             md.key1 = (uint32_t)(c.P.seed >> 32);
             md.step = c.step;
-            bead_md_kernel<S, R, PhiT, DEV><<<1, BEAD_THREADS, 0, c.stream>>>(md);
+            static bool attr_set = false;
+            if (!attr_set) {
+                cudaFuncSetAttribute(bead_md_kernel<S, R, PhiT, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)md_smem_bytes<R>(MAX_BEADS));
+                attr_set = true;
+            }
+            bead_md_kernel<S, R, PhiT, DEV><<<1, MdThreads<R>::value, md_smem_bytes<R>(c.nb), c.stream>>>(md);
             c.launches++;
         }
         phase_end(c, PH_MD);
