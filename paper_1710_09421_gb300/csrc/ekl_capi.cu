@@ -108,6 +108,7 @@ void release(Ctx &c)
     dev_free(c, c.status, 0);
     dev_free(c, c.pois_iters, 0);
     dev_free(c, c.pois_res, 0);
+    dev_free(c, c.omegas, 0);
     dev_free(c, c.R, 0);
     dev_free(c, c.V, 0);
     dev_free(c, c.q, 0);
@@ -369,6 +370,15 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
     c.status = (int *)A(sizeof(int));
     c.pois_iters = (int *)A(sizeof(int));
     c.pois_res = (double *)A(sizeof(double));
+    // Chebyshev schedule (Sec. II.C, Press et al.): 1 for the first half
+    // sweep, 1/(1 - rJ^2/2) for the second, then 1/(1 - rJ^2 omega/4)
+    const int limit = (c.P.poisson_fixed_iter > c.P.poisson_max_iter ? c.P.poisson_fixed_iter : c.P.poisson_max_iter) + 1;
+    std::vector<double> om(2 * (size_t)limit);
+    const double rJ = c.rJ;
+    for (size_t k = 0; k < om.size(); k++)
+        om[k] = k == 0 ? 1.0 : (k == 1 ? 1.0 / (1.0 - 0.5 * rJ * rJ) : 1.0 / (1.0 - 0.25 * rJ * rJ * om[k - 1]));
+    std::vector<float> omf(om.begin(), om.end());
+    c.omegas = A(om.size() * (c.prec == EKL_F64 ? sizeof(double) : sizeof(float)));
     c.patch_count = (int *)A(sizeof(int));
     c.patch_node = (int *)A(MAX_ENTRIES * sizeof(int));
     c.patch_q = A(MAX_ENTRIES * rs);
@@ -428,6 +438,8 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
         cudaMemsetAsync(c.status, 0, sizeof(int), c.stream);
         cudaMemsetAsync(c.pois_iters, 0, sizeof(int), c.stream);
         cudaMemsetAsync(c.pois_res, 0, sizeof(double), c.stream);
+        if (c.prec == EKL_F64) cudaMemcpyAsync(c.omegas, om.data(), om.size() * 8, cudaMemcpyHostToDevice, c.stream);
+        else cudaMemcpyAsync(c.omegas, omf.data(), omf.size() * 4, cudaMemcpyHostToDevice, c.stream);
         double nfd = (double)nf;
         cudaMemcpyAsync(c.part_pois + 2 * (size_t)c.pois_blocks, &nfd, sizeof(double), cudaMemcpyHostToDevice, c.stream);
         e = cudaStreamSynchronize(c.stream);

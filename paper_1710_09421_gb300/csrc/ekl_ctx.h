@@ -61,6 +61,7 @@ struct Ctx {
     int *status;          // device status word
     int *pois_iters;      // last step's sweep count
     double *pois_res;     // last step's relative residual
+    void *omegas;         // Chebyshev relaxation factor per half sweep
     int charge_blocks;
     int lb_blocks;
     int pois_blocks;

@@ -215,7 +215,45 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, un
     return ok_s != 0;
 }
 
+// ---------------------------------------------------------------- conversions
+// GB300 runs FP64 (and 64-bit integer<->float conversions) at a small
+// fraction of the FP32 rate, so per-node work avoids them.
+// int64 -> float, round to nearest for |r| < 2^31, within one float ulp above.
+__device__ __forceinline__ float ll_to_float(long long r)
+{
+    if (r == (long long)(int)r) return __int2float_rn((int)r);
+    return fmaf(__int2float_rn((int)(r >> 32)), 4294967296.0f, __uint2float_rn((unsigned)r));
+}
+// float -> int64, round to nearest; exact split above 2^31 where d is a
+// multiple of 256.
+__device__ __forceinline__ long long float_to_ll(float d)
+{
+    if (fabsf(d) < 2147483520.0f) return (long long)__float2int_rn(d);
+    float hi = floorf(d * 2.3283064365386963e-10f);  // d / 2^32
+    float lo = d - hi * 4294967296.0f;               // exact, in [0, 2^32)
+    return ((long long)__float2int_rn(hi) << 32) + (long long)__float2uint_rn(lo);
+}
+
 // ---------------------------------------------------------------- reductions
+// Warp sum of FP32 values carried as an unevaluated float pair (TwoSum at
+// each level of a fixed xor tree): about 48 bits, FP32 pipe only; the result
+// is returned as a double in every lane.
+__device__ __forceinline__ double warp_sum_ff(float v)
+{
+    float hi = v, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+        float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        float s = hi + oh;
+        float bb = s - hi;
+        float err = (hi - (s - bb)) + (oh - bb);
+        hi = s;
+        lo = lo + ol + err;
+    }
+    return (double)hi + (double)lo;
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -231,6 +269,22 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     v = warp_sum(v);
     __syncthreads();
     if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < nw; k++) t += sh[k];
+    }
+    return t;
+}
+
+// Block sum of per-warp values already reduced within each warp (lane 0
+// holds the warp's value); fixed warp order; result valid in thread 0.
+__device__ __forceinline__ double block_sum_lanes0(double wv, double *sh)
+{
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = wv;
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x == 0) {

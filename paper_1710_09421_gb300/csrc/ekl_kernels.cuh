@@ -56,6 +56,7 @@ template <typename S, typename R, typename PhiT> struct StepArgs {
     int *pois_iters;
     double *pois_res;
     // Poisson controls
+    const void *omegas;  // Chebyshev schedule per half sweep (double, or float for fixed point)
     double tol;
     int max_iter, check_every, fixed_iter;
     double rJ;
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(CHARGE_THREADS) charge_kernel(StepArgs<S, R, P
 {
     const Grid3 g = a.g;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double mine = 0.0;
+    R mine = R(0);
     if (i < g.N) {
         const uint32_t m = a.mask[i];
         R rho = R(0);
@@ -179,12 +180,14 @@ __global__ void __launch_bounds__(CHARGE_THREADS) charge_kernel(StepArgs<S, R, P
                 int k = lower_bound_i(a.patch_node, pc, i);
                 if (k < pc && a.patch_node[k] == i) rho = rho + a.patch_q[k];
             }
-            mine = (double)rho;
+            mine = rho;
         }
         a.rho[i] = rho;
     }
     // one FP64 partial per warp (fixed shuffle tree), no block barrier
-    double t = warp_sum(mine);
+    double t;
+    if constexpr (sizeof(R) == 8) t = warp_sum((double)mine);
+    else t = warp_sum_ff((float)mine);
     if ((threadIdx.x & 31) == 0) a.part_charge[i >> 5] = t;
 }
 
@@ -199,25 +202,28 @@ __global__ void __launch_bounds__(CHARGE_THREADS) charge_kernel(StepArgs<S, R, P
 // decision from the same block partials summed in the same order.
 template <typename PhiT> struct PoisUpd;
 template <> struct PoisUpd<double> {
+    typedef double acc_t;
+    typedef double om_t;
     __device__ static double resid(double acc, int deg, double pi) { return acc - deg * pi; }
     __device__ static double apply(double pi, double omega, double r, int deg)
     {
         return pi + omega * r / deg;
     }
-    typedef double acc_t;
     __device__ static double r2(double r) { return r * r; }
 };
 template <> struct PoisUpd<long long> {
-    __device__ static long long resid(long long acc, int deg, long long pi) { return acc - deg * pi; }
-    __device__ static long long apply(long long pi, double omega, long long r, int deg)
-    {
-        float d = (float)omega * __ll2float_rn(r) / (float)deg;
-        return pi + __float2ll_rn(d);
-    }
     typedef float acc_t;
+    typedef float om_t;
+    __device__ static long long resid(long long acc, int deg, long long pi) { return acc - deg * pi; }
+    __device__ static long long apply(long long pi, float omega, long long r, int deg)
+    {
+        const float inv = deg == 6 ? (1.f / 6.f) : deg == 5 ? 0.2f : deg == 4 ? 0.25f
+                        : deg == 3 ? (1.f / 3.f) : deg == 2 ? 0.5f : 1.f;
+        return pi + float_to_ll(omega * ll_to_float(r) * inv);
+    }
     __device__ static float r2(long long r)
     {
-        float v = __ll2float_rn(r) * (float)PHI_INV;
+        float v = ll_to_float(r) * (float)PHI_INV;
         return v * v;
     }
 };
@@ -226,7 +232,8 @@ template <> struct PoisUpd<long long> {
 // node's link word, source and own potential supplied by the caller.
 template <typename PhiT>
 __device__ __forceinline__ void sor_node(const Grid3 &g, PhiT *phi, int x, int y, int z, int i,
-                                         uint32_t m, PhiT bi, PhiT &pi, double omega,
+                                         uint32_t m, PhiT bi, PhiT &pi,
+                                         typename PoisUpd<PhiT>::om_t omega,
                                          typename PoisUpd<PhiT>::acc_t &r2)
 {
     const int nx = g.nx, nxy = g.nx * g.ny;
@@ -269,7 +276,9 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
     // number of fluid nodes is carried in part_pois[2*nblk] by the host
     const double nfl = a.part_pois[2 * nblk];
     const double mean = nfl > 0 ? csum / nfl : 0.0;
+    const float meanf = (float)mean;
     double bl = 0.0;
+    float blf = 0.f;
     for (long long i = tid; i < g.N; i += nthr) {
         uint32_t m = a.mask[i];
         PhiT bv;
@@ -280,14 +289,16 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
             bv = (PhiT)v;
             bl += v * v;
         } else {
-            double v = (double)a.c4 * ((double)a.rho[i] - mean);
-            bv = __double2ll_rn(v * PHI_SCALE);
-            double q = (double)bv * PHI_INV;
-            bl += q * q;
+            // source in FP32, then exact scaling to fixed point
+            float v = (float)a.c4 * ((float)a.rho[i] - meanf);
+            bv = float_to_ll(v * (float)PHI_SCALE);
+            blf += v * v;
         }
         __stcg(a.b + i, bv);
     }
-    double t = block_sum(bl, sh);
+    double t;
+    if constexpr (((PhiT)0.5) != 0) t = block_sum(bl, sh);
+    else t = block_sum_lanes0(warp_sum_ff(blf), sh);
     if (threadIdx.x == 0) a.part_pois[blockIdx.x] = t;
     if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return;
     const double bn2 = sum_partials(a.part_pois, (int)nblk, bc);
@@ -300,7 +311,6 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
         }
         return;
     }
-    const double rJ = a.rJ;
     const int hx = (g.nx + 1) >> 1;
     const int nhalf = hx * g.ny * g.nz;
     // register cache of this thread's nodes (both colours) when they fit
@@ -331,12 +341,14 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
                 cp[colour][k] = __ldcg(a.phi + i);
             }
     }
-    double omega = 1.0;
     int it = 0, converged = 0;
     double r2tot = 0.0;
+    const typename PoisUpd<PhiT>::om_t *oms = (const typename PoisUpd<PhiT>::om_t *)a.omegas;
     for (it = 0; it < limit; it++) {
         typename PoisUpd<PhiT>::acc_t r2 = 0;
         for (int colour = 0; colour < 2; colour++) {
+            // Chebyshev relaxation factor of this half sweep (host-computed schedule)
+            const typename PoisUpd<PhiT>::om_t omega = __ldg(oms + 2 * it + colour);
             if (cached) {
 #pragma unroll
                 for (int k = 0; k < POIS_KMAX; k++) {
@@ -357,10 +369,11 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
                     sor_node<PhiT>(g, a.phi, x, y, z, i, m, __ldcg(a.b + i), pi, omega, r2);
                 }
             }
-            if (it == 0 && colour == 0) omega = 1.0 / (1.0 - 0.5 * rJ * rJ);
-            else omega = 1.0 / (1.0 - 0.25 * rJ * rJ * omega);
             if (colour == 1) {
-                double tb = block_sum((double)r2, sh);
+                double wsum;
+                if constexpr (((PhiT)0.5) != 0) wsum = warp_sum((double)r2);
+                else wsum = warp_sum_ff((float)r2);
+                double tb = block_sum_lanes0(wsum, sh);
                 if (threadIdx.x == 0) a.part_pois[blockIdx.x] = tb;
             }
             if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return;
@@ -981,7 +994,7 @@ __global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 2 : 1) lb_fused_k
 {
     const Grid3 g = a.g;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double msum[NS] = {0.0, 0.0, 0.0};
+    R msum[NS] = {R(0), R(0), R(0)};
     int bad = 0, cfl = 0;
     if (i < g.N) {
         const uint32_t m = a.mask[i];
@@ -1022,7 +1035,7 @@ __global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 2 : 1) lb_fused_k
                 dn[s] = nn;
                 n[s] = DEV ? a.n_ref[s] + nn : nn;
                 if (!(n[s] > R(0)) || !isfinite(n[s])) bad = 1;
-                msum[s] = (double)n[s];
+                msum[s] = n[s];
                 h[s] = R(0.5) * a.wd[s];
                 R j[3] = {jx, jy, jz};
                 for (int c = 0; c < 3; c++) {
@@ -1079,7 +1092,9 @@ __global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 2 : 1) lb_fused_k
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(a.status, ST_UNSTABLE);
     if (__any_sync(0xffffffffu, cfl) && (threadIdx.x & 31) == 0) atomicOr(a.status, ST_CFL);
     for (int s = 0; s < NS; s++) {
-        double t = warp_sum(msum[s]);
+        double t;
+        if constexpr (sizeof(R) == 8) t = warp_sum((double)msum[s]);
+        else t = warp_sum_ff((float)msum[s]);
         if ((threadIdx.x & 31) == 0) a.part_mass[(i >> 5) * NS + s] = t;
     }
 }

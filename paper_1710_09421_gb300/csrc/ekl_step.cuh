@@ -47,6 +47,7 @@ static StepArgs<S, R, PhiT> make_args(Ctx &c)
     a.check_every = c.P.poisson_check_every < 1 ? 1 : c.P.poisson_check_every;
     a.fixed_iter = c.P.poisson_fixed_iter;
     a.rJ = c.rJ;
+    a.omegas = c.omegas;
     a.nblocks_charge = c.charge_blocks * (CHARGE_THREADS / 32);  // one partial per warp
     return a;
 }
