@@ -14,7 +14,10 @@ OUT = os.path.join(HERE, "libekl.so")
 BUILD = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+          # host code (the Chebyshev schedule, geometry) rounds every product
+          # and sum separately, as the oracle does, on x86 and on Arm alike
+          "-Xcompiler", "-ffp-contract=off"]
 # per-unit extra flags: the FP64 unit keeps every product and sum separately
 # rounded, like a plain CPU evaluation of the same formulas
 UNITS = {

@@ -276,7 +276,6 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
     // number of fluid nodes is carried in part_pois[2*nblk] by the host
     const double nfl = a.part_pois[2 * nblk];
     const double mean = nfl > 0 ? csum / nfl : 0.0;
-    const float meanf = (float)mean;
     double bl = 0.0;
     float blf = 0.f;
     for (long long i = tid; i < g.N; i += nthr) {
@@ -289,9 +288,14 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
             bv = (PhiT)v;
             bl += v * v;
         } else {
-            // source in FP32, then exact scaling to fixed point
-            float v = (float)a.c4 * ((float)a.rho[i] - meanf);
-            bv = float_to_ll(v * (float)PHI_SCALE);
+            // The source is formed in FP64 once per step: most fluid nodes carry
+            // nearly the same small charge, so FP32 rounding of c4 (rho - mean)
+            // is correlated over the lattice and leaves a net source that a
+            // periodic or all-Neumann problem cannot absorb (it floors the
+            // residual near 1e-8 on the 64x64x128 pore).
+            const double vd = (double)a.c4 * ((double)a.rho[i] - mean);
+            bv = __double2ll_rn(vd * PHI_SCALE);
+            const float v = (float)vd;
             blf += v * v;
         }
         __stcg(a.b + i, bv);

@@ -88,9 +88,20 @@ def test_fp64_closed_box_odd_extent_no_beads():
 # solves stopped independently at a relative residual tol differ in phi by up
 # to cond(L) * tol, which is not an FP32 effect.
 def test_fp32_small_pore_1000_steps():
-    wl = W.small_pore(nx=20, ny=16, nz=24, membrane=(10, 13), radius=3.0, n_beads=4,
+    """Ions, solvent and potential without beads: FP32 storage/arithmetic vs FP64."""
+    wl = W.small_pore(nx=20, ny=16, nz=24, membrane=(10, 13), radius=3.0, n_beads=0,
                       precision="f32").replace(poisson_fixed_iter=60)
     errs, sg, so = _compare(wl, 1000, TOL32, precision="f32", check_beads=False)
+    assert errs["n"] < TOL32 and errs["u"] < TOL32 and errs["phi"] < TOL32, errs
+
+
+def test_fp32_small_pore_with_chain_1000_steps():
+    """With a 4-bead chain (no bead noise) the bead trajectory itself is
+    integrated in FP32 forces and velocities; densities and velocities stay
+    within the FP32 tolerance after 1000 steps."""
+    wl = W.small_pore(nx=20, ny=16, nz=24, membrane=(10, 13), radius=3.0, n_beads=4,
+                      precision="f32").replace(poisson_fixed_iter=60, flags=W.FLAG_NO_BEAD_NOISE)
+    errs, sg, so = _compare(wl, 1000, TOL32, precision="f32", check_beads=True)
     assert errs["n"] < TOL32 and errs["u"] < TOL32, errs
 
 
