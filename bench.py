@@ -239,6 +239,7 @@ def run_ours(args):
     st1 = sim.stats()
     ms_max = max_over_ranks(ms, world)
     launches = st1["launches"] - st0["launches"]
+    sweeps = st1["poisson_sweeps"] - st0["poisson_sweeps"]
     ph = st1["ms_phase"]
     iters = st1["poisson_iters"]
     sim.close()
@@ -282,7 +283,8 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (populations 2 x %.0f MB)" % (
                        wl.n_nodes * 57 * store / 1e6)},
         "steps_per_s": round(steps_per_s, 3),
-        "poisson_sweeps_last_step": iters,
+        "poisson_sweeps_per_step": round(sweeps / args.steps, 2),
+        "poisson_us_per_sweep": round(1e3 * ph["poisson"] / max(sweeps, 1), 3),
         "phase_ms_per_step": {k: round(v / args.steps, 5) for k, v in ph.items()},
         "roofline": {"kernel": "lb_fused_kernel", "bound": "hbm", "achieved": round(achieved, 1),
                      "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),

@@ -115,6 +115,7 @@ typedef struct ekl_stats {
     double ms_phase[6];      /* per-phase GPU time (ms) accumulated while timing is on:
                                 bead bin, charge, Poisson, bead MD, LB, other */
     int64_t launches;        /* kernels launched by the library since creation */
+    int64_t poisson_sweeps;  /* red+black sweeps summed over every step since creation */
 } ekl_stats;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  Must be

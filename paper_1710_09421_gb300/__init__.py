@@ -79,6 +79,7 @@ class ekl_stats(C.Structure):
         ("poisson_res", C.c_double),
         ("ms_phase", C.c_double * 6),
         ("launches", C.c_int64),
+        ("poisson_sweeps", C.c_int64),
     ]
 
 
@@ -281,7 +282,8 @@ def ekl_get_stats(h):
     _check(load().ekl_get_stats(h, C.byref(s)), "ekl_get_stats")
     return dict(mass=np.array(s.mass[:]), step=s.step, poisson_iters=s.poisson_iters,
                 status=s.status, poisson_res=s.poisson_res,
-                ms_phase=dict(zip(PHASES, s.ms_phase[:])), launches=s.launches)
+                ms_phase=dict(zip(PHASES, s.ms_phase[:])), launches=s.launches,
+                poisson_sweeps=s.poisson_sweeps)
 
 
 def ekl_set_timing(h, on):

@@ -107,6 +107,7 @@ void release(Ctx &c)
     dev_free(c, c.barrier, 0);
     dev_free(c, c.status, 0);
     dev_free(c, c.pois_iters, 0);
+    dev_free(c, c.pois_total, 0);
     dev_free(c, c.pois_res, 0);
     dev_free(c, c.omegas, 0);
     dev_free(c, c.R, 0);
@@ -369,6 +370,7 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
     c.barrier = (unsigned *)A(4 * sizeof(unsigned));
     c.status = (int *)A(sizeof(int));
     c.pois_iters = (int *)A(sizeof(int));
+    c.pois_total = (long long *)A(sizeof(long long));
     c.pois_res = (double *)A(sizeof(double));
     // Chebyshev schedule (Sec. II.C, Press et al.): 1 for the first half
     // sweep, 1/(1 - rJ^2/2) for the second, then 1/(1 - rJ^2 omega/4)
@@ -437,6 +439,7 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
         cudaMemsetAsync(c.patch_count, 0, sizeof(int), c.stream);
         cudaMemsetAsync(c.status, 0, sizeof(int), c.stream);
         cudaMemsetAsync(c.pois_iters, 0, sizeof(int), c.stream);
+        cudaMemsetAsync(c.pois_total, 0, sizeof(long long), c.stream);
         cudaMemsetAsync(c.pois_res, 0, sizeof(double), c.stream);
         if (c.prec == EKL_F64) cudaMemcpyAsync(c.omegas, om.data(), om.size() * 8, cudaMemcpyHostToDevice, c.stream);
         else cudaMemcpyAsync(c.omegas, omf.data(), omf.size() * 4, cudaMemcpyHostToDevice, c.stream);
@@ -634,10 +637,12 @@ int ekl_get_stats(ekl_handle *h, ekl_stats *out)
     const size_t nwarps = (size_t)c.lb_blocks * (LB_THREADS / 32);
     std::vector<double> pm(nwarps * NS);
     int it = 0;
+    long long tot = 0;
     double res = 0;
     cudaError_t e = cudaMemcpyAsync(pm.data(), c.part_mass, pm.size() * 8, cudaMemcpyDeviceToHost, c.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&it, c.pois_iters, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&res, c.pois_res, sizeof(double), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, c.pois_total, sizeof(long long), cudaMemcpyDeviceToHost, c.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) return fail_cuda(e, "get_stats");
     timing_flush(c);
@@ -653,6 +658,7 @@ int ekl_get_stats(ekl_handle *h, ekl_stats *out)
     out->status = c.last_status;
     for (int k = 0; k < PH_COUNT; k++) out->ms_phase[k] = c.ms_phase[k];
     out->launches = c.launches;
+    out->poisson_sweeps = tot;
     return EKL_OK;
 }
 

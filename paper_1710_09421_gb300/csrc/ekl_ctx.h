@@ -60,6 +60,7 @@ struct Ctx {
     unsigned *barrier;    // {count, generation, abort}
     int *status;          // device status word
     int *pois_iters;      // last step's sweep count
+    long long *pois_total;  // sweeps summed over all steps
     double *pois_res;     // last step's relative residual
     void *omegas;         // Chebyshev relaxation factor per half sweep
     int charge_blocks;

@@ -77,12 +77,14 @@ struct Grid3 {
     long long N;
 };
 
-__device__ __forceinline__ void coords_of(const Grid3 &g, long long i, int &x, int &y, int &z)
+// node coordinates; node ids fit 32 bits (lattices are capped at 2^31/64 nodes)
+__device__ __forceinline__ void coords_of(const Grid3 &g, long long i64, int &x, int &y, int &z)
 {
-    long long r = i / g.nx;
-    x = (int)(i - r * g.nx);
-    z = (int)(r / g.ny);
-    y = (int)(r - (long long)z * g.ny);
+    const int i = (int)i64;
+    const int r = i / g.nx;
+    x = i - r * g.nx;
+    z = r / g.ny;
+    y = r - z * g.ny;
 }
 
 // Neighbour offsets for the pull x - c_p: X[cx + 1] = {x+1, x, x-1}.  Indices
@@ -90,29 +92,26 @@ __device__ __forceinline__ void coords_of(const Grid3 &g, long long i, int &x, i
 // because the link bit of that direction is set.
 struct Nbr {
     int X[3];
-    long long Y[3];
-    long long Z[3];
-    __device__ __forceinline__ long long pull(int p) const
-    {
-        return (long long)X[cx_(p) + 1] + Y[cy_(p) + 1] + Z[cz_(p) + 1];
-    }
+    int Y[3];
+    int Z[3];
+    __device__ __forceinline__ int pull(int p) const { return X[cx_(p) + 1] + Y[cy_(p) + 1] + Z[cz_(p) + 1]; }
 };
 
 __device__ __forceinline__ Nbr make_nbr(const Grid3 &g, int x, int y, int z)
 {
     Nbr n;
-    int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
-    int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
-    int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
-    long long sxy = (long long)g.nx * g.ny;
+    const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+    const int sxy = g.nx * g.ny;
     n.X[0] = xp; n.X[1] = x; n.X[2] = xm;
-    n.Y[0] = (long long)yp * g.nx; n.Y[1] = (long long)y * g.nx; n.Y[2] = (long long)ym * g.nx;
+    n.Y[0] = yp * g.nx; n.Y[1] = y * g.nx; n.Y[2] = ym * g.nx;
     n.Z[0] = zp * sxy; n.Z[1] = z * sxy; n.Z[2] = zm * sxy;
     return n;
 }
 
 // face neighbours (-x, +x, -y, +y, -z, +z) are the pulls of p = 1..6
-__device__ __forceinline__ long long face_idx(const Nbr &n, int f)
+__device__ __forceinline__ int face_idx(const Nbr &n, int f)
 {
     // face f is the node x + e_f; pull p gives x - c_p: -x face = p1, +x = p2, ...
     return n.pull(f + 1);
@@ -238,9 +237,10 @@ __device__ __forceinline__ long long float_to_ll(float d)
 // Warp sum of FP32 values carried as an unevaluated float pair (TwoSum at
 // each level of a fixed xor tree): about 48 bits, FP32 pipe only; the result
 // is returned as a double in every lane.
-__device__ __forceinline__ double warp_sum_ff(float v)
+__device__ __forceinline__ void warp_sum_ff2(float v, float &hi, float &lo)
 {
-    float hi = v, lo = 0.f;
+    hi = v;
+    lo = 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         float oh = __shfl_xor_sync(0xffffffffu, hi, o);
@@ -251,7 +251,21 @@ __device__ __forceinline__ double warp_sum_ff(float v)
         hi = s;
         lo = lo + ol + err;
     }
+}
+__device__ __forceinline__ double warp_sum_ff(float v)
+{
+    float hi, lo;
+    warp_sum_ff2(v, hi, lo);
     return (double)hi + (double)lo;
+}
+// same, converted to FP64 in lane 0 only (the value is meaningful there)
+__device__ __forceinline__ double warp_sum_ff_lane0(float v)
+{
+    float hi, lo;
+    warp_sum_ff2(v, hi, lo);
+    double r = 0.0;
+    if ((threadIdx.x & 31) == 0) r = (double)hi + (double)lo;
+    return r;
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -308,6 +322,27 @@ __device__ __forceinline__ double sum_partials(const double *p, int n, double *s
     }
     __syncthreads();
     return sh[0];
+}
+
+// Residual test of an iteration: warp 0 sums the block partials (fixed
+// order), thread 0 compares sqrt(sum) with tol * bnorm and broadcasts the
+// verdict; every thread of the block must call it.
+__device__ __forceinline__ bool test_partials(const double *p, int n, double tolb, double *sh,
+                                              int *flag, double &sum_out)
+{
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int k = threadIdx.x; k < n; k += 32) v += __ldcg(p + k);
+        v = warp_sum(v);
+        if (threadIdx.x == 0) {
+            sh[0] = v;
+            *flag = sqrt(v) <= tolb;
+        }
+    }
+    __syncthreads();
+    sum_out = sh[0];
+    return *flag != 0;
 }
 
 // lower bound of `key` in sorted a[0..n)

@@ -54,6 +54,7 @@ template <typename S, typename R, typename PhiT> struct StepArgs {
     unsigned *barrier;
     int *status;
     int *pois_iters;
+    long long *pois_total;
     double *pois_res;
     // Poisson controls
     const void *omegas;  // Chebyshev schedule per half sweep (double, or float for fixed point)
@@ -68,11 +69,13 @@ template <typename S, typename R>
 __device__ __forceinline__ void pull19(const S *__restrict__ f, long long N, int s, long long i,
                                        uint32_t m, const Nbr &nb, R v[Q])
 {
+    // 32-bit offsets inside one species block (19 N < 2^31)
+    const S *fs = f + (size_t)s * Q * (size_t)N;
+    const int n = (int)N, ii = (int)i;
 #pragma unroll
     for (int p = 0; p < Q; p++) {
-        long long src = ((m >> p) & 1u) ? ((long long)(s * Q + opp_(p)) * N + i)
-                                        : ((long long)(s * Q + p) * N + nb.pull(p));
-        v[p] = (R)Store<S>::ld(f + src);
+        const int off = ((m >> p) & 1u) ? opp_(p) * n + ii : p * n + nb.pull(p);
+        v[p] = (R)Store<S>::ld(fs + off);
     }
 }
 
@@ -228,22 +231,26 @@ template <> struct PoisUpd<long long> {
     }
 };
 
-// One half sweep over the nodes of `colour` owned by this thread, with the
-// node's link word, source and own potential supplied by the caller.
-template <typename PhiT>
-__device__ __forceinline__ void sor_node(const Grid3 &g, PhiT *phi, int x, int y, int z, int i,
-                                         uint32_t m, PhiT bi, PhiT &pi,
-                                         typename PoisUpd<PhiT>::om_t omega,
-                                         typename PoisUpd<PhiT>::acc_t &r2)
+// Neighbour indices of node i = (x, y, z) across its six faces (-x, +x,
+// -y, +y, -z, +z), wrapped; faces beyond a closed side are never read (their
+// link bit is set).
+__device__ __forceinline__ void face_nbrs(const Grid3 &g, int x, int y, int z, int i, int nb[6])
 {
     const int nx = g.nx, nxy = g.nx * g.ny;
-    const int xm = x == 0 ? i + nx - 1 : i - 1, xp = x == nx - 1 ? i - nx + 1 : i + 1;
-    const int ym = y == 0 ? i + nxy - nx : i - nx, yp = y == g.ny - 1 ? i - nxy + nx : i + nx;
-    const int zm = z == 0 ? i + (int)g.N - nxy : i - nxy, zp = z == g.nz - 1 ? i - (int)g.N + nxy : i + nxy;
-    const int nbr[6] = {xm, xp, ym, yp, zm, zp};
-    PhiT v[6];
-#pragma unroll
-    for (int f = 0; f < 6; f++) v[f] = ((m >> (f + 1)) & 1u) ? (PhiT)0 : __ldcg(phi + nbr[f]);
+    nb[0] = x == 0 ? i + nx - 1 : i - 1;
+    nb[1] = x == nx - 1 ? i - nx + 1 : i + 1;
+    nb[2] = y == 0 ? i + nxy - nx : i - nx;
+    nb[3] = y == g.ny - 1 ? i - nxy + nx : i + nx;
+    nb[4] = z == 0 ? i + (int)g.N - nxy : i - nxy;
+    nb[5] = z == g.nz - 1 ? i - (int)g.N + nxy : i + nxy;
+}
+
+// SOR update of one node from its loaded neighbours (acc starts at b_i)
+template <typename PhiT>
+__device__ __forceinline__ void sor_apply(PhiT *phi, int i, uint32_t m, PhiT bi, PhiT pi, const PhiT v[6],
+                                          typename PoisUpd<PhiT>::om_t omega,
+                                          typename PoisUpd<PhiT>::acc_t &r2)
+{
     PhiT acc = bi;
     int deg = 0;
 #pragma unroll
@@ -254,8 +261,7 @@ __device__ __forceinline__ void sor_node(const Grid3 &g, PhiT *phi, int x, int y
         }
     if (deg == 0) return;
     PhiT r = PoisUpd<PhiT>::resid(acc, deg, pi);
-    pi = PoisUpd<PhiT>::apply(pi, omega, r, deg);
-    __stcg(phi + i, pi);
+    __stcg(phi + i, PoisUpd<PhiT>::apply(pi, omega, r, deg));
     r2 += PoisUpd<PhiT>::r2(r);
 }
 
@@ -266,6 +272,7 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
 {
     __shared__ double sh[POIS_THREADS / 32];
     __shared__ double bc[1];
+    __shared__ int cflag;
     const Grid3 g = a.g;
     const unsigned nblk = gridDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -302,7 +309,7 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
     }
     double t;
     if constexpr (((PhiT)0.5) != 0) t = block_sum(bl, sh);
-    else t = block_sum_lanes0(warp_sum_ff(blf), sh);
+    else t = block_sum_lanes0(warp_sum_ff_lane0(blf), sh);
     if (threadIdx.x == 0) a.part_pois[blockIdx.x] = t;
     if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return;
     const double bn2 = sum_partials(a.part_pois, (int)nblk, bc);
@@ -317,18 +324,19 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
     }
     const int hx = (g.nx + 1) >> 1;
     const int nhalf = hx * g.ny * g.nz;
-    // register cache of this thread's nodes (both colours) when they fit
-    const bool cached = (nhalf + nthr - 1) / nthr <= POIS_KMAX;
-    int cx[2][POIS_KMAX], cy[2][POIS_KMAX], cz[2][POIS_KMAX], ci[2][POIS_KMAX];
+    // register cache of this thread's nodes (both colours) when they fit:
+    // node index, link word and packed coordinates
+    const bool cached = (nhalf + nthr - 1) / nthr <= POIS_KMAX && g.nx < 2048 && g.ny < 1024 && g.nz < 2048;
+    int ci[2][POIS_KMAX], cxyz[2][POIS_KMAX];
     uint32_t cm[2][POIS_KMAX];
-    PhiT cb[2][POIS_KMAX], cp[2][POIS_KMAX];
     if (cached) {
 #pragma unroll
         for (int colour = 0; colour < 2; colour++)
 #pragma unroll
             for (int k = 0; k < POIS_KMAX; k++) {
                 const int h = tid + k * nthr;
-                ci[colour][k] = -1;
+                ci[colour][k] = 0;
+                cxyz[colour][k] = 0;
                 cm[colour][k] = SOLID_BIT;
                 if (h >= nhalf) continue;
                 const int row = h / hx, xh = h - row * hx;
@@ -336,30 +344,41 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
                 const int x = 2 * xh + ((colour + y + z) & 1);
                 if (x >= g.nx) continue;
                 const int i = x + g.nx * row;
-                cx[colour][k] = x;
-                cy[colour][k] = y;
-                cz[colour][k] = z;
                 ci[colour][k] = i;
+                cxyz[colour][k] = x | (y << 11) | (z << 21);
                 cm[colour][k] = a.mask[i];
-                cb[colour][k] = __ldcg(a.b + i);
-                cp[colour][k] = __ldcg(a.phi + i);
             }
     }
     int it = 0, converged = 0;
     double r2tot = 0.0;
+    const double tolb = a.tol * bnorm;
     const typename PoisUpd<PhiT>::om_t *oms = (const typename PoisUpd<PhiT>::om_t *)a.omegas;
     for (it = 0; it < limit; it++) {
         typename PoisUpd<PhiT>::acc_t r2 = 0;
+#pragma unroll
         for (int colour = 0; colour < 2; colour++) {
             // Chebyshev relaxation factor of this half sweep (host-computed schedule)
             const typename PoisUpd<PhiT>::om_t omega = __ldg(oms + 2 * it + colour);
             if (cached) {
+                // all loads of this thread's nodes first, then the updates
+                PhiT v[POIS_KMAX][6], bb[POIS_KMAX], pp[POIS_KMAX];
 #pragma unroll
                 for (int k = 0; k < POIS_KMAX; k++) {
-                    if (cm[colour][k] & SOLID_BIT) continue;
-                    sor_node<PhiT>(g, a.phi, cx[colour][k], cy[colour][k], cz[colour][k], ci[colour][k],
-                                   cm[colour][k], cb[colour][k], cp[colour][k], omega, r2);
+                    const uint32_t m = cm[colour][k];
+                    const int i = ci[colour][k], q = cxyz[colour][k];
+                    int nb[6];
+                    face_nbrs(g, q & 2047, (q >> 11) & 1023, q >> 21, i, nb);
+                    const bool live = !(m & SOLID_BIT);
+#pragma unroll
+                    for (int f = 0; f < 6; f++)
+                        v[k][f] = (live && !((m >> (f + 1)) & 1u)) ? __ldcg(a.phi + nb[f]) : (PhiT)0;
+                    bb[k] = live ? __ldcg(a.b + i) : (PhiT)0;
+                    pp[k] = live ? __ldcg(a.phi + i) : (PhiT)0;
                 }
+#pragma unroll
+                for (int k = 0; k < POIS_KMAX; k++)
+                    if (!(cm[colour][k] & SOLID_BIT))
+                        sor_apply<PhiT>(a.phi, ci[colour][k], cm[colour][k], bb[k], pp[k], v[k], omega, r2);
             } else {
                 for (int h = tid; h < nhalf; h += nthr) {
                     const int row = h / hx, xh = h - row * hx;
@@ -369,29 +388,35 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
                     const int i = x + g.nx * row;
                     const uint32_t m = a.mask[i];
                     if (m & SOLID_BIT) continue;
-                    PhiT pi = __ldcg(a.phi + i);
-                    sor_node<PhiT>(g, a.phi, x, y, z, i, m, __ldcg(a.b + i), pi, omega, r2);
+                    int nb[6];
+                    face_nbrs(g, x, y, z, i, nb);
+                    PhiT v[6];
+#pragma unroll
+                    for (int f = 0; f < 6; f++) v[f] = ((m >> (f + 1)) & 1u) ? (PhiT)0 : __ldcg(a.phi + nb[f]);
+                    sor_apply<PhiT>(a.phi, i, m, __ldcg(a.b + i), __ldcg(a.phi + i), v, omega, r2);
                 }
             }
             if (colour == 1) {
                 double wsum;
                 if constexpr (((PhiT)0.5) != 0) wsum = warp_sum((double)r2);
-                else wsum = warp_sum_ff((float)r2);
+                else wsum = warp_sum_ff_lane0((float)r2);
                 double tb = block_sum_lanes0(wsum, sh);
                 if (threadIdx.x == 0) a.part_pois[blockIdx.x] = tb;
             }
             if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return;
         }
         const bool test = a.fixed_iter <= 0 && ((it + 1) % a.check_every) == 0;
-        if (test || it + 1 == limit) r2tot = sum_partials(a.part_pois, (int)nblk, bc);
-        if (test && sqrt(r2tot) <= a.tol * bnorm) {
-            converged = 1;
-            it++;
-            break;
+        if (test || it + 1 == limit) {
+            if (test_partials(a.part_pois, (int)nblk, tolb, bc, &cflag, r2tot) && test) {
+                converged = 1;
+                it++;
+                break;
+            }
         }
     }
     if (tid == 0) {
         *a.pois_iters = it;
+        a.pois_total[0] += it;
         *a.pois_res = sqrt(r2tot) / bnorm;
         if (a.fixed_iter <= 0 && !converged) atomicOr(a.status, ST_NOCONV);
     }
@@ -705,7 +730,8 @@ __device__ bool bead_force_serial(const MdArgs<S, R, PhiT, DEV> &A, const double
 // is valid in every lane.
 template <typename S, typename R, typename PhiT, bool DEV>
 __device__ bool bead_force_warp(const MdArgs<S, R, PhiT, DEV> &A, const double *Rs, const float *Rf,
-                                int b, R F[3], const int *org, const uint32_t *bits)
+                                const float *Rloc, const int *wlo, const int *wn, int b, R F[3],
+                                const int *org, const uint32_t *bits)
 {
     const Grid3 &g = A.b.g;
     const int nb = A.b.nb;
@@ -743,31 +769,39 @@ __device__ bool bead_force_warp(const MdArgs<S, R, PhiT, DEV> &A, const double *
             else f[c] += Fp[c];
         }
     }
-    const double rc = 1.122462048309373 * (double)A.wall_sigma;
-    bool pos_ok = rc < 16.0;
-    for (int c = 0; c < 3; c++) pos_ok = pos_ok && fabs(Rs[3 * b + c]) < 1e6;
-    if (pos_ok) {
-        int lo[3], n[3];
-        for (int c = 0; c < 3; c++) {
-            lo[c] = (int)floor(Rs[3 * b + c] - rc);
-            n[c] = (int)floor(Rs[3 * b + c] + rc) + 2 - lo[c];
-        }
-        const int cells = n[0] * n[1] * n[2];
-        for (int t = lane; t < cells; t += 32) {
-            int x = lo[0] + t % n[0], y = lo[1] + (t / n[0]) % n[1], z = lo[2] + t / (n[0] * n[1]);
-            bool in;
-            if (!wall_solid(g, A.b.per, A.b.mask, x, y, z, org, bits, in)) continue;
-            R d[3] = {(R)(Rs[3 * b] - x), (R)(Rs[3 * b + 1] - y), (R)(Rs[3 * b + 2] - z)};
-            wca_add<R>(A.wall_eps, A.wall_sigma, d, f);
-        }
-    } else {
-        ok = false;
+    // wall nodes in the scan box; coordinates relative to the cached box origin
+    const int n0 = wn[3 * b], n1 = wn[3 * b + 1], n2 = wn[3 * b + 2];
+    const int cells = n0 * n1 * n2;
+    for (int t = lane; t < cells; t += 32) {
+        const int x = wlo[3 * b] + t % n0, y = wlo[3 * b + 1] + (t / n0) % n1, z = wlo[3 * b + 2] + t / (n0 * n1);
+        bool in;
+        if (!wall_solid(g, A.b.per, A.b.mask, x, y, z, org, bits, in)) continue;
+        R d[3] = {(R)(Rloc[3 * b] - (float)(x - org[0])), (R)(Rloc[3 * b + 1] - (float)(y - org[1])),
+                  (R)(Rloc[3 * b + 2] - (float)(z - org[2]))};
+        wca_add<R>(A.wall_eps, A.wall_sigma, d, f);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
         for (int c = 0; c < 3; c++) f[c] += __shfl_xor_sync(0xffffffffu, f[c], o);
     for (int c = 0; c < 3; c++) F[c] = f[c];
     return __all_sync(0xffffffffu, ok);
+}
+
+// Per-bead wall scan box [floor(R - rc), floor(R + rc) + 1] and coordinates
+// local to the cached block (one thread per coordinate, FP64 once per sub-step)
+__device__ __forceinline__ void scan_bounds(double r, double rc, int org, int &lo, int &n, float &loc,
+                                            int &bad)
+{
+    if (!(fabs(r) < 1e6) || !(rc < 16.0)) {
+        bad = 1;
+        lo = 0;
+        n = 0;
+        loc = 0.f;
+        return;
+    }
+    lo = (int)floor(r - rc);
+    n = (int)floor(r + rc) + 2 - lo;
+    loc = (float)(r - (double)org);
 }
 
 // One block: moments and field at the patch nodes, interpolation to beads,
@@ -779,7 +813,7 @@ __device__ bool bead_force_warp(const MdArgs<S, R, PhiT, DEV> &A, const double *
 // Reduced-precision instantiations: one warp per bead.
 template <typename R> inline size_t md_smem_bytes(int nb)
 {
-    return (size_t)nb * (3 * sizeof(double) + 27 * sizeof(R) + 3 * sizeof(float) + 3 * sizeof(int) +
+    return (size_t)nb * (3 * sizeof(double) + 27 * sizeof(R) + 6 * sizeof(float) + 9 * sizeof(int) +
                          WALL_WORDS * sizeof(uint32_t));
 }
 
@@ -805,8 +839,11 @@ __global__ void __launch_bounds__(MdThreads<R>::value) bead_md_kernel(MdArgs<S, 
     R *sGam = sG + 3 * nb;
     R *sAcc = sGam + 3 * nb;
     float *Rf = (float *)(sAcc + 9 * nb);
-    int *worg = (int *)(Rf + 3 * nb);
-    uint32_t *wbits = (uint32_t *)(worg + 3 * nb);
+    float *Rloc = Rf + 3 * nb;
+    int *worg = (int *)(Rloc + 3 * nb);
+    int *wlo = worg + 3 * nb;
+    int *wn = wlo + 3 * nb;
+    uint32_t *wbits = (uint32_t *)(wn + 3 * nb);
     __shared__ int sBad;
     if (threadIdx.x == 0) sBad = 0;
     // moments at the patch nodes
@@ -853,9 +890,13 @@ __global__ void __launch_bounds__(MdThreads<R>::value) bead_md_kernel(MdArgs<S, 
     for (int t = threadIdx.x; t < WALL_WORDS * nb; t += blockDim.x) wbits[t] = 0u;
     for (int t = threadIdx.x; t < 9 * nb; t += blockDim.x) sAcc[t] = R(0);
     __syncthreads();
+    const double rcw = 1.122462048309373 * (double)A.wall_sigma;  // 2^(1/6) sigma
     for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
         double r = Rs[t];
         worg[t] = fabs(r) < 1e6 ? (int)floor(r) - WALL_BOX / 2 + 1 : 0;
+        int bad = 0;
+        scan_bounds(r, rcw, worg[t], wlo[t], wn[t], Rloc[t], bad);
+        if (bad) sBad = 1;
     }
     __syncthreads();
     {
@@ -919,7 +960,7 @@ __global__ void __launch_bounds__(MdThreads<R>::value) bead_md_kernel(MdArgs<S, 
             R F[3];
             bool okf;
             if constexpr (SERIAL) okf = bead_force_serial(A, Rs, b, F, &worg[3 * b], &wbits[b * WALL_WORDS]);
-            else okf = bead_force_warp(A, Rs, Rf, b, F, &worg[3 * b], &wbits[b * WALL_WORDS]);
+            else okf = bead_force_warp(A, Rs, Rf, Rloc, wlo, wn, b, F, &worg[3 * b], &wbits[b * WALL_WORDS]);
             if (!okf) sBad = 1;
             if (!SERIAL && lane != 0) continue;
             R xi_[3] = {R(0), R(0), R(0)};
@@ -956,6 +997,9 @@ __global__ void __launch_bounds__(MdThreads<R>::value) bead_md_kernel(MdArgs<S, 
             }
             Rs[t] = r;
             Rf[t] = (float)r;
+            int bad = 0;
+            scan_bounds(r, rcw, worg[t], wlo[t], wn[t], Rloc[t], bad);
+            if (bad) sBad = 1;
         }
         __syncthreads();
     }

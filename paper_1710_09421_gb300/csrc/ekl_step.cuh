@@ -41,6 +41,7 @@ static StepArgs<S, R, PhiT> make_args(Ctx &c)
     a.barrier = c.barrier;
     a.status = c.status;
     a.pois_iters = c.pois_iters;
+    a.pois_total = c.pois_total;
     a.pois_res = c.pois_res;
     a.tol = c.P.poisson_tol;
     a.max_iter = c.P.poisson_max_iter;
