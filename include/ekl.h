@@ -67,6 +67,7 @@ extern "C" {
 #define EKL_EQ_BARYCENTRIC 1   /* f_eq and S use the barycentric velocity (printed Eq. 10) */
 #define EKL_GAMMA_LITERAL 2    /* bead drag gamma^a = xi for every species (literal Sec. II.B) */
 #define EKL_NO_BEAD_NOISE 4    /* no Langevin noise on the beads */
+#define EKL_POISSON_GLOBAL 8   /* always use the global-memory SOR kernel (no shared-memory tiles) */
 
 #define EKL_BOND_FENE 0
 #define EKL_BOND_HARMONIC 1

@@ -348,6 +348,33 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
         return fail(EKL_ERR_CUDA, "Poisson kernel cannot be resident");
     }
     c.pois_blocks = c.num_sms;  // one block of POIS_THREADS per SM
+    // Shared-memory tiles for the SOR kernel: full-x slabs of ty x tz rows,
+    // one per SM, each with a 2-deep halo; chosen to minimise the extended
+    // tile (per-block work and halo traffic).  Periodic y/z extents are even.
+    {
+        int maxdyn = 0;
+        cudaDeviceGetAttribute(&maxdyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device);
+        const size_t per_node = 2 * phi_size(c.prec) + sizeof(uint32_t);
+        long long best = -1;
+        if (!(P->flags & EKL_POISSON_GLOBAL))
+            for (int ty = 2; ty <= c.ny; ty++) {
+                if (c.ny % ty) continue;
+                for (int tz = 2; tz <= c.nz; tz++) {
+                    if (c.nz % tz) continue;
+                    const int nt = (c.ny / ty) * (c.nz / tz);
+                    const long long E = (long long)c.nx * (ty + 4) * (tz + 4);
+                    if (nt > c.num_sms || (size_t)E * per_node + 1024 > (size_t)maxdyn) continue;
+                    if (best < 0 || E < best || (E == best && nt > c.tile_nty * c.tile_ntz)) {
+                        best = E;
+                        c.tile_ty = ty;
+                        c.tile_tz = tz;
+                        c.tile_nty = c.ny / ty;
+                        c.tile_ntz = c.nz / tz;
+                    }
+                }
+            }
+        c.pois_tiled = best > 0;
+    }
     bool okall = true;
     auto A = [&](size_t bytes) {
         void *p = dev_alloc(c, bytes);

@@ -66,6 +66,8 @@ struct Ctx {
     int charge_blocks;
     int lb_blocks;
     int pois_blocks;
+    int pois_tiled;          // shared-memory tiled Poisson kernel in use
+    int tile_ty, tile_tz, tile_nty, tile_ntz;
 
     // beads
     int nb;

@@ -396,7 +396,9 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
                     sor_apply<PhiT>(a.phi, i, m, __ldcg(a.b + i), __ldcg(a.phi + i), v, omega, r2);
                 }
             }
-            if (colour == 1) {
+            // the residual norm is only needed on the sweeps that test it
+            const bool need = (a.fixed_iter <= 0 && ((it + 1) % a.check_every) == 0) || it + 1 == limit;
+            if (colour == 1 && need) {
                 double wsum;
                 if constexpr (((PhiT)0.5) != 0) wsum = warp_sum((double)r2);
                 else wsum = warp_sum_ff_lane0((float)r2);
@@ -420,6 +422,216 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
         *a.pois_res = sqrt(r2tot) / bnorm;
         if (a.fixed_iter <= 0 && !converged) atomicOr(a.status, ST_NOCONV);
     }
+}
+
+// ---------------------------------------------------------------- tiled SOR
+// Shared-memory-resident variant for lattices whose (y, z) tiles fit one SM
+// each: block t owns the full-x slab tile T = [y0, y0+ty) x [z0, z0+tz) and
+// keeps T plus a 2-deep (y, z) halo of phi, the source and the link words in
+// shared memory for the whole solve.  A sweep updates the red nodes of T and
+// of the first halo layer (the halo red values are recomputed from the same
+// inputs as their owner's, so they are bitwise the owner's), then the black
+// nodes of T, writes T to global memory and passes one grid barrier; the
+// next sweep reloads only the halo.  Results are bitwise those of the
+// global-memory kernel (same node updates, same schedule).
+struct TileGeom {
+    int ty, tz, nty, ntz;  // tile extents and tile counts along y and z
+};
+
+template <typename PhiT>
+__device__ __forceinline__ void tile_update(PhiT *ps, const PhiT *bs, const uint32_t *ms, int nx, int ey,
+                                            int e, int x, uint32_t m, typename PoisUpd<PhiT>::om_t omega,
+                                            typename PoisUpd<PhiT>::acc_t &r2, bool count)
+{
+    const int ex = nx * ey;  // stride of lz
+    // face neighbours in the extended frame (x wraps inside the row)
+    const int nb[6] = {x == 0 ? e + nx - 1 : e - 1, x == nx - 1 ? e - nx + 1 : e + 1, e - nx, e + nx,
+                       e - ex, e + ex};
+    PhiT acc = bs[e];
+    int deg = 0;
+#pragma unroll
+    for (int f = 0; f < 6; f++)
+        if (!((m >> (f + 1)) & 1u)) {
+            acc += ps[nb[f]];
+            deg++;
+        }
+    if (deg == 0) return;
+    const PhiT pi = ps[e];
+    const PhiT r = PoisUpd<PhiT>::resid(acc, deg, pi);
+    ps[e] = PoisUpd<PhiT>::apply(pi, omega, r, deg);
+    if (count) r2 += PoisUpd<PhiT>::r2(r);
+}
+
+template <typename S, typename R, typename PhiT>
+__global__ void __launch_bounds__(POIS_THREADS, 1) poisson_tiled_kernel(StepArgs<S, R, PhiT> a, TileGeom tg)
+{
+    extern __shared__ __align__(16) unsigned char tsm[];
+    __shared__ double sh[POIS_THREADS / 32];
+    __shared__ double bc[1];
+    __shared__ int cflag;
+    const Grid3 g = a.g;
+    const unsigned nblk = gridDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthr = nblk * blockDim.x;
+    unsigned bar_k = 0;
+    const int nx = g.nx, ey = tg.ty + 4, ez = tg.tz + 4, E = nx * ey * ez;
+    PhiT *ps = (PhiT *)tsm;
+    PhiT *bs = ps + E;
+    uint32_t *ms = (uint32_t *)(bs + E);
+    const int by = blockIdx.x % tg.nty, bz = blockIdx.x / tg.nty;
+    const int y0 = by * tg.ty - 2, z0 = bz * tg.tz - 2;  // global coordinates of the extended origin
+    // --- source (grid-wide, as in the global kernel)
+    const double csum = sum_partials(a.part_charge, a.nblocks_charge, bc);
+    const double nfl = a.part_pois[2 * nblk];
+    const double mean = nfl > 0 ? csum / nfl : 0.0;
+    double bl = 0.0;
+    float blf = 0.f;
+    for (long long i = tid; i < g.N; i += nthr) {
+        uint32_t m = a.mask[i];
+        PhiT bv;
+        if (m & SOLID_BIT) {
+            bv = (PhiT)0;
+        } else if constexpr (((PhiT)0.5) != 0) {
+            double v = (double)a.c4 * ((double)a.rho[i] - mean);
+            bv = (PhiT)v;
+            bl += v * v;
+        } else {
+            const double vd = (double)a.c4 * ((double)a.rho[i] - mean);
+            bv = __double2ll_rn(vd * PHI_SCALE);
+            const float v = (float)vd;
+            blf += v * v;
+        }
+        __stcg(a.b + i, bv);
+    }
+    double t;
+    if constexpr (((PhiT)0.5) != 0) t = block_sum(bl, sh);
+    else t = block_sum_lanes0(warp_sum_ff_lane0(blf), sh);
+    if (threadIdx.x == 0) a.part_pois[blockIdx.x] = t;
+    if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return;
+    const double bn2 = sum_partials(a.part_pois, (int)nblk, bc);
+    const double bnorm = sqrt(bn2);
+    const int limit = a.fixed_iter > 0 ? a.fixed_iter : a.max_iter;
+    if (a.fixed_iter <= 0 && bnorm == 0.0) {
+        if (tid == 0) {
+            *a.pois_iters = 0;
+            *a.pois_res = 0.0;
+        }
+        return;
+    }
+    // --- load the extended tile: link words, source, potential
+    auto gidx = [&](int ly, int lz, int &gi) -> bool {
+        int y = y0 + ly, z = z0 + lz;
+        if (y < 0 || y >= g.ny) {
+            if (!a.per[1]) return false;
+            y = (y % g.ny + g.ny) % g.ny;
+        }
+        if (z < 0 || z >= g.nz) {
+            if (!a.per[2]) return false;
+            z = (z % g.nz + g.nz) % g.nz;
+        }
+        gi = nx * (y + g.ny * z);
+        return true;
+    };
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        const int x = e % nx, r = e / nx, ly = r % ey, lz = r / ey;
+        int gi;
+        if (gidx(ly, lz, gi)) {
+            ms[e] = a.mask[gi + x];
+            bs[e] = __ldcg(a.b + gi + x);
+            ps[e] = __ldcg(a.phi + gi + x);
+        } else {
+            ms[e] = SOLID_BIT;
+            bs[e] = (PhiT)0;
+            ps[e] = (PhiT)0;
+        }
+    }
+    __syncthreads();
+    int it = 0, converged = 0;
+    double r2tot = 0.0;
+    const double tolb = a.tol * bnorm;
+    const typename PoisUpd<PhiT>::om_t *oms = (const typename PoisUpd<PhiT>::om_t *)a.omegas;
+    const int ty = tg.ty, tz = tg.tz;
+    const int hx = (nx + 1) >> 1;
+    for (it = 0; it < limit; it++) {
+        typename PoisUpd<PhiT>::acc_t r2 = 0;
+        if (it > 0) {
+            // reload the halo (rows with ly or lz outside the owned tile)
+            const int rows = ey * ez;
+            for (int q = threadIdx.x; q < rows * nx; q += blockDim.x) {
+                const int x = q % nx, r = q / nx, ly = r % ey, lz = r / ey;
+                if (ly >= 2 && ly < ty + 2 && lz >= 2 && lz < tz + 2) continue;
+                int gi;
+                if (gidx(ly, lz, gi)) ps[q] = __ldcg(a.phi + gi + x);
+            }
+            __syncthreads();
+        }
+        const typename PoisUpd<PhiT>::om_t om_r = __ldg(oms + 2 * it), om_b = __ldg(oms + 2 * it + 1);
+        // red nodes of T and of the first halo layer
+        {
+            const int ny1 = ty + 2, nz1 = tz + 2, cnt = hx * ny1 * nz1;
+            for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+                const int xh = q % hx, r = q / hx, ly = 1 + r % ny1, lz = 1 + r / ny1;
+                const int gy = y0 + ly, gz = z0 + lz;
+                const int x = 2 * xh + ((gy + gz) & 1);  // red: (x + y + z) even
+                if (x >= nx) continue;
+                const int e = x + nx * (ly + ey * lz);
+                const uint32_t m = ms[e];
+                if (m & SOLID_BIT) continue;
+                const bool own = ly >= 2 && ly < ty + 2 && lz >= 2 && lz < tz + 2;
+                tile_update<PhiT>(ps, bs, ms, nx, ey, e, x, m, om_r, r2, own);
+            }
+        }
+        __syncthreads();
+        // black nodes of T
+        {
+            const int cnt = hx * ty * tz;
+            for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+                const int xh = q % hx, r = q / hx, ly = 2 + r % ty, lz = 2 + r / ty;
+                const int gy = y0 + ly, gz = z0 + lz;
+                const int x = 2 * xh + ((gy + gz + 1) & 1);  // black: (x + y + z) odd
+                if (x >= nx) continue;
+                const int e = x + nx * (ly + ey * lz);
+                const uint32_t m = ms[e];
+                if (m & SOLID_BIT) continue;
+                tile_update<PhiT>(ps, bs, ms, nx, ey, e, x, m, om_b, r2, true);
+            }
+        }
+        __syncthreads();
+        // owned tile back to global memory
+        for (int q = threadIdx.x; q < nx * ty * tz; q += blockDim.x) {
+            const int x = q % nx, r = q / nx, ly = 2 + r % ty, lz = 2 + r / ty;
+            const int gi = nx * ((y0 + ly) + g.ny * (z0 + lz));
+            __stcg(a.phi + gi + x, ps[x + nx * (ly + ey * lz)]);
+        }
+        const bool need = (a.fixed_iter <= 0 && ((it + 1) % a.check_every) == 0) || it + 1 == limit;
+        if (need) {
+            double wsum;
+            if constexpr (((PhiT)0.5) != 0) wsum = warp_sum((double)r2);
+            else wsum = warp_sum_ff_lane0((float)r2);
+            double tb = block_sum_lanes0(wsum, sh);
+            if (threadIdx.x == 0) a.part_pois[blockIdx.x] = tb;
+        }
+        if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return;
+        const bool test = a.fixed_iter <= 0 && ((it + 1) % a.check_every) == 0;
+        if (test || it + 1 == limit) {
+            if (test_partials(a.part_pois, (int)nblk, tolb, bc, &cflag, r2tot) && test) {
+                converged = 1;
+                it++;
+                break;
+            }
+        }
+    }
+    if (tid == 0) {
+        *a.pois_iters = it;
+        a.pois_total[0] += it;
+        *a.pois_res = sqrt(r2tot) / bnorm;
+        if (a.fixed_iter <= 0 && !converged) atomicOr(a.status, ST_NOCONV);
+    }
+}
+
+template <typename PhiT> inline size_t tile_smem_bytes(int nx, const TileGeom &tg)
+{
+    return (size_t)nx * (tg.ty + 4) * (tg.tz + 4) * (2 * sizeof(PhiT) + sizeof(uint32_t));
 }
 
 // ============================================================== beads

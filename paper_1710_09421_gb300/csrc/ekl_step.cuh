@@ -118,7 +118,22 @@ template <typename S, typename R, typename PhiT, bool DEV> int steps_impl(Ctx &c
         // 3. Poisson: one cooperative launch for all sweeps
         phase_begin(c, PH_POISSON);
         cudaMemsetAsync(c.barrier, 0, 4 * sizeof(unsigned), c.stream);
-        {
+        if (c.pois_tiled) {
+            TileGeom tg{c.tile_ty, c.tile_tz, c.tile_nty, c.tile_ntz};
+            const size_t smem = tile_smem_bytes<PhiT>(c.nx, tg);
+            static size_t attr_bytes = 0;
+            if (smem > attr_bytes) {
+                cudaFuncSetAttribute(poisson_tiled_kernel<S, R, PhiT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                attr_bytes = smem;
+            }
+            void *args[] = {&a, &tg};
+            cudaError_t e = cudaLaunchCooperativeKernel((const void *)poisson_tiled_kernel<S, R, PhiT>,
+                                                        dim3(c.tile_nty * c.tile_ntz), dim3(POIS_THREADS),
+                                                        args, smem, c.stream);
+            c.launches++;
+            if (e != cudaSuccess) return EKL_ERR_CUDA;
+        } else {
             void *args[] = {&a};
             cudaError_t e = cudaLaunchCooperativeKernel((const void *)poisson_kernel<S, R, PhiT>,
                                                         dim3(c.pois_blocks), dim3(POIS_THREADS),

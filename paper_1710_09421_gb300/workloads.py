@@ -32,6 +32,7 @@ PRECISION = {"f64": 0, "f32": 1, "bf16": 2, "fp16": 3}
 FLAG_EQ_BARYCENTRIC = 1 << 0   # f_eq and S use the barycentric u* (printed reading)
 FLAG_GAMMA_LITERAL = 1 << 1    # gamma^alpha = xi for every species (literal Sec. II.B)
 FLAG_NO_BEAD_NOISE = 1 << 2    # switch off the Langevin noise on the beads
+FLAG_POISSON_GLOBAL = 1 << 3   # CUDA library only: no shared-memory Poisson tiles
 
 BOND_FENE = 0
 BOND_HARMONIC = 1

@@ -128,6 +128,30 @@ def test_fp32_tolerance_stopping_bounded_by_solver_tolerance():
     assert errs["n"] < TOL32 and errs["u_flow"] < 1e-4, errs
 
 
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+@pytest.mark.parametrize("which", ["small", "bench"])
+def test_tiled_poisson_bitwise_equals_global(precision, which):
+    """The shared-memory tiled SOR kernel performs the same node updates in
+    the same schedule as the global-memory kernel: identical bits."""
+    if which == "small":
+        wl = W.small_pore(precision=precision)
+        steps = 20
+    else:
+        wl = W.config_pore_fp32().replace(precision=precision, rho_jacobi=0.9999,
+                                          poisson_check_every=4)
+        steps = 4
+    out = []
+    for flags in (0, W.FLAG_POISSON_GLOBAL):
+        sim = E.Simulation(wl.replace(flags=wl.flags | flags))
+        sim.step(steps)
+        f, phi, _ = sim.get_state()
+        st = sim.stats()
+        out.append((f, phi, st["poisson_sweeps"]))
+        sim.close()
+    assert out[0][2] == out[1][2]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][0], out[1][0])
+
+
 def test_mass_conservation_fp32():
     wl = W.small_pore(precision="f32")
     sim = E.Simulation(wl)
