@@ -393,7 +393,7 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
     c.phi = A(N * ps);
     c.part_charge = (double *)A((size_t)c.charge_blocks * (CHARGE_THREADS / 32) * sizeof(double));
     c.part_mass = (double *)A((size_t)c.lb_blocks * (LB_THREADS / 32) * NS * sizeof(double));
-    c.part_pois = (double *)A((2 * (size_t)c.pois_blocks + 1) * sizeof(double));
+    c.part_pois = (double *)A((size_t)c.pois_blocks * sizeof(double));
     c.barrier = (unsigned *)A(4 * sizeof(unsigned));
     c.status = (int *)A(sizeof(int));
     c.pois_iters = (int *)A(sizeof(int));
@@ -470,8 +470,7 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
         cudaMemsetAsync(c.pois_res, 0, sizeof(double), c.stream);
         if (c.prec == EKL_F64) cudaMemcpyAsync(c.omegas, om.data(), om.size() * 8, cudaMemcpyHostToDevice, c.stream);
         else cudaMemcpyAsync(c.omegas, omf.data(), omf.size() * 4, cudaMemcpyHostToDevice, c.stream);
-        double nfd = (double)nf;
-        cudaMemcpyAsync(c.part_pois + 2 * (size_t)c.pois_blocks, &nfd, sizeof(double), cudaMemcpyHostToDevice, c.stream);
+
         e = cudaStreamSynchronize(c.stream);
         if (e != cudaSuccess) { rc = fail_cuda(e, "create"); break; }
     } while (0);

@@ -61,6 +61,7 @@ template <typename S, typename R, typename PhiT> struct StepArgs {
     double tol;
     int max_iter, check_every, fixed_iter;
     double rJ;
+    double n_fluid;  // number of fluid nodes (mean charge divisor)
     int nblocks_charge;
 };
 
@@ -280,8 +281,7 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
     unsigned bar_k = 0;
     // --- source: subtract the mean charge over fluid nodes (neutralisation)
     const double csum = sum_partials(a.part_charge, a.nblocks_charge, bc);
-    // number of fluid nodes is carried in part_pois[2*nblk] by the host
-    const double nfl = a.part_pois[2 * nblk];
+    const double nfl = a.n_fluid;
     const double mean = nfl > 0 ? csum / nfl : 0.0;
     double bl = 0.0;
     float blf = 0.f;
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_tiled_kernel(StepArgs
     const int y0 = by * tg.ty - 2, z0 = bz * tg.tz - 2;  // global coordinates of the extended origin
     // --- source (grid-wide, as in the global kernel)
     const double csum = sum_partials(a.part_charge, a.nblocks_charge, bc);
-    const double nfl = a.part_pois[2 * nblk];
+    const double nfl = a.n_fluid;
     const double mean = nfl > 0 ? csum / nfl : 0.0;
     double bl = 0.0;
     float blf = 0.f;

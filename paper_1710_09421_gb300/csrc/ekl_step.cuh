@@ -49,6 +49,7 @@ static StepArgs<S, R, PhiT> make_args(Ctx &c)
     a.fixed_iter = c.P.poisson_fixed_iter;
     a.rJ = c.rJ;
     a.omegas = c.omegas;
+    a.n_fluid = (double)c.n_fluid;
     a.nblocks_charge = c.charge_blocks * (CHARGE_THREADS / 32);  // one partial per warp
     return a;
 }
