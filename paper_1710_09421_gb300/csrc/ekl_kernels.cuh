@@ -518,7 +518,9 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_tiled_kernel(StepArgs
         }
         return;
     }
-    // --- load the extended tile: link words, source, potential
+    // --- load the extended tile: link words, source, potential.  Loops run
+    // one warp per (ly, lz) row and one lane per x, so the row decomposition
+    // costs one division per row.
     auto gidx = [&](int ly, int lz, int &gi) -> bool {
         int y = y0 + ly, z = z0 + lz;
         if (y < 0 || y >= g.ny) {
@@ -532,17 +534,17 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_tiled_kernel(StepArgs
         gi = nx * (y + g.ny * z);
         return true;
     };
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        const int x = e % nx, r = e / nx, ly = r % ey, lz = r / ey;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int rows = ey * ez;
+    for (int row = warp; row < rows; row += nwarps) {
+        const int ly = row % ey, lz = row / ey;
         int gi;
-        if (gidx(ly, lz, gi)) {
-            ms[e] = a.mask[gi + x];
-            bs[e] = __ldcg(a.b + gi + x);
-            ps[e] = __ldcg(a.phi + gi + x);
-        } else {
-            ms[e] = SOLID_BIT;
-            bs[e] = (PhiT)0;
-            ps[e] = (PhiT)0;
+        const bool in = gidx(ly, lz, gi);
+        const int e0 = nx * row;
+        for (int x = lane; x < nx; x += 32) {
+            ms[e0 + x] = in ? a.mask[gi + x] : SOLID_BIT;
+            bs[e0 + x] = in ? __ldcg(a.b + gi + x) : (PhiT)0;
+            ps[e0 + x] = in ? __ldcg(a.phi + gi + x) : (PhiT)0;
         }
     }
     __syncthreads();
@@ -555,53 +557,59 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_tiled_kernel(StepArgs
     for (it = 0; it < limit; it++) {
         typename PoisUpd<PhiT>::acc_t r2 = 0;
         if (it > 0) {
-            // reload the halo (rows with ly or lz outside the owned tile)
-            const int rows = ey * ez;
-            for (int q = threadIdx.x; q < rows * nx; q += blockDim.x) {
-                const int x = q % nx, r = q / nx, ly = r % ey, lz = r / ey;
+            // reload the halo rows (rows outside the owned tile)
+            for (int row = warp; row < rows; row += nwarps) {
+                const int ly = row % ey, lz = row / ey;
                 if (ly >= 2 && ly < ty + 2 && lz >= 2 && lz < tz + 2) continue;
                 int gi;
-                if (gidx(ly, lz, gi)) ps[q] = __ldcg(a.phi + gi + x);
+                if (!gidx(ly, lz, gi)) continue;
+                const int e0 = nx * row;
+                for (int x = lane; x < nx; x += 32) ps[e0 + x] = __ldcg(a.phi + gi + x);
             }
             __syncthreads();
         }
         const typename PoisUpd<PhiT>::om_t om_r = __ldg(oms + 2 * it), om_b = __ldg(oms + 2 * it + 1);
         // red nodes of T and of the first halo layer
         {
-            const int ny1 = ty + 2, nz1 = tz + 2, cnt = hx * ny1 * nz1;
-            for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-                const int xh = q % hx, r = q / hx, ly = 1 + r % ny1, lz = 1 + r / ny1;
-                const int gy = y0 + ly, gz = z0 + lz;
-                const int x = 2 * xh + ((gy + gz) & 1);  // red: (x + y + z) even
-                if (x >= nx) continue;
-                const int e = x + nx * (ly + ey * lz);
-                const uint32_t m = ms[e];
-                if (m & SOLID_BIT) continue;
+            const int ny1 = ty + 2, nrow = ny1 * (tz + 2);
+            for (int rr = warp; rr < nrow; rr += nwarps) {
+                const int ly = 1 + rr % ny1, lz = 1 + rr / ny1;
+                const int par = (y0 + ly + z0 + lz) & 1;   // red: (x + y + z) even
                 const bool own = ly >= 2 && ly < ty + 2 && lz >= 2 && lz < tz + 2;
-                tile_update<PhiT>(ps, bs, ms, nx, ey, e, x, m, om_r, r2, own);
+                const int e0 = nx * (ly + ey * lz);
+                for (int xh = lane; xh < hx; xh += 32) {
+                    const int x = 2 * xh + par;
+                    if (x >= nx) continue;
+                    const uint32_t m = ms[e0 + x];
+                    if (m & SOLID_BIT) continue;
+                    tile_update<PhiT>(ps, bs, ms, nx, ey, e0 + x, x, m, om_r, r2, own);
+                }
             }
         }
         __syncthreads();
         // black nodes of T
         {
-            const int cnt = hx * ty * tz;
-            for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-                const int xh = q % hx, r = q / hx, ly = 2 + r % ty, lz = 2 + r / ty;
-                const int gy = y0 + ly, gz = z0 + lz;
-                const int x = 2 * xh + ((gy + gz + 1) & 1);  // black: (x + y + z) odd
-                if (x >= nx) continue;
-                const int e = x + nx * (ly + ey * lz);
-                const uint32_t m = ms[e];
-                if (m & SOLID_BIT) continue;
-                tile_update<PhiT>(ps, bs, ms, nx, ey, e, x, m, om_b, r2, true);
+            const int nrow = ty * tz;
+            for (int rr = warp; rr < nrow; rr += nwarps) {
+                const int ly = 2 + rr % ty, lz = 2 + rr / ty;
+                const int par = (y0 + ly + z0 + lz + 1) & 1;  // black: (x + y + z) odd
+                const int e0 = nx * (ly + ey * lz);
+                for (int xh = lane; xh < hx; xh += 32) {
+                    const int x = 2 * xh + par;
+                    if (x >= nx) continue;
+                    const uint32_t m = ms[e0 + x];
+                    if (m & SOLID_BIT) continue;
+                    tile_update<PhiT>(ps, bs, ms, nx, ey, e0 + x, x, m, om_b, r2, true);
+                }
             }
         }
         __syncthreads();
-        // owned tile back to global memory
-        for (int q = threadIdx.x; q < nx * ty * tz; q += blockDim.x) {
-            const int x = q % nx, r = q / nx, ly = 2 + r % ty, lz = 2 + r / ty;
+        // owned rows back to global memory
+        for (int rr = warp; rr < ty * tz; rr += nwarps) {
+            const int ly = 2 + rr % ty, lz = 2 + rr / ty;
             const int gi = nx * ((y0 + ly) + g.ny * (z0 + lz));
-            __stcg(a.phi + gi + x, ps[x + nx * (ly + ey * lz)]);
+            const int e0 = nx * (ly + ey * lz);
+            for (int x = lane; x < nx; x += 32) __stcg(a.phi + gi + x, ps[e0 + x]);
         }
         const bool need = (a.fixed_iter <= 0 && ((it + 1) % a.check_every) == 0) || it + 1 == limit;
         if (need) {
