@@ -183,6 +183,45 @@ const char *ekl_last_error(void);
 int64_t ekl_sizeof_params(void);
 
 /* ---------------------------------------------------------------------------
+ * Batched replicas.  Many independent simulations of uneven size (e.g.
+ * translocation events with different boxes, pores, chains and seeds; the
+ * paper runs 100 such events, Sec. IV.A) stepped together: each phase of
+ * the step is one launch for all replicas, the Poisson solve one persistent
+ * cooperative launch whose blocks are shared out among the replicas (each
+ * with its own schedule, tolerance and convergence).  All replicas share the
+ * precision of params[0] and the stream.  Replicas are ordinary handles
+ * (ekl_batch_replica) for set-up and read-back, but must only be advanced
+ * through ekl_batch_step. */
+typedef struct ekl_batch ekl_batch;
+
+/* nrep parameter blocks (params[r]); errors as ekl_create, plus
+ * EKL_ERR_ARG when nrep exceeds the number of co-resident Poisson blocks. */
+int ekl_batch_create(int32_t nrep, const ekl_params *params, void *stream, ekl_batch **out);
+
+/* beads of replica rep, as ekl_set_beads */
+int ekl_batch_set_beads(ekl_batch *b, int32_t rep, int32_t n, const double *R, const double *V,
+                        const double *q, const int32_t *chain);
+
+/* advance every replica by nsteps; returns the OR of warning bits, or the
+ * first error of any replica */
+int ekl_batch_step(ekl_batch *b, int32_t nsteps);
+
+/* handle of replica rep (owned by the batch; for get_fields / get_stats) */
+ekl_handle *ekl_batch_replica(ekl_batch *b, int32_t rep);
+
+/* Autotuner: time each Poisson schedule (1024-thread blocks one per SM or
+ * 512-thread blocks two per SM; blocks shared by all nodes or by fluid
+ * nodes) over trial_steps steps of the live batch (the steps are real: the
+ * batch advances by 4 * trial_steps) and keep the fastest; *choice_out gets
+ * its index (bit 0: 512-thread blocks, bit 1: fluid weighting). */
+int ekl_batch_autotune(ekl_batch *b, int32_t trial_steps, int32_t *choice_out);
+
+/* kernels launched by the batch itself since creation */
+int64_t ekl_batch_launches(ekl_batch *b);
+
+void ekl_batch_destroy(ekl_batch *b);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free field read-back.  The paper has no counterpart: this entry
  * serves callers that may not allocate GPU memory while they run (code
  * running between capture and replay of a CUDA graph on a pool-allocated

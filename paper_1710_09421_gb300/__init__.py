@@ -122,6 +122,16 @@ def load(build_if_missing: bool = True):
         L.ekl_last_error.restype = C.c_char_p
         L.ekl_sizeof_params.restype = C.c_int64
         L.ekl_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
+        L.ekl_batch_create.argtypes = [C.c_int32, C.POINTER(ekl_params), vp, C.POINTER(vp)]
+        L.ekl_batch_set_beads.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, vp]
+        L.ekl_batch_step.argtypes = [vp, C.c_int32]
+        L.ekl_batch_replica.argtypes = [vp, C.c_int32]
+        L.ekl_batch_replica.restype = vp
+        L.ekl_batch_autotune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
+        L.ekl_batch_launches.argtypes = [vp]
+        L.ekl_batch_launches.restype = C.c_int64
+        L.ekl_batch_destroy.argtypes = [vp]
+        L.ekl_batch_destroy.restype = None
         if L.ekl_sizeof_params() != C.sizeof(ekl_params):
             raise RuntimeError("ekl_params layout of the binding does not match the library")
         _lib = L
@@ -353,3 +363,94 @@ class Simulation:
 
     def set_timing(self, on=True):
         return ekl_set_timing(self.h, on)
+
+
+# ------------------------------------------------------------------ batches
+def ekl_batch_create(params_list, stream=None):
+    arr = (ekl_params * len(params_list))(*params_list)
+    h = C.c_void_p()
+    _check(load().ekl_batch_create(len(params_list), arr, stream, C.byref(h)), "ekl_batch_create")
+    return h
+
+
+def ekl_batch_set_beads(b, rep, R, V, q, chain):
+    R = np.ascontiguousarray(R, np.float64)
+    V = None if V is None else np.ascontiguousarray(V, np.float64)
+    q = np.ascontiguousarray(q, np.float64)
+    ch = None if chain is None else np.ascontiguousarray(chain, np.int32)
+    return _check(load().ekl_batch_set_beads(b, int(rep), len(R), _ptr(R), _ptr(V), _ptr(q), _ptr(ch)),
+                  "ekl_batch_set_beads")
+
+
+def ekl_batch_step(b, nsteps):
+    return _check(load().ekl_batch_step(b, int(nsteps)), "ekl_batch_step")
+
+
+def ekl_batch_replica(b, rep):
+    return C.c_void_p(load().ekl_batch_replica(b, int(rep)))
+
+
+def ekl_batch_autotune(b, trial_steps):
+    c = C.c_int32(0)
+    _check(load().ekl_batch_autotune(b, int(trial_steps), C.byref(c)), "ekl_batch_autotune")
+    return c.value
+
+
+def ekl_batch_destroy(b):
+    if b:
+        load().ekl_batch_destroy(b)
+
+
+class _Replica:
+    """Read-back view of one replica of a Batch."""
+
+    def __init__(self, h, wl, nb):
+        self.h, self.wl, self.N, self.nb = h, wl, wl.n_nodes, nb
+
+    def fields(self, which=("n", "j", "phi", "R", "V")):
+        return ekl_get_fields(self.h, self.N, self.nb, which)
+
+    def stats(self):
+        return ekl_get_stats(self.h)
+
+    def get_state(self):
+        return ekl_get_state(self.h, self.N)
+
+
+class Batch:
+    """Many independent workloads stepped together (marshalling only)."""
+
+    def __init__(self, wls, precision=None, stream=None):
+        self.wls = list(wls)
+        plist, keep = [], []
+        for wl in self.wls:
+            P, k = make_params(wl, precision)
+            plist.append(P)
+            keep.append(k)
+        self.h = ekl_batch_create(plist, stream)
+        del keep
+        self.reps = []
+        for r, wl in enumerate(self.wls):
+            if wl.n_beads:
+                ekl_batch_set_beads(self.h, r, wl.R, wl.V, wl.charge, wl.chain)
+            self.reps.append(_Replica(ekl_batch_replica(self.h, r), wl, wl.n_beads))
+
+    def step(self, n=1):
+        return ekl_batch_step(self.h, n)
+
+    def autotune(self, trial_steps=2):
+        return ekl_batch_autotune(self.h, trial_steps)
+
+    def launches(self):
+        return load().ekl_batch_launches(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ekl_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -5,15 +5,20 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
-#include "ekl_dev.cuh"
+#include "ekl_kernels.cuh"
 
 using namespace ekl;
 
 struct ekl_handle {
     Ctx c;
+};
+
+struct ekl_batch {
+    Batch b;
 };
 
 namespace {
@@ -713,6 +718,210 @@ void ekl_destroy(ekl_handle *h)
     cudaStreamSynchronize(h->c.stream);
     release(h->c);
     delete h;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+namespace {
+
+int batch_run(Batch &B, int nsteps)
+{
+    switch (B.prec) {
+    case EKL_F64: return run_batch_f64(B, nsteps);
+    case EKL_F32: return run_batch_f32(B, nsteps);
+    case EKL_BF16DEV: return run_batch_bf16(B, nsteps);
+    default: return run_batch_fp16(B, nsteps);
+    }
+}
+
+void batch_release(Batch &B)
+{
+    if (!B.reps) return;
+    Ctx &c0 = *B.reps[0];
+    for (int q = 0; q < 2; q++) {
+        dev_free(c0, B.d_args[q], 0);
+        dev_free(c0, B.d_bargs[q], 0);
+        dev_free(c0, B.d_mdargs[q], 0);
+    }
+    dev_free(c0, B.d_block_rep, 0);
+    dev_free(c0, B.d_block_local, 0);
+    dev_free(c0, B.d_rep_blocks, 0);
+    dev_free(c0, B.barrier, 0);
+    dev_free(c0, B.status, 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ekl_batch_create(int32_t nrep, const ekl_params *params, void *stream, ekl_batch **out)
+{
+    if (!out) return fail(EKL_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (nrep < 1 || nrep > MAX_REPS || !params) return fail(EKL_ERR_ARG, "replica count out of range (1..256)");
+    for (int r = 1; r < nrep; r++)
+        if (params[r].precision != params[0].precision) return fail(EKL_ERR_ARG, "replicas must share one precision");
+    ekl_batch *bh = new (std::nothrow) ekl_batch();
+    if (!bh) return fail(EKL_ERR_ALLOC, "host allocation failed");
+    Batch &B = bh->b;
+    B.nrep = nrep;
+    B.reps = new Ctx *[nrep]();
+    B.handles = new void *[nrep]();
+    B.stream = (cudaStream_t)stream;
+    B.prec = params[0].precision;
+    int rc = EKL_OK;
+    for (int r = 0; r < nrep && rc == EKL_OK; r++) {
+        ekl_handle *h = nullptr;
+        rc = ekl_create(&params[r], stream, &h);
+        if (rc == EKL_OK) {
+            B.handles[r] = h;
+            B.reps[r] = &h->c;
+        }
+    }
+    int sms = rc == EKL_OK ? B.reps[0]->num_sms : 0;
+    if (rc == EKL_OK && nrep > sms) rc = fail(EKL_ERR_ARG, "more replicas than SMs for the batched Poisson launch");
+    if (rc == EKL_OK) {
+        Ctx &c0 = *B.reps[0];
+        size_t sa = 0, sb = 0, sm = 0;
+        switch (B.prec) {  // descriptor sizes per precision
+        case EKL_F64:
+            sa = sizeof(StepArgs<double, double, double>);
+            sb = sizeof(BeadArgs<double>);
+            sm = sizeof(MdArgs<double, double, double, false>);
+            break;
+        default:
+            sa = sizeof(StepArgs<float, float, long long>);
+            sb = sizeof(BeadArgs<float>);
+            sm = sizeof(MdArgs<float, float, long long, true>);
+            break;
+        }
+        bool ok = true;
+        auto A = [&](size_t bytes) {
+            void *p = dev_alloc(c0, bytes);
+            if (!p) ok = false;
+            return p;
+        };
+        for (int q = 0; q < 2; q++) {
+            B.d_args[q] = A(nrep * sa);
+            B.d_bargs[q] = A(nrep * sb);
+            B.d_mdargs[q] = A(nrep * sm);
+        }
+        B.d_block_rep = (int *)A(4 * (size_t)sms * 2);
+        B.d_block_local = (int *)A(4 * (size_t)sms * 2);
+        B.d_rep_blocks = (int *)A(4 * (size_t)nrep);
+        B.barrier = (unsigned *)A(4 * sizeof(unsigned));
+        B.status = (int *)A(sizeof(int));
+        if (!ok) rc = fail(EKL_ERR_ALLOC, "device allocation failed");
+        else {
+            cudaMemsetAsync(B.status, 0, sizeof(int), B.stream);
+            B.pois_threads = POIS_THREADS;
+            B.pois_blocks = sms;
+            B.weight_fluid = 1;
+        }
+    }
+    if (rc != EKL_OK) {
+        batch_release(B);
+        for (int r = 0; r < nrep; r++)
+            if (B.handles[r]) ekl_destroy((ekl_handle *)B.handles[r]);
+        delete[] B.reps;
+        delete[] B.handles;
+        delete bh;
+        return rc;
+    }
+    *out = bh;
+    return EKL_OK;
+}
+
+int ekl_batch_set_beads(ekl_batch *bh, int32_t rep, int32_t n, const double *R, const double *V, const double *q,
+                        const int32_t *chain)
+{
+    if (!bh || rep < 0 || rep >= bh->b.nrep) return fail(EKL_ERR_ARG, "bad batch or replica index");
+    bh->b.ready = 0;  // descriptor tables carry the bead count
+    return ekl_set_beads((ekl_handle *)bh->b.handles[rep], n, R, V, q, chain);
+}
+
+ekl_handle *ekl_batch_replica(ekl_batch *bh, int32_t rep)
+{
+    if (!bh || rep < 0 || rep >= bh->b.nrep) return nullptr;
+    return (ekl_handle *)bh->b.handles[rep];
+}
+
+int ekl_batch_step(ekl_batch *bh, int32_t nsteps)
+{
+    if (!bh || nsteps < 0) return fail(EKL_ERR_ARG, "bad batch or step count");
+    Batch &B = bh->b;
+    for (int r = 0; r < B.nrep; r++) cudaMemsetAsync(B.reps[r]->status, 0, sizeof(int), B.stream);
+    cudaMemsetAsync(B.status, 0, sizeof(int), B.stream);
+    int rc = batch_run(B, nsteps);
+    if (rc != EKL_OK) return fail(rc, "batch launch failed");
+    std::vector<int> st(B.nrep + 1, 0);
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < B.nrep && e == cudaSuccess; r++)
+        e = cudaMemcpyAsync(&st[r], B.reps[r]->status, sizeof(int), cudaMemcpyDeviceToHost, B.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st[B.nrep], B.status, sizeof(int), cudaMemcpyDeviceToHost, B.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B.stream);
+    if (e != cudaSuccess) return fail_cuda(e, "batch step");
+    int all = 0;
+    for (int r = 0; r <= B.nrep; r++) all |= st[r];
+    for (int r = 0; r < B.nrep; r++) B.reps[r]->last_status = st[r] | st[B.nrep];
+    return status_to_code(all);
+}
+
+int ekl_batch_autotune(ekl_batch *bh, int32_t trial_steps, int32_t *choice_out)
+{
+    if (!bh || trial_steps < 1) return fail(EKL_ERR_ARG, "bad batch or trial length");
+    Batch &B = bh->b;
+    const int sms = B.reps[0]->num_sms;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bestc = 0;
+    for (int choice = 0; choice < 4; choice++) {
+        B.pois_threads = (choice & 1) ? 512 : 1024;
+        B.pois_blocks = (choice & 1) ? 2 * sms : sms;
+        B.weight_fluid = (choice >> 1) & 1;
+        B.ready = 0;
+        if (B.nrep > B.pois_blocks) continue;
+        cudaEventRecord(e0, B.stream);
+        int rc = batch_run(B, trial_steps);
+        cudaEventRecord(e1, B.stream);
+        if (rc != EKL_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(EKL_ERR_CUDA, "autotune trial failed");
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bestc = choice;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    B.pois_threads = (bestc & 1) ? 512 : 1024;
+    B.pois_blocks = (bestc & 1) ? 2 * sms : sms;
+    B.weight_fluid = (bestc >> 1) & 1;
+    B.ready = 0;
+    if (choice_out) *choice_out = bestc;
+    return EKL_OK;
+}
+
+int64_t ekl_batch_launches(ekl_batch *bh) { return bh ? bh->b.launches : 0; }
+
+void ekl_batch_destroy(ekl_batch *bh)
+{
+    if (!bh) return;
+    Batch &B = bh->b;
+    cudaStreamSynchronize(B.stream);
+    batch_release(B);
+    for (int r = 0; r < B.nrep; r++)
+        if (B.handles[r]) ekl_destroy((ekl_handle *)B.handles[r]);
+    delete[] B.reps;
+    delete[] B.handles;
+    delete bh;
 }
 
 }  // extern "C"

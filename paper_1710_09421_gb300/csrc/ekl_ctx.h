@@ -99,6 +99,29 @@ struct Ctx {
 void timing_record(Ctx &c, int phase, int begin);
 void timing_flush(Ctx &c);
 
+// A batch of independent replicas stepped together (every phase is one
+// launch for all replicas).
+struct Batch {
+    int nrep;
+    Ctx **reps;              // replica contexts (owned through their handles)
+    void **handles;          // the ekl_handle of each replica
+    cudaStream_t stream;
+    int prec;
+    int ready;               // descriptor tables current
+    void *d_args[2], *d_bargs[2], *d_mdargs[2];  // per parity
+    int *d_block_rep, *d_block_local, *d_rep_blocks;
+    unsigned *barrier;
+    int *status;
+    int pois_threads, pois_blocks;  // schedule of the batched Poisson launch
+    int weight_fluid;        // split Poisson blocks by fluid nodes (1) or all nodes (0)
+    int max_lb_blocks, max_charge_blocks, max_nb;
+    long long launches;
+};
+int run_batch_f64(Batch &b, int nsteps);
+int run_batch_f32(Batch &b, int nsteps);
+int run_batch_bf16(Batch &b, int nsteps);
+int run_batch_fp16(Batch &b, int nsteps);
+
 // message returned by ekl_last_error() on this thread
 void set_last_error(const char *msg);
 

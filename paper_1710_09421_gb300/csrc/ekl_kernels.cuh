@@ -150,10 +150,10 @@ __global__ void init_kernel(Grid3 g, const uint32_t *__restrict__ mask,
 // rho_i = sum_a z^a n^a + wall charge + bead charge (Eq. 2), n^a pulled from
 // the post-collision state (the streamed densities of this step, Eq. 15).
 template <typename S, typename R, typename PhiT, bool DEV>
-__global__ void __launch_bounds__(CHARGE_THREADS) charge_kernel(StepArgs<S, R, PhiT> a)
+__device__ __forceinline__ void charge_body(const StepArgs<S, R, PhiT> &a, long long blk)
 {
     const Grid3 g = a.g;
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long i = blk * (long long)blockDim.x + threadIdx.x;
     R mine = R(0);
     if (i < g.N) {
         const uint32_t m = a.mask[i];
@@ -193,6 +193,21 @@ __global__ void __launch_bounds__(CHARGE_THREADS) charge_kernel(StepArgs<S, R, P
     if constexpr (sizeof(R) == 8) t = warp_sum((double)mine);
     else t = warp_sum_ff((float)mine);
     if ((threadIdx.x & 31) == 0) a.part_charge[i >> 5] = t;
+}
+
+template <typename S, typename R, typename PhiT, bool DEV>
+__global__ void __launch_bounds__(CHARGE_THREADS) charge_kernel(StepArgs<S, R, PhiT> a)
+{
+    charge_body<S, R, PhiT, DEV>(a, blockIdx.x);
+}
+
+// every replica of a batch in one launch: blockIdx.y selects the replica
+template <typename S, typename R, typename PhiT, bool DEV>
+__global__ void __launch_bounds__(CHARGE_THREADS) charge_batch_kernel(const StepArgs<S, R, PhiT> *reps)
+{
+    const StepArgs<S, R, PhiT> &a = reps[blockIdx.y];
+    if ((long long)blockIdx.x * blockDim.x >= a.g.N) return;
+    charge_body<S, R, PhiT, DEV>(a, blockIdx.x);
 }
 
 // ============================================================== Poisson
@@ -637,6 +652,160 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_tiled_kernel(StepArgs
     }
 }
 
+// ---------------------------------------------------------------- batched SOR
+// Every replica of a batch in one persistent cooperative launch.  Blocks are
+// split among replicas (block_rep / block_local, rep_blocks per replica); all
+// replicas sweep in lockstep behind one grid barrier per half sweep, each with
+// its own Chebyshev schedule, tolerance and iteration cap, and a replica that
+// has converged (or reached its cap) stops updating.  Every block evaluates
+// every replica's residual test from the same partials in the same order, so
+// all blocks agree on who is still active without extra synchronisation.
+constexpr int MAX_REPS = 256;
+
+struct PoisBatch {
+    int nrep;
+    const int *block_rep;
+    const int *block_local;
+    const int *rep_blocks;
+    unsigned *barrier;
+    int *status;
+};
+
+template <typename S, typename R, typename PhiT>
+__global__ void __launch_bounds__(POIS_THREADS, 1) poisson_batch_kernel(const StepArgs<S, R, PhiT> *reps, PoisBatch pb)
+{
+    __shared__ double sh[POIS_THREADS / 32];
+    __shared__ double s_tolb[MAX_REPS], s_bnorm[MAX_REPS], s_res[MAX_REPS];
+    __shared__ int s_active[MAX_REPS], s_iters[MAX_REPS], s_conv[MAX_REPS], s_any;
+    const int rep = pb.block_rep[blockIdx.x], lb = pb.block_local[blockIdx.x], kr = pb.rep_blocks[rep];
+    const StepArgs<S, R, PhiT> &a = reps[rep];
+    const Grid3 g = a.g;
+    const int tid = lb * blockDim.x + threadIdx.x, nthr = kr * blockDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    unsigned bar_k = 0;
+    // --- source of this replica (mean over its fluid nodes)
+    __shared__ double bc[1];
+    const double csum = sum_partials(a.part_charge, a.nblocks_charge, bc);
+    const double mean = a.n_fluid > 0 ? csum / a.n_fluid : 0.0;
+    double bl = 0.0;
+    float blf = 0.f;
+    for (long long i = tid; i < g.N; i += nthr) {
+        const uint32_t m = a.mask[i];
+        PhiT bv;
+        if (m & SOLID_BIT) {
+            bv = (PhiT)0;
+        } else if constexpr (((PhiT)0.5) != 0) {
+            const double v = (double)a.c4 * ((double)a.rho[i] - mean);
+            bv = (PhiT)v;
+            bl += v * v;
+        } else {
+            const double vd = (double)a.c4 * ((double)a.rho[i] - mean);
+            bv = __double2ll_rn(vd * PHI_SCALE);
+            const float v = (float)vd;
+            blf += v * v;
+        }
+        __stcg(a.b + i, bv);
+    }
+    double t;
+    if constexpr (((PhiT)0.5) != 0) t = block_sum(bl, sh);
+    else t = block_sum_lanes0(warp_sum_ff_lane0(blf), sh);
+    if (threadIdx.x == 0) a.part_pois[lb] = t;
+    if (!grid_barrier(pb.barrier, gridDim.x, bar_k, pb.status)) return;
+    // every replica's source norm and activity, in every block
+    for (int r = threadIdx.x; r < pb.nrep; r += blockDim.x) {
+        const StepArgs<S, R, PhiT> &q = reps[r];
+        double v = 0.0;
+        for (int k = 0; k < pb.rep_blocks[r]; k++) v += __ldcg(q.part_pois + k);
+        const double bn = sqrt(v);
+        s_bnorm[r] = bn;
+        s_tolb[r] = q.tol * bn;
+        s_active[r] = !(q.fixed_iter <= 0 && bn == 0.0);
+        s_iters[r] = 0;
+        s_res[r] = 0.0;
+        s_conv[r] = 0;
+    }
+    __syncthreads();
+    const int hx = (g.nx + 1) >> 1;
+    const int rows = g.ny * g.nz;
+    const typename PoisUpd<PhiT>::om_t *oms = (const typename PoisUpd<PhiT>::om_t *)a.omegas;
+    for (int it = 0;; it++) {
+        // who is still sweeping: within its cap and not converged
+        if (threadIdx.x == 0) {
+            int any = 0;
+            for (int r = 0; r < pb.nrep; r++) {
+                const StepArgs<S, R, PhiT> &q = reps[r];
+                const int lim = q.fixed_iter > 0 ? q.fixed_iter : q.max_iter;
+                if (s_active[r] && it >= lim) s_active[r] = 0;
+                any |= s_active[r];
+            }
+            s_any = any;
+        }
+        __syncthreads();
+        if (!s_any) break;
+        const bool mine = s_active[rep] != 0;
+        const bool need = mine && ((a.fixed_iter <= 0 && ((it + 1) % a.check_every) == 0) ||
+                                   it + 1 == (a.fixed_iter > 0 ? a.fixed_iter : a.max_iter));
+        typename PoisUpd<PhiT>::acc_t r2 = 0;
+#pragma unroll
+        for (int colour = 0; colour < 2; colour++) {
+            if (mine) {
+                const typename PoisUpd<PhiT>::om_t omega = __ldg(oms + 2 * it + colour);
+                for (int row = lb * nwarps + warp; row < rows; row += kr * nwarps) {
+                    const int z = row / g.ny, y = row - z * g.ny;
+                    const int par = (colour + y + z) & 1;
+                    for (int xh = lane; xh < hx; xh += 32) {
+                        const int x = 2 * xh + par;
+                        if (x >= g.nx) continue;
+                        const int i = x + g.nx * row;
+                        const uint32_t m = a.mask[i];
+                        if (m & SOLID_BIT) continue;
+                        int nb[6];
+                        face_nbrs(g, x, y, z, i, nb);
+                        PhiT v[6];
+#pragma unroll
+                        for (int f = 0; f < 6; f++) v[f] = ((m >> (f + 1)) & 1u) ? (PhiT)0 : __ldcg(a.phi + nb[f]);
+                        sor_apply<PhiT>(a.phi, i, m, __ldcg(a.b + i), __ldcg(a.phi + i), v, omega, r2);
+                    }
+                }
+            }
+            if (colour == 1 && need) {
+                double wsum;
+                if constexpr (((PhiT)0.5) != 0) wsum = warp_sum((double)r2);
+                else wsum = warp_sum_ff_lane0((float)r2);
+                double tb = block_sum_lanes0(wsum, sh);
+                if (threadIdx.x == 0) a.part_pois[lb] = tb;
+            }
+            if (!grid_barrier(pb.barrier, gridDim.x, bar_k, pb.status)) return;
+        }
+        // residual tests of every replica that tests at this sweep
+        for (int r = threadIdx.x; r < pb.nrep; r += blockDim.x) {
+            if (!s_active[r]) continue;
+            const StepArgs<S, R, PhiT> &q = reps[r];
+            const int lim = q.fixed_iter > 0 ? q.fixed_iter : q.max_iter;
+            const bool test = q.fixed_iter <= 0 && ((it + 1) % q.check_every) == 0;
+            if (!test && it + 1 != lim) continue;
+            double v = 0.0;
+            for (int k = 0; k < pb.rep_blocks[r]; k++) v += __ldcg(q.part_pois + k);
+            s_res[r] = v;
+            s_iters[r] = it + 1;
+            if (test && sqrt(v) <= s_tolb[r]) {
+                s_active[r] = 0;
+                s_conv[r] = 1;
+            }
+        }
+        for (int r = threadIdx.x; r < pb.nrep; r += blockDim.x)
+            if (s_active[r]) s_iters[r] = it + 1;
+        __syncthreads();
+    }
+    if (lb == 0 && threadIdx.x == 0) {
+        const int itr = s_iters[rep];
+        *a.pois_iters = itr;
+        a.pois_total[0] += itr;
+        *a.pois_res = s_bnorm[rep] > 0 ? sqrt(s_res[rep]) / s_bnorm[rep] : 0.0;
+        if (a.fixed_iter <= 0 && !s_conv[rep] && s_bnorm[rep] > 0.0) atomicOr(a.status, ST_NOCONV);
+    }
+}
+
 template <typename PhiT> inline size_t tile_smem_bytes(int nx, const TileGeom &tg)
 {
     return (size_t)nx * (tg.ty + 4) * (tg.tz + 4) * (2 * sizeof(PhiT) + sizeof(uint32_t));
@@ -716,7 +885,7 @@ __device__ bool bead_stencil(const Grid3 &g, const int per[3], const uint32_t *m
 // bitonic sort in shared memory, unique nodes -> patch slots (ascending node
 // id), the sorted entry list with each slot's first position, and the bead
 // charge per slot summed in bead order.
-template <typename R> __global__ void __launch_bounds__(BEAD_THREADS) bead_bin_kernel(BeadArgs<R> a)
+template <typename R> __device__ void bead_bin_body(const BeadArgs<R> &a)
 {
     __shared__ unsigned long long key[MAX_ENTRIES];
     __shared__ int flag[MAX_ENTRIES];
@@ -798,6 +967,18 @@ template <typename R> __global__ void __launch_bounds__(BEAD_THREADS) bead_bin_k
         }
         a.patch_q[k] = acc;
     }
+}
+
+template <typename R> __global__ void __launch_bounds__(BEAD_THREADS) bead_bin_kernel(BeadArgs<R> a)
+{
+    bead_bin_body<R>(a);
+}
+
+template <typename R> __global__ void __launch_bounds__(BEAD_THREADS) bead_bin_batch_kernel(const BeadArgs<R> *reps)
+{
+    const BeadArgs<R> &a = reps[blockIdx.y];
+    if (a.nb == 0) return;
+    bead_bin_body<R>(a);
 }
 
 template <typename R>
@@ -1042,7 +1223,7 @@ template <typename R> struct MdThreads {
 };
 
 template <typename S, typename R, typename PhiT, bool DEV>
-__global__ void __launch_bounds__(MdThreads<R>::value) bead_md_kernel(MdArgs<S, R, PhiT, DEV> A)
+__device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
 {
     constexpr bool SERIAL = sizeof(R) == 8;
     const StepArgs<S, R, PhiT> &a = A.s;
@@ -1248,6 +1429,22 @@ __global__ void __launch_bounds__(MdThreads<R>::value) bead_md_kernel(MdArgs<S, 
     }
 }
 
+template <typename S, typename R, typename PhiT, bool DEV>
+__global__ void __launch_bounds__(MdThreads<R>::value) bead_md_kernel(MdArgs<S, R, PhiT, DEV> A)
+{
+    bead_md_body<S, R, PhiT, DEV>(A);
+}
+
+template <typename S, typename R, typename PhiT, bool DEV>
+__global__ void __launch_bounds__(MdThreads<R>::value)
+    bead_md_batch_kernel(const MdArgs<S, R, PhiT, DEV> *reps, long long step)
+{
+    MdArgs<S, R, PhiT, DEV> A = reps[blockIdx.y];
+    if (A.b.nb == 0) return;
+    A.step = step;
+    bead_md_body<S, R, PhiT, DEV>(A);
+}
+
 // ============================================================== fused LB
 // Per fluid node: pull the 3 x 19 populations (halfway bounce-back on set
 // link bits), moments (Eqs. 15-16), force per particle (Eq. 5: external,
@@ -1258,10 +1455,10 @@ __global__ void __launch_bounds__(MdThreads<R>::value) bead_md_kernel(MdArgs<S, 
 //   u* = sum n a/(1+h) / sum n/(1+h), u^a* = (a^a + h^a u*)/(1+h^a),
 //   Phi^a = G^a - omega_d^a (u^a* - u*).
 template <typename S, typename R, typename PhiT, bool DEV>
-__global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 2 : 1) lb_fused_kernel(StepArgs<S, R, PhiT> a)
+__device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long blk)
 {
     const Grid3 g = a.g;
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long i = blk * (long long)blockDim.x + threadIdx.x;
     R msum[NS] = {R(0), R(0), R(0)};
     int bad = 0, cfl = 0;
     if (i < g.N) {
@@ -1365,6 +1562,21 @@ __global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 2 : 1) lb_fused_k
         else t = warp_sum_ff((float)msum[s]);
         if ((threadIdx.x & 31) == 0) a.part_mass[(i >> 5) * NS + s] = t;
     }
+}
+
+template <typename S, typename R, typename PhiT, bool DEV>
+__global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 2 : 1) lb_fused_kernel(StepArgs<S, R, PhiT> a)
+{
+    lb_body<S, R, PhiT, DEV>(a, blockIdx.x);
+}
+
+template <typename S, typename R, typename PhiT, bool DEV>
+__global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 2 : 1)
+    lb_fused_batch_kernel(const StepArgs<S, R, PhiT> *reps)
+{
+    const StepArgs<S, R, PhiT> &a = reps[blockIdx.y];
+    if ((long long)blockIdx.x * blockDim.x >= a.g.N) return;
+    lb_body<S, R, PhiT, DEV>(a, blockIdx.x);
 }
 
 // ============================================================== outputs

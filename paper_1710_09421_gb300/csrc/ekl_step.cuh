@@ -3,19 +3,23 @@
 #pragma once
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "ekl_kernels.cuh"
 
 namespace ekl {
 
 template <typename S, typename R, typename PhiT>
-static StepArgs<S, R, PhiT> make_args(Ctx &c)
+static StepArgs<S, R, PhiT> make_args(Ctx &c, int parity = -1)
 {
     StepArgs<S, R, PhiT> a;
+    const int cur = parity < 0 ? c.cur : parity;
     a.g = Grid3{c.nx, c.ny, c.nz, c.N};
     for (int k = 0; k < 3; k++) a.per[k] = c.per[k];
     a.mask = c.mask;
-    a.fin = (const S *)c.f[c.cur];
-    a.fout = (S *)c.f[1 - c.cur];
+    a.fin = (const S *)c.f[cur];
+    a.fout = (S *)c.f[1 - cur];
     a.phi = (PhiT *)c.phi;
     a.b = (PhiT *)c.b;
     a.rho = (R *)c.rho;
@@ -76,6 +80,30 @@ template <typename R> static BeadArgs<R> make_bead_args(Ctx &c)
     b.slot_first = c.slot_first;
     b.status = c.status;
     return b;
+}
+
+template <typename S, typename R, typename PhiT, bool DEV>
+static MdArgs<S, R, PhiT, DEV> make_md_args(Ctx &c, const StepArgs<S, R, PhiT> &a, const BeadArgs<R> &ba)
+{
+    MdArgs<S, R, PhiT, DEV> md;
+    md.s = a;
+    md.b = ba;
+    md.md_substeps = c.P.md_substeps < 1 ? 1 : c.P.md_substeps;
+    md.xi = (R)c.P.bead_xi;
+    md.mass = (R)c.P.bead_mass;
+    md.bead_kT = (R)c.P.bead_kT;
+    md.bond_kind = c.P.bond_kind;
+    md.bond_k = (R)c.P.bond_k;
+    md.bond_r0 = (R)c.P.bond_r0;
+    md.bond_l0 = (R)c.P.bond_l0;
+    md.wca_eps = (R)c.P.wca_eps;
+    md.wca_sigma = (R)c.P.wca_sigma;
+    md.wall_eps = (R)c.P.wall_eps;
+    md.wall_sigma = (R)c.P.wall_sigma;
+    md.key0 = (uint32_t)c.P.seed;
+    md.key1 = (uint32_t)(c.P.seed >> 32);
+    md.step = c.step;
+    return md;
 }
 
 static inline int cuda_ok(cudaError_t e) { return e == cudaSuccess ? EKL_OK : EKL_ERR_CUDA; }
@@ -146,24 +174,7 @@ template <typename S, typename R, typename PhiT, bool DEV> int steps_impl(Ctx &c
         // 4. beads: interpolate, Langevin sub-steps, spread
         phase_begin(c, PH_MD);
         if (c.nb > 0) {
-            MdArgs<S, R, PhiT, DEV> md;
-            md.s = a;
-            md.b = ba;
-            md.md_substeps = c.P.md_substeps < 1 ? 1 : c.P.md_substeps;
-            md.xi = (R)c.P.bead_xi;
-            md.mass = (R)c.P.bead_mass;
-            md.bead_kT = (R)c.P.bead_kT;
-            md.bond_kind = c.P.bond_kind;
-            md.bond_k = (R)c.P.bond_k;
-            md.bond_r0 = (R)c.P.bond_r0;
-            md.bond_l0 = (R)c.P.bond_l0;
-            md.wca_eps = (R)c.P.wca_eps;
-            md.wca_sigma = (R)c.P.wca_sigma;
-            md.wall_eps = (R)c.P.wall_eps;
-            md.wall_sigma = (R)c.P.wall_sigma;
-            md.key0 = (uint32_t)c.P.seed;
-            md.key1 = (uint32_t)(c.P.seed >> 32);
-            md.step = c.step;
+            MdArgs<S, R, PhiT, DEV> md = make_md_args<S, R, PhiT, DEV>(c, a, ba);
             static bool attr_set = false;
             if (!attr_set) {
                 cudaFuncSetAttribute(bead_md_kernel<S, R, PhiT, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -207,6 +218,120 @@ int state_impl(Ctx &c, double *d_f, double *d_phi, int to_host)
     return cuda_ok(cudaGetLastError());
 }
 
+// ------------------------------------------------------------------ batch
+template <typename S, typename R, typename PhiT, bool DEV> int batch_tables(Batch &B)
+{
+    const int n = B.nrep;
+    std::vector<StepArgs<S, R, PhiT>> args(n);
+    std::vector<BeadArgs<R>> bargs(n);
+    std::vector<MdArgs<S, R, PhiT, DEV>> md(n);
+    for (int q = 0; q < 2; q++) {
+        for (int r = 0; r < n; r++) {
+            Ctx &c = *B.reps[r];
+            args[r] = make_args<S, R, PhiT>(c, q);
+            bargs[r] = make_bead_args<R>(c);
+            md[r] = make_md_args<S, R, PhiT, DEV>(c, args[r], bargs[r]);
+        }
+        if (cudaMemcpyAsync(B.d_args[q], args.data(), n * sizeof(args[0]), cudaMemcpyHostToDevice, B.stream) != cudaSuccess ||
+            cudaMemcpyAsync(B.d_bargs[q], bargs.data(), n * sizeof(bargs[0]), cudaMemcpyHostToDevice, B.stream) != cudaSuccess ||
+            cudaMemcpyAsync(B.d_mdargs[q], md.data(), n * sizeof(md[0]), cudaMemcpyHostToDevice, B.stream) != cudaSuccess)
+            return EKL_ERR_CUDA;
+    }
+    // Poisson blocks: at least one per replica, the rest in proportion to
+    // the replica's (fluid) node count, largest remainders first
+    const int total = B.pois_blocks;
+    std::vector<double> w(n);
+    double W = 0.0;
+    for (int r = 0; r < n; r++) {
+        w[r] = (double)(B.weight_fluid ? B.reps[r]->n_fluid : B.reps[r]->N);
+        W += w[r];
+    }
+    std::vector<int> k(n, 1);
+    int used = n;
+    std::vector<std::pair<double, int>> frac;
+    for (int r = 0; r < n; r++) {
+        double share = (total - n) * w[r] / W;
+        int extra = (int)share;
+        k[r] += extra;
+        used += extra;
+        frac.push_back({share - extra, r});
+    }
+    std::sort(frac.begin(), frac.end(), [](auto &x, auto &y) { return x.first > y.first || (x.first == y.first && x.second < y.second); });
+    for (int t = 0; used < total && t < n; t++, used++) k[frac[t].second]++;
+    std::vector<int> brep, bloc;
+    for (int r = 0; r < n; r++)
+        for (int j = 0; j < k[r]; j++) {
+            brep.push_back(r);
+            bloc.push_back(j);
+        }
+    B.pois_blocks = (int)brep.size();
+    if (cudaMemcpyAsync(B.d_block_rep, brep.data(), brep.size() * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess ||
+        cudaMemcpyAsync(B.d_block_local, bloc.data(), bloc.size() * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess ||
+        cudaMemcpyAsync(B.d_rep_blocks, k.data(), n * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess)
+        return EKL_ERR_CUDA;
+    if (cudaStreamSynchronize(B.stream) != cudaSuccess) return EKL_ERR_CUDA;
+    B.max_nb = 0;
+    B.max_lb_blocks = B.max_charge_blocks = 0;
+    for (int r = 0; r < n; r++) {
+        B.max_nb = std::max(B.max_nb, B.reps[r]->nb);
+        B.max_lb_blocks = std::max(B.max_lb_blocks, B.reps[r]->lb_blocks);
+        B.max_charge_blocks = std::max(B.max_charge_blocks, B.reps[r]->charge_blocks);
+    }
+    B.ready = 1;
+    return EKL_OK;
+}
+
+template <typename S, typename R, typename PhiT, bool DEV> int batch_impl(Batch &B, int nsteps)
+{
+    if (!B.ready) {
+        int rc = batch_tables<S, R, PhiT, DEV>(B);
+        if (rc != EKL_OK) return rc;
+    }
+    const int n = B.nrep;
+    for (int k = 0; k < nsteps; k++) {
+        const int q = B.reps[0]->cur;
+        const long long step = B.reps[0]->step;
+        if (B.max_nb > 0) {
+            bead_bin_batch_kernel<R><<<dim3(1, n), BEAD_THREADS, 0, B.stream>>>((const BeadArgs<R> *)B.d_bargs[q]);
+            B.launches++;
+        }
+        charge_batch_kernel<S, R, PhiT, DEV><<<dim3(B.max_charge_blocks, n), CHARGE_THREADS, 0, B.stream>>>(
+            (const StepArgs<S, R, PhiT> *)B.d_args[q]);
+        B.launches++;
+        cudaMemsetAsync(B.barrier, 0, 4 * sizeof(unsigned), B.stream);
+        {
+            PoisBatch pb{n, B.d_block_rep, B.d_block_local, B.d_rep_blocks, B.barrier, B.status};
+            const StepArgs<S, R, PhiT> *reps = (const StepArgs<S, R, PhiT> *)B.d_args[q];
+            void *args[] = {&reps, &pb};
+            cudaError_t e = cudaLaunchCooperativeKernel((const void *)poisson_batch_kernel<S, R, PhiT>,
+                                                        dim3(B.pois_blocks), dim3(B.pois_threads), args, 0, B.stream);
+            B.launches++;
+            if (e != cudaSuccess) return EKL_ERR_CUDA;
+        }
+        if (B.max_nb > 0) {
+            static size_t attr = 0;
+            const size_t smem = md_smem_bytes<R>(B.max_nb);
+            if (smem > attr) {
+                cudaFuncSetAttribute(bead_md_batch_kernel<S, R, PhiT, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)md_smem_bytes<R>(MAX_BEADS));
+                attr = md_smem_bytes<R>(MAX_BEADS);
+            }
+            bead_md_batch_kernel<S, R, PhiT, DEV><<<dim3(1, n), MdThreads<R>::value, smem, B.stream>>>(
+                (const MdArgs<S, R, PhiT, DEV> *)B.d_mdargs[q], step);
+            B.launches++;
+        }
+        lb_fused_batch_kernel<S, R, PhiT, DEV><<<dim3(B.max_lb_blocks, n), LB_THREADS, 0, B.stream>>>(
+            (const StepArgs<S, R, PhiT> *)B.d_args[q]);
+        B.launches++;
+        if (cudaGetLastError() != cudaSuccess) return EKL_ERR_CUDA;
+        for (int r = 0; r < n; r++) {
+            B.reps[r]->cur ^= 1;
+            B.reps[r]->step++;
+        }
+    }
+    return EKL_OK;
+}
+
 // occupancy of the cooperative Poisson kernel for this instantiation
 template <typename S, typename R, typename PhiT> int poisson_max_blocks_per_sm()
 {
@@ -231,4 +356,5 @@ template <typename S, typename R, typename PhiT> int poisson_max_blocks_per_sm()
         return state_impl<S, R, PhiT, DEV>(c, (double *)f, (double *)p, 0);                      \
     }                                                                                            \
     int pois_blocks_##SUFFIX() { return poisson_max_blocks_per_sm<S, R, PhiT>(); }                \
+    int run_batch_##SUFFIX(Batch &b, int n) { return batch_impl<S, R, PhiT, DEV>(b, n); }         \
     }

@@ -151,27 +151,28 @@ def wall_nodes_touching_fluid(solid, periodic):
 # polymer chains
 # ----------------------------------------------------------------------------
 
+_OFFS = np.array([(dx, dy, dz) for dz in range(-3, 4) for dy in range(-3, 4) for dx in range(-3, 4)])
+
+
 def _min_dist_to_solid(p, solid, periodic, reach=3):
+    """Distance from p to the nearest wall node (or closed-box outside) within
+    `reach` nodes; 1e30 when there is none."""
     nz, ny, nx = solid.shape
-    best = 1e30
+    dims = np.array([nx, ny, nz])
     base = np.floor(p).astype(int)
-    dims = (nx, ny, nz)
-    for dz in range(-reach, reach + 1):
-        for dy in range(-reach, reach + 1):
-            for dx in range(-reach, reach + 1):
-                q = base + np.array([dx, dy, dz])
-                ok = True
-                for a in range(3):
-                    if periodic[a]:
-                        q[a] %= dims[a]
-                    elif q[a] < 0 or q[a] >= dims[a]:
-                        ok = False
-                if ok and not solid[q[2], q[1], q[0]]:
-                    continue
-                node = base + np.array([dx, dy, dz])
-                d = np.linalg.norm(p - node)
-                best = min(best, d)
-    return best
+    nodes = base[None, :] + _OFFS
+    q = nodes.copy()
+    inside = np.ones(len(q), bool)
+    for a in range(3):
+        if periodic[a]:
+            q[:, a] %= dims[a]
+        else:
+            inside &= (q[:, a] >= 0) & (q[:, a] < dims[a])
+    qc = np.clip(q, 0, dims - 1)
+    wall = ~inside | (solid[qc[:, 2], qc[:, 1], qc[:, 0]] == 1)
+    if not wall.any():
+        return 1e30
+    return float(np.min(np.linalg.norm(p[None, :] - nodes[wall], axis=1)))
 
 
 def threaded_chain(n, center, bond, solid, periodic, rng, straight_zone, wall_clear=1.2,
@@ -199,6 +200,8 @@ def threaded_chain(n, center, bond, solid, periodic, rng, straight_zone, wall_cl
                 if attempt > 200:
                     kick *= 1.5
                 nd = d + kick * rng.standard_normal(3)
+                if attempt > 500:  # crowded: any direction
+                    nd = rng.standard_normal(3)
                 nd /= np.linalg.norm(nd)
                 cand = prev + bond * nd
                 w = [cand[a] % dims[a] if periodic[a] else cand[a] for a in range(3)]
@@ -335,3 +338,28 @@ def small_pore(nx=40, ny=24, nz=36, membrane=(16, 19), radius=4.0, n_beads=8,
     """A small pore box with ragged extents (x not a multiple of the tile width)."""
     return translocation(nx=nx, ny=ny, nz=nz, membrane=membrane, radius=radius,
                          n_beads=n_beads, precision=precision, **kw)
+
+
+def replica_set(n_rep=96, seed=1000, sizes_xy=(48, 64, 96), sizes_z=(96, 128, 192),
+                radius=(3.0, 8.0), beads=(16, 128), salt=(0.002, 0.02), E_z=5e-3,
+                membrane_thickness=8, precision="f32"):
+    """Independent translocation pores of uneven size: each replica draws its
+    box from sizes_xy^2 x sizes_z, a pore radius, a chain length and a salt
+    concentration (seeded), with its own seeds; membrane of the given
+    thickness centred in z."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(n_rep):
+        L = int(rng.choice(sizes_xy))
+        Lz = int(rng.choice(sizes_z))
+        R = float(rng.uniform(*radius))
+        nb = int(rng.integers(beads[0], beads[1] + 1))
+        c0 = float(rng.uniform(*salt))
+        zc = Lz // 2
+        mem = (zc - membrane_thickness // 2, zc + membrane_thickness // 2 - 1)
+        wl = translocation(nx=L, ny=L, nz=Lz, membrane=mem, radius=R, salt=c0, n_beads=nb,
+                           E=(0.0, 0.0, E_z), precision=precision, seed_init=seed + r,
+                           seed_chain=seed + 5000 + r, seed_noise=seed + 10000 + r)
+        wl.name = f"rep{r}_{L}x{L}x{Lz}_r{R:.1f}_N{nb}"
+        out.append(wl)
+    return out

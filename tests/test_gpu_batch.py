@@ -1,0 +1,49 @@
+"""Batched replicas: every replica of a batch evolves exactly as the same
+workload run on its own handle (equal sweep counts), and a tolerance-based
+batch converges each replica to its own tolerance."""
+import numpy as np
+import pytest
+
+import paper_1710_09421_gb300 as E
+from paper_1710_09421_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _uneven(fixed):
+    wls = [W.small_pore(nx=20, ny=16, nz=24, membrane=(10, 13), radius=3.0, n_beads=4),
+           W.small_pore(nx=24, ny=20, nz=28, membrane=(12, 15), radius=4.0, n_beads=6, seed_noise=7),
+           W.small_pore(nx=16, ny=16, nz=20, membrane=(8, 11), radius=3.0, n_beads=0, seed_init=9)]
+    return [w.replace(poisson_fixed_iter=fixed) for w in wls]
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_batch_replicas_bitwise_equal_single_runs(precision):
+    wls = _uneven(40)
+    batch = E.Batch(wls, precision=precision)
+    assert batch.step(15) >= 0
+    for r, wl in enumerate(wls):
+        sim = E.Simulation(wl, precision=precision)
+        sim.step(15)
+        a, b = sim.get_state(), batch.reps[r].get_state()
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), r
+        fa, fb = sim.fields(("R", "V")), batch.reps[r].fields(("R", "V"))
+        assert np.array_equal(fa["R"], fb["R"]), r
+        sim.close()
+    batch.close()
+
+
+def test_batch_tolerance_and_autotune():
+    wls = [w.replace(poisson_tol=1e-9) for w in _uneven(0)]
+    batch = E.Batch(wls)
+    choice = batch.autotune(1)
+    assert 0 <= choice < 4
+    assert batch.step(5) >= 0
+    for r in range(len(wls)):
+        st = batch.reps[r].stats()
+        assert st["poisson_res"] <= 1e-9 and st["poisson_iters"] > 0
+    # one launch per phase per step for the whole batch (5 phases)
+    l0 = batch.launches()
+    batch.step(3)
+    assert batch.launches() - l0 == 3 * 5
+    batch.close()
