@@ -322,8 +322,11 @@ def config_slit_fp64():
 
 
 def config_pore_fp32():
-    """64x64x128 pore of radius 4, N=32, FP32, SOR to 1e-8 (the timed workload)."""
-    return translocation()
+    """64x64x128 pore of radius 4, N=32, FP32, SOR to 1e-8 (the timed workload).
+    Solver knobs: Chebyshev spectral radius 0.9999 (fastest in a scan of the
+    pore: 584 sweeps/step against 1136 at the slowest-box-mode default) and a
+    residual test every 4 sweeps."""
+    return translocation().replace(rho_jacobi=0.9999, poisson_check_every=4)
 
 
 def config_precision_sweep(precision="f32"):
