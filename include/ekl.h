@@ -222,6 +222,30 @@ int64_t ekl_batch_launches(ekl_batch *b);
 void ekl_batch_destroy(ekl_batch *b);
 
 /* ---------------------------------------------------------------------------
+ * Learned warm start of the Poisson solve (not in the paper): a 3D
+ * convolutional network, 3^3 kernels, channels 2 -> 16 -> 16 -> 16 -> 1, ReLU
+ * between layers, linear output, mapping (change of the Poisson source,
+ * previous potential) to the change of the potential.  Parameters are one
+ * FP32 vector of EKL_NET_PARAMS values, per layer W[co][ci][k] then b[co],
+ * k = (dz+1)*9 + (dy+1)*3 + (dx+1).  Inputs x[2][N] (channel-major), output
+ * y[N]; periodic wrap on periodic axes, zeros beyond closed ones.  The two
+ * 16 -> 16 layers run as BF16 implicit GEMMs on tensor cores with FP32
+ * accumulation.  All pointers are host memory. */
+#define EKL_NET_PARAMS 15169
+int ekl_net_eval(const int32_t dims[3], const int32_t periodic[3], const float *x, const float *w,
+                 float *y);
+/* mean squared error over mask (NULL = all nodes) and its gradient [EKL_NET_PARAMS] */
+int ekl_net_loss_grad(const int32_t dims[3], const int32_t periodic[3], const float *x,
+                      const float *target, const uint8_t *mask, const float *w, double *loss,
+                      float *grad);
+/* Adam training on nsamples crops (closed boundaries): x[s][2][N], target[s][N],
+ * mask[N] selects the nodes whose receptive field lies inside the crop;
+ * w is read and written; loss_out[iters] (may be NULL). */
+int ekl_net_train(int32_t nsamples, const int32_t dims[3], const float *x, const float *target,
+                  const uint8_t *mask, float *w, int32_t iters, int32_t batch, float lr,
+                  uint64_t seed, float *loss_out);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free field read-back.  The paper has no counterpart: this entry
  * serves callers that may not allocate GPU memory while they run (code
  * running between capture and replay of a CUDA graph on a pool-allocated

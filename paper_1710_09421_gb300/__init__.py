@@ -132,6 +132,10 @@ def load(build_if_missing: bool = True):
         L.ekl_batch_launches.restype = C.c_int64
         L.ekl_batch_destroy.argtypes = [vp]
         L.ekl_batch_destroy.restype = None
+        L.ekl_net_eval.argtypes = [vp, vp, vp, vp, vp]
+        L.ekl_net_loss_grad.argtypes = [vp, vp, vp, vp, vp, vp, C.POINTER(C.c_double), vp]
+        L.ekl_net_train.argtypes = [C.c_int32, vp, vp, vp, vp, vp, C.c_int32, C.c_int32, C.c_float,
+                                    C.c_uint64, vp]
         if L.ekl_sizeof_params() != C.sizeof(ekl_params):
             raise RuntimeError("ekl_params layout of the binding does not match the library")
         _lib = L
@@ -454,3 +458,47 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ warm-start network
+EKL_NET_PARAMS = 15169
+
+
+def _i3(v):
+    return np.ascontiguousarray(v, np.int32)
+
+
+def ekl_net_eval(dims, periodic, x, w):
+    """dims = (nx, ny, nz); x[2][nz][ny][nx]; returns y[nz][ny][nx]."""
+    d, p = _i3(dims), _i3(periodic)
+    x = np.ascontiguousarray(x, np.float32)
+    w = np.ascontiguousarray(w, np.float32)
+    y = np.zeros(x.shape[1:], np.float32)
+    _check(load().ekl_net_eval(_ptr(d), _ptr(p), _ptr(x), _ptr(w), _ptr(y)), "ekl_net_eval")
+    return y
+
+
+def ekl_net_loss_grad(dims, periodic, x, target, mask, w):
+    d, p = _i3(dims), _i3(periodic)
+    x = np.ascontiguousarray(x, np.float32)
+    t = np.ascontiguousarray(target, np.float32)
+    m = None if mask is None else np.ascontiguousarray(mask, np.uint8)
+    w = np.ascontiguousarray(w, np.float32)
+    g = np.zeros(EKL_NET_PARAMS, np.float32)
+    loss = C.c_double(0)
+    _check(load().ekl_net_loss_grad(_ptr(d), _ptr(p), _ptr(x), _ptr(t), _ptr(m), _ptr(w),
+                                     C.byref(loss), _ptr(g)), "ekl_net_loss_grad")
+    return loss.value, g
+
+
+def ekl_net_train(dims, x, target, mask, w, iters, batch=4, lr=1e-3, seed=0):
+    """x[S][2][...], target[S][...]; returns (trained w, per-iteration loss)."""
+    d = _i3(dims)
+    x = np.ascontiguousarray(x, np.float32)
+    t = np.ascontiguousarray(target, np.float32)
+    m = None if mask is None else np.ascontiguousarray(mask, np.uint8)
+    w = np.ascontiguousarray(w, np.float32).copy()
+    curve = np.zeros(iters, np.float32)
+    _check(load().ekl_net_train(len(x), _ptr(d), _ptr(x), _ptr(t), _ptr(m), _ptr(w), int(iters),
+                                int(batch), float(lr), int(seed), _ptr(curve)), "ekl_net_train")
+    return w, curve

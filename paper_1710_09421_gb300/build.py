@@ -26,6 +26,7 @@ UNITS = {
     "ekl_inst_f32.cu": [],
     "ekl_inst_lp.cu": [],
     "ekl_noalloc.cu": [],
+    "ekl_net.cu": [],
 }
 
 

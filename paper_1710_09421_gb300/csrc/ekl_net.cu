@@ -1,0 +1,578 @@
+// Learned warm start for the Poisson solve: a 3D convolutional network
+// (3^3 kernels, channels 2 -> 16 -> 16 -> 16 -> 1, ReLU between layers,
+// linear output) mapping the step's change of the Poisson source and the
+// previous potential to the change of the potential.  The solver then runs to
+// its usual residual from the improved start, so only iterations are saved.
+//
+// Layout: activations node-major, 16 channels contiguous (NDHWC) in BF16;
+// parameters as one FP32 vector, per layer W[co][ci][k] then b[co] with
+// k = (dz+1)*9 + (dy+1)*3 + (dx+1); periodic wrap on periodic axes, zeros
+// beyond closed ones.
+//
+// The two 16 -> 16 layers (about 93 % of the arithmetic) are implicit GEMMs
+// on the tensor cores: per warp 16 nodes x 16 output channels, K = 27 offsets
+// x 16 input channels, BF16 operands, FP32 accumulation (mma.sync m16n8k16);
+// the data gradient of those layers is the same kernel with flipped offsets
+// and transposed channels.  The 2 -> 16 and 16 -> 1 layers, the weight
+// gradients (per-block partial sums reduced in a fixed order) and Adam run on
+// the CUDA cores in FP32.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
+
+#include "ekl_kernels.cuh"
+
+namespace {
+
+using namespace ekl;
+
+constexpr int C = 16;     // hidden channels
+constexpr int K27 = 27;
+constexpr int NT = 256;   // threads per block of the CUDA-core kernels
+// parameter offsets
+constexpr int OW1 = 0, OB1 = OW1 + 16 * 2 * 27, OW2 = OB1 + 16, OB2 = OW2 + 16 * 16 * 27,
+              OW3 = OB2 + 16, OB3 = OW3 + 16 * 16 * 27, OW4 = OB3 + 16, OB4 = OW4 + 16 * 27,
+              NPARAM = OB4 + 1;
+static_assert(NPARAM == EKL_NET_PARAMS, "parameter count");
+
+struct NetGrid {
+    int nx, ny, nz;
+    int per[3];
+    int N;
+};
+
+// neighbour of node (x,y,z) at offset k; -1 beyond a closed face
+__device__ __forceinline__ int nbr_off(const NetGrid &g, int x, int y, int z, int k)
+{
+    int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+    int X = x + dx, Y = y + dy, Z = z + dz;
+    if (X < 0 || X >= g.nx) {
+        if (!g.per[0]) return -1;
+        X = X < 0 ? X + g.nx : X - g.nx;
+    }
+    if (Y < 0 || Y >= g.ny) {
+        if (!g.per[1]) return -1;
+        Y = Y < 0 ? Y + g.ny : Y - g.ny;
+    }
+    if (Z < 0 || Z >= g.nz) {
+        if (!g.per[2]) return -1;
+        Z = Z < 0 ? Z + g.nz : Z - g.nz;
+    }
+    return X + g.nx * (Y + g.ny * Z);
+}
+
+__device__ __forceinline__ void xyz_of(const NetGrid &g, int n, int &x, int &y, int &z)
+{
+    int r = n / g.nx;
+    x = n - r * g.nx;
+    z = r / g.ny;
+    y = r - z * g.ny;
+}
+
+// ---------------------------------------------------------------- layer 1
+// act1[n][co] = relu(b1[co] + sum_k sum_ci W1[co][ci][k] x[ci][n + off_k])
+__global__ void __launch_bounds__(NT) l1_fwd(NetGrid g, const float *__restrict__ x, const float *__restrict__ w,
+                                             __nv_bfloat16 *__restrict__ act)
+{
+    __shared__ float sw[16 * 2 * 27 + 16];
+    for (int t = threadIdx.x; t < 16 * 2 * 27 + 16; t += blockDim.x) sw[t] = w[OW1 + t];
+    __syncthreads();
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.N) return;
+    int X, Y, Z;
+    xyz_of(g, n, X, Y, Z);
+    float acc[16];
+    for (int c = 0; c < 16; c++) acc[c] = sw[16 * 54 + c];
+    for (int k = 0; k < K27; k++) {
+        const int j = nbr_off(g, X, Y, Z, k);
+        if (j < 0) continue;
+        const float x0 = x[j], x1 = x[g.N + j];
+        for (int c = 0; c < 16; c++) acc[c] += sw[c * 54 + k] * x0 + sw[c * 54 + 27 + k] * x1;
+    }
+    for (int c = 0; c < 16; c += 2) {
+        __nv_bfloat162 v = __floats2bfloat162_rn(fmaxf(acc[c], 0.f), fmaxf(acc[c + 1], 0.f));
+        *(__nv_bfloat162 *)(act + (size_t)n * 16 + c) = v;
+    }
+}
+
+// ---------------------------------------------------------------- 16 -> 16 on tensor cores
+__device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// out[n][co] = act?(bias[co] + sum_k sum_ci Wt[k][co][ci] in[n + off_k][ci]); flip = use -off_k.
+// Wt is BF16 [27][16 co][16 ci] (ci contiguous).  One warp: 16 consecutive nodes.
+template <bool RELU, bool OUT_F32>
+__global__ void __launch_bounds__(256) conv16_mma(NetGrid g, const __nv_bfloat16 *__restrict__ in,
+                                                  const __nv_bfloat16 *__restrict__ Wt,
+                                                  const float *__restrict__ bias, int flip, void *out,
+                                                  const __nv_bfloat16 *__restrict__ relu_mask_src)
+{
+    __shared__ uint32_t sW[27 * 16 * 8];  // [k][co][ci pair]
+    for (int t = threadIdx.x; t < 27 * 16 * 8; t += blockDim.x) sW[t] = ((const uint32_t *)Wt)[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n0 = warp_global * 16;
+    if (n0 >= g.N) return;
+    const int na = n0 + gid, nb = n0 + gid + 8;
+    int xa, ya, za, xb, yb, zb;
+    xyz_of(g, na < g.N ? na : 0, xa, ya, za);
+    xyz_of(g, nb < g.N ? nb : 0, xb, yb, zb);
+    float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    const uint32_t *in32 = (const uint32_t *)in;
+    for (int k = 0; k < K27; k++) {
+        const int kk = flip ? 26 - k : k;
+        const int ja = na < g.N ? nbr_off(g, xa, ya, za, kk) : -1;
+        const int jb = nb < g.N ? nbr_off(g, xb, yb, zb, kk) : -1;
+        uint32_t a[4];
+        a[0] = ja >= 0 ? in32[(size_t)ja * 8 + tig] : 0u;
+        a[1] = jb >= 0 ? in32[(size_t)jb * 8 + tig] : 0u;
+        a[2] = ja >= 0 ? in32[(size_t)ja * 8 + tig + 4] : 0u;
+        a[3] = jb >= 0 ? in32[(size_t)jb * 8 + tig + 4] : 0u;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int co = h * 8 + gid;
+            uint32_t b[2] = {sW[(k * 16 + co) * 8 + tig], sW[(k * 16 + co) * 8 + tig + 4]};
+            mma_bf16(d[h], a, b);
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int co = h * 8 + 2 * tig;
+        float v[4] = {d[h][0], d[h][1], d[h][2], d[h][3]};
+        if (bias) {
+            v[0] += bias[co];
+            v[1] += bias[co + 1];
+            v[2] += bias[co];
+            v[3] += bias[co + 1];
+        }
+        if (RELU)
+            for (int q = 0; q < 4; q++) v[q] = fmaxf(v[q], 0.f);
+        // gradient through the ReLU of the layer that produced `relu_mask_src`
+        if (relu_mask_src) {
+            if (na < g.N) {
+                if (!(__bfloat162float(relu_mask_src[(size_t)na * 16 + co]) > 0.f)) v[0] = 0.f;
+                if (!(__bfloat162float(relu_mask_src[(size_t)na * 16 + co + 1]) > 0.f)) v[1] = 0.f;
+            }
+            if (nb < g.N) {
+                if (!(__bfloat162float(relu_mask_src[(size_t)nb * 16 + co]) > 0.f)) v[2] = 0.f;
+                if (!(__bfloat162float(relu_mask_src[(size_t)nb * 16 + co + 1]) > 0.f)) v[3] = 0.f;
+            }
+        }
+        if (OUT_F32) {
+            float *o = (float *)out;
+            if (na < g.N) { o[(size_t)na * 16 + co] = v[0]; o[(size_t)na * 16 + co + 1] = v[1]; }
+            if (nb < g.N) { o[(size_t)nb * 16 + co] = v[2]; o[(size_t)nb * 16 + co + 1] = v[3]; }
+        } else {
+            __nv_bfloat16 *o = (__nv_bfloat16 *)out;
+            if (na < g.N) *(__nv_bfloat162 *)(o + (size_t)na * 16 + co) = __floats2bfloat162_rn(v[0], v[1]);
+            if (nb < g.N) *(__nv_bfloat162 *)(o + (size_t)nb * 16 + co) = __floats2bfloat162_rn(v[2], v[3]);
+        }
+    }
+}
+
+// BF16 B-operand tables of a 16->16 layer: forward Wt[k][co][ci] = W[co][ci][k];
+// data gradient Wb[k][ci][co] = W[co][ci][k] (used with flipped offsets).
+__global__ void prep_w16(const float *__restrict__ w, int ow, __nv_bfloat16 *__restrict__ Wf, __nv_bfloat16 *__restrict__ Wb)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 27 * 16 * 16) return;
+    int k = t / 256, r = t % 256, co = r / 16, ci = r % 16;
+    float v = w[ow + (co * 16 + ci) * 27 + k];
+    Wf[(k * 16 + co) * 16 + ci] = __float2bfloat16_rn(v);
+    Wb[(k * 16 + ci) * 16 + co] = __float2bfloat16_rn(v);
+}
+
+// ---------------------------------------------------------------- layer 4
+__global__ void __launch_bounds__(NT) l4_fwd(NetGrid g, const __nv_bfloat16 *__restrict__ act, const float *__restrict__ w,
+                                             float *__restrict__ y)
+{
+    __shared__ float sw[16 * 27 + 1];
+    for (int t = threadIdx.x; t < 16 * 27 + 1; t += blockDim.x) sw[t] = w[OW4 + t];
+    __syncthreads();
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.N) return;
+    int X, Y, Z;
+    xyz_of(g, n, X, Y, Z);
+    float acc = sw[16 * 27];
+    for (int k = 0; k < K27; k++) {
+        const int j = nbr_off(g, X, Y, Z, k);
+        if (j < 0) continue;
+        const __nv_bfloat162 *a = (const __nv_bfloat162 *)(act + (size_t)j * 16);
+        for (int c = 0; c < 8; c++) {
+            float2 v = __bfloat1622float2(a[c]);
+            acc += sw[(2 * c) * 27 + k] * v.x + sw[(2 * c + 1) * 27 + k] * v.y;
+        }
+    }
+    y[n] = acc;
+}
+
+// loss gradient g = 2 (y - t) / cnt on masked nodes; per-block loss partials
+__global__ void __launch_bounds__(NT) loss_grad_k(int N, const float *y, const float *t, const uint8_t *mask, float inv_cnt,
+                                                  float *g, double *part)
+{
+    __shared__ double sh[NT / 32];
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.f;
+    if (n < N) {
+        float d = (mask == nullptr || mask[n]) ? y[n] - t[n] : 0.f;
+        g[n] = 2.f * d * inv_cnt;
+        l = d * d;
+    }
+    double s = block_sum((double)l, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// d_act3[m][ci] = relu'(act3) * sum_k W4[ci][k] g[m - off_k]  (BF16 out)
+__global__ void __launch_bounds__(NT) l4_bwd_data(NetGrid g, const float *__restrict__ gy, const float *__restrict__ w,
+                                                  const __nv_bfloat16 *__restrict__ act3, __nv_bfloat16 *__restrict__ dz)
+{
+    __shared__ float sw[16 * 27];
+    for (int t = threadIdx.x; t < 16 * 27; t += blockDim.x) sw[t] = w[OW4 + t];
+    __syncthreads();
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= g.N) return;
+    int X, Y, Z;
+    xyz_of(g, m, X, Y, Z);
+    float acc[16];
+    for (int c = 0; c < 16; c++) acc[c] = 0.f;
+    for (int k = 0; k < K27; k++) {
+        const int j = nbr_off(g, X, Y, Z, 26 - k);  // m - off_k
+        if (j < 0) continue;
+        const float gv = gy[j];
+        for (int c = 0; c < 16; c++) acc[c] += sw[c * 27 + k] * gv;
+    }
+    for (int c = 0; c < 16; c += 2) {
+        float v0 = __bfloat162float(act3[(size_t)m * 16 + c]) > 0.f ? acc[c] : 0.f;
+        float v1 = __bfloat162float(act3[(size_t)m * 16 + c + 1]) > 0.f ? acc[c + 1] : 0.f;
+        *(__nv_bfloat162 *)(dz + (size_t)m * 16 + c) = __floats2bfloat162_rn(v0, v1);
+    }
+}
+
+// ---------------------------------------------------------------- weight gradients
+// Per-block partials of dW[co][ci][k] = sum_n dz[n][co] a[ci][n + off_k] and
+// db[co] = sum_n dz[n][co], for CI input channels stored either as BF16
+// node-major [n][16] (hidden) or FP32 channel-major [ci][N] (network input),
+// CO output channels stored as BF16 [n][16] or FP32 [N] (CO = 1).
+template <int CI, int CO>
+__global__ void __launch_bounds__(NT) wgrad_partial(NetGrid g, const void *a_in, int a_bf16, const void *dz, int dz_bf16,
+                                                    float *part)
+{
+    constexpr int NW = CO * CI * 27 + CO;
+    constexpr int CH = 16;  // nodes per shared-memory chunk
+    __shared__ float sa[CH][CI][27];
+    __shared__ float sd[CH][CO];
+    float acc[(NW + NT - 1) / NT];
+    for (int q = 0; q < (NW + NT - 1) / NT; q++) acc[q] = 0.f;
+    const int base = blockIdx.x * 512;
+    for (int chunk = 0; chunk < 512; chunk += CH) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < CH * CI * 27; t += blockDim.x) {
+            int nn = t / (CI * 27), r = t % (CI * 27), ci = r / 27, k = r % 27;
+            int n = base + chunk + nn;
+            float v = 0.f;
+            if (n < g.N) {
+                int X, Y, Z;
+                xyz_of(g, n, X, Y, Z);
+                int j = nbr_off(g, X, Y, Z, k);
+                if (j >= 0)
+                    v = a_bf16 ? __bfloat162float(((const __nv_bfloat16 *)a_in)[(size_t)j * 16 + ci])
+                               : ((const float *)a_in)[(size_t)ci * g.N + j];
+            }
+            sa[nn][ci][k] = v;
+        }
+        for (int t = threadIdx.x; t < CH * CO; t += blockDim.x) {
+            int nn = t / CO, co = t % CO, n = base + chunk + nn;
+            float v = 0.f;
+            if (n < g.N)
+                v = dz_bf16 ? __bfloat162float(((const __nv_bfloat16 *)dz)[(size_t)n * 16 + co])
+                            : ((const float *)dz)[n];
+            sd[nn][co] = v;
+        }
+        __syncthreads();
+        for (int q = 0; q < (NW + NT - 1) / NT; q++) {
+            int wi = q * NT + threadIdx.x;
+            if (wi >= NW) break;
+            float s = 0.f;
+            if (wi < CO * CI * 27) {
+                int co = wi / (CI * 27), r = wi % (CI * 27), ci = r / 27, k = r % 27;
+                for (int nn = 0; nn < CH; nn++) s += sd[nn][co] * sa[nn][ci][k];
+            } else {
+                int co = wi - CO * CI * 27;
+                for (int nn = 0; nn < CH; nn++) s += sd[nn][co];
+            }
+            acc[q] += s;
+        }
+    }
+    for (int q = 0; q < (NW + NT - 1) / NT; q++) {
+        int wi = q * NT + threadIdx.x;
+        if (wi < NW) part[(size_t)blockIdx.x * NW + wi] = acc[q];
+    }
+}
+
+// grad[o + i] += sum over blocks (fixed order) of part[b][i]
+__global__ void reduce_partials(const float *part, int nblocks, int nw, float *grad, int o)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nw) return;
+    float s = 0.f;
+    for (int b = 0; b < nblocks; b++) s += part[(size_t)b * nw + i];
+    grad[o + i] += s;
+}
+
+// Adam (Kingma & Ba) on the FP32 master parameters
+__global__ void adam_k(int n, float *w, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,
+                       float c1, float c2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float gi = g[i];
+    m[i] = b1 * m[i] + (1.f - b1) * gi;
+    v[i] = b2 * v[i] + (1.f - b2) * gi * gi;
+    w[i] -= lr * (m[i] / c1) / (sqrtf(v[i] / c2) + eps);
+}
+
+// ---------------------------------------------------------------- host side
+struct NetWork {
+    NetGrid g;
+    float *x = nullptr;         // [2][N]
+    __nv_bfloat16 *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *dz = nullptr, *dz2 = nullptr;
+    float *y = nullptr, *gy = nullptr;
+    float *w = nullptr, *grad = nullptr;
+    __nv_bfloat16 *W2f = nullptr, *W2b = nullptr, *W3f = nullptr, *W3b = nullptr;
+    float *part = nullptr;
+    double *lpart = nullptr;
+    size_t part_floats = 0;
+    int cap = 0;
+};
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? EKL_OK : EKL_ERR_CUDA; }
+
+int work_alloc(NetWork &W, int N)
+{
+    if (N <= W.cap) return EKL_OK;
+    cudaFree(W.x); cudaFree(W.a1); cudaFree(W.a2); cudaFree(W.a3); cudaFree(W.dz); cudaFree(W.dz2);
+    cudaFree(W.y); cudaFree(W.gy); cudaFree(W.part); cudaFree(W.lpart);
+    const int nblk_w = (N + 511) / 512;
+    W.part_floats = (size_t)nblk_w * (16 * 16 * 27 + 16);
+    cudaError_t e = cudaMalloc(&W.x, 2 * (size_t)N * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&W.a1, (size_t)N * 32);
+    if (e == cudaSuccess) e = cudaMalloc(&W.a2, (size_t)N * 32);
+    if (e == cudaSuccess) e = cudaMalloc(&W.a3, (size_t)N * 32);
+    if (e == cudaSuccess) e = cudaMalloc(&W.dz, (size_t)N * 32);
+    if (e == cudaSuccess) e = cudaMalloc(&W.dz2, (size_t)N * 32);
+    if (e == cudaSuccess) e = cudaMalloc(&W.y, (size_t)N * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&W.gy, (size_t)N * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&W.part, W.part_floats * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&W.lpart, ((N + NT - 1) / NT) * sizeof(double));
+    if (!W.w) {
+        if (e == cudaSuccess) e = cudaMalloc(&W.w, NPARAM * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&W.grad, NPARAM * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&W.W2f, 27 * 256 * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&W.W2b, 27 * 256 * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&W.W3f, 27 * 256 * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&W.W3b, 27 * 256 * 2);
+    }
+    if (e != cudaSuccess) return EKL_ERR_ALLOC;
+    W.cap = N;
+    return EKL_OK;
+}
+
+void work_free(NetWork &W)
+{
+    cudaFree(W.x); cudaFree(W.a1); cudaFree(W.a2); cudaFree(W.a3); cudaFree(W.dz); cudaFree(W.dz2);
+    cudaFree(W.y); cudaFree(W.gy); cudaFree(W.part); cudaFree(W.lpart); cudaFree(W.w); cudaFree(W.grad);
+    cudaFree(W.W2f); cudaFree(W.W2b); cudaFree(W.W3f); cudaFree(W.W3b);
+    W = NetWork();
+}
+
+// forward pass on W.x with the parameters in W.w; output in W.y
+void net_forward(NetWork &W, cudaStream_t s)
+{
+    const NetGrid &g = W.g;
+    prep_w16<<<27, 256, 0, s>>>(W.w, OW2, W.W2f, W.W2b);
+    prep_w16<<<27, 256, 0, s>>>(W.w, OW3, W.W3f, W.W3b);
+    const int bn = (g.N + NT - 1) / NT;
+    const int bm = (g.N + 127) / 128;  // 8 warps x 16 nodes per block
+    l1_fwd<<<bn, NT, 0, s>>>(g, W.x, W.w, W.a1);
+    conv16_mma<true, false><<<bm, 256, 0, s>>>(g, W.a1, W.W2f, W.w + OB2, 0, W.a2, nullptr);
+    conv16_mma<true, false><<<bm, 256, 0, s>>>(g, W.a2, W.W3f, W.w + OB3, 0, W.a3, nullptr);
+    l4_fwd<<<bn, NT, 0, s>>>(g, W.a3, W.w, W.y);
+}
+
+// loss and gradient (W.grad) for target t and mask on W.x
+int net_backward(NetWork &W, const float *d_t, const uint8_t *d_mask, float inv_cnt, double *loss, cudaStream_t s)
+{
+    const NetGrid &g = W.g;
+    const int bn = (g.N + NT - 1) / NT;
+    const int bm = (g.N + 127) / 128;
+    const int bw = (g.N + 511) / 512;
+    loss_grad_k<<<bn, NT, 0, s>>>(g.N, W.y, d_t, d_mask, inv_cnt, W.gy, W.lpart);
+    // layer 4
+    wgrad_partial<16, 1><<<bw, NT, 0, s>>>(g, W.a3, 1, W.gy, 0, W.part);
+    reduce_partials<<<(16 * 27 + 1 + 255) / 256, 256, 0, s>>>(W.part, bw, 16 * 27 + 1, W.grad, OW4);
+    l4_bwd_data<<<bn, NT, 0, s>>>(g, W.gy, W.w, W.a3, W.dz);
+    // layer 3: dz holds d z3 (through relu of a3)
+    wgrad_partial<16, 16><<<bw, NT, 0, s>>>(g, W.a2, 1, W.dz, 1, W.part);
+    reduce_partials<<<(16 * 16 * 27 + 16 + 255) / 256, 256, 0, s>>>(W.part, bw, 16 * 16 * 27 + 16, W.grad, OW3);
+    conv16_mma<false, false><<<bm, 256, 0, s>>>(g, W.dz, W.W3b, nullptr, 1, W.dz2, W.a2);
+    // layer 2
+    wgrad_partial<16, 16><<<bw, NT, 0, s>>>(g, W.a1, 1, W.dz2, 1, W.part);
+    reduce_partials<<<(16 * 16 * 27 + 16 + 255) / 256, 256, 0, s>>>(W.part, bw, 16 * 16 * 27 + 16, W.grad, OW2);
+    conv16_mma<false, false><<<bm, 256, 0, s>>>(g, W.dz2, W.W2b, nullptr, 1, W.dz, W.a1);
+    // layer 1
+    wgrad_partial<2, 16><<<bw, NT, 0, s>>>(g, W.x, 0, W.dz, 1, W.part);
+    reduce_partials<<<(16 * 2 * 27 + 16 + 255) / 256, 256, 0, s>>>(W.part, bw, 16 * 2 * 27 + 16, W.grad, OW1);
+    if (loss) {
+        std::vector<double> lp(bn);
+        cudaError_t e = cudaMemcpyAsync(lp.data(), W.lpart, bn * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return EKL_ERR_CUDA;
+        double t = 0;
+        for (int b = 0; b < bn; b++) t += lp[b];
+        *loss = t * inv_cnt;
+    }
+    return cuda_err(cudaGetLastError());
+}
+
+NetGrid make_grid(const int32_t dims[3], const int32_t periodic[3])
+{
+    NetGrid g;
+    g.nx = dims[0];
+    g.ny = dims[1];
+    g.nz = dims[2];
+    for (int a = 0; a < 3; a++) g.per[a] = periodic ? (periodic[a] ? 1 : 0) : 0;
+    g.N = g.nx * g.ny * g.nz;
+    return g;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ekl_net_eval(const int32_t dims[3], const int32_t periodic[3], const float *x, const float *w, float *y)
+{
+    if (!dims || !x || !w || !y || dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return EKL_ERR_ARG;
+    NetWork W;
+    W.g = make_grid(dims, periodic);
+    int rc = work_alloc(W, W.g.N);
+    if (rc != EKL_OK) { work_free(W); return rc; }
+    cudaError_t e = cudaMemcpy(W.x, x, 2 * (size_t)W.g.N * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(W.w, w, NPARAM * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        net_forward(W, 0);
+        e = cudaMemcpy(y, W.y, (size_t)W.g.N * 4, cudaMemcpyDeviceToHost);
+    }
+    work_free(W);
+    return cuda_err(e);
+}
+
+int ekl_net_loss_grad(const int32_t dims[3], const int32_t periodic[3], const float *x, const float *target,
+                      const uint8_t *mask, const float *w, double *loss, float *grad)
+{
+    if (!dims || !x || !target || !w || !grad) return EKL_ERR_ARG;
+    NetWork W;
+    W.g = make_grid(dims, periodic);
+    const int N = W.g.N;
+    int rc = work_alloc(W, N);
+    if (rc != EKL_OK) { work_free(W); return rc; }
+    float *dt = nullptr;
+    uint8_t *dm = nullptr;
+    long long cnt = N;
+    if (mask) {
+        cnt = 0;
+        for (int i = 0; i < N; i++) cnt += mask[i] ? 1 : 0;
+    }
+    cudaError_t e = cudaMalloc(&dt, (size_t)N * 4);
+    if (e == cudaSuccess && mask) e = cudaMalloc(&dm, N);
+    if (e == cudaSuccess) e = cudaMemcpy(W.x, x, 2 * (size_t)N * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(W.w, w, NPARAM * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dt, target, (size_t)N * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && mask) e = cudaMemcpy(dm, mask, N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(W.grad, 0, NPARAM * 4);
+    if (e == cudaSuccess) {
+        net_forward(W, 0);
+        rc = net_backward(W, dt, dm, 1.f / (float)(cnt > 0 ? cnt : 1), loss, 0);
+        if (rc == EKL_OK) e = cudaMemcpy(grad, W.grad, NPARAM * 4, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(dt);
+    cudaFree(dm);
+    work_free(W);
+    if (rc != EKL_OK) return rc;
+    return cuda_err(e);
+}
+
+int ekl_net_train(int32_t nsamples, const int32_t dims[3], const float *x, const float *target,
+                  const uint8_t *mask, float *w, int32_t iters, int32_t batch, float lr, uint64_t seed,
+                  float *loss_out)
+{
+    if (nsamples < 1 || !dims || !x || !target || !w || iters < 0 || batch < 1) return EKL_ERR_ARG;
+    NetWork W;
+    const int32_t closed[3] = {0, 0, 0};
+    W.g = make_grid(dims, closed);
+    const int N = W.g.N;
+    int rc = work_alloc(W, N);
+    if (rc != EKL_OK) { work_free(W); return rc; }
+    float *dx = nullptr, *dt = nullptr, *m1 = nullptr, *m2 = nullptr;
+    uint8_t *dm = nullptr;
+    long long cnt = N;
+    if (mask) {
+        cnt = 0;
+        for (int i = 0; i < N; i++) cnt += mask[i] ? 1 : 0;
+    }
+    cudaError_t e = cudaMalloc(&dx, (size_t)nsamples * 2 * N * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dt, (size_t)nsamples * N * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&m1, NPARAM * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&m2, NPARAM * 4);
+    if (e == cudaSuccess && mask) e = cudaMalloc(&dm, N);
+    if (e == cudaSuccess) e = cudaMemcpy(dx, x, (size_t)nsamples * 2 * N * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dt, target, (size_t)nsamples * N * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && mask) e = cudaMemcpy(dm, mask, N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(W.w, w, NPARAM * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m1, 0, NPARAM * 4);
+    if (e == cudaSuccess) e = cudaMemset(m2, 0, NPARAM * 4);
+    // seeded sample order (splitmix64)
+    uint64_t st = seed;
+    auto next = [&]() {
+        st += 0x9E3779B97F4A7C15ull;
+        uint64_t z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int it = 0; it < iters && e == cudaSuccess && rc == EKL_OK; it++) {
+        cudaMemsetAsync(W.grad, 0, NPARAM * 4, 0);
+        double lsum = 0.0;
+        for (int bidx = 0; bidx < batch; bidx++) {
+            const int smp = (int)(next() % (uint64_t)nsamples);
+            e = cudaMemcpyAsync(W.x, dx + (size_t)smp * 2 * N, 2 * (size_t)N * 4, cudaMemcpyDeviceToDevice, 0);
+            if (e != cudaSuccess) break;
+            net_forward(W, 0);
+            double l = 0.0;
+            rc = net_backward(W, dt + (size_t)smp * N, dm, 1.f / (float)(cnt * batch), &l, 0);
+            lsum += l * batch;
+            if (rc != EKL_OK) break;
+        }
+        const float c1 = 1.f - powf(b1, (float)(it + 1)), c2 = 1.f - powf(b2, (float)(it + 1));
+        adam_k<<<(NPARAM + 255) / 256, 256>>>(NPARAM, W.w, W.grad, m1, m2, lr, b1, b2, eps, c1, c2);
+        if (loss_out) loss_out[it] = (float)(lsum / batch);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && rc == EKL_OK) e = cudaMemcpy(w, W.w, NPARAM * 4, cudaMemcpyDeviceToHost);
+    cudaFree(dx); cudaFree(dt); cudaFree(m1); cudaFree(m2); cudaFree(dm);
+    work_free(W);
+    if (rc != EKL_OK) return rc;
+    return cuda_err(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,60 @@
+"""Warm-start network kernels (BF16 tensor-core implicit GEMMs, FP32
+accumulation) against the FP64 numpy oracle: forward output, loss and every
+parameter gradient within BF16-level tolerances, and GPU training lowers the
+loss on a learnable mapping."""
+import numpy as np
+import pytest
+
+import paper_1710_09421_gb300 as E
+from oracle import net
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(seed, shape=(12, 10, 14)):
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((2,) + shape).astype(np.float32)
+    w = (net.init_params(seed) + 0.02 * rng.standard_normal(net.n_params())).astype(np.float32)
+    return rng, x, w
+
+
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (1, 0, 1)])
+def test_forward_matches_oracle(periodic):
+    rng, x, w = _case(0)
+    nz, ny, nx = x.shape[1:]
+    y = E.ekl_net_eval((nx, ny, nz), periodic, x, w)
+    ref = net.forward(x.astype(np.float64), w.astype(np.float64), periodic)
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 2e-2
+
+
+def test_loss_and_gradient_match_oracle():
+    rng, x, w = _case(1)
+    nz, ny, nx = x.shape[1:]
+    t = rng.standard_normal(x.shape[1:]).astype(np.float32)
+    mask = (rng.random(x.shape[1:]) < 0.8).astype(np.uint8)
+    loss, g = E.ekl_net_loss_grad((nx, ny, nz), (1, 1, 1), x, t, mask, w)
+    lref, gref = net.loss_grad(x.astype(np.float64), t.astype(np.float64), mask,
+                               w.astype(np.float64), (1, 1, 1))
+    assert abs(loss - lref) / lref < 2e-2
+    # per layer: W then b
+    o = 0
+    for ci, co in zip(net.CHANNELS[:-1], net.CHANNELS[1:]):
+        for n in (co * ci * 27, co):
+            seg, ref = g[o:o + n], gref[o:o + n]
+            assert np.linalg.norm(seg - ref) <= 5e-2 * np.linalg.norm(ref) + 1e-7, (ci, co, n)
+            o += n
+
+
+def test_training_lowers_loss():
+    """Learn a fixed random network's mapping from its own outputs."""
+    rng, _, w_true = _case(2, (16, 16, 16))
+    S = 12
+    xs = rng.standard_normal((S, 2, 16, 16, 16)).astype(np.float32)
+    ts = np.stack([net.forward(xs[s].astype(np.float64), w_true.astype(np.float64), (0, 0, 0))
+                   for s in range(S)]).astype(np.float32)
+    mask = np.zeros((16, 16, 16), np.uint8)
+    mask[4:-4, 4:-4, 4:-4] = 1
+    w0 = net.init_params(7).astype(np.float32)
+    w1, curve = E.ekl_net_train((16, 16, 16), xs, ts, mask, w0, iters=150, batch=4, lr=3e-3, seed=1)
+    assert np.isfinite(curve).all()
+    assert curve[-10:].mean() < 0.5 * curve[:10].mean(), (curve[:5], curve[-5:])
