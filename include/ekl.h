@@ -245,6 +245,20 @@ int ekl_net_train(int32_t nsamples, const int32_t dims[3], const float *x, const
                   const uint8_t *mask, float *w, int32_t iters, int32_t batch, float lr,
                   uint64_t seed, float *loss_out);
 
+/* Install trained parameters w[EKL_NET_PARAMS] as the warm start of every
+ * later step's Poisson solve (NULL switches it off): the network reads
+ * scales[0] * (b(t) - b(t-1)) and scales[1] * phi(t-1), b = 4 pi l_B
+ * (rho - mean), and phi(t-1) + scales[2] * output starts the iteration, which
+ * still runs to poisson_tol.  The first step after installation has no b(t-1)
+ * and starts from phi(t-1). */
+int ekl_set_warmstart(ekl_handle *h, const float *w, const float scales[3]);
+
+/* Run nsteps plain steps and record ncrops training crops per step, cubes of
+ * crop^3 nodes centred near the beads: out[k][3][crop^3] = (b(t) - b(t-1),
+ * phi(t-1), phi(t) - phi(t-1)), unscaled; *n_out crops written.  Needs beads. */
+int ekl_warmstart_collect(ekl_handle *h, int32_t nsteps, int32_t crop, int32_t ncrops, uint64_t seed,
+                          float *out, int64_t *n_out);
+
 /* ---------------------------------------------------------------------------
  * Allocation-free field read-back.  The paper has no counterpart: this entry
  * serves callers that may not allocate GPU memory while they run (code

@@ -133,6 +133,9 @@ def load(build_if_missing: bool = True):
         L.ekl_batch_destroy.argtypes = [vp]
         L.ekl_batch_destroy.restype = None
         L.ekl_net_eval.argtypes = [vp, vp, vp, vp, vp]
+        L.ekl_set_warmstart.argtypes = [vp, vp, vp]
+        L.ekl_warmstart_collect.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, vp,
+                                            C.POINTER(C.c_int64)]
         L.ekl_net_loss_grad.argtypes = [vp, vp, vp, vp, vp, vp, C.POINTER(C.c_double), vp]
         L.ekl_net_train.argtypes = [C.c_int32, vp, vp, vp, vp, vp, C.c_int32, C.c_int32, C.c_float,
                                     C.c_uint64, vp]
@@ -368,6 +371,12 @@ class Simulation:
     def set_timing(self, on=True):
         return ekl_set_timing(self.h, on)
 
+    def set_warmstart(self, w, scales=(1.0, 1.0, 1.0)):
+        return ekl_set_warmstart(self.h, w, scales)
+
+    def collect(self, nsteps, crop=16, ncrops=8, seed=0):
+        return ekl_warmstart_collect(self.h, nsteps, crop, ncrops, seed)
+
 
 # ------------------------------------------------------------------ batches
 def ekl_batch_create(params_list, stream=None):
@@ -502,3 +511,19 @@ def ekl_net_train(dims, x, target, mask, w, iters, batch=4, lr=1e-3, seed=0):
     _check(load().ekl_net_train(len(x), _ptr(d), _ptr(x), _ptr(t), _ptr(m), _ptr(w), int(iters),
                                 int(batch), float(lr), int(seed), _ptr(curve)), "ekl_net_train")
     return w, curve
+
+
+def ekl_set_warmstart(h, w, scales=(1.0, 1.0, 1.0)):
+    """Install (w: EKL_NET_PARAMS floats) or remove (w=None) the warm start."""
+    wp = None if w is None else np.ascontiguousarray(w, np.float32)
+    sc = np.ascontiguousarray(scales, np.float32)
+    return _check(load().ekl_set_warmstart(h, _ptr(wp), _ptr(sc)), "ekl_set_warmstart")
+
+
+def ekl_warmstart_collect(h, nsteps, crop=16, ncrops=8, seed=0):
+    """Returns crops[k][3][crop][crop][crop] = (db, phi_prev, dphi)."""
+    out = np.zeros((nsteps * ncrops, 3, crop, crop, crop), np.float32)
+    n = C.c_int64(0)
+    _check(load().ekl_warmstart_collect(h, int(nsteps), int(crop), int(ncrops), int(seed), _ptr(out),
+                                        C.byref(n)), "ekl_warmstart_collect")
+    return out[: n.value]

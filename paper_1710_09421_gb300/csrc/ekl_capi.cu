@@ -128,6 +128,7 @@ void release(Ctx &c)
     dev_free(c, c.sorted_entry, 0);
     dev_free(c, c.slot_first, 0);
     dev_free(c, c.entry_w, 0);
+    warmstart_free(c);
     (void)rs;
     for (int k = 0; k < 2 * PH_COUNT; k++)
         if (c.ev[k]) cudaEventDestroy(c.ev[k]);

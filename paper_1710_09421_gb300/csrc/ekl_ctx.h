@@ -83,6 +83,9 @@ struct Ctx {
     int *slot_first;      // [MAX_ENTRIES + 1]
     void *entry_w;        // Real[MAX_ENTRIES]
 
+    // learned warm start of the Poisson solve (ekl_net.cu)
+    void *net;
+
     // timing / accounting
     int timing;
     cudaEvent_t ev[2 * PH_COUNT];
@@ -121,6 +124,12 @@ int run_batch_f64(Batch &b, int nsteps);
 int run_batch_f32(Batch &b, int nsteps);
 int run_batch_bf16(Batch &b, int nsteps);
 int run_batch_fp16(Batch &b, int nsteps);
+
+// learned warm start hooks (ekl_net.cu): before the Poisson launch (inputs,
+// network, potential update) and after it (training-crop collection)
+int warmstart_before_poisson(Ctx &c);
+int warmstart_after_poisson(Ctx &c);
+void warmstart_free(Ctx &c);
 
 // message returned by ekl_last_error() on this thread
 void set_last_error(const char *msg);

@@ -23,7 +23,14 @@
 
 #include <vector>
 
+#include <new>
+#include <utility>
+
 #include "ekl_kernels.cuh"
+
+struct ekl_handle {
+    ekl::Ctx c;
+};
 
 namespace {
 
@@ -455,7 +462,191 @@ NetGrid make_grid(const int32_t dims[3], const int32_t periodic[3])
     return g;
 }
 
+// ---------------------------------------------------------------- in-step warm start
+struct WarmStart {
+    NetWork W;
+    float s_db = 1.f, s_phi = 1.f, s_out = 1.f;
+    int enabled = 0;
+    int have_prev = 0;
+    float *bprev = nullptr, *bcur = nullptr, *phiprev = nullptr;
+    double *mean = nullptr;
+    int collect = 0, crop = 0, ncrops = 0;
+    float *crops = nullptr;  // [cap][3][crop^3]: dB, phi_prev, dphi
+    long long cap = 0, used = 0;
+    uint64_t seed = 0;
+};
+
+__global__ void mean_k(const double *part, int n, double nfl, double *mean)
+{
+    __shared__ double sh[32];
+    double v = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) v += part[k];
+    double t = block_sum(v, sh);
+    if (threadIdx.x == 0) *mean = nfl > 0 ? t / nfl : 0.0;
+}
+
+// network inputs: x0 = s_db (b(t) - b(t-1)), x1 = s_phi phi(t-1); b = 4 pi l_B (rho - mean)
+template <typename R, typename PhiT>
+__global__ void ws_inputs(int N, const uint32_t *mask, const R *rho, const double *mean, double c4, const PhiT *phi,
+                          const float *bprev, int have_prev, float s_db, float s_phi, float *x, float *bcur,
+                          float *phiprev)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const bool solid = mask[n] & SOLID_BIT;
+    float b = solid ? 0.f : (float)(c4 * ((double)rho[n] - *mean));
+    float p;
+    if constexpr (((PhiT)0.5) != 0) p = (float)phi[n];
+    else p = ll_to_float(phi[n]) * (float)PHI_INV;
+    if (solid) p = 0.f;
+    bcur[n] = b;
+    if (phiprev) phiprev[n] = p;
+    x[n] = solid ? 0.f : s_db * (b - (have_prev ? bprev[n] : b));
+    x[N + n] = s_phi * p;
+}
+
+template <typename PhiT>
+__global__ void ws_apply(int N, const uint32_t *mask, const float *y, float s_out, PhiT *phi)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N || (mask[n] & SOLID_BIT)) return;
+    const float d = s_out * y[n];
+    if constexpr (((PhiT)0.5) != 0) phi[n] += (double)d;
+    else phi[n] += float_to_ll(d * (float)PHI_SCALE);
+}
+
+// training crops centred on beads (seeded jitter): inputs and the change of
+// the converged potential
+template <typename PhiT>
+__global__ void ws_crops(NetGrid g, const float *x, const float *phiprev, const PhiT *phi, const double *Rb,
+                         int nb, int crop, int ncrops, long long step, uint64_t seed, float *out)
+{
+    const int j = blockIdx.x;
+    const int c3 = crop * crop * crop;
+    const int b = (int)((step * ncrops + j) % nb);
+    uint32_t ctr[4] = {(uint32_t)j, 3u << 24, (uint32_t)step, (uint32_t)((uint64_t)step >> 32)};
+    philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32));
+    int o[3];
+    for (int a = 0; a < 3; a++) {
+        int jit = (int)(ctr[a] % 5u) - 2;
+        o[a] = (int)floor(Rb[3 * b + a]) + jit - crop / 2;
+    }
+    for (int t = threadIdx.x; t < c3; t += blockDim.x) {
+        int cx = t % crop, cy = (t / crop) % crop, cz = t / (crop * crop);
+        int q[3] = {o[0] + cx, o[1] + cy, o[2] + cz};
+        const int dims[3] = {g.nx, g.ny, g.nz};
+        bool in = true;
+        for (int a = 0; a < 3; a++) {
+            if (q[a] < 0 || q[a] >= dims[a]) {
+                if (g.per[a]) q[a] = ((q[a] % dims[a]) + dims[a]) % dims[a];
+                else in = false;
+            }
+        }
+        float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+        if (in) {
+            int n = q[0] + g.nx * (q[1] + g.ny * q[2]);
+            v0 = x[n];
+            v1 = x[g.N + n];
+            float pn;
+            if constexpr (((PhiT)0.5) != 0) pn = (float)phi[n];
+            else pn = ll_to_float(phi[n]) * (float)PHI_INV;
+            v2 = (v1 == 0.f && phiprev[n] == 0.f) ? 0.f : pn - phiprev[n];
+        }
+        float *dst = out + (size_t)j * 3 * c3;
+        dst[t] = v0;
+        dst[c3 + t] = v1;
+        dst[2 * c3 + t] = v2;
+    }
+}
+
 }  // namespace
+
+namespace ekl {
+
+int warmstart_before_poisson(Ctx &c)
+{
+    WarmStart &ws = *(WarmStart *)c.net;
+    const int N = (int)c.N;
+    mean_k<<<1, 1024, 0, c.stream>>>(c.part_charge, c.charge_blocks * (CHARGE_THREADS / 32), (double)c.n_fluid, ws.mean);
+    const int bn = (N + 255) / 256;
+    const int have = ws.have_prev;
+    if (c.prec == EKL_F64)
+        ws_inputs<double, double><<<bn, 256, 0, c.stream>>>(N, c.mask, (const double *)c.rho, ws.mean, c.c4,
+                                                           (const double *)c.phi, ws.bprev, have, ws.s_db, ws.s_phi,
+                                                           ws.W.x, ws.bcur, ws.collect ? ws.phiprev : nullptr);
+    else
+        ws_inputs<float, long long><<<bn, 256, 0, c.stream>>>(N, c.mask, (const float *)c.rho, ws.mean, c.c4,
+                                                             (const long long *)c.phi, ws.bprev, have, ws.s_db,
+                                                             ws.s_phi, ws.W.x, ws.bcur, ws.collect ? ws.phiprev : nullptr);
+    c.launches += 2;
+    if (ws.enabled && have) {
+        net_forward(ws.W, c.stream);
+        const int bm = bn;
+        if (c.prec == EKL_F64) ws_apply<double><<<bm, 256, 0, c.stream>>>(N, c.mask, ws.W.y, ws.s_out, (double *)c.phi);
+        else ws_apply<long long><<<bm, 256, 0, c.stream>>>(N, c.mask, ws.W.y, ws.s_out, (long long *)c.phi);
+        c.launches += 8;
+    }
+    std::swap(ws.bprev, ws.bcur);
+    ws.have_prev = 1;
+    return cudaGetLastError() == cudaSuccess ? EKL_OK : EKL_ERR_CUDA;
+}
+
+int warmstart_after_poisson(Ctx &c)
+{
+    WarmStart &ws = *(WarmStart *)c.net;
+    if (!ws.collect || c.nb == 0 || ws.used + ws.ncrops > ws.cap) return EKL_OK;
+    const size_t c3 = (size_t)ws.crop * ws.crop * ws.crop;
+    float *dst = ws.crops + (size_t)ws.used * 3 * c3;
+    if (c.prec == EKL_F64)
+        ws_crops<double><<<ws.ncrops, 256, 0, c.stream>>>(ws.W.g, ws.W.x, ws.phiprev, (const double *)c.phi,
+                                                         (const double *)c.R, c.nb, ws.crop, ws.ncrops, c.step,
+                                                         ws.seed, dst);
+    else
+        ws_crops<long long><<<ws.ncrops, 256, 0, c.stream>>>(ws.W.g, ws.W.x, ws.phiprev, (const long long *)c.phi,
+                                                            (const double *)c.R, c.nb, ws.crop, ws.ncrops, c.step,
+                                                            ws.seed, dst);
+    c.launches++;
+    ws.used += ws.ncrops;
+    return cudaGetLastError() == cudaSuccess ? EKL_OK : EKL_ERR_CUDA;
+}
+
+void warmstart_free(Ctx &c)
+{
+    if (!c.net) return;
+    WarmStart *ws = (WarmStart *)c.net;
+    work_free(ws->W);
+    cudaFree(ws->bprev);
+    cudaFree(ws->bcur);
+    cudaFree(ws->phiprev);
+    cudaFree(ws->mean);
+    cudaFree(ws->crops);
+    delete ws;
+    c.net = nullptr;
+}
+
+static int warmstart_ensure(Ctx &c)
+{
+    if (c.net) return EKL_OK;
+    WarmStart *ws = new (std::nothrow) WarmStart();
+    if (!ws) return EKL_ERR_ALLOC;
+    const int32_t dims[3] = {c.nx, c.ny, c.nz};
+    ws->W.g = make_grid(dims, c.per);
+    const int N = (int)c.N;
+    int rc = work_alloc(ws->W, N);
+    cudaError_t e = rc == EKL_OK ? cudaSuccess : cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = cudaMalloc(&ws->bprev, (size_t)N * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&ws->bcur, (size_t)N * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&ws->phiprev, (size_t)N * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&ws->mean, sizeof(double));
+    c.net = ws;
+    if (e != cudaSuccess) {
+        warmstart_free(c);
+        return EKL_ERR_ALLOC;
+    }
+    return EKL_OK;
+}
+
+}  // namespace ekl
 
 extern "C" {
 
@@ -573,6 +764,71 @@ int ekl_net_train(int32_t nsamples, const int32_t dims[3], const float *x, const
     work_free(W);
     if (rc != EKL_OK) return rc;
     return cuda_err(e);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int ekl_set_warmstart(ekl_handle *h, const float *w, const float scales[3])
+{
+    if (!h) return EKL_ERR_ARG;
+    ekl::Ctx &c = h->c;
+    if (!w) {
+        if (c.net) ((WarmStart *)c.net)->enabled = 0;
+        return EKL_OK;
+    }
+    int rc = ekl::warmstart_ensure(c);
+    if (rc != EKL_OK) return rc;
+    WarmStart &ws = *(WarmStart *)c.net;
+    if (cudaMemcpy(ws.W.w, w, NPARAM * 4, cudaMemcpyHostToDevice) != cudaSuccess) return EKL_ERR_CUDA;
+    if (scales) {
+        ws.s_db = scales[0];
+        ws.s_phi = scales[1];
+        ws.s_out = scales[2];
+    }
+    ws.enabled = 1;
+    return EKL_OK;
+}
+
+int ekl_warmstart_collect(ekl_handle *h, int32_t nsteps, int32_t crop, int32_t ncrops, uint64_t seed, float *out,
+                          int64_t *n_out)
+{
+    if (!h || nsteps < 1 || crop < 4 || ncrops < 1 || !out) return EKL_ERR_ARG;
+    ekl::Ctx &c = h->c;
+    if (c.nb == 0) return EKL_ERR_ARG;
+    int rc = ekl::warmstart_ensure(c);
+    if (rc != EKL_OK) return rc;
+    WarmStart &ws = *(WarmStart *)c.net;
+    const int en = ws.enabled;
+    const float s0 = ws.s_db, s1 = ws.s_phi, s2 = ws.s_out;
+    ws.enabled = 0;
+    ws.s_db = ws.s_phi = ws.s_out = 1.f;
+    ws.collect = 1;
+    ws.crop = crop;
+    ws.ncrops = ncrops;
+    ws.seed = seed;
+    ws.cap = (long long)nsteps * ncrops;
+    ws.used = 0;
+    const size_t c3 = (size_t)crop * crop * crop;
+    if (cudaMalloc(&ws.crops, (size_t)ws.cap * 3 * c3 * 4) != cudaSuccess) {
+        ws.collect = 0;
+        return EKL_ERR_ALLOC;
+    }
+    rc = ekl_step(h, nsteps);
+    if (rc >= 0) {
+        if (cudaMemcpy(out, ws.crops, (size_t)ws.used * 3 * c3 * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = EKL_ERR_CUDA;
+        if (n_out) *n_out = ws.used;
+    }
+    cudaFree(ws.crops);
+    ws.crops = nullptr;
+    ws.collect = 0;
+    ws.enabled = en;
+    ws.s_db = s0;
+    ws.s_phi = s1;
+    ws.s_out = s2;
+    return rc;
 }
 
 }  // extern "C"

@@ -144,7 +144,14 @@ template <typename S, typename R, typename PhiT, bool DEV> int steps_impl(Ctx &c
         charge_kernel<S, R, PhiT, DEV><<<c.charge_blocks, CHARGE_THREADS, 0, c.stream>>>(a);
         c.launches++;
         phase_end(c, PH_CHARGE);
-        // 3. Poisson: one cooperative launch for all sweeps
+        // 3. Poisson: one cooperative launch for all sweeps (after the learned
+        //    warm start, when one is installed)
+        if (c.net) {
+            phase_begin(c, PH_OTHER);
+            int rc = warmstart_before_poisson(c);
+            phase_end(c, PH_OTHER);
+            if (rc != EKL_OK) return rc;
+        }
         phase_begin(c, PH_POISSON);
         cudaMemsetAsync(c.barrier, 0, 4 * sizeof(unsigned), c.stream);
         if (c.pois_tiled) {
@@ -171,6 +178,10 @@ template <typename S, typename R, typename PhiT, bool DEV> int steps_impl(Ctx &c
             if (e != cudaSuccess) return EKL_ERR_CUDA;
         }
         phase_end(c, PH_POISSON);
+        if (c.net) {
+            int rc = warmstart_after_poisson(c);
+            if (rc != EKL_OK) return rc;
+        }
         // 4. beads: interpolate, Langevin sub-steps, spread
         phase_begin(c, PH_MD);
         if (c.nb > 0) {
