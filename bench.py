@@ -165,6 +165,8 @@ def workload_for(name, rank=0, args=None):
         wl = wl.replace(rho_jacobi=args.rho_jacobi)
     if args is not None and args.check_every > 0:
         wl = wl.replace(poisson_check_every=args.check_every)
+    if args is not None and getattr(args, "poisson", "sor") == "mg":
+        wl = wl.replace(flags=wl.flags | W.FLAG_POISSON_MG)
     return wl
 
 
@@ -391,9 +393,61 @@ def run_ours(args):
                 "what": "create from host arrays + beads + %d steps + all fields to host" % e2e_steps},
         "status": rc,
     }
+    if world == 1 and not args.no_learned:
+        line["learned_vs_plain"] = learned_vs_plain(E, wl, args, sraw)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget)
     print(json.dumps(line))
+
+
+def learned_vs_plain(E, wl, args, sraw, collect_steps=60, ncrops=8, crop=16, train_iters=400,
+                     compare_steps=40):
+    """Train the warm-start network on crops the solver records on this
+    workload (a separate run with another seed), then time the same steps
+    with and without it from identical states.  Both runs iterate to the same
+    residual tolerance; only sweeps and time are compared."""
+    import numpy as np
+    import torch
+    from paper_1710_09421_gb300 import warmstart as WS
+
+    t0 = time.perf_counter()
+    src = E.Simulation(wl.replace(seed=wl.seed + 101), precision=args.precision, stream=sraw)
+    src.step(args.warmup)
+    crops = src.collect(collect_steps, crop=crop, ncrops=ncrops, seed=7)
+    src.close()
+    t1 = time.perf_counter()
+    w, scales, curve = WS.train(crops, iters=train_iters, batch=8, lr=2e-3, seed=0)
+    t2 = time.perf_counter()
+    out = {"crops": int(len(crops)), "crop": crop, "collect_s": round(t1 - t0, 3),
+           "train_s": round(t2 - t1, 3), "train_iters": train_iters,
+           "rel_loss_first": round(float(np.mean(curve[:20])), 4),
+           "rel_loss_last": round(float(np.mean(curve[-20:])), 4)}
+    for name, use in (("plain", False), ("learned", True)):
+        sim = E.Simulation(wl, precision=args.precision, stream=sraw)
+        sim.step(args.warmup)
+        if use:
+            sim.set_warmstart(w, scales)
+            sim.step(2)   # the network needs the previous source
+        else:
+            sim.step(2)
+        s0 = sim.stats()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.ExternalStream(sraw) if sraw else torch.cuda.current_stream()
+        e0.record(st)
+        sim.step(compare_steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        s1 = sim.stats()
+        sim.close()
+        out[name] = {"steps_per_s": round(compare_steps / (ms / 1e3), 3),
+                     "poisson_sweeps_per_step": round((s1["poisson_sweeps"] - s0["poisson_sweeps"]) / compare_steps, 2),
+                     "poisson_res_last": s1["poisson_res"]}
+    out["sweeps_saved_frac"] = round(1 - out["learned"]["poisson_sweeps_per_step"]
+                                     / max(out["plain"]["poisson_sweeps_per_step"], 1e-9), 4)
+    return out
 
 
 def main():
@@ -410,7 +464,11 @@ def main():
                     help="Chebyshev spectral radius (0: library default)")
     ap.add_argument("--check-every", type=int, default=0,
                     help="Poisson residual test interval (0: workload default)")
+    ap.add_argument("--poisson", default="mg", choices=["mg", "sor"],
+                    help="Poisson solver: multigrid-preconditioned CG or Chebyshev red-black SOR")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-vs-plain warm-start comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -68,6 +68,17 @@ extern "C" {
 #define EKL_GAMMA_LITERAL 2    /* bead drag gamma^a = xi for every species (literal Sec. II.B) */
 #define EKL_NO_BEAD_NOISE 4    /* no Langevin noise on the beads */
 #define EKL_POISSON_GLOBAL 8   /* always use the global-memory SOR kernel (no shared-memory tiles) */
+/* Solve the Poisson equation of each step by conjugate gradients
+ * preconditioned with one geometric multigrid V-cycle (2x2x2 aggregation,
+ * red-black Gauss-Seidel smoothing) instead of the Chebyshev SOR of
+ * Sec. II.C.  Same operator, source and stopping rule ||r||_2 <= tol ||b||_2,
+ * with r = b - A phi the true residual of the returned potential (not the
+ * residual met during a sweep).  poisson_max_iter and poisson_fixed_iter
+ * then count CG iterations, poisson_check_every and rho_jacobi are unused,
+ * and ekl_stats.poisson_iters / poisson_sweeps report CG iterations.
+ * ekl_create fails with EKL_ERR_ARG when no coarser level exists (a
+ * periodic extent that is not a multiple of 4). */
+#define EKL_POISSON_MG 16
 
 #define EKL_BOND_FENE 0
 #define EKL_BOND_HARMONIC 1

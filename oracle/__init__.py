@@ -92,6 +92,9 @@ def lib():
                                             dp]
             L.eko_poisson_solve.restype = C.c_int
             L.eko_node_gradient.argtypes = [vp, vp, vp]
+            L.eko_poisson_residual.argtypes = [vp, vp, vp]
+            L.eko_poisson_residual.restype = C.c_double
+            L.eko_last_rho.argtypes = [vp, vp]
             L.eko_bead_stencil.argtypes = [vp, vp, vp, vp]
             L.eko_bead_stencil.restype = C.c_int
             L.eko_philox4x32_10.argtypes = [vp, vp, vp]
@@ -243,6 +246,18 @@ class Sim:
         it = lib().eko_poisson_solve(self.h, _ptr(rho), _ptr(phi), tol, max_iter, check_every,
                                      fixed_iter, C.byref(res))
         return phi, it, res.value
+
+    def poisson_residual(self, rho, phi):
+        """||b - A phi|| / ||b|| of phi for the charge density rho."""
+        rho = np.ascontiguousarray(rho, np.float64).ravel()
+        phi = np.ascontiguousarray(phi, np.float64).ravel()
+        return lib().eko_poisson_residual(self.h, _ptr(rho), _ptr(phi))
+
+    def last_rho(self):
+        """Charge density rho_e of the last step."""
+        out = np.zeros(self.N)
+        lib().eko_last_rho(self.h, _ptr(out))
+        return out
 
     def node_gradient(self, phi):
         phi = np.ascontiguousarray(phi, np.float64).ravel()

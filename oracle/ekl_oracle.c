@@ -532,6 +532,48 @@ int eko_poisson_solve(eko_sim *s, const double *rho, double *phi, double tol, in
     return converged ? it : -it;
 }
 
+/* Relative residual ||b - A phi||_2 / ||b||_2 of a potential for the charge
+ * density rho, with b = 4 pi l_B (rho - <rho>_fluid) on the fluid nodes and
+ * (A phi)_i = sum_{fluid faces j} (phi_i - phi_j): the equation that
+ * eko_poisson_solve iterates on (Eqs. 2-3), evaluated once, written out
+ * directly.  Nodes without a fluid face are left out, as in the solver. */
+double eko_poisson_residual(const eko_sim *s, const double *rho, const double *phi)
+{
+    const long N = s->N;
+    double sum = 0.0;
+    long nf = 0;
+    for (long i = 0; i < N; i++)
+        if (!s->solid[i]) {
+            sum += rho[i];
+            nf++;
+        }
+    const double mean = nf ? sum / nf : 0.0;
+    double r2 = 0.0, b2 = 0.0;
+    for (long i = 0; i < N; i++) {
+        if (s->solid[i]) continue;
+        const double b = 4.0 * M_PI * s->P.bjerrum * (rho[i] - mean);
+        b2 += b * b;
+        int x, y, z;
+        coords(s, i, &x, &y, &z);
+        double Aphi = 0.0;
+        int deg = 0;
+        for (int f = 0; f < 6; f++) {
+            int in;
+            long j = node_id(s, x + FACE[f][0], y + FACE[f][1], z + FACE[f][2], &in);
+            if (in && !s->solid[j]) {
+                Aphi += phi[i] - phi[j];
+                deg++;
+            }
+        }
+        if (deg == 0) continue;
+        r2 += (b - Aphi) * (b - Aphi);
+    }
+    return b2 > 0.0 ? sqrt(r2 / b2) : sqrt(r2);
+}
+
+/* charge density rho_e of the last step (ions, wall charge, beads) */
+void eko_last_rho(const eko_sim *s, double *out) { memcpy(out, s->rho, sizeof(double) * s->N); }
+
 /* Field at the fluid nodes by central differences; a wall (or closed-box)
  * neighbour is replaced by the Neumann ghost phi_i + 4 pi l_B sigma_face,
  * sigma_face being the wall node's charge share on that face (Sec. II.A:

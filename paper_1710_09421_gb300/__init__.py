@@ -30,6 +30,7 @@ EKL_ERR_TIMEOUT = -5
 EKL_ERR_CUDA = -6
 
 EKL_F64, EKL_F32, EKL_BF16DEV, EKL_FP16DEV = 0, 1, 2, 3
+EKL_EQ_BARYCENTRIC, EKL_GAMMA_LITERAL, EKL_NO_BEAD_NOISE, EKL_POISSON_GLOBAL, EKL_POISSON_MG = 1, 2, 4, 8, 16
 PRECISION = {"f64": EKL_F64, "f32": EKL_F32, "bf16": EKL_BF16DEV, "fp16": EKL_FP16DEV}
 
 Q = 19

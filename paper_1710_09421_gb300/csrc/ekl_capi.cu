@@ -47,15 +47,16 @@ struct PrecOps {
     int (*get_state)(Ctx &, double *, double *);
     int (*set_state)(Ctx &, const double *, const double *);
     int (*pois_blocks)();
+    int (*mg_blocks)();
 };
 
 const PrecOps &ops(int prec)
 {
     static const PrecOps t[4] = {
-        {init_populations_f64, run_steps_f64, get_fields_f64, get_state_f64, set_state_f64, pois_blocks_f64},
-        {init_populations_f32, run_steps_f32, get_fields_f32, get_state_f32, set_state_f32, pois_blocks_f32},
-        {init_populations_bf16, run_steps_bf16, get_fields_bf16, get_state_bf16, set_state_bf16, pois_blocks_bf16},
-        {init_populations_fp16, run_steps_fp16, get_fields_fp16, get_state_fp16, set_state_fp16, pois_blocks_fp16},
+        {init_populations_f64, run_steps_f64, get_fields_f64, get_state_f64, set_state_f64, pois_blocks_f64, mg_blocks_f64},
+        {init_populations_f32, run_steps_f32, get_fields_f32, get_state_f32, set_state_f32, pois_blocks_f32, mg_blocks_f32},
+        {init_populations_bf16, run_steps_bf16, get_fields_bf16, get_state_bf16, set_state_bf16, pois_blocks_bf16, mg_blocks_bf16},
+        {init_populations_fp16, run_steps_fp16, get_fields_fp16, get_state_fp16, set_state_fp16, pois_blocks_fp16, mg_blocks_fp16},
     };
     return t[prec];
 }
@@ -128,6 +129,17 @@ void release(Ctx &c)
     dev_free(c, c.sorted_entry, 0);
     dev_free(c, c.slot_first, 0);
     dev_free(c, c.entry_w, 0);
+    for (int l = 1; l < MG_MAXLEV; l++) {
+        dev_free(c, c.mg_lev[l].sig, 0);
+        dev_free(c, c.mg_lev[l].e, 0);
+        dev_free(c, c.mg_lev[l].f, 0);
+    }
+    dev_free(c, c.mg_r, 0);
+    dev_free(c, c.mg_z, 0);
+    dev_free(c, c.mg_q, 0);
+    dev_free(c, c.mg_p[0], 0);
+    dev_free(c, c.mg_p[1], 0);
+    dev_free(c, c.mg_part, 0);
     warmstart_free(c);
     (void)rs;
     for (int k = 0; k < 2 * PH_COUNT; k++)
@@ -210,6 +222,128 @@ void dev_free(Ctx &c, void *p, size_t bytes)
 }
 
 }  // namespace ekl
+
+namespace {
+
+// Multigrid hierarchy of the Poisson operator (EKL_POISSON_MG): levels halve
+// every extent (rounding up) while each periodic extent stays even, down to
+// MG_COARSEST_CELLS cells.  Face conductances: 1 on the lattice's open faces
+// (fluid to fluid, inside or across a periodic side); on level l+1, half the
+// sum of the level-l conductances crossing the aggregated face.  Returns an
+// error message, or null.
+template <typename Alloc>
+static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A)
+{
+    if (ops(c.prec).mg_blocks() < 1) return "multigrid kernel cannot be resident";
+    int d[MG_MAXLEV][3];
+    d[0][0] = c.nx;
+    d[0][1] = c.ny;
+    d[0][2] = c.nz;
+    int nlev = 1;
+    while (nlev < MG_MAXLEV) {
+        const int *p = d[nlev - 1];
+        if ((long long)p[0] * p[1] * p[2] <= MG_COARSEST_CELLS) break;
+        bool ok = true;
+        for (int a = 0; a < 3; a++)
+            if (p[a] < 2 || (c.per[a] && p[a] % 4)) ok = false;
+        if (!ok) break;
+        for (int a = 0; a < 3; a++) d[nlev][a] = (p[a] + 1) / 2;
+        nlev++;
+    }
+    if (nlev < 2) return "multigrid needs a coarser level: periodic extents must be multiples of 4";
+    // lattice conductances of the +x, +y, +z faces
+    const long long N = c.N;
+    std::vector<float> sg[3];
+    for (int a = 0; a < 3; a++) sg[a].assign(N, 0.f);
+    for (int z = 0; z < c.nz; z++)
+        for (int y = 0; y < c.ny; y++)
+            for (int x = 0; x < c.nx; x++) {
+                const long long i = x + (long long)c.nx * (y + (long long)c.ny * z);
+                if (solid[i]) continue;
+                const int q[3] = {x, y, z}, L[3] = {c.nx, c.ny, c.nz};
+                for (int a = 0; a < 3; a++) {
+                    int r[3] = {q[0], q[1], q[2]};
+                    r[a]++;
+                    if (r[a] == L[a]) {
+                        if (!c.per[a]) continue;
+                        r[a] = 0;
+                    }
+                    const long long j = r[0] + (long long)c.nx * (r[1] + (long long)c.ny * r[2]);
+                    if (!solid[j]) sg[a][i] = 1.f;
+                }
+            }
+    for (int l = 1; l < nlev; l++) {
+        const int *F = d[l - 1], *C = d[l];
+        const long long NC = (long long)C[0] * C[1] * C[2];
+        std::vector<float> cs[3];
+        for (int a = 0; a < 3; a++) cs[a].assign(NC, 0.f);
+        for (int Z = 0; Z < C[2]; Z++)
+            for (int Y = 0; Y < C[1]; Y++)
+                for (int X = 0; X < C[0]; X++) {
+                    const long long I = X + (long long)C[0] * (Y + (long long)C[1] * Z);
+                    const int Q3[3] = {X, Y, Z};
+                    for (int a = 0; a < 3; a++) {
+                        // fine faces crossing the coarse +a face: the +a faces of
+                        // the children at coordinate 2 Q + 1 along a
+                        double acc = 0.0;
+                        for (int u = 0; u < 2; u++)
+                            for (int v = 0; v < 2; v++) {
+                                int f[3];
+                                f[a] = 2 * Q3[a] + 1;
+                                f[(a + 1) % 3] = 2 * Q3[(a + 1) % 3] + u;
+                                f[(a + 2) % 3] = 2 * Q3[(a + 2) % 3] + v;
+                                if (f[0] >= F[0] || f[1] >= F[1] || f[2] >= F[2]) continue;
+                                acc += sg[a][f[0] + (long long)F[0] * (f[1] + (long long)F[1] * f[2])];
+                            }
+                        cs[a][I] = (float)(0.5 * acc);
+                    }
+                }
+        std::vector<float4> h4(NC);
+        for (int Z = 0; Z < C[2]; Z++)
+            for (int Y = 0; Y < C[1]; Y++)
+                for (int X = 0; X < C[0]; X++) {
+                    const long long I = X + (long long)C[0] * (Y + (long long)C[1] * Z);
+                    const long long xm = X == 0 ? I + C[0] - 1 : I - 1;
+                    const long long ym = Y == 0 ? I + (long long)C[0] * (C[1] - 1) : I - C[0];
+                    const long long zm = Z == 0 ? I + (long long)C[0] * C[1] * (C[2] - 1) : I - (long long)C[0] * C[1];
+                    const double diag = (double)cs[0][I] + cs[1][I] + cs[2][I] + cs[0][xm] + cs[1][ym] + cs[2][zm];
+                    h4[I] = make_float4(cs[0][I], cs[1][I], cs[2][I], diag > 0.0 ? (float)(1.0 / diag) : 0.f);
+                }
+        MgLevel &ml = c.mg_lev[l];
+        ml.nx = C[0];
+        ml.ny = C[1];
+        ml.nz = C[2];
+        ml.N = (int)NC;
+        ml.sig = (float4 *)A(NC * sizeof(float4));
+        ml.e = (float *)A(NC * sizeof(float));
+        ml.f = (float *)A(NC * sizeof(float));
+        if (!ml.sig || !ml.e || !ml.f) return nullptr;
+        if (cudaMemcpy(ml.sig, h4.data(), NC * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess)
+            return "multigrid upload failed";
+        for (int a = 0; a < 3; a++) sg[a].swap(cs[a]);
+    }
+    c.mg_lev[0].nx = c.nx;
+    c.mg_lev[0].ny = c.ny;
+    c.mg_lev[0].nz = c.nz;
+    c.mg_lev[0].N = (int)N;
+    c.mg_nlev = nlev;
+    c.mg_cta_from = nlev - 1;
+    for (int l = 1; l < nlev; l++)
+        if (c.mg_lev[l].N <= MG_CTA_CELLS) {
+            c.mg_cta_from = l;
+            break;
+        }
+    c.mg_r = (float *)A(N * sizeof(float));
+    c.mg_z = (float *)A(N * sizeof(float));
+    c.mg_q = (float *)A(N * sizeof(float));
+    c.mg_p[0] = (float *)A(N * sizeof(float));
+    c.mg_p[1] = (float *)A(N * sizeof(float));
+    c.mg_part = (double *)A((size_t)4 * c.pois_blocks * sizeof(double));
+    c.mg = 1;
+    return nullptr;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -431,6 +565,15 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
         release(c);
         delete h;
         return fail(EKL_ERR_ALLOC, "device allocation failed");
+    }
+    if (P->flags & EKL_POISSON_MG) {
+        const char *why = build_multigrid(c, solid, A);
+        if (!why && !okall) why = "device allocation failed";
+        if (why) {
+            release(c);
+            delete h;
+            return fail(okall ? EKL_ERR_ARG : EKL_ERR_ALLOC, why);
+        }
     }
     for (int k = 0; k < 2 * PH_COUNT; k++) cudaEventCreate(&c.ev[k]);
 

@@ -26,6 +26,22 @@ constexpr int ST_UNSTABLE = 4;
 constexpr int ST_BEAD = 8;
 constexpr int ST_TIMEOUT = 16;
 
+// Multigrid hierarchy of the Poisson operator (levels >= 1; level 0 is the
+// lattice itself).  Cell (X, Y, Z) of level l+1 aggregates the cells
+// (2X + {0,1}, 2Y + {0,1}, 2Z + {0,1}) of level l.
+constexpr int MG_MAXLEV = 12;
+constexpr int MG_NU = 2;                 // red-black smoothing sweeps before and after the coarse correction
+constexpr int MG_COARSE_SWEEPS = 8;      // (R B)^k R half sweeps on the coarsest level
+constexpr float MG_INNER_RED = 1e-4f;    // CG residual reduction before the true residual is formed
+constexpr int MG_COARSEST_CELLS = 512;   // stop coarsening at or below this many cells
+constexpr int MG_CTA_CELLS = 16384;      // levels this small are handled by one block
+struct MgLevel {
+    int nx, ny, nz, N;
+    float4 *sig;  // conductances of the +x, +y, +z faces and 1 / diagonal (0: inactive cell)
+    float *e;     // correction
+    float *f;     // right-hand side (restricted residual)
+};
+
 enum Phase { PH_BIN = 0, PH_CHARGE, PH_POISSON, PH_MD, PH_LB, PH_OTHER, PH_COUNT };
 
 struct Ctx {
@@ -82,6 +98,14 @@ struct Ctx {
     int *sorted_entry;    // [MAX_ENTRIES]
     int *slot_first;      // [MAX_ENTRIES + 1]
     void *entry_w;        // Real[MAX_ENTRIES]
+
+    // multigrid-preconditioned CG Poisson solver (EKL_POISSON_MG)
+    int mg;                  // solver in use
+    int mg_nlev;             // levels including the lattice
+    int mg_cta_from;         // first level handled by one block alone
+    MgLevel mg_lev[MG_MAXLEV];
+    float *mg_r, *mg_z, *mg_q, *mg_p[2];  // lattice-level CG vectors
+    double *mg_part;         // [4][pois_blocks] reduction partials
 
     // learned warm start of the Poisson solve (ekl_net.cu)
     void *net;
@@ -145,6 +169,7 @@ int get_fields_f64(Ctx &c, double *d_n, double *d_j, double *d_phi);
 int get_state_f64(Ctx &c, double *d_f, double *d_phi);
 int set_state_f64(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_f64();
+int mg_blocks_f64();
 
 int init_populations_f32(Ctx &c, const double *d_n_init);
 int run_steps_f32(Ctx &c, int nsteps);
@@ -152,6 +177,7 @@ int get_fields_f32(Ctx &c, double *d_n, double *d_j, double *d_phi);
 int get_state_f32(Ctx &c, double *d_f, double *d_phi);
 int set_state_f32(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_f32();
+int mg_blocks_f32();
 
 int init_populations_bf16(Ctx &c, const double *d_n_init);
 int run_steps_bf16(Ctx &c, int nsteps);
@@ -159,6 +185,7 @@ int get_fields_bf16(Ctx &c, double *d_n, double *d_j, double *d_phi);
 int get_state_bf16(Ctx &c, double *d_f, double *d_phi);
 int set_state_bf16(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_bf16();
+int mg_blocks_bf16();
 
 int init_populations_fp16(Ctx &c, const double *d_n_init);
 int run_steps_fp16(Ctx &c, int nsteps);
@@ -166,6 +193,7 @@ int get_fields_fp16(Ctx &c, double *d_n, double *d_j, double *d_phi);
 int get_state_fp16(Ctx &c, double *d_f, double *d_phi);
 int set_state_fp16(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_fp16();
+int mg_blocks_fp16();
 
 size_t real_size(int prec);
 size_t store_size(int prec);

@@ -283,24 +283,19 @@ __device__ __forceinline__ void sor_apply(PhiT *phi, int i, uint32_t m, PhiT bi,
 
 constexpr int POIS_KMAX = 2;  // nodes per colour a thread keeps in registers
 
+// Poisson source of the step, b = 4 pi l_B (rho - <rho>_fluid) on fluid
+// nodes and 0 on walls (Eqs. 2-3 with the neutralising mean of Sec. III),
+// written to a.b; returns this block's sum of b^2 (valid in thread 0).
+// Every thread of the block must call it.
 template <typename S, typename R, typename PhiT>
-__global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R, PhiT> a)
+__device__ double form_source(const StepArgs<S, R, PhiT> &a, int tid, int nthr, double *sh, double *bc)
 {
-    __shared__ double sh[POIS_THREADS / 32];
-    __shared__ double bc[1];
-    __shared__ int cflag;
-    const Grid3 g = a.g;
-    const unsigned nblk = gridDim.x;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nthr = nblk * blockDim.x;
-    unsigned bar_k = 0;
-    // --- source: subtract the mean charge over fluid nodes (neutralisation)
     const double csum = sum_partials(a.part_charge, a.nblocks_charge, bc);
     const double nfl = a.n_fluid;
     const double mean = nfl > 0 ? csum / nfl : 0.0;
     double bl = 0.0;
     float blf = 0.f;
-    for (long long i = tid; i < g.N; i += nthr) {
+    for (long long i = tid; i < a.g.N; i += nthr) {
         uint32_t m = a.mask[i];
         PhiT bv;
         if (m & SOLID_BIT) {
@@ -322,9 +317,23 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R,
         }
         __stcg(a.b + i, bv);
     }
-    double t;
-    if constexpr (((PhiT)0.5) != 0) t = block_sum(bl, sh);
-    else t = block_sum_lanes0(warp_sum_ff_lane0(blf), sh);
+    if constexpr (((PhiT)0.5) != 0) return block_sum(bl, sh);
+    else return block_sum_lanes0(warp_sum_ff_lane0(blf), sh);
+}
+
+template <typename S, typename R, typename PhiT>
+__global__ void __launch_bounds__(POIS_THREADS, 1) poisson_kernel(StepArgs<S, R, PhiT> a)
+{
+    __shared__ double sh[POIS_THREADS / 32];
+    __shared__ double bc[1];
+    __shared__ int cflag;
+    const Grid3 g = a.g;
+    const unsigned nblk = gridDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthr = nblk * blockDim.x;
+    unsigned bar_k = 0;
+    // --- source: subtract the mean charge over fluid nodes (neutralisation)
+    const double t = form_source(a, tid, nthr, sh, bc);
     if (threadIdx.x == 0) a.part_pois[blockIdx.x] = t;
     if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return;
     const double bn2 = sum_partials(a.part_pois, (int)nblk, bc);

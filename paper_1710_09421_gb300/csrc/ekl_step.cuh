@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "ekl_kernels.cuh"
+#include "ekl_mg.cuh"
 
 namespace ekl {
 
@@ -106,6 +107,24 @@ static MdArgs<S, R, PhiT, DEV> make_md_args(Ctx &c, const StepArgs<S, R, PhiT> &
     return md;
 }
 
+static inline MgArgs make_mg_args(const Ctx &c)
+{
+    MgArgs m;
+    m.r = c.mg_r;
+    m.z = c.mg_z;
+    m.q = c.mg_q;
+    m.p[0] = c.mg_p[0];
+    m.p[1] = c.mg_p[1];
+    m.part = c.mg_part;
+    m.nlev = c.mg_nlev;
+    m.cta_from = c.mg_cta_from;
+    m.nu = MG_NU;
+    m.coarse_sweeps = MG_COARSE_SWEEPS;
+    m.inner_red = MG_INNER_RED;
+    for (int l = 0; l < MG_MAXLEV; l++) m.lev[l] = c.mg_lev[l];
+    return m;
+}
+
 static inline int cuda_ok(cudaError_t e) { return e == cudaSuccess ? EKL_OK : EKL_ERR_CUDA; }
 
 static inline void phase_begin(Ctx &c, int ph)
@@ -154,7 +173,15 @@ template <typename S, typename R, typename PhiT, bool DEV> int steps_impl(Ctx &c
         }
         phase_begin(c, PH_POISSON);
         cudaMemsetAsync(c.barrier, 0, 4 * sizeof(unsigned), c.stream);
-        if (c.pois_tiled) {
+        if (c.mg) {
+            MgArgs m = make_mg_args(c);
+            void *args[] = {&a, &m};
+            cudaError_t e = cudaLaunchCooperativeKernel((const void *)poisson_mg_kernel<S, R, PhiT>,
+                                                        dim3(c.pois_blocks), dim3(POIS_THREADS), args, 0,
+                                                        c.stream);
+            c.launches++;
+            if (e != cudaSuccess) return EKL_ERR_CUDA;
+        } else if (c.pois_tiled) {
             TileGeom tg{c.tile_ty, c.tile_tz, c.tile_nty, c.tile_ntz};
             const size_t smem = tile_smem_bytes<PhiT>(c.nx, tg);
             static size_t attr_bytes = 0;
@@ -344,6 +371,13 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_impl(Batch 
 }
 
 // occupancy of the cooperative Poisson kernel for this instantiation
+template <typename S, typename R, typename PhiT> int mg_max_blocks_per_sm()
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, poisson_mg_kernel<S, R, PhiT>, POIS_THREADS, 0);
+    return nb;
+}
+
 template <typename S, typename R, typename PhiT> int poisson_max_blocks_per_sm()
 {
     int nb = 0;
@@ -367,5 +401,6 @@ template <typename S, typename R, typename PhiT> int poisson_max_blocks_per_sm()
         return state_impl<S, R, PhiT, DEV>(c, (double *)f, (double *)p, 0);                      \
     }                                                                                            \
     int pois_blocks_##SUFFIX() { return poisson_max_blocks_per_sm<S, R, PhiT>(); }                \
+    int mg_blocks_##SUFFIX() { return mg_max_blocks_per_sm<S, R, PhiT>(); }                       \
     int run_batch_##SUFFIX(Batch &b, int n) { return batch_impl<S, R, PhiT, DEV>(b, n); }         \
     }

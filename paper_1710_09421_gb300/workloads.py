@@ -33,6 +33,7 @@ FLAG_EQ_BARYCENTRIC = 1 << 0   # f_eq and S use the barycentric u* (printed read
 FLAG_GAMMA_LITERAL = 1 << 1    # gamma^alpha = xi for every species (literal Sec. II.B)
 FLAG_NO_BEAD_NOISE = 1 << 2    # switch off the Langevin noise on the beads
 FLAG_POISSON_GLOBAL = 1 << 3   # CUDA library only: no shared-memory Poisson tiles
+FLAG_POISSON_MG = 1 << 4       # CUDA library only: multigrid-preconditioned CG Poisson solver
 
 BOND_FENE = 0
 BOND_HARMONIC = 1

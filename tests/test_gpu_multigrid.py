@@ -1,0 +1,115 @@
+"""The multigrid-preconditioned CG Poisson solver (EKL_POISSON_MG) through the C ABI.
+
+Its answer is defined as the solution of the same discrete Poisson equation
+(Eqs. 2-3) to the same relative tolerance, so the oracle judges it by the
+true residual of the GPU potential under the oracle's own operator and
+source (oracle.Sim.poisson_residual, pinned by a manufactured solution), and
+by the trajectory against the oracle's SOR run at a tight tolerance: two
+potentials that both meet ||b - A phi|| <= tol ||b|| differ by at most about
+cond(A) tol in relative terms (cond ~ 1e3 on these boxes), which moves
+densities and velocities by far less than that.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1710_09421_gb300 as E
+from paper_1710_09421_gb300 import workloads as W
+from helpers import box, rel
+from test_gpu_parity import _compare
+
+pytestmark = pytest.mark.gpu
+
+MG = W.FLAG_POISSON_MG
+
+
+def _residual_steps(wl, steps, tol):
+    sim = E.Simulation(wl)
+    ref = oracle.Sim(wl.replace(poisson_tol=min(tol, 1e-13)), threads=8)
+    out = []
+    for _ in range(steps):
+        assert sim.step(1) >= 0
+        assert ref.step(1) >= 0
+        _, phi, _ = sim.get_state()
+        st = sim.stats()
+        out.append((ref.poisson_residual(ref.last_rho(), phi), st["poisson_res"], st["poisson_iters"]))
+    sim.close()
+    return out
+
+
+def test_mg_true_residual_under_oracle_operator_pore_f64():
+    wl = W.small_pore(nx=16, ny=16, nz=20, membrane=(8, 11), radius=3.0, n_beads=4,
+                      precision="f64").replace(poisson_tol=1e-10, flags=MG)
+    for res_oracle, res_gpu, iters in _residual_steps(wl, 4, 1e-10):
+        assert res_gpu <= 1e-10 and 0 < iters < 40, (res_gpu, iters)
+        # same source to ~1e-15, so the oracle sees the tolerance met
+        assert res_oracle <= 1.001e-10, res_oracle
+
+
+def test_mg_closed_box_odd_extents_f64():
+    """No periodic axis and odd extents: coarse cells with a single child
+    column (padding) and zero conductance on the box faces."""
+    solid = np.zeros((11, 9, 13), np.uint8)
+    solid[4:7, 3:6, 5:9] = 1
+    wl = box(13, 9, 11, periodic=(0, 0, 0), solid=solid, E_app=(1e-3, 2e-3, 0.0),
+             n_init=W.ion_densities(solid, 0.01, 1.0, 0.0, 1e-3, 5), poisson_tol=1e-11, flags=MG)
+    for res_oracle, res_gpu, iters in _residual_steps(wl, 3, 1e-11):
+        assert res_gpu <= 1e-11 and 0 < iters < 40, (res_gpu, iters)
+        assert res_oracle <= 1.001e-11, res_oracle
+
+
+def test_mg_trajectory_f64_matches_oracle():
+    """30 steps of the pore with a 4-bead chain: the MG run (tol 1e-12) against
+    the oracle's SOR run at the same tolerance."""
+    wl = W.small_pore(nx=16, ny=16, nz=20, membrane=(8, 11), radius=3.0, n_beads=4,
+                      precision="f64").replace(poisson_tol=1e-12, flags=MG)
+    errs, sg, so = _compare(wl, 30, 1e-12, precision="f64")
+    print(errs, sg["poisson_iters"], so["poisson_iters"])
+    assert errs["n"] < 1e-10 and errs["u_flow"] < 1e-8 and errs["R"] < 1e-8, errs
+    assert errs["phi"] < 1e-8, errs
+
+
+def test_mg_fp32_bench_pore_converges_and_agrees_with_sor():
+    wl = W.config_pore_fp32()
+    mg = E.Simulation(wl.replace(flags=MG))
+    sor = E.Simulation(wl)
+    # the chain's own field trips the CFL warning bit on this workload
+    for sim in (mg, sor):
+        rc = sim.step(5)
+        assert rc >= 0 and not (rc & E.EKL_WARN_NOCONV), rc
+    st = mg.stats()
+    print("mg", st["poisson_iters"], st["poisson_res"], "sor", sor.stats()["poisson_iters"])
+    assert st["poisson_res"] <= wl.poisson_tol and 0 < st["poisson_iters"] <= 30
+    fluid = wl.solid.ravel() == 0
+    pm, ps = mg.fields(("phi",))["phi"], sor.fields(("phi",))["phi"]
+    d = rel(pm[fluid], ps[fluid])
+    print("phi mg vs sor", d)
+    assert d < 1e-4
+    mg.close()
+    sor.close()
+
+
+def test_mg_bitwise_reproducible_and_fixed_iterations():
+    wl = W.small_pore(nx=16, ny=16, nz=20, membrane=(8, 11), radius=3.0, n_beads=4,
+                      precision="f32").replace(flags=MG)
+    a, b = E.Simulation(wl), E.Simulation(wl)
+    a.step(10)
+    b.step(10)
+    fa, fb = a.fields(), b.fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    a.close()
+    b.close()
+    c = E.Simulation(wl.replace(poisson_fixed_iter=3))
+    c.step(2)
+    st = c.stats()
+    assert st["poisson_iters"] == 3 and st["poisson_sweeps"] == 6
+    c.close()
+
+
+def test_mg_rejects_periodic_extent_without_coarse_level():
+    wl = box(6, 8, 8, periodic=(1, 1, 1), flags=MG)
+    with pytest.raises(E.EklError) as ei:
+        E.Simulation(wl)
+    assert ei.value.code == E.EKL_ERR_ARG
+    assert b"multiple" in E.load().ekl_last_error()

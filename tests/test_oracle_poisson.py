@@ -140,3 +140,35 @@ def test_node_gradient_linear_and_ghost():
     assert np.allclose(g[2][lo], (phi[lo] + 0.3 - (phi[lo] + 4 * math.pi * 0.8 * 0.02)) / 2)
     hi = fluid & (z == nz - 2)
     assert np.allclose(g[2][hi], (phi[hi] - (phi[hi] - 0.3)) / 2)
+
+
+def test_residual_function_manufactured_solution():
+    """eko_poisson_residual against an independently assembled operator:
+    rho = -L phi / (4 pi l_B) makes phi an exact solution; a kick delta at one
+    node leaves exactly ||L delta|| / ||b||; phi = 0 leaves ||b|| / ||b|| = 1;
+    and the SOR solver's answer meets its own tolerance."""
+    rng = np.random.default_rng(11)
+    nx, ny, nz = 6, 4, 6
+    periodic = (1, 1, 0)
+    while True:
+        solid = (rng.random((nz, ny, nx)) < 0.2).astype(np.uint8)
+        lab, nlab = ndimage.label(solid == 0)
+        if nlab == 1:
+            break
+    lb = 0.7
+    wl = box(nx, ny, nz, periodic=periodic, solid=solid, bjerrum=lb)
+    s = oracle.Sim(wl)
+    L, fluid = _laplacian(solid, periodic)
+    phi = rng.standard_normal(solid.size) * fluid
+    rho = -(L @ phi) / (4 * math.pi * lb)
+    assert abs(rho[fluid].sum()) < 1e-12
+    assert s.poisson_residual(rho, phi) < 1e-14
+    assert s.poisson_residual(rho, np.zeros_like(phi)) == pytest.approx(1.0, rel=1e-14)
+    i = int(np.flatnonzero(fluid)[5])
+    kick = np.zeros_like(phi)
+    kick[i] = 1e-3
+    b = -(L @ phi)
+    want = np.linalg.norm(L @ kick) / np.linalg.norm(b)
+    assert s.poisson_residual(rho, phi + kick) == pytest.approx(want, rel=1e-9)
+    sol, it, res = s.poisson(rho, tol=1e-11)
+    assert it > 0 and s.poisson_residual(rho, sol) <= 1e-11 * 1.01
