@@ -47,7 +47,7 @@ struct PrecOps {
     int (*get_state)(Ctx &, double *, double *);
     int (*set_state)(Ctx &, const double *, const double *);
     int (*pois_blocks)();
-    int (*mg_blocks)();
+    int (*mg_blocks)(size_t);
 };
 
 const PrecOps &ops(int prec)
@@ -140,6 +140,7 @@ void release(Ctx &c)
     dev_free(c, c.mg_p[0], 0);
     dev_free(c, c.mg_p[1], 0);
     dev_free(c, c.mg_part, 0);
+    dev_free(c, c.mg_dense, 0);
     warmstart_free(c);
     (void)rs;
     for (int k = 0; k < 2 * PH_COUNT; k++)
@@ -225,6 +226,107 @@ void dev_free(Ctx &c, void *p, size_t bytes)
 
 namespace {
 
+// Pseudo-inverse of the coarsest multigrid operator A (cells with conductances
+// sig: +x, +y, +z faces, 1/diag; inactive cells have none).  A is the graph
+// Laplacian of the active cells, symmetric positive semi-definite with the
+// constants of each connected part as null space, so
+//   A^+ = (A + sum_parts 1_p 1_p^T / n_p)^-1 - sum_parts 1_p 1_p^T / n_p,
+// the bracket being positive definite (Cholesky, FP64).  Returns row-major
+// FP32 [n][n] with zero rows and columns on inactive cells.
+static std::vector<float> coarse_pinv(int nx, int ny, int nz, const std::vector<float4> &sig)
+{
+    const int n = nx * ny * nz;
+    std::vector<double> B((size_t)n * n, 0.0);
+    auto at = [&](int i, int j) -> double & { return B[(size_t)i * n + j]; };
+    std::vector<int> act(n), part(n, -1);
+    for (int i = 0; i < n; i++) act[i] = sig[i].w != 0.f;
+    auto nbr = [&](int i, int a) {
+        int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+        if (a == 0) x = (x + 1) % nx;
+        if (a == 1) y = (y + 1) % ny;
+        if (a == 2) z = (z + 1) % nz;
+        return x + nx * (y + ny * z);
+    };
+    for (int i = 0; i < n; i++) {
+        const float s3[3] = {sig[i].x, sig[i].y, sig[i].z};
+        for (int a = 0; a < 3; a++) {
+            if (s3[a] == 0.f) continue;
+            const int j = nbr(i, a);
+            at(i, i) += s3[a];
+            at(j, j) += s3[a];
+            at(i, j) -= s3[a];
+            at(j, i) -= s3[a];
+        }
+    }
+    // connected parts of the active cells (faces with sigma > 0)
+    std::vector<int> count, stack;
+    for (int i = 0; i < n; i++) {
+        if (!act[i] || part[i] >= 0) continue;
+        const int p = (int)count.size();
+        count.push_back(0);
+        stack.assign(1, i);
+        part[i] = p;
+        while (!stack.empty()) {
+            const int u = stack.back();
+            stack.pop_back();
+            count[p]++;
+            for (int j = 0; j < n; j++)
+                if (j != u && at(u, j) != 0.0 && part[j] < 0) {
+                    part[j] = p;
+                    stack.push_back(j);
+                }
+        }
+    }
+    for (int i = 0; i < n; i++) {
+        if (!act[i]) {
+            at(i, i) = 1.0;
+            continue;
+        }
+        for (int j = 0; j < n; j++)
+            if (act[j] && part[j] == part[i]) at(i, j) += 1.0 / count[part[i]];
+    }
+    // Cholesky B = L L^T (lower triangle in place)
+    for (int j = 0; j < n; j++) {
+        double d = at(j, j);
+        for (int k = 0; k < j; k++) d -= at(j, k) * at(j, k);
+        if (!(d > 0.0)) return {};
+        d = sqrt(d);
+        at(j, j) = d;
+        for (int i = j + 1; i < n; i++) {
+            double v = at(i, j);
+            const double *ri = &B[(size_t)i * n], *rj = &B[(size_t)j * n];
+            for (int k = 0; k < j; k++) v -= ri[k] * rj[k];
+            at(i, j) = v / d;
+        }
+    }
+    // Wt = (L^-1)^T (upper, row j = column j of L^-1), then B^-1 = Wt Wt^T
+    std::vector<double> Wt((size_t)n * n, 0.0);
+    for (int j = 0; j < n; j++) {
+        double *w = &Wt[(size_t)j * n];
+        w[j] = 1.0 / at(j, j);
+        for (int i = j + 1; i < n; i++) {
+            const double *ri = &B[(size_t)i * n];
+            double v = 0.0;
+            for (int k = j; k < i; k++) v -= ri[k] * w[k];
+            w[i] = v / ri[i];
+        }
+    }
+    std::vector<float> M((size_t)n * n, 0.f);
+    for (int i = 0; i < n; i++) {
+        if (!act[i]) continue;
+        const double *wi = &Wt[(size_t)i * n];
+        for (int j = 0; j <= i; j++) {
+            if (!act[j]) continue;
+            const double *wj = &Wt[(size_t)j * n];
+            double v = 0.0;
+            for (int k = i; k < n; k++) v += wi[k] * wj[k];
+            if (part[i] == part[j]) v -= 1.0 / count[part[i]];
+            M[(size_t)i * n + j] = M[(size_t)j * n + i] = (float)v;
+        }
+    }
+    return M;
+}
+
 // Multigrid hierarchy of the Poisson operator (EKL_POISSON_MG): levels halve
 // every extent (rounding up) while each periodic extent stays even, down to
 // MG_COARSEST_CELLS cells.  Face conductances: 1 on the lattice's open faces
@@ -234,7 +336,6 @@ namespace {
 template <typename Alloc>
 static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A)
 {
-    if (ops(c.prec).mg_blocks() < 1) return "multigrid kernel cannot be resident";
     int d[MG_MAXLEV][3];
     d[0][0] = c.nx;
     d[0][1] = c.ny;
@@ -318,8 +419,18 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A)
         ml.e = (float *)A(NC * sizeof(float));
         ml.f = (float *)A(NC * sizeof(float));
         if (!ml.sig || !ml.e || !ml.f) return nullptr;
+        // inactive cells are never written and must read as 0
+        if (cudaMemset(ml.e, 0, NC * sizeof(float)) != cudaSuccess) return "multigrid setup failed";
         if (cudaMemcpy(ml.sig, h4.data(), NC * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess)
             return "multigrid upload failed";
+        if (l == nlev - 1 && NC <= MG_DENSE_CELLS) {
+            const std::vector<float> M = coarse_pinv(C[0], C[1], C[2], h4);
+            if (M.empty()) return "coarsest multigrid operator is not semi-definite";
+            c.mg_dense = (float *)A(M.size() * sizeof(float));
+            if (!c.mg_dense) return nullptr;
+            if (cudaMemcpy(c.mg_dense, M.data(), M.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+                return "multigrid upload failed";
+        }
         for (int a = 0; a < 3; a++) sg[a].swap(cs[a]);
     }
     c.mg_lev[0].nx = c.nx;
@@ -327,12 +438,30 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A)
     c.mg_lev[0].nz = c.nz;
     c.mg_lev[0].N = (int)N;
     c.mg_nlev = nlev;
+    // block 0 takes every level from the first one of at most MG_CTA_CELLS
+    // cells (their e and f in its shared memory); at least the coarsest
+    int maxdyn = 0;
+    cudaDeviceGetAttribute(&maxdyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device);
     c.mg_cta_from = nlev - 1;
+    // per level: e and f (padded to 16 bytes) and the float4 conductances
+    auto cta_bytes = [&](int from) {
+        size_t bytes = 0;
+        for (int k = from; k < nlev; k++)
+            bytes += sizeof(float) * (((2 * (size_t)c.mg_lev[k].N + 3) & ~(size_t)3) + 4 * (size_t)c.mg_lev[k].N);
+        return bytes;
+    };
     for (int l = 1; l < nlev; l++)
-        if (c.mg_lev[l].N <= MG_CTA_CELLS) {
+        if (c.mg_lev[l].N <= MG_CTA_CELLS && cta_bytes(l) + 4096 <= (size_t)maxdyn) {
             c.mg_cta_from = l;
             break;
         }
+    c.mg_smem = cta_bytes(c.mg_cta_from);
+    if (c.mg_dense) {  // exact coarsest solve: every other level is grid-wide
+        c.mg_cta_from = nlev - 1;
+        c.mg_smem = 0;
+    }
+    if (c.mg_smem + 4096 > (size_t)maxdyn) return "coarsest multigrid level too large for shared memory";
+    if (ops(c.prec).mg_blocks(c.mg_smem) < 1) return "multigrid kernel cannot be resident";
     c.mg_r = (float *)A(N * sizeof(float));
     c.mg_z = (float *)A(N * sizeof(float));
     c.mg_q = (float *)A(N * sizeof(float));

@@ -33,8 +33,9 @@ constexpr int MG_MAXLEV = 12;
 constexpr int MG_NU = 2;                 // red-black smoothing sweeps before and after the coarse correction
 constexpr int MG_COARSE_SWEEPS = 8;      // (R B)^k R half sweeps on the coarsest level
 constexpr float MG_INNER_RED = 1e-4f;    // CG residual reduction before the true residual is formed
-constexpr int MG_COARSEST_CELLS = 512;   // stop coarsening at or below this many cells
-constexpr int MG_CTA_CELLS = 16384;      // levels this small are handled by one block
+constexpr int MG_COARSEST_CELLS = 1024;  // stop coarsening at or below this many cells
+constexpr int MG_DENSE_CELLS = 1024;     // coarsest levels this small are solved exactly (dense pseudo-inverse)
+constexpr int MG_CTA_CELLS = 2048;       // levels this small are handled by one block
 struct MgLevel {
     int nx, ny, nz, N;
     float4 *sig;  // conductances of the +x, +y, +z faces and 1 / diagonal (0: inactive cell)
@@ -103,8 +104,10 @@ struct Ctx {
     int mg;                  // solver in use
     int mg_nlev;             // levels including the lattice
     int mg_cta_from;         // first level handled by one block alone
+    size_t mg_smem;          // dynamic shared memory of the multigrid launch
     MgLevel mg_lev[MG_MAXLEV];
     float *mg_r, *mg_z, *mg_q, *mg_p[2];  // lattice-level CG vectors
+    float *mg_dense;         // pseudo-inverse of the coarsest operator, or null
     double *mg_part;         // [4][pois_blocks] reduction partials
 
     // learned warm start of the Poisson solve (ekl_net.cu)
@@ -169,7 +172,7 @@ int get_fields_f64(Ctx &c, double *d_n, double *d_j, double *d_phi);
 int get_state_f64(Ctx &c, double *d_f, double *d_phi);
 int set_state_f64(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_f64();
-int mg_blocks_f64();
+int mg_blocks_f64(size_t smem);
 
 int init_populations_f32(Ctx &c, const double *d_n_init);
 int run_steps_f32(Ctx &c, int nsteps);
@@ -177,7 +180,7 @@ int get_fields_f32(Ctx &c, double *d_n, double *d_j, double *d_phi);
 int get_state_f32(Ctx &c, double *d_f, double *d_phi);
 int set_state_f32(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_f32();
-int mg_blocks_f32();
+int mg_blocks_f32(size_t smem);
 
 int init_populations_bf16(Ctx &c, const double *d_n_init);
 int run_steps_bf16(Ctx &c, int nsteps);
@@ -185,7 +188,7 @@ int get_fields_bf16(Ctx &c, double *d_n, double *d_j, double *d_phi);
 int get_state_bf16(Ctx &c, double *d_f, double *d_phi);
 int set_state_bf16(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_bf16();
-int mg_blocks_bf16();
+int mg_blocks_bf16(size_t smem);
 
 int init_populations_fp16(Ctx &c, const double *d_n_init);
 int run_steps_fp16(Ctx &c, int nsteps);
@@ -193,7 +196,7 @@ int get_fields_fp16(Ctx &c, double *d_n, double *d_j, double *d_phi);
 int get_state_fp16(Ctx &c, double *d_f, double *d_phi);
 int set_state_fp16(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_fp16();
-int mg_blocks_fp16();
+int mg_blocks_fp16(size_t smem);
 
 size_t real_size(int prec);
 size_t store_size(int prec);

@@ -35,7 +35,8 @@ namespace ekl {
 
 struct MgArgs {
     float *r, *z, *q, *p[2];
-    double *part;  // [4][gridDim.x]
+    double *part;         // [4][gridDim.x]
+    const float *dense;   // pseudo-inverse of the coarsest operator [N][N], or null
     int nlev, cta_from, nu, coarse_sweeps;
     float inner_red;
     MgLevel lev[MG_MAXLEV];
@@ -66,14 +67,78 @@ __device__ __forceinline__ Pair mg_pair(int h, int hx, int ny, int c)
     return p;
 }
 
+template <bool SH> __device__ __forceinline__ float mg_ld(const float *p)
+{
+    if constexpr (SH) return *p;
+    else return __ldcg(p);
+}
+template <bool SH> __device__ __forceinline__ void mg_st(float *p, float v)
+{
+    if constexpr (SH) *p = v;
+    else __stcg(p, v);
+}
+// conductances: read-only global memory, or block 0's shared-memory copy
+template <bool SH> __device__ __forceinline__ float4 mg_sig(const float4 *p)
+{
+    if constexpr (SH) return *p;
+    else return __ldg(p);
+}
+template <bool SH> __device__ __forceinline__ float mg_sx(const float4 *p)
+{
+    if constexpr (SH) return p->x;
+    else return __ldg(&p->x);
+}
+template <bool SH> __device__ __forceinline__ float mg_sy(const float4 *p)
+{
+    if constexpr (SH) return p->y;
+    else return __ldg(&p->y);
+}
+template <bool SH> __device__ __forceinline__ float mg_sz(const float4 *p)
+{
+    if constexpr (SH) return p->z;
+    else return __ldg(&p->z);
+}
+template <bool SH> __device__ __forceinline__ float mg_sw(const float4 *p)
+{
+    if constexpr (SH) return p->w;
+    else return __ldg(&p->w);
+}
+
 // ------------------------------------------------------------ lattice level
-// Half sweep of colour c of z <- (r + sum_open z_j) / deg.  `first`: z starts
-// from zero (colour c takes r / deg, the other colour 0).  `rz`: add r_i z_i
-// of both nodes of each pair (only meaningful on the last half sweep of a
-// V-cycle, when the other colour is final).
-template <bool RZ>
-static __device__ void fine_half(const Grid3 &g, const uint32_t *__restrict__ mask, const float *r, float *z, int c,
-                          bool first, int t0, int nt, float &rz)
+// The first half sweep of every smoothing pass starts from zero, so it only
+// sets the colour-0 nodes to r / deg (colour-1 values are overwritten before
+// they are read); it is fused into the phase that produces r.  Likewise a
+// red-black update never reads the node's own old value, so the coarse-grid
+// correction is added on the fly where the first post-smoothing half sweep
+// (colour 1) reads its colour-0 neighbours, and colour-0 nodes take the
+// corrected neighbours in the next half sweep: no separate prolongation pass.
+
+// neighbour across face f (order -x, +x, -y, +y, -z, +z), wrapped
+__device__ __forceinline__ void mg_face_coord(int nx, int ny, int nz, int x, int y, int z, int f, int &X, int &Y,
+                                              int &Z)
+{
+    X = x;
+    Y = y;
+    Z = z;
+    if (f == 0) X = x == 0 ? nx - 1 : x - 1;
+    if (f == 1) X = x == nx - 1 ? 0 : x + 1;
+    if (f == 2) Y = y == 0 ? ny - 1 : y - 1;
+    if (f == 3) Y = y == ny - 1 ? 0 : y + 1;
+    if (f == 4) Z = z == 0 ? nz - 1 : z - 1;
+    if (f == 5) Z = z == nz - 1 ? 0 : z + 1;
+}
+__device__ __forceinline__ int mg_parent(const MgLevel &C, int x, int y, int z)
+{
+    return (x >> 1) + C.nx * ((y >> 1) + C.ny * (z >> 1));
+}
+
+// Half sweep of colour c of z <- (r + sum_open z_j) / deg.  PRO: the
+// neighbours' values include the level-1 correction C.e(parent).  RZ: add
+// r_i z_i of both nodes of each pair (the last half sweep of a V-cycle, when
+// the other colour is final).
+template <bool RZ, bool PRO>
+static __device__ void fine_half(const Grid3 &g, const uint32_t *__restrict__ mask, const float *r, float *z,
+                                 const MgLevel &C, int c, int t0, int nt, float &rz)
 {
     const int hx = (g.nx + 1) >> 1, np = hx * g.ny * g.nz;
     for (int h = t0; h < np; h += nt) {
@@ -81,84 +146,94 @@ static __device__ void fine_half(const Grid3 &g, const uint32_t *__restrict__ ma
         if (p.x < g.nx) {
             const int i = p.x + g.nx * p.row;
             const uint32_t m = __ldg(mask + i);
-            if (!(m & SOLID_BIT)) {
-                const unsigned o = mg_open(m);
+            const unsigned o = mg_open(m);
+            if (!(m & SOLID_BIT) && o) {
+                int nb[6];
+                face_nbrs(g, p.x, p.y, p.z, i, nb);
                 const float ri = __ldcg(r + i);
                 float v = ri;
-                if (!first) {
-                    int nb[6];
-                    face_nbrs(g, p.x, p.y, p.z, i, nb);
 #pragma unroll
-                    for (int f = 0; f < 6; f++)
-                        if ((o >> f) & 1u) v += __ldcg(z + nb[f]);
-                }
-                v = o ? v * mg_inv_deg(__popc(o)) : 0.f;
+                for (int f = 0; f < 6; f++)
+                    if ((o >> f) & 1u) {
+                        v += __ldcg(z + nb[f]);
+                        if (PRO) {
+                            int X, Y, Z;
+                            mg_face_coord(g.nx, g.ny, g.nz, p.x, p.y, p.z, f, X, Y, Z);
+                            v += __ldcg(C.e + mg_parent(C, X, Y, Z));
+                        }
+                    }
+                v *= mg_inv_deg(__popc(o));
                 __stcg(z + i, v);
                 if (RZ) rz += ri * v;
             }
         }
-        if (p.xo < g.nx) {
+        if (RZ && p.xo < g.nx) {
             const int io = p.xo + g.nx * p.row;
-            if (first) {
-                __stcg(z + io, 0.f);
-            } else if (RZ) {
-                const uint32_t m = __ldg(mask + io);
-                if (!(m & SOLID_BIT) && mg_open(m)) rz += __ldcg(r + io) * __ldcg(z + io);
-            }
+            const uint32_t m = __ldg(mask + io);
+            if (!(m & SOLID_BIT) && mg_open(m)) rz += __ldcg(r + io) * __ldcg(z + io);
         }
     }
 }
 
-// f1 = sum over the children of each level-1 cell of (r - A z)
-static __device__ void fine_restrict(const Grid3 &g, const uint32_t *__restrict__ mask, const float *r, const float *z,
-                              const MgLevel &C, int t0, int nt)
+// Restriction: a warp takes 8 consecutive coarse cells; lane = X + 8 k
+// computes the two x-children (dx = 0, 1) in the (dy, dz) = (k & 1, k >> 1)
+// row of cell X, so each quarter-warp reads 16 consecutive fine nodes; the
+// four rows of a cell are summed by shuffles.  The loop is warp-uniform.
+__device__ __forceinline__ float mg_sum_rows(float v)
 {
-    for (int I = t0; I < C.N; I += nt) {
-        const int X = I % C.nx, t = I / C.nx, Y = t % C.ny, Z = t / C.ny;
-        float s = 0.f;
-        for (int dz = 0; dz < 2; dz++) {
-            const int z0 = 2 * Z + dz;
-            if (z0 >= g.nz) continue;
-            for (int dy = 0; dy < 2; dy++) {
-                const int y0 = 2 * Y + dy;
-                if (y0 >= g.ny) continue;
-                for (int dx = 0; dx < 2; dx++) {
-                    const int x0 = 2 * X + dx;
-                    if (x0 >= g.nx) continue;
-                    const int i = x0 + g.nx * (y0 + g.ny * z0);
-                    const uint32_t m = __ldg(mask + i);
-                    if (m & SOLID_BIT) continue;
-                    const unsigned o = mg_open(m);
-                    if (!o) continue;
-                    int nb[6];
-                    face_nbrs(g, x0, y0, z0, i, nb);
-                    float acc = __ldcg(r + i) - (float)__popc(o) * __ldcg(z + i);
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    return v;
+}
+
+// residual r - A z of one fluid node of the lattice (0 elsewhere)
+__device__ __forceinline__ float fine_resid(const Grid3 &g, const uint32_t *__restrict__ mask, const float *r,
+                                            const float *z, int x, int y, int zz)
+{
+    if (x >= g.nx || y >= g.ny || zz >= g.nz) return 0.f;
+    const int i = x + g.nx * (y + g.ny * zz);
+    const uint32_t m = __ldg(mask + i);
+    const unsigned o = mg_open(m);
+    if ((m & SOLID_BIT) || !o) return 0.f;
+    int nb[6];
+    face_nbrs(g, x, y, zz, i, nb);
+    float acc = __ldcg(r + i) - (float)__popc(o) * __ldcg(z + i);
 #pragma unroll
-                    for (int f = 0; f < 6; f++)
-                        if ((o >> f) & 1u) acc += __ldcg(z + nb[f]);
-                    s += acc;
-                }
-            }
-        }
-        __stcg(C.f + I, s);
-    }
+    for (int f = 0; f < 6; f++)
+        if ((o >> f) & 1u) acc += __ldcg(z + nb[f]);
+    return acc;
 }
 
-// z += e1(parent) on the fluid nodes
-static __device__ void fine_prolong(const Grid3 &g, const uint32_t *__restrict__ mask, float *z, const MgLevel &C, int t0,
-                             int nt)
+// C.f = sum over the children of each level-1 cell of (r - A z); FIRST: also
+// start level 1's pre-smoothing (colour-0 cells take f / diag)
+template <bool FIRST>
+static __device__ void fine_restrict(const Grid3 &g, const uint32_t *__restrict__ mask, const float *r,
+                                     const float *z, const MgLevel &C, int t0, int nt)
 {
-    const int N = (int)g.N;
-    for (int i = t0; i < N; i += nt) {
-        const uint32_t m = __ldg(mask + i);
-        if ((m & SOLID_BIT) || !mg_open(m)) continue;
-        const int x = i % g.nx, t = i / g.nx, y = t % g.ny, zz = t / g.ny;
-        const int I = (x >> 1) + C.nx * ((y >> 1) + C.ny * (zz >> 1));
-        __stcg(z + i, __ldcg(z + i) + __ldcg(C.e + I));
+    const int lane = threadIdx.x & 31, total = ((C.N + 7) >> 3) * 32;
+    for (int base = t0 - lane; base < total; base += nt) {
+        const int I = (base >> 2) + (lane & 7), k = lane >> 3;
+        float acc = 0.f;
+        int X = 0, Y = 0, Z = 0;
+        if (I < C.N) {
+            X = I % C.nx;
+            const int t = I / C.nx;
+            Y = t % C.ny;
+            Z = t / C.ny;
+            const int y0 = 2 * Y + (k & 1), z0 = 2 * Z + (k >> 1);
+            acc = fine_resid(g, mask, r, z, 2 * X, y0, z0) + fine_resid(g, mask, r, z, 2 * X + 1, y0, z0);
+        }
+        const float sum = mg_sum_rows(acc);
+        if (I < C.N && k == 0) {
+            __stcg(C.f + I, sum);
+            if (FIRST && !((X + Y + Z) & 1)) __stcg(C.e + I, sum * __ldg(&C.sig[I].w));
+        }
     }
 }
 
 // ------------------------------------------------------------ coarse levels
+// SH: the level's e and f live in shared memory (block 0's part of the cycle);
+// the conductances always come from global memory.
 struct CNbr {
     int xm, xp, ym, yp, zm, zp;
 };
@@ -175,83 +250,94 @@ __device__ __forceinline__ CNbr coarse_nbrs(const MgLevel &L, int x, int y, int 
     return n;
 }
 
+// value of neighbour j (coordinates X, Y, Z), with the coarser correction when PRO
+template <bool SH, bool PRO>
+__device__ __forceinline__ float coarse_val(const MgLevel &L, const MgLevel &C, int j, int X, int Y, int Z)
+{
+    float v = mg_ld<SH>(L.e + j);
+    if (PRO) v += mg_ld<SH>(C.e + mg_parent(C, X, Y, Z));
+    return v;
+}
+
 // Half sweep of colour c of e <- (f + sum sigma e_j) / diag.  Faces beyond a
-// closed side carry sigma = 0, so the wrapped neighbour contributes nothing.
-static __device__ void coarse_half(const MgLevel &L, int c, bool first, int t0, int nt)
+// closed side carry sigma = 0 and inactive cells keep e = 0, so wrapped or
+// inactive neighbours contribute nothing.
+template <bool SH, bool PRO>
+static __device__ void coarse_half(const MgLevel &L, const MgLevel &C, int c, int t0, int nt)
 {
     const int hx = (L.nx + 1) >> 1, np = hx * L.ny * L.nz;
     for (int h = t0; h < np; h += nt) {
         const Pair p = mg_pair(h, hx, L.ny, c);
-        if (p.x < L.nx) {
-            const int i = p.x + L.nx * p.row;
-            const float4 s = __ldg(L.sig + i);
-            if (first) {
-                __stcg(L.e + i, s.w != 0.f ? __ldcg(L.f + i) * s.w : 0.f);
-            } else if (s.w != 0.f) {
-                const CNbr n = coarse_nbrs(L, p.x, p.y, p.z, i);
-                float acc = __ldcg(L.f + i);
-                acc += s.x * __ldcg(L.e + n.xp) + __ldg(&L.sig[n.xm].x) * __ldcg(L.e + n.xm);
-                acc += s.y * __ldcg(L.e + n.yp) + __ldg(&L.sig[n.ym].y) * __ldcg(L.e + n.ym);
-                acc += s.z * __ldcg(L.e + n.zp) + __ldg(&L.sig[n.zm].z) * __ldcg(L.e + n.zm);
-                __stcg(L.e + i, acc * s.w);
-            }
-        }
-        if (first && p.xo < L.nx) __stcg(L.e + p.xo + L.nx * p.row, 0.f);
+        if (p.x >= L.nx) continue;
+        const int i = p.x + L.nx * p.row;
+        const float4 s = mg_sig<SH>(L.sig + i);
+        if (s.w == 0.f) continue;
+        const CNbr n = coarse_nbrs(L, p.x, p.y, p.z, i);
+        const int xm = p.x == 0 ? L.nx - 1 : p.x - 1, xp = p.x == L.nx - 1 ? 0 : p.x + 1;
+        const int ym = p.y == 0 ? L.ny - 1 : p.y - 1, yp = p.y == L.ny - 1 ? 0 : p.y + 1;
+        const int zm = p.z == 0 ? L.nz - 1 : p.z - 1, zp = p.z == L.nz - 1 ? 0 : p.z + 1;
+        float acc = mg_ld<SH>(L.f + i);
+        acc += s.x * coarse_val<SH, PRO>(L, C, n.xp, xp, p.y, p.z) +
+               mg_sx<SH>(L.sig + n.xm) * coarse_val<SH, PRO>(L, C, n.xm, xm, p.y, p.z);
+        acc += s.y * coarse_val<SH, PRO>(L, C, n.yp, p.x, yp, p.z) +
+               mg_sy<SH>(L.sig + n.ym) * coarse_val<SH, PRO>(L, C, n.ym, p.x, ym, p.z);
+        acc += s.z * coarse_val<SH, PRO>(L, C, n.zp, p.x, p.y, zp) +
+               mg_sz<SH>(L.sig + n.zm) * coarse_val<SH, PRO>(L, C, n.zm, p.x, p.y, zm);
+        mg_st<SH>(L.e + i, acc * s.w);
     }
 }
 
-// C.f = sum over the children of each cell of level l+1 of (f - A e) on level l
+// residual f - A e of one cell of a coarse level (0 outside or inactive)
+template <bool SH>
+__device__ __forceinline__ float coarse_resid(const MgLevel &L, int x, int y, int z)
+{
+    if (x >= L.nx || y >= L.ny || z >= L.nz) return 0.f;
+    const int i = x + L.nx * (y + L.ny * z);
+    const float4 sg = mg_sig<SH>(L.sig + i);
+    if (sg.w == 0.f) return 0.f;
+    const CNbr n = coarse_nbrs(L, x, y, z, i);
+    const float sxm = mg_sx<SH>(L.sig + n.xm), sym = mg_sy<SH>(L.sig + n.ym), szm = mg_sz<SH>(L.sig + n.zm);
+    const float diag = sg.x + sg.y + sg.z + sxm + sym + szm;
+    float acc = mg_ld<SH>(L.f + i) - diag * mg_ld<SH>(L.e + i);
+    acc += sg.x * mg_ld<SH>(L.e + n.xp) + sxm * mg_ld<SH>(L.e + n.xm);
+    acc += sg.y * mg_ld<SH>(L.e + n.yp) + sym * mg_ld<SH>(L.e + n.ym);
+    acc += sg.z * mg_ld<SH>(L.e + n.zp) + szm * mg_ld<SH>(L.e + n.zm);
+    return acc;
+}
+
+// C.f = sum over the children of each cell of level l+1 of (f - A e) on
+// level l; FIRST: also start C's pre-smoothing
+template <bool SH, bool FIRST>
 static __device__ void coarse_restrict(const MgLevel &L, const MgLevel &C, int t0, int nt)
 {
-    for (int I = t0; I < C.N; I += nt) {
-        const int X = I % C.nx, t = I / C.nx, Y = t % C.ny, Z = t / C.ny;
-        float s = 0.f;
-        for (int dz = 0; dz < 2; dz++) {
-            const int z0 = 2 * Z + dz;
-            if (z0 >= L.nz) continue;
-            for (int dy = 0; dy < 2; dy++) {
-                const int y0 = 2 * Y + dy;
-                if (y0 >= L.ny) continue;
-                for (int dx = 0; dx < 2; dx++) {
-                    const int x0 = 2 * X + dx;
-                    if (x0 >= L.nx) continue;
-                    const int i = x0 + L.nx * (y0 + L.ny * z0);
-                    const float4 sg = __ldg(L.sig + i);
-                    if (sg.w == 0.f) continue;
-                    const CNbr n = coarse_nbrs(L, x0, y0, z0, i);
-                    const float sxm = __ldg(&L.sig[n.xm].x), sym = __ldg(&L.sig[n.ym].y),
-                                szm = __ldg(&L.sig[n.zm].z);
-                    const float diag = sg.x + sg.y + sg.z + sxm + sym + szm;
-                    float acc = __ldcg(L.f + i) - diag * __ldcg(L.e + i);
-                    acc += sg.x * __ldcg(L.e + n.xp) + sxm * __ldcg(L.e + n.xm);
-                    acc += sg.y * __ldcg(L.e + n.yp) + sym * __ldcg(L.e + n.ym);
-                    acc += sg.z * __ldcg(L.e + n.zp) + szm * __ldcg(L.e + n.zm);
-                    s += acc;
-                }
-            }
+    const int lane = threadIdx.x & 31, total = ((C.N + 7) >> 3) * 32;
+    for (int base = t0 - lane; base < total; base += nt) {
+        const int I = (base >> 2) + (lane & 7), k = lane >> 3;
+        float acc = 0.f;
+        int X = 0, Y = 0, Z = 0;
+        if (I < C.N) {
+            X = I % C.nx;
+            const int t = I / C.nx;
+            Y = t % C.ny;
+            Z = t / C.ny;
+            const int y0 = 2 * Y + (k & 1), z0 = 2 * Z + (k >> 1);
+            acc = coarse_resid<SH>(L, 2 * X, y0, z0) + coarse_resid<SH>(L, 2 * X + 1, y0, z0);
         }
-        __stcg(C.f + I, s);
+        const float sum = mg_sum_rows(acc);
+        if (I < C.N && k == 0) {
+            mg_st<SH>(C.f + I, sum);
+            if (FIRST && !((X + Y + Z) & 1)) mg_st<SH>(C.e + I, sum * mg_sw<SH>(C.sig + I));
+        }
     }
 }
 
-// e_l += e_{l+1}(parent) on the active cells of level l
-static __device__ void coarse_prolong(const MgLevel &L, const MgLevel &C, int t0, int nt)
-{
-    for (int i = t0; i < L.N; i += nt) {
-        if (__ldg(&L.sig[i].w) == 0.f) continue;
-        const int x = i % L.nx, t = i / L.nx, y = t % L.ny, z = t / L.ny;
-        const int I = (x >> 1) + C.nx * ((y >> 1) + C.ny * (z >> 1));
-        __stcg(L.e + i, __ldcg(L.e + i) + __ldcg(C.e + I));
-    }
-}
-
-// subtract the mean over the active cells of level L from v (block-wide)
-static __device__ void coarse_project(const MgLevel &L, float *v, double *sh, double *bc)
+// mean of v over the active cells of level L (block-wide, every thread gets it)
+static __device__ float coarse_mean(const MgLevel &L, const float *v, double *sh, double *bc)
 {
     double s = 0.0, n = 0.0;
     for (int i = threadIdx.x; i < L.N; i += blockDim.x)
-        if (__ldg(&L.sig[i].w) != 0.f) {
-            s += (double)__ldcg(v + i);
+        if (L.sig[i].w != 0.f) {
+            s += (double)v[i];
             n += 1.0;
         }
     const double ts = block_sum(s, sh);
@@ -259,95 +345,178 @@ static __device__ void coarse_project(const MgLevel &L, float *v, double *sh, do
     if (threadIdx.x == 0) bc[0] = tn > 0 ? ts / tn : 0.0;
     __syncthreads();
     const float mean = (float)bc[0];
-    for (int i = threadIdx.x; i < L.N; i += blockDim.x)
-        if (__ldg(&L.sig[i].w) != 0.f) __stcg(v + i, __ldcg(v + i) - mean);
+    __syncthreads();
+    return mean;
+}
+
+// Shared-memory layout of block 0's levels (l >= cta_from): per level e[N]
+// and f[N] (floats, padded to 16 bytes) then sig[N] (float4).
+__device__ __forceinline__ void mg_cta_levels(const MgArgs &m, float *sm, MgLevel *Ls)
+{
+    size_t off = 0;
+    for (int l = m.cta_from; l < m.nlev; l++) {
+        Ls[l] = m.lev[l];
+        const size_t n2 = (2 * (size_t)Ls[l].N + 3) & ~(size_t)3;
+        Ls[l].e = sm + off;
+        Ls[l].f = sm + off + Ls[l].N;
+        Ls[l].sig = (float4 *)(sm + off + n2);
+        off += n2 + 4 * (size_t)Ls[l].N;
+    }
+}
+
+// block 0, once per launch: the conductances of its levels into shared memory
+static __device__ void mg_cta_load(const MgArgs &m, float *sm)
+{
+    MgLevel Ls[MG_MAXLEV];
+    mg_cta_levels(m, sm, Ls);
+    for (int l = m.cta_from; l < m.nlev; l++)
+        for (int i = threadIdx.x; i < Ls[l].N; i += blockDim.x) Ls[l].sig[i] = __ldg(m.lev[l].sig + i);
     __syncthreads();
 }
 
-// Block 0 alone: the V-cycle below (and including) level m.cta_from.
-static __device__ void mg_cta_cycle(const MgArgs &m, double *sh, double *bc)
+// Block 0 alone: the V-cycle at and below level m.cta_from in shared memory.
+// On entry the level's right-hand side is in global memory; on exit its
+// correction is written back there.
+static __device__ void mg_cta_cycle(const MgArgs &m, float *sm, double *sh, double *bc)
 {
     const int t0 = threadIdx.x, nt = blockDim.x;
-    const int last = m.nlev - 1;
-    for (int l = m.cta_from; l < last; l++) {
-        for (int s = 0; s < 2 * m.nu; s++) {
-            coarse_half(m.lev[l], s & 1, s == 0, t0, nt);
-            __syncthreads();
+    const int k0 = m.cta_from, last = m.nlev - 1;
+    MgLevel Ls[MG_MAXLEV];
+    mg_cta_levels(m, sm, Ls);
+    // the right-hand side, and the first half sweep unless k0 is the coarsest
+    {
+        const MgLevel &L = Ls[k0];
+        for (int i = t0; i < L.N; i += nt) {
+            const float f = __ldcg(m.lev[k0].f + i);
+            L.f[i] = f;
+            L.e[i] = k0 < last ? f * L.sig[i].w : 0.f;  // colour 1 is overwritten first
         }
-        coarse_restrict(m.lev[l], m.lev[l + 1], t0, nt);
         __syncthreads();
     }
-    const MgLevel &L = m.lev[last];
-    coarse_project(L, L.f, sh, bc);
-    for (int s = 0; s < 2 * m.coarse_sweeps + 1; s++) {
-        coarse_half(L, s & 1, s == 0, t0, nt);
-        __syncthreads();
-    }
-    coarse_project(L, L.e, sh, bc);
-    for (int l = last - 1; l >= m.cta_from; l--) {
-        coarse_prolong(m.lev[l], m.lev[l + 1], t0, nt);
-        __syncthreads();
-        for (int s = 0; s < 2 * m.nu; s++) {
-            coarse_half(m.lev[l], (s & 1) ^ 1, false, t0, nt);
+    for (int l = k0; l < last; l++) {
+        for (int s = 1; s < 2 * m.nu; s++) {
+            coarse_half<true, false>(Ls[l], Ls[l], s & 1, t0, nt);
             __syncthreads();
         }
+        if (l + 1 < last) coarse_restrict<true, true>(Ls[l], Ls[l + 1], t0, nt);
+        else coarse_restrict<true, false>(Ls[l], Ls[l + 1], t0, nt);
+        __syncthreads();
+    }
+    // coarsest: zero-mean right-hand side, (R B)^k R from zero, zero-mean result
+    {
+        const MgLevel &L = Ls[last];
+        const float mean = coarse_mean(L, L.f, sh, bc);
+        for (int i = t0; i < L.N; i += nt) {
+            const float w = L.sig[i].w;
+            const float f = w != 0.f ? L.f[i] - mean : 0.f;
+            L.f[i] = f;
+            L.e[i] = f * w;  // colour 0 from zero; colour 1 is overwritten first
+        }
+        __syncthreads();
+        for (int s = 1; s < 2 * m.coarse_sweeps + 1; s++) {
+            coarse_half<true, false>(L, L, s & 1, t0, nt);
+            __syncthreads();
+        }
+        const float emean = coarse_mean(L, L.e, sh, bc);
+        for (int i = t0; i < L.N; i += nt)
+            if (L.sig[i].w != 0.f) L.e[i] -= emean;
+        __syncthreads();
+    }
+    for (int l = last - 1; l >= k0; l--) {
+        coarse_half<true, true>(Ls[l], Ls[l + 1], 1, t0, nt);
+        __syncthreads();
+        for (int s = 1; s < 2 * m.nu; s++) {
+            coarse_half<true, false>(Ls[l], Ls[l], (s & 1) ^ 1, t0, nt);
+            __syncthreads();
+        }
+    }
+    for (int i = t0; i < Ls[k0].N; i += nt) __stcg(m.lev[k0].e + i, Ls[k0].e[i]);
+}
+
+// Exact coarsest-level solve e = A^+ f with the host-computed pseudo-inverse
+// (symmetric; it removes the null-space part of f and returns a zero-mean e
+// on every connected part): one warp per row, grid-wide.
+static __device__ void mg_dense_solve(const MgArgs &m, int t0, int nt)
+{
+    const MgLevel &L = m.lev[m.nlev - 1];
+    const int n = L.N, lane = threadIdx.x & 31;
+    for (int I = t0 >> 5; I < n; I += nt >> 5) {
+        const float *row = m.dense + (size_t)I * n;
+        float acc = 0.f;
+        for (int J = lane; J < n; J += 32) acc += __ldg(row + J) * __ldcg(L.f + J);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) __stcg(L.e + I, acc);
     }
 }
 
-// One V-cycle z = M^-1 r over the grid; returns this block's partial of r.z
-// in thread 0 (through *rz_block) or false on a barrier abort.
+// One V-cycle z = M^-1 r over the grid, entered with z's colour-0 nodes
+// already set to r / deg; returns this block's partial of r.z in thread 0
+// (through rz_block), or false on a barrier abort.
 template <typename S, typename R, typename PhiT>
-__device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, unsigned &bar_k, double *sh, double *bc,
-                          double &rz_block)
+__device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, unsigned &bar_k, float *sm, double *sh,
+                          double *bc, double &rz_block)
 {
     const Grid3 g = a.g;
     const unsigned nblk = gridDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x, nt = nblk * blockDim.x;
     float dummy = 0.f;
-    // lattice level: pre-smoothing from zero, residual restricted to level 1
-    for (int s = 0; s < 2 * m.nu; s++) {
-        fine_half<false>(g, a.mask, m.r, m.z, s & 1, s == 0, t0, nt, dummy);
-        if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return false;
+#define MG_BAR()                                                     \
+    do {                                                             \
+        if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return false; \
+    } while (0)
+    // lattice level: rest of the pre-smoothing, residual restricted to level 1
+    for (int s = 1; s < 2 * m.nu; s++) {
+        fine_half<false, false>(g, a.mask, m.r, m.z, m.lev[1], s & 1, t0, nt, dummy);
+        MG_BAR();
     }
-    fine_restrict(g, a.mask, m.r, m.z, m.lev[1], t0, nt);
-    if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return false;
+    if (m.cta_from > 1) fine_restrict<true>(g, a.mask, m.r, m.z, m.lev[1], t0, nt);
+    else fine_restrict<false>(g, a.mask, m.r, m.z, m.lev[1], t0, nt);
+    MG_BAR();
     // grid-wide coarse levels
     for (int l = 1; l < m.cta_from; l++) {
-        for (int s = 0; s < 2 * m.nu; s++) {
-            coarse_half(m.lev[l], s & 1, s == 0, t0, nt);
-            if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return false;
+        for (int s = 1; s < 2 * m.nu; s++) {
+            coarse_half<false, false>(m.lev[l], m.lev[l], s & 1, t0, nt);
+            MG_BAR();
         }
-        coarse_restrict(m.lev[l], m.lev[l + 1], t0, nt);
-        if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return false;
+        if (l + 1 < m.cta_from) coarse_restrict<false, true>(m.lev[l], m.lev[l + 1], t0, nt);
+        else coarse_restrict<false, false>(m.lev[l], m.lev[l + 1], t0, nt);
+        MG_BAR();
     }
-    if (blockIdx.x == 0) mg_cta_cycle(m, sh, bc);
-    if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return false;
+    if (m.dense) mg_dense_solve(m, t0, nt);
+    else if (blockIdx.x == 0) mg_cta_cycle(m, sm, sh, bc);
+    MG_BAR();
     for (int l = m.cta_from - 1; l >= 1; l--) {
-        coarse_prolong(m.lev[l], m.lev[l + 1], t0, nt);
-        if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return false;
-        for (int s = 0; s < 2 * m.nu; s++) {
-            coarse_half(m.lev[l], (s & 1) ^ 1, false, t0, nt);
-            if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return false;
+        coarse_half<false, true>(m.lev[l], m.lev[l + 1], 1, t0, nt);
+        MG_BAR();
+        for (int s = 1; s < 2 * m.nu; s++) {
+            coarse_half<false, false>(m.lev[l], m.lev[l], (s & 1) ^ 1, t0, nt);
+            MG_BAR();
         }
     }
-    fine_prolong(g, a.mask, m.z, m.lev[1], t0, nt);
-    if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return false;
+    fine_half<false, true>(g, a.mask, m.r, m.z, m.lev[1], 1, t0, nt, dummy);
+    MG_BAR();
     float rz = 0.f;
-    for (int s = 0; s < 2 * m.nu; s++) {
+    for (int s = 1; s < 2 * m.nu; s++) {
         const int c = (s & 1) ^ 1;
-        if (s == 2 * m.nu - 1) fine_half<true>(g, a.mask, m.r, m.z, c, false, t0, nt, rz);
-        else fine_half<false>(g, a.mask, m.r, m.z, c, false, t0, nt, dummy);
-        if (s < 2 * m.nu - 1 && !grid_barrier(a.barrier, nblk, bar_k, a.status)) return false;
+        if (s == 2 * m.nu - 1) {
+            fine_half<true, false>(g, a.mask, m.r, m.z, m.lev[1], c, t0, nt, rz);
+        } else {
+            fine_half<false, false>(g, a.mask, m.r, m.z, m.lev[1], c, t0, nt, dummy);
+            MG_BAR();
+        }
     }
+#undef MG_BAR
     rz_block = block_sum_lanes0(warp_sum_ff_lane0(rz), sh);
     return true;
 }
 
-// true residual r = b - A phi (exact in the potential type), as FP32, and
-// this block's sum of r^2 (thread 0)
+// true residual r = b - A phi (exact in the potential type), as FP32, with
+// the first pre-smoothing half sweep (colour-0 z = r / deg); returns this
+// block's sum of r^2 (thread 0)
 template <typename PhiT>
 __device__ double mg_true_residual(const Grid3 &g, const uint32_t *__restrict__ mask, const PhiT *phi,
-                                   const PhiT *b, float *r, int t0, int nt, double *sh)
+                                   const PhiT *b, float *r, float *z, int t0, int nt, double *sh)
 {
     float rr = 0.f;
     const int N = (int)g.N;
@@ -357,9 +526,9 @@ __device__ double mg_true_residual(const Grid3 &g, const uint32_t *__restrict__ 
         const unsigned o = mg_open(m);
         float rv = 0.f;
         if (o) {
-            const int x = i % g.nx, t = i / g.nx, y = t % g.ny, z = t / g.ny;
+            const int x = i % g.nx, t = i / g.nx, y = t % g.ny, zz = t / g.ny;
             int nb[6];
-            face_nbrs(g, x, y, z, i, nb);
+            face_nbrs(g, x, y, zz, i, nb);
             PhiT acc = __ldcg(b + i);
 #pragma unroll
             for (int f = 0; f < 6; f++)
@@ -367,6 +536,7 @@ __device__ double mg_true_residual(const Grid3 &g, const uint32_t *__restrict__ 
             acc -= (PhiT)__popc(o) * __ldcg(phi + i);
             if constexpr (((PhiT)0.5) != 0) rv = (float)acc;
             else rv = ll_to_float(acc) * (float)PHI_INV;
+            if (!((x + y + zz) & 1)) __stcg(z + i, rv * mg_inv_deg(__popc(o)));
         }
         __stcg(r + i, rv);
         rr += rv * rv;
@@ -374,11 +544,109 @@ __device__ double mg_true_residual(const Grid3 &g, const uint32_t *__restrict__ 
     return block_sum_lanes0(warp_sum_ff_lane0(rr), sh);
 }
 
+// The CG passes walk the lattice by pairs (2 xh, 2 xh + 1) of one x-row: one
+// division chain per two nodes and the loads of both issued together.
+
+// p = z + beta p_old and q = A p on the fluid nodes; returns sum p q
+template <bool FRESH>
+__device__ __forceinline__ void mg_pq_node(const Grid3 &g, const uint32_t *__restrict__ mask, const float *z,
+                                           const float *pold, float beta, int x, int y, int zz, int i, float &pn,
+                                           float &qv, bool &live)
+{
+    const uint32_t mk = __ldg(mask + i);
+    const unsigned o = mg_open(mk);
+    live = !(mk & SOLID_BIT);
+    pn = 0.f;
+    qv = 0.f;
+    if (!live || !o) return;
+    int nb[6];
+    face_nbrs(g, x, y, zz, i, nb);
+    pn = FRESH ? __ldcg(z + i) : __ldcg(z + i) + beta * __ldcg(pold + i);
+    float acc = 0.f;
+#pragma unroll
+    for (int f = 0; f < 6; f++)
+        if ((o >> f) & 1u) acc += FRESH ? __ldcg(z + nb[f]) : __ldcg(z + nb[f]) + beta * __ldcg(pold + nb[f]);
+    qv = (float)__popc(o) * pn - acc;
+}
+
+template <bool FRESH>
+__device__ float mg_pq_pass(const Grid3 &g, const uint32_t *__restrict__ mask, const float *z, const float *pold,
+                            float *pnew, float *q, float beta, int t0, int nt)
+{
+    const int hx = (g.nx + 1) >> 1, np = hx * g.ny * g.nz;
+    float pq = 0.f;
+    for (int h = t0; h < np; h += nt) {
+        const int row = h / hx, xh = h - row * hx;
+        const int zz = row / g.ny, y = row - zz * g.ny;
+        const int x0 = 2 * xh, i0 = x0 + g.nx * row;
+        const bool two = x0 + 1 < g.nx;
+        float pn0, q0, pn1 = 0.f, q1 = 0.f;
+        bool l0, l1 = false;
+        mg_pq_node<FRESH>(g, mask, z, pold, beta, x0, y, zz, i0, pn0, q0, l0);
+        if (two) mg_pq_node<FRESH>(g, mask, z, pold, beta, x0 + 1, y, zz, i0 + 1, pn1, q1, l1);
+        if (l0) {
+            __stcg(pnew + i0, pn0);
+            __stcg(q + i0, q0);
+        }
+        if (l1) {
+            __stcg(pnew + i0 + 1, pn1);
+            __stcg(q + i0 + 1, q1);
+        }
+        pq += pn0 * q0 + pn1 * q1;
+    }
+    return pq;
+}
+
+// phi += alpha p, r -= alpha q and colour-0 z = r / deg on the fluid nodes
+// with an open face; returns sum r^2
+template <typename PhiT>
+__device__ float mg_update_pass(const Grid3 &g, const uint32_t *__restrict__ mask, PhiT *phi, const float *p,
+                                const float *q, float *r, float *z, double alpha, int t0, int nt)
+{
+    const int hx = (g.nx + 1) >> 1, np = hx * g.ny * g.nz;
+    const float af = (float)alpha;
+    const float afx = (float)(alpha * PHI_SCALE);
+    float rr = 0.f;
+    for (int h = t0; h < np; h += nt) {
+        const int row = h / hx, xh = h - row * hx;
+        const int zz = row / g.ny, y = row - zz * g.ny;
+        const int x0 = 2 * xh, i0 = x0 + g.nx * row;
+        const int nk = x0 + 1 < g.nx ? 2 : 1;
+        uint32_t mk[2];
+        float pv[2], qv[2], rv[2];
+        PhiT ph[2];
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            mk[k] = SOLID_BIT;
+            if (k < nk) mk[k] = __ldg(mask + i0 + k);
+            const bool live = !(mk[k] & SOLID_BIT) && mg_open(mk[k]);
+            pv[k] = live ? __ldcg(p + i0 + k) : 0.f;
+            qv[k] = live ? __ldcg(q + i0 + k) : 0.f;
+            rv[k] = live ? __ldcg(r + i0 + k) : 0.f;
+            ph[k] = live ? __ldcg(phi + i0 + k) : (PhiT)0;
+        }
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const unsigned o = mg_open(mk[k]);
+            if ((mk[k] & SOLID_BIT) || !o) continue;
+            const int i = i0 + k;
+            if constexpr (((PhiT)0.5) != 0) __stcg(phi + i, ph[k] + (double)af * (double)pv[k]);
+            else __stcg(phi + i, ph[k] + float_to_ll(afx * pv[k]));
+            const float rn = rv[k] - af * qv[k];
+            __stcg(r + i, rn);
+            rr += rn * rn;
+            if (!((x0 + k + y + zz) & 1)) __stcg(z + i, rn * mg_inv_deg(__popc(o)));
+        }
+    }
+    return rr;
+}
+
 template <typename S, typename R, typename PhiT>
 __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_mg_kernel(StepArgs<S, R, PhiT> a, MgArgs m)
 {
     __shared__ double sh[POIS_THREADS / 32];
     __shared__ double bc[1];
+    extern __shared__ float mg_sm[];  // block 0: e and f of the levels it handles alone
     const Grid3 g = a.g;
     const unsigned nblk = gridDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -396,6 +664,7 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_mg_kernel(StepArgs<S,
         out = sum_partials(p, (int)nblk, bc);
         return true;
     };
+    if (blockIdx.x == 0 && !m.dense) mg_cta_load(m, mg_sm);
     double bb;
     if (!reduce(form_source(a, tid, nthr, sh, bc), bb)) return;
     if (a.fixed_iter <= 0 && bb == 0.0) {
@@ -408,7 +677,7 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_mg_kernel(StepArgs<S,
     const double tol2 = a.tol * a.tol * bb;
     const int limit = a.fixed_iter > 0 ? a.fixed_iter : a.max_iter;
     double rr_true;
-    if (!reduce(mg_true_residual<PhiT>(g, a.mask, a.phi, a.b, m.r, tid, nthr, sh), rr_true)) return;
+    if (!reduce(mg_true_residual<PhiT>(g, a.mask, a.phi, a.b, m.r, m.z, tid, nthr, sh), rr_true)) return;
     double rr_ref = rr_true;
     bool current = true;  // rr_true belongs to the present phi
     bool converged = a.fixed_iter <= 0 && rr_true <= tol2;
@@ -417,7 +686,7 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_mg_kernel(StepArgs<S,
     double rz_old = 1.0;
     while (!converged && it < limit) {
         double rzb = 0.0, rz;
-        if (!mg_vcycle(a, m, bar_k, sh, bc, rzb)) return;
+        if (!mg_vcycle(a, m, bar_k, mg_sm, sh, bc, rzb)) return;
         if (!reduce(rzb, rz)) return;
         if (!(rz > 0.0)) break;
         const float beta = fresh ? 0.f : (float)(rz / rz_old);
@@ -426,48 +695,16 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_mg_kernel(StepArgs<S,
         // formed from their z and p_old)
         const float *pold = m.p[pi];
         float *pnew = m.p[pi ^ 1];
-        float pq_t = 0.f;
-        for (int i = tid; i < N; i += nthr) {
-            const uint32_t mk = __ldg(a.mask + i);
-            if (mk & SOLID_BIT) continue;
-            const unsigned o = mg_open(mk);
-            if (!o) {
-                __stcg(pnew + i, 0.f);
-                __stcg(m.q + i, 0.f);
-                continue;
-            }
-            const int x = i % g.nx, t = i / g.nx, y = t % g.ny, z = t / g.ny;
-            int nb[6];
-            face_nbrs(g, x, y, z, i, nb);
-            const float pn = fresh ? __ldcg(m.z + i) : __ldcg(m.z + i) + beta * __ldcg(pold + i);
-            float qv = (float)__popc(o) * pn;
-#pragma unroll
-            for (int f = 0; f < 6; f++)
-                if ((o >> f) & 1u)
-                    qv -= fresh ? __ldcg(m.z + nb[f]) : __ldcg(m.z + nb[f]) + beta * __ldcg(pold + nb[f]);
-            __stcg(pnew + i, pn);
-            __stcg(m.q + i, qv);
-            pq_t += pn * qv;
-        }
+        float pq_t = fresh ? mg_pq_pass<true>(g, a.mask, m.z, pold, pnew, m.q, beta, tid, nthr)
+                           : mg_pq_pass<false>(g, a.mask, m.z, pold, pnew, m.q, beta, tid, nthr);
         pi ^= 1;
         double pq;
         if (!reduce(block_sum_lanes0(warp_sum_ff_lane0(pq_t), sh), pq)) return;
         if (!(pq > 0.0)) break;
         const double alpha = rz / pq;
-        // phi += alpha p, r -= alpha q
-        const float alpha_f = (float)alpha;
-        const float alpha_fx = (float)(alpha * PHI_SCALE);
-        float rr_t = 0.f;
-        for (int i = tid; i < N; i += nthr) {
-            const uint32_t mk = __ldg(a.mask + i);
-            if ((mk & SOLID_BIT) || !mg_open(mk)) continue;
-            const float pv = __ldcg(m.p[pi] + i);
-            if constexpr (((PhiT)0.5) != 0) __stcg(a.phi + i, __ldcg(a.phi + i) + (double)alpha_f * (double)pv);
-            else __stcg(a.phi + i, __ldcg(a.phi + i) + float_to_ll(alpha_fx * pv));
-            const float rv = __ldcg(m.r + i) - alpha_f * __ldcg(m.q + i);
-            __stcg(m.r + i, rv);
-            rr_t += rv * rv;
-        }
+        // phi += alpha p, r -= alpha q, and the next V-cycle's first half
+        // sweep (colour-0 z = r / deg)
+        const float rr_t = mg_update_pass<PhiT>(g, a.mask, a.phi, m.p[pi], m.q, m.r, m.z, alpha, tid, nthr);
         double rr;
         if (!reduce(block_sum_lanes0(warp_sum_ff_lane0(rr_t), sh), rr)) return;
         it++;
@@ -475,7 +712,7 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_mg_kernel(StepArgs<S,
         current = false;
         if (a.fixed_iter > 0) continue;
         if (rr <= 0.25 * tol2 || rr <= (double)m.inner_red * m.inner_red * rr_ref || it == limit) {
-            if (!reduce(mg_true_residual<PhiT>(g, a.mask, a.phi, a.b, m.r, tid, nthr, sh), rr_true)) return;
+            if (!reduce(mg_true_residual<PhiT>(g, a.mask, a.phi, a.b, m.r, m.z, tid, nthr, sh), rr_true)) return;
             current = true;
             if (rr_true <= tol2) {
                 converged = true;
@@ -486,7 +723,7 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_mg_kernel(StepArgs<S,
         }
     }
     if (!current)
-        if (!reduce(mg_true_residual<PhiT>(g, a.mask, a.phi, a.b, m.r, tid, nthr, sh), rr_true)) return;
+        if (!reduce(mg_true_residual<PhiT>(g, a.mask, a.phi, a.b, m.r, m.z, tid, nthr, sh), rr_true)) return;
     if (tid == 0) {
         *a.pois_iters = it;
         a.pois_total[0] += it;

@@ -116,6 +116,7 @@ static inline MgArgs make_mg_args(const Ctx &c)
     m.p[0] = c.mg_p[0];
     m.p[1] = c.mg_p[1];
     m.part = c.mg_part;
+    m.dense = c.mg_dense;
     m.nlev = c.mg_nlev;
     m.cta_from = c.mg_cta_from;
     m.nu = MG_NU;
@@ -176,8 +177,14 @@ template <typename S, typename R, typename PhiT, bool DEV> int steps_impl(Ctx &c
         if (c.mg) {
             MgArgs m = make_mg_args(c);
             void *args[] = {&a, &m};
+            static size_t attr_bytes = 0;
+            if (c.mg_smem > attr_bytes) {
+                cudaFuncSetAttribute(poisson_mg_kernel<S, R, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)c.mg_smem);
+                attr_bytes = c.mg_smem;
+            }
             cudaError_t e = cudaLaunchCooperativeKernel((const void *)poisson_mg_kernel<S, R, PhiT>,
-                                                        dim3(c.pois_blocks), dim3(POIS_THREADS), args, 0,
+                                                        dim3(c.pois_blocks), dim3(POIS_THREADS), args, c.mg_smem,
                                                         c.stream);
             c.launches++;
             if (e != cudaSuccess) return EKL_ERR_CUDA;
@@ -371,10 +378,13 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_impl(Batch 
 }
 
 // occupancy of the cooperative Poisson kernel for this instantiation
-template <typename S, typename R, typename PhiT> int mg_max_blocks_per_sm()
+template <typename S, typename R, typename PhiT> int mg_max_blocks_per_sm(size_t smem)
 {
+    if (cudaFuncSetAttribute(poisson_mg_kernel<S, R, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, poisson_mg_kernel<S, R, PhiT>, POIS_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, poisson_mg_kernel<S, R, PhiT>, POIS_THREADS, smem);
     return nb;
 }
 
@@ -401,6 +411,6 @@ template <typename S, typename R, typename PhiT> int poisson_max_blocks_per_sm()
         return state_impl<S, R, PhiT, DEV>(c, (double *)f, (double *)p, 0);                      \
     }                                                                                            \
     int pois_blocks_##SUFFIX() { return poisson_max_blocks_per_sm<S, R, PhiT>(); }                \
-    int mg_blocks_##SUFFIX() { return mg_max_blocks_per_sm<S, R, PhiT>(); }                       \
+    int mg_blocks_##SUFFIX(size_t smem) { return mg_max_blocks_per_sm<S, R, PhiT>(smem); }        \
     int run_batch_##SUFFIX(Batch &b, int n) { return batch_impl<S, R, PhiT, DEV>(b, n); }         \
     }
