@@ -1020,6 +1020,24 @@ __device__ __forceinline__ void separation(const Grid3 &g, const int per[3], con
     }
 }
 
+// Reduced-precision paths: inside the MD kernel bead positions are signed
+// 64-bit fixed point with 40 fractional bits, so separations, wraps and the
+// position update stay on the integer pipe (GB300's FP64 rate would
+// otherwise dominate the sub-steps); the separation is then converted to FP32.
+__device__ __forceinline__ void separation(const Grid3 &g, const int per[3], const long long *Rb,
+                                           const long long *Rc, float d[3])
+{
+    const long long L[3] = {(long long)g.nx << 40, (long long)g.ny << 40, (long long)g.nz << 40};
+    for (int c = 0; c < 3; c++) {
+        long long v = Rb[c] - Rc[c];
+        if (per[c]) {
+            if (v > (L[c] >> 1)) v -= L[c];
+            else if (v < -(L[c] >> 1)) v += L[c];
+        }
+        d[c] = ll_to_float(v) * (float)PHI_INV;
+    }
+}
+
 template <typename S, typename R, typename PhiT, bool DEV> struct MdArgs {
     StepArgs<S, R, PhiT> s;
     BeadArgs<R> b;
@@ -1063,14 +1081,14 @@ __device__ __forceinline__ bool wall_solid(const Grid3 &g, const int per[3], con
 }
 
 // bond force on bead b from the pair (lo, lo+1); side 0: b = lo+1, side 1: b = lo
-template <typename S, typename R, typename PhiT, bool DEV>
-__device__ __forceinline__ bool bond_add(const MdArgs<S, R, PhiT, DEV> &A, const double *Rs, int b,
+template <typename S, typename R, typename PhiT, bool DEV, typename P>
+__device__ __forceinline__ bool bond_add(const MdArgs<S, R, PhiT, DEV> &A, const P *Rs, int b,
                                          int side, R F[3])
 {
     const int lo = side == 0 ? b - 1 : b;
     if (lo < 0 || lo + 1 >= A.b.nb || A.b.chain[lo] != A.b.chain[lo + 1]) return true;
     R d[3];
-    separation<R>(A.b.g, A.b.per, &Rs[3 * lo], &Rs[3 * (lo + 1)], d);
+    separation(A.b.g, A.b.per, &Rs[3 * lo], &Rs[3 * (lo + 1)], d);
     R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     R fac;
     bool ok = true;
@@ -1108,7 +1126,7 @@ __device__ bool bead_force_serial(const MdArgs<S, R, PhiT, DEV> &A, const double
         if (A.bond_kind == EKL_BOND_HARMONIC && A.b.chain[lo] == A.b.chain[hi] && hi - lo <= 1)
             continue;
         R d[3];
-        separation<R>(g, A.b.per, &Rs[3 * lo], &Rs[3 * hi], d);
+        separation(g, A.b.per, &Rs[3 * lo], &Rs[3 * hi], d);
         R Fp[3] = {R(0), R(0), R(0)};
         wca_add<R>(A.wca_eps, A.wca_sigma, d, Fp);
         for (int c = 0; c < 3; c++) {
@@ -1139,7 +1157,7 @@ __device__ bool bead_force_serial(const MdArgs<S, R, PhiT, DEV> &A, const double
 // (reduced-precision paths); the result is reduced with a fixed xor tree and
 // is valid in every lane.
 template <typename S, typename R, typename PhiT, bool DEV>
-__device__ bool bead_force_warp(const MdArgs<S, R, PhiT, DEV> &A, const double *Rs, const float *Rf,
+__device__ bool bead_force_warp(const MdArgs<S, R, PhiT, DEV> &A, const long long *Rq, const float *Rf,
                                 const float *Rloc, const int *wlo, const int *wn, int b, R F[3],
                                 const int *org, const uint32_t *bits)
 {
@@ -1149,8 +1167,8 @@ __device__ bool bead_force_warp(const MdArgs<S, R, PhiT, DEV> &A, const double *
     R f[3] = {R(0), R(0), R(0)};
     bool ok = true;
     if (lane == 0) {
-        ok = bond_add(A, Rs, b, 0, f);
-        ok = bond_add(A, Rs, b, 1, f) && ok;
+        ok = bond_add(A, Rq, b, 0, f);
+        ok = bond_add(A, Rq, b, 1, f) && ok;
     }
     const float Lf[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
     const float cut2 = 1.2599210498948732f * (float)A.wca_sigma * (float)A.wca_sigma;
@@ -1171,7 +1189,7 @@ __device__ bool bead_force_warp(const MdArgs<S, R, PhiT, DEV> &A, const double *
         }
         if (q2 > 1.1f * cut2 + 0.01f) continue;
         R d[3];
-        separation<R>(g, A.b.per, &Rs[3 * lo], &Rs[3 * hi], d);
+        separation(g, A.b.per, &Rq[3 * lo], &Rq[3 * hi], d);
         R Fp[3] = {R(0), R(0), R(0)};
         wca_add<R>(A.wca_eps, A.wca_sigma, d, Fp);
         for (int c = 0; c < 3; c++) {
@@ -1213,6 +1231,21 @@ __device__ __forceinline__ void scan_bounds(double r, double rc, int org, int &l
     n = (int)floor(r + rc) + 2 - lo;
     loc = (float)(r - (double)org);
 }
+// the same from a fixed-point position rq and cut-off rcq (40 fractional bits)
+__device__ __forceinline__ void scan_bounds_q(long long rq, long long rcq, int org, int &lo, int &n, float &loc,
+                                              int &bad)
+{
+    if (!(rq < (1ll << 60) && rq > -(1ll << 60)) || !(rcq < (16ll << 40))) {
+        bad = 1;
+        lo = 0;
+        n = 0;
+        loc = 0.f;
+        return;
+    }
+    lo = (int)((rq - rcq) >> 40);
+    n = (int)((rq + rcq) >> 40) + 2 - lo;
+    loc = ll_to_float(rq - ((long long)org << 40)) * (float)PHI_INV;
+}
 
 // One block: moments and field at the patch nodes, interpolation to beads,
 // md_substeps Langevin sub-steps with implicit friction, spreading of the
@@ -1242,7 +1275,8 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
     const int pc = *B.patch_count;
     // dynamic shared memory, sized for nb beads (md_smem_bytes)
     extern __shared__ __align__(16) unsigned char md_smem[];
-    double *Rs = (double *)md_smem;
+    double *Rs = (double *)md_smem;              // positions, FP64 path
+    long long *Rq = (long long *)md_smem;        // positions, fixed point (other paths)
     R *sV = (R *)(Rs + 3 * nb);
     R *sU = sV + 3 * nb;
     R *sG = sU + 9 * nb;
@@ -1293,16 +1327,19 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
         out[14] = gr[2];
     }
     for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
-        Rs[t] = B.Rb[t];
-        Rf[t] = (float)B.Rb[t];
+        const double r = B.Rb[t];
+        if constexpr (SERIAL) Rs[t] = r;
+        else Rq[t] = __double2ll_rn(r * PHI_SCALE);
+        Rf[t] = (float)r;
         sV[t] = B.Vb[t];
     }
     for (int t = threadIdx.x; t < WALL_WORDS * nb; t += blockDim.x) wbits[t] = 0u;
     for (int t = threadIdx.x; t < 9 * nb; t += blockDim.x) sAcc[t] = R(0);
     __syncthreads();
     const double rcw = 1.122462048309373 * (double)A.wall_sigma;  // 2^(1/6) sigma
+    const long long rcq = rcw < 16.0 ? __double2ll_rn(rcw * PHI_SCALE) : (16ll << 40);
     for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
-        double r = Rs[t];
+        const double r = B.Rb[t];
         worg[t] = fabs(r) < 1e6 ? (int)floor(r) - WALL_BOX / 2 + 1 : 0;
         int bad = 0;
         scan_bounds(r, rcw, worg[t], wlo[t], wn[t], Rloc[t], bad);
@@ -1370,7 +1407,7 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
             R F[3];
             bool okf;
             if constexpr (SERIAL) okf = bead_force_serial(A, Rs, b, F, &worg[3 * b], &wbits[b * WALL_WORDS]);
-            else okf = bead_force_warp(A, Rs, Rf, Rloc, wlo, wn, b, F, &worg[3 * b], &wbits[b * WALL_WORDS]);
+            else okf = bead_force_warp(A, Rq, Rf, Rloc, wlo, wn, b, F, &worg[3 * b], &wbits[b * WALL_WORDS]);
             if (!okf) sBad = 1;
             if (!SERIAL && lane != 0) continue;
             R xi_[3] = {R(0), R(0), R(0)};
@@ -1396,26 +1433,40 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
             }
         }
         __syncthreads();
-        // positions (FP64), wrapped into [0, L) on periodic axes
+        // positions, wrapped into [0, L) on periodic axes
         for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
             const int c = t % 3;
-            const double L = c == 0 ? g.nx : (c == 1 ? g.ny : g.nz);
-            double r = Rs[t] + (double)(dt * sV[t]);
-            if (B.per[c]) {
-                if (r < 0.0) r += L;
-                else if (r >= L) r -= L;
-            }
-            Rs[t] = r;
-            Rf[t] = (float)r;
+            const int Li = c == 0 ? g.nx : (c == 1 ? g.ny : g.nz);
             int bad = 0;
-            scan_bounds(r, rcw, worg[t], wlo[t], wn[t], Rloc[t], bad);
+            if constexpr (SERIAL) {
+                const double L = Li;
+                double r = Rs[t] + (double)(dt * sV[t]);
+                if (B.per[c]) {
+                    if (r < 0.0) r += L;
+                    else if (r >= L) r -= L;
+                }
+                Rs[t] = r;
+                Rf[t] = (float)r;
+                scan_bounds(r, rcw, worg[t], wlo[t], wn[t], Rloc[t], bad);
+            } else {
+                const long long L = (long long)Li << 40;
+                long long r = Rq[t] + float_to_ll((float)(dt * sV[t]) * (float)PHI_SCALE);
+                if (B.per[c]) {
+                    if (r < 0) r += L;
+                    else if (r >= L) r -= L;
+                }
+                Rq[t] = r;
+                Rf[t] = ll_to_float(r) * (float)PHI_INV;
+                scan_bounds_q(r, rcq, worg[t], wlo[t], wn[t], Rloc[t], bad);
+            }
             if (bad) sBad = 1;
         }
         __syncthreads();
     }
     if (threadIdx.x == 0 && sBad) atomicOr(a.status, ST_BEAD);
     for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
-        B.Rb[t] = Rs[t];
+        if constexpr (SERIAL) B.Rb[t] = Rs[t];
+        else B.Rb[t] = __ll2double_rn(Rq[t]) * PHI_INV;
         B.Vb[t] = sV[t];
     }
     // spread: per slot, entries in bead order (ascending b), then per particle

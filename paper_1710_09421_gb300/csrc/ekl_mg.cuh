@@ -37,7 +37,7 @@ struct MgArgs {
     float *r, *z, *q, *p[2];
     double *part;         // [4][gridDim.x]
     const float *dense;   // pseudo-inverse of the coarsest operator [N][N], or null
-    int nlev, cta_from, nu, coarse_sweeps;
+    int nlev, cta_from, nu, nu_c, coarse_sweeps;  // smoothing sweeps: lattice level, coarse levels
     float inner_red;
     MgLevel lev[MG_MAXLEV];
 };
@@ -394,7 +394,7 @@ static __device__ void mg_cta_cycle(const MgArgs &m, float *sm, double *sh, doub
         __syncthreads();
     }
     for (int l = k0; l < last; l++) {
-        for (int s = 1; s < 2 * m.nu; s++) {
+        for (int s = 1; s < 2 * m.nu_c; s++) {
             coarse_half<true, false>(Ls[l], Ls[l], s & 1, t0, nt);
             __syncthreads();
         }
@@ -425,7 +425,7 @@ static __device__ void mg_cta_cycle(const MgArgs &m, float *sm, double *sh, doub
     for (int l = last - 1; l >= k0; l--) {
         coarse_half<true, true>(Ls[l], Ls[l + 1], 1, t0, nt);
         __syncthreads();
-        for (int s = 1; s < 2 * m.nu; s++) {
+        for (int s = 1; s < 2 * m.nu_c; s++) {
             coarse_half<true, false>(Ls[l], Ls[l], (s & 1) ^ 1, t0, nt);
             __syncthreads();
         }
@@ -475,7 +475,7 @@ __device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, unsign
     MG_BAR();
     // grid-wide coarse levels
     for (int l = 1; l < m.cta_from; l++) {
-        for (int s = 1; s < 2 * m.nu; s++) {
+        for (int s = 1; s < 2 * m.nu_c; s++) {
             coarse_half<false, false>(m.lev[l], m.lev[l], s & 1, t0, nt);
             MG_BAR();
         }
@@ -489,7 +489,7 @@ __device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, unsign
     for (int l = m.cta_from - 1; l >= 1; l--) {
         coarse_half<false, true>(m.lev[l], m.lev[l + 1], 1, t0, nt);
         MG_BAR();
-        for (int s = 1; s < 2 * m.nu; s++) {
+        for (int s = 1; s < 2 * m.nu_c; s++) {
             coarse_half<false, false>(m.lev[l], m.lev[l], (s & 1) ^ 1, t0, nt);
             MG_BAR();
         }

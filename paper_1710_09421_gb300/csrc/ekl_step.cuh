@@ -120,6 +120,7 @@ static inline MgArgs make_mg_args(const Ctx &c)
     m.nlev = c.mg_nlev;
     m.cta_from = c.mg_cta_from;
     m.nu = MG_NU;
+    m.nu_c = MG_NU_COARSE;
     m.coarse_sweeps = MG_COARSE_SWEEPS;
     m.inner_red = MG_INNER_RED;
     for (int l = 0; l < MG_MAXLEV; l++) m.lev[l] = c.mg_lev[l];
