@@ -33,17 +33,31 @@ METRIC = "EK-LB-MD steps/s & species-MLUPS vs HBM roofline; learned vs plain Poi
 UNIT = "species-MLUPS"
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM bytes per launch from the committed ncu capture (profiles/*_pore_64x64x128.md),
-# valid only while the kernel source is the one that was profiled
-PROFILED_SRC_SHA16 = "4716937725c2c176"
-PROFILED_TRAFFIC = {"poisson_tiled_kernel": 8468736 + 20224, "lb_fused_kernel": 119326208 + 65220096}
+# DRAM bytes per launch from the committed ncu captures (profiles/*_pore_64x64x128.md),
+# each valid only while the source files it was taken on are unchanged
+PROFILED = {
+    # kernel: (sha256 prefix of its source files, dram read + write bytes per launch)
+    "lb_fused_kernel": ("0dbea948a5c7d63c", 119344896 + 67133184),
+    "poisson_mg_kernel": ("5bfbe8cea0638c11", 16019968 + 563712),
+}
+KERNEL_SOURCES = {
+    "lb_fused_kernel": ("ekl_kernels.cuh", "ekl_dev.cuh"),
+    "poisson_mg_kernel": ("ekl_mg.cuh", "ekl_kernels.cuh", "ekl_dev.cuh"),
+    "poisson_tiled_kernel": ("ekl_kernels.cuh", "ekl_dev.cuh"),
+}
+
+
+def source_sha16(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES.get(kernel, ()):
+        h.update(open(os.path.join(ROOT, "paper_1710_09421_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic(kernel):
-    import hashlib
-    src = os.path.join(ROOT, "paper_1710_09421_gb300", "csrc", "ekl_kernels.cuh")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return PROFILED_TRAFFIC.get(kernel) if sha == PROFILED_SRC_SHA16 else None
+    sha, traffic = PROFILED.get(kernel, (None, None))
+    return traffic if sha is not None and sha == source_sha16(kernel) else None
 
 
 def peaks():
@@ -112,6 +126,20 @@ def poisson_algorithmic_bytes(wl, sweeps):
     potential read and written (8 + 8 B); the neighbours come from cache."""
     nf = int((wl.solid == 0).sum())
     return sweeps * nf * 28
+
+
+# Multigrid solve, per fluid node (FP32 path, 8-byte fixed-point potential):
+# per CG iteration 5.5 lattice sweeps x 16 B (r, z read, z written, link
+# word), restriction 12 B, p/q pass 20 B, update pass 38 B, coarse levels
+# 14 B (1/7 of the lattice smoothing and restriction); per solve the source
+# (16 B) and two true-residual passes (26 B each).
+MG_BYTES_PER_ITER = 5.5 * 16 + 12 + 20 + 38 + 14
+MG_BYTES_PER_SOLVE = 16 + 2 * 26
+
+
+def mg_algorithmic_bytes(wl, iters):
+    nf = int((wl.solid == 0).sum())
+    return nf * (iters * MG_BYTES_PER_ITER + MG_BYTES_PER_SOLVE)
 
 
 def lb_algorithmic_bytes(wl, store_bytes):
@@ -296,6 +324,7 @@ def run_ours(args):
 
     torch.cuda.set_device(local)
     import paper_1710_09421_gb300 as E
+    from paper_1710_09421_gb300 import workloads as W
 
     E.load()
     wl = workload_for(args.workload, rank, args)
@@ -336,7 +365,13 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     achieved = lb_bytes / (lb_ms / 1e3) / 1e9
     pois_ms = ph["poisson"] / args.steps
-    pois_bytes = poisson_algorithmic_bytes(wl, sweeps / args.steps)
+    mg = bool(wl.flags & W.FLAG_POISSON_MG)
+    if mg:
+        pois_kernel = "poisson_mg_kernel"
+        pois_bytes = mg_algorithmic_bytes(wl, sweeps / args.steps)
+    else:
+        pois_kernel = "poisson_tiled_kernel" if wl.n_nodes <= 1 << 21 else "poisson_kernel"
+        pois_bytes = poisson_algorithmic_bytes(wl, sweeps / args.steps)
     pois_achieved = pois_bytes / (pois_ms / 1e3) / 1e9
 
     # ---- end to end through the public API: host inputs in, fields out
@@ -370,17 +405,17 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (populations 2 x %.0f MB)" % (
                        wl.n_nodes * 57 * store / 1e6)},
         "steps_per_s": round(steps_per_s, 3),
-        "poisson_sweeps_per_step": round(sweeps / args.steps, 2),
-        "poisson_us_per_sweep": round(1e3 * ph["poisson"] / max(sweeps, 1), 3),
+        "poisson_solver": "multigrid-CG" if mg else "chebyshev-sor",
+        "poisson_iterations_per_step": round(sweeps / args.steps, 2),
+        "poisson_us_per_iteration": round(1e3 * ph["poisson"] / max(sweeps, 1), 3),
         "phase_ms_per_step": {k: round(v / args.steps, 5) for k, v in ph.items()},
-        "roofline": {"kernel": "poisson_tiled_kernel" if wl.n_nodes <= 1 << 21 else "poisson_kernel",
-                     "bound": "hbm", "achieved": round(pois_achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(pois_achieved / hbm, 4), "peak_kind": peak_kind,
-                     "traffic": profiled_traffic("poisson_tiled_kernel"),
+        "roofline": {"kernel": pois_kernel, "bound": "hbm", "achieved": round(pois_achieved, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(pois_achieved / hbm, 4), "peak_kind": peak_kind,
+                     "traffic": profiled_traffic(pois_kernel),
                      "algorithmic_bytes_per_launch": int(pois_bytes),
                      "avg_launch_ms": round(pois_ms, 5),
-                     "note": "dominant kernel; operands resident in shared memory, bound by the "
-                             "per-sweep grid barrier and int64 update issue, not by DRAM"},
+                     "note": "dominant kernel (one launch = one step's solve); its working set is "
+                             "L2-resident and it is bound by grid-barrier latency, not by DRAM"},
         "roofline_lb": {"kernel": "lb_fused_kernel", "bound": "hbm", "achieved": round(achieved, 1),
                         "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                         "peak_kind": peak_kind, "traffic": profiled_traffic("lb_fused_kernel"),
