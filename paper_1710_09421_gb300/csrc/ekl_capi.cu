@@ -121,6 +121,7 @@ void release(Ctx &c)
     dev_free(c, c.q, 0);
     dev_free(c, c.chain, 0);
     dev_free(c, c.patch_count, 0);
+    dev_free(c, c.patch_bits, 0);
     dev_free(c, c.patch_node, 0);
     dev_free(c, c.patch_q, 0);
     dev_free(c, c.patch_f, 0);
@@ -678,6 +679,7 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
     std::vector<float> omf(om.begin(), om.end());
     c.omegas = A(om.size() * (c.prec == EKL_F64 ? sizeof(double) : sizeof(float)));
     c.patch_count = (int *)A(sizeof(int));
+    c.patch_bits = (uint32_t *)A(((size_t)N / 32 + 1) * sizeof(uint32_t));
     c.patch_node = (int *)A(MAX_ENTRIES * sizeof(int));
     c.patch_q = A(MAX_ENTRIES * rs);
     c.patch_f = A((size_t)(MAX_ENTRIES + MAX_BEADS) * 9 * rs);
@@ -742,6 +744,7 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
         if (rc != EKL_OK) { fail(rc, "init kernel failed"); break; }
         cudaMemsetAsync(c.phi, 0, N * ps, c.stream);
         cudaMemsetAsync(c.patch_count, 0, sizeof(int), c.stream);
+        cudaMemsetAsync(c.patch_bits, 0, ((size_t)N / 32 + 1) * sizeof(uint32_t), c.stream);
         cudaMemsetAsync(c.status, 0, sizeof(int), c.stream);
         cudaMemsetAsync(c.pois_iters, 0, sizeof(int), c.stream);
         cudaMemsetAsync(c.pois_total, 0, sizeof(long long), c.stream);
@@ -798,6 +801,8 @@ int ekl_set_beads(ekl_handle *h, int32_t n, const double *R, const double *V, co
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(c.chain, ch.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, c.stream);
     if (e == cudaSuccess && n == 0) e = cudaMemsetAsync(c.patch_count, 0, sizeof(int), c.stream);
+    if (e == cudaSuccess && n == 0)
+        e = cudaMemsetAsync(c.patch_bits, 0, ((size_t)c.N / 32 + 1) * sizeof(uint32_t), c.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) return fail_cuda(e, "set_beads");
     c.nb = n;

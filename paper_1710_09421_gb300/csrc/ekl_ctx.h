@@ -92,6 +92,7 @@ struct Ctx {
     void *R, *V, *q;      // Real[nb*3], Real[nb*3], Real[nb]
     int *chain;           // [nb]
     int *patch_count;     // [1]
+    uint32_t *patch_bits; // [N/32 + 1] bit per node: in the patch list
     int *patch_node;      // [MAX_ENTRIES]
     void *patch_q;        // Real[MAX_ENTRIES]
     void *patch_f;        // Real[MAX_ENTRIES][9]

@@ -56,21 +56,6 @@ template <> struct Store<__half> {
     __device__ static void st(__half *p, float v) { *p = __float2half_rn(v); }
 };
 
-// ---------------------------------------------------------------- potential
-// FP64 path: phi stored as double.  Reduced-precision paths: phi stored as a
-// signed 64-bit fixed-point number with 40 fractional bits, so that the
-// 7-point residual is computed exactly in integer arithmetic.
-template <typename PhiT> struct PhiOps;
-template <> struct PhiOps<double> {
-    __device__ static double diff(double a, double b) { return a - b; }  // as real
-};
-template <> struct PhiOps<long long> {
-    __device__ static float diff(long long a, long long b)
-    {
-        return __ll2float_rn(a - b) * (float)PHI_INV;
-    }
-};
-
 // ---------------------------------------------------------------- indexing
 struct Grid3 {
     int nx, ny, nz;
@@ -232,6 +217,18 @@ __device__ __forceinline__ long long float_to_ll(float d)
     float lo = d - hi * 4294967296.0f;               // exact, in [0, 2^32)
     return ((long long)__float2int_rn(hi) << 32) + (long long)__float2uint_rn(lo);
 }
+
+// ---------------------------------------------------------------- potential
+// FP64 path: phi stored as double.  Reduced-precision paths: phi stored as a
+// signed 64-bit fixed-point number with 40 fractional bits, so that the
+// 7-point residual is computed exactly in integer arithmetic.
+template <typename PhiT> struct PhiOps;
+template <> struct PhiOps<double> {
+    __device__ static double diff(double a, double b) { return a - b; }  // as real
+};
+template <> struct PhiOps<long long> {
+    __device__ static float diff(long long a, long long b) { return ll_to_float(a - b) * (float)PHI_INV; }
+};
 
 // ---------------------------------------------------------------- reductions
 // Warp sum of FP32 values carried as an unevaluated float pair (TwoSum at

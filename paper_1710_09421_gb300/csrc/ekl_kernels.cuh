@@ -44,6 +44,7 @@ template <typename S, typename R, typename PhiT> struct StepArgs {
     int flags;
     // bead patch
     const int *patch_count;
+    const uint32_t *patch_bits;  // bit i set when node i is in the patch list
     const int *patch_node;
     const R *patch_q;
     const R *patch_f;
@@ -179,8 +180,8 @@ __device__ __forceinline__ void charge_body(const StepArgs<S, R, PhiT> &a, long 
                 r += a.zv[s] * n;
             }
             rho = r + (a.src_wall ? a.src_wall[i] : R(0));
-            const int pc = *a.patch_count;
-            if (pc > 0) {
+            if ((__ldg(a.patch_bits + (i >> 5)) >> (i & 31)) & 1u) {
+                const int pc = *a.patch_count;
                 int k = lower_bound_i(a.patch_node, pc, i);
                 if (k < pc && a.patch_node[k] == i) rho = rho + a.patch_q[k];
             }
@@ -834,6 +835,7 @@ template <typename R> struct BeadArgs {
     const R *qb;
     const int *chain;
     int *patch_count;
+    uint32_t *patch_bits;
     int *patch_node;
     R *patch_q;
     R *patch_f;
@@ -901,6 +903,15 @@ template <typename R> __device__ void bead_bin_body(const BeadArgs<R> &a)
     const int ne = a.nb * 8;
     int npow = 1;
     while (npow < ne) npow <<= 1;
+    // clear the previous step's patch bits (the list is rewritten below,
+    // after several block barriers)
+    {
+        const int old = *a.patch_count;
+        for (int k = threadIdx.x; k < old; k += blockDim.x) {
+            const int nd = a.patch_node[k];
+            atomicAnd(a.patch_bits + (nd >> 5), ~(1u << (nd & 31)));
+        }
+    }
     for (int b = threadIdx.x; b < a.nb; b += blockDim.x) {
         double Rb[3] = {a.Rb[3 * b], a.Rb[3 * b + 1], a.Rb[3 * b + 2]};
         long long nd[8];
@@ -963,7 +974,11 @@ template <typename R> __device__ void bead_bin_body(const BeadArgs<R> &a)
         int e = (int)(u & 0xFFFFFu);
         a.entry_slot[e] = flag[t];
         a.sorted_entry[t] = e;
-        if (t == 0 || (key[t - 1] >> 20) != (u >> 20)) a.patch_node[flag[t]] = (int)(u >> 20);
+        if (t == 0 || (key[t - 1] >> 20) != (u >> 20)) {
+            const int nd = (int)(u >> 20);
+            a.patch_node[flag[t]] = nd;
+            atomicOr(a.patch_bits + (nd >> 5), 1u << (nd & 31));
+        }
     }
     __syncthreads();
     const int pc = *a.patch_count;
@@ -1537,12 +1552,12 @@ __device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long
             for (int c = 0; c < 3; c++)
                 if (fabs(gphi[c]) >= R(1)) cfl = 1;
             int slot = -1;
-            const int pc = *a.patch_count;
-            if (pc > 0) {
+            if ((__ldg(a.patch_bits + (i >> 5)) >> (i & 31)) & 1u) {
+                const int pc = *a.patch_count;
                 int k = lower_bound_i(a.patch_node, pc, i);
                 if (k < pc && a.patch_node[k] == i) slot = k;
             }
-            R n[NS], dn[NS], av[NS][3], G[NS][3], h[NS];
+            R n[NS], dn[NS], av[NS][3], G[NS][3], h[NS], ih[NS];
 #pragma unroll
             for (int s = 0; s < NS; s++) {
                 R nn = R(0), jx = R(0), jy = R(0), jz = R(0);
@@ -1562,27 +1577,41 @@ __device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long
                 if (!(n[s] > R(0)) || !isfinite(n[s])) bad = 1;
                 msum[s] = n[s];
                 h[s] = R(0.5) * a.wd[s];
+                ih[s] = R(1) / (R(1) + h[s]);
+                // reduced-precision paths multiply by reciprocals; the FP64
+                // path divides exactly as the oracle does
+                const R in_ = DEV ? R(1) / n[s] : R(0);
                 R j[3] = {jx, jy, jz};
                 for (int c = 0; c < 3; c++) {
                     R zk = a.zv[s] * Consts<R>::KT;
                     R Gc = a.body[s][c] - zk * gphi[c] + zk * a.E[c];
                     if (slot >= 0) Gc = Gc + a.patch_f[(long long)slot * 9 + 3 * s + c];
                     G[s][c] = Gc;
-                    av[s][c] = j[c] / n[s] + R(0.5) * Gc;
+                    av[s][c] = (DEV ? j[c] * in_ : j[c] / n[s]) + R(0.5) * Gc;
                 }
             }
             R num[3] = {R(0), R(0), R(0)}, den = R(0), us[3];
 #pragma unroll
             for (int s = 0; s < NS; s++) {
-                den += n[s] / (R(1) + h[s]);
-                for (int c = 0; c < 3; c++) num[c] += n[s] * av[s][c] / (R(1) + h[s]);
+                if constexpr (DEV) {
+                    den += n[s] * ih[s];
+                    for (int c = 0; c < 3; c++) num[c] += n[s] * av[s][c] * ih[s];
+                } else {
+                    den += n[s] / (R(1) + h[s]);
+                    for (int c = 0; c < 3; c++) num[c] += n[s] * av[s][c] / (R(1) + h[s]);
+                }
             }
-            for (int c = 0; c < 3; c++) us[c] = num[c] / den;
+            if constexpr (DEV) {
+                const R iden = R(1) / den;
+                for (int c = 0; c < 3; c++) us[c] = num[c] * iden;
+            } else {
+                for (int c = 0; c < 3; c++) us[c] = num[c] / den;
+            }
 #pragma unroll
             for (int s = 0; s < NS; s++) {
                 R ue[3], Ph[3];
                 for (int c = 0; c < 3; c++) {
-                    R ua = (av[s][c] + h[s] * us[c]) / (R(1) + h[s]);
+                    R ua = DEV ? (av[s][c] + h[s] * us[c]) * ih[s] : (av[s][c] + h[s] * us[c]) / (R(1) + h[s]);
                     Ph[c] = G[s][c] - a.wd[s] * (ua - us[c]);
                     ue[c] = (a.flags & EKL_EQ_BARYCENTRIC) ? us[c] : ua;
                 }
@@ -1591,25 +1620,39 @@ __device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long
                 const R Fu = Ph[0] * ue[0] + Ph[1] * ue[1] + Ph[2] * ue[2];
                 const R cS = R(1) - R(0.5) * om;
                 S *out = a.fout + (long long)(s * Q) * g.N + i;
+                if constexpr (!DEV) {
 #pragma unroll
-                for (int p = 0; p < Q; p++) {
-                    const R cu = (R)cx_(p) * ue[0] + (R)cy_(p) * ue[1] + (R)cz_(p) * ue[2];
-                    const R cF = (R)cx_(p) * Ph[0] + (R)cy_(p) * Ph[1] + (R)cz_(p) * Ph[2];
-                    const R w = (R)w_(p);
-                    R fs;
-                    if constexpr (!DEV) {
+                    for (int p = 0; p < Q; p++) {
+                        const R cu = (R)cx_(p) * ue[0] + (R)cy_(p) * ue[1] + (R)cz_(p) * ue[2];
+                        const R cF = (R)cx_(p) * Ph[0] + (R)cy_(p) * Ph[1] + (R)cz_(p) * Ph[2];
+                        const R w = (R)w_(p);
                         const R VT2 = Consts<R>::VT2;
                         R feq = w * n[s] * (R(1) + cu / VT2 + (cu * cu - VT2 * u2) / (R(2) * VT2 * VT2));
                         R Sp = w * n[s] * (cF / VT2 + (cu * cF - VT2 * Fu) / (VT2 * VT2));
-                        fs = f[s][p] - om * (f[s][p] - feq) + cS * Sp;
-                    } else {
-                        // deviation form: s_eq = f_eq - w n_ref
-                        R poly = R(3) * cu + R(4.5) * cu * cu - R(1.5) * u2;
-                        R seq = w * (dn[s] + n[s] * poly);
-                        R Sp = w * n[s] * (R(3) * cF + R(9) * cu * cF - R(3) * Fu);
-                        fs = f[s][p] - om * (f[s][p] - seq) + cS * Sp;
+                        R fs = f[s][p] - om * (f[s][p] - feq) + cS * Sp;
+                        Store<S>::st(out + (long long)p * g.N, fs);
                     }
-                    Store<S>::st(out + (long long)p * g.N, fs);
+                } else {
+                    // deviation form, s_eq = f_eq - w n_ref:
+                    //   out = (1 - om) f + om s_eq + cS S
+                    //   s_eq = w (dn + n (3 cu + 4.5 cu^2 - 1.5 u^2)), S = w n (3 cF + 9 cu cF - 3 F.u)
+                    // a velocity and its opposite share the parts even in c
+                    const R keep = R(1) - om;
+                    const R w0 = (R)w_(0);
+                    Store<S>::st(out, keep * f[s][0] + w0 * (om * (dn[s] - R(1.5) * n[s] * u2) - cS * R(3) * n[s] * Fu));
+#pragma unroll
+                    for (int p = 1; p < Q; p += 2) {
+                        const int q = p + 1;  // opposite of p
+                        const R cu = (R)cx_(p) * ue[0] + (R)cy_(p) * ue[1] + (R)cz_(p) * ue[2];
+                        const R cF = (R)cx_(p) * Ph[0] + (R)cy_(p) * Ph[1] + (R)cz_(p) * Ph[2];
+                        const R w = (R)w_(p);
+                        const R wn = w * n[s];
+                        const R even = om * (R(4.5) * cu * cu - R(1.5) * u2) + cS * (R(9) * cu * cF - R(3) * Fu);
+                        const R odd = R(3) * (om * cu + cS * cF);
+                        const R base = om * w * dn[s];
+                        Store<S>::st(out + (long long)p * g.N, keep * f[s][p] + (base + wn * (even + odd)));
+                        Store<S>::st(out + (long long)q * g.N, keep * f[s][q] + (base + wn * (even - odd)));
+                    }
                 }
             }
         }

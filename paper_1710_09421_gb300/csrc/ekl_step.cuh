@@ -37,6 +37,7 @@ static StepArgs<S, R, PhiT> make_args(Ctx &c, int parity = -1)
     a.c4 = (R)c.c4;
     a.flags = c.P.flags;
     a.patch_count = c.patch_count;
+    a.patch_bits = c.patch_bits;
     a.patch_node = c.patch_node;
     a.patch_q = (const R *)c.patch_q;
     a.patch_f = (const R *)c.patch_f;
@@ -71,6 +72,7 @@ template <typename R> static BeadArgs<R> make_bead_args(Ctx &c)
     b.qb = (const R *)c.q;
     b.chain = c.chain;
     b.patch_count = c.patch_count;
+    b.patch_bits = c.patch_bits;
     b.patch_node = c.patch_node;
     b.patch_q = (R *)c.patch_q;
     b.patch_f = (R *)c.patch_f;
