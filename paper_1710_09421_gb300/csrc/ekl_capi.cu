@@ -48,15 +48,16 @@ struct PrecOps {
     int (*set_state)(Ctx &, const double *, const double *);
     int (*pois_blocks)();
     int (*mg_blocks)(size_t);
+    int (*mass)(Ctx &);
 };
 
 const PrecOps &ops(int prec)
 {
     static const PrecOps t[4] = {
-        {init_populations_f64, run_steps_f64, get_fields_f64, get_state_f64, set_state_f64, pois_blocks_f64, mg_blocks_f64},
-        {init_populations_f32, run_steps_f32, get_fields_f32, get_state_f32, set_state_f32, pois_blocks_f32, mg_blocks_f32},
-        {init_populations_bf16, run_steps_bf16, get_fields_bf16, get_state_bf16, set_state_bf16, pois_blocks_bf16, mg_blocks_bf16},
-        {init_populations_fp16, run_steps_fp16, get_fields_fp16, get_state_fp16, set_state_fp16, pois_blocks_fp16, mg_blocks_fp16},
+        {init_populations_f64, run_steps_f64, get_fields_f64, get_state_f64, set_state_f64, pois_blocks_f64, mg_blocks_f64, mass_f64},
+        {init_populations_f32, run_steps_f32, get_fields_f32, get_state_f32, set_state_f32, pois_blocks_f32, mg_blocks_f32, mass_f32},
+        {init_populations_bf16, run_steps_bf16, get_fields_bf16, get_state_bf16, set_state_bf16, pois_blocks_bf16, mg_blocks_bf16, mass_bf16},
+        {init_populations_fp16, run_steps_fp16, get_fields_fp16, get_state_fp16, set_state_fp16, pois_blocks_fp16, mg_blocks_fp16, mass_fp16},
     };
     return t[prec];
 }
@@ -662,7 +663,7 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
     c.b = A(N * ps);
     c.phi = A(N * ps);
     c.part_charge = (double *)A((size_t)c.charge_blocks * (CHARGE_THREADS / 32) * sizeof(double));
-    c.part_mass = (double *)A((size_t)c.lb_blocks * (LB_THREADS / 32) * NS * sizeof(double));
+    c.part_mass = (double *)A((size_t)((N + 255) / 256) * NS * sizeof(double));
     c.part_pois = (double *)A((size_t)c.pois_blocks * sizeof(double));
     c.barrier = (unsigned *)A(4 * sizeof(unsigned));
     c.status = (int *)A(sizeof(int));
@@ -943,7 +944,9 @@ int ekl_get_stats(ekl_handle *h, ekl_stats *out)
 {
     if (!h || !out) return fail(EKL_ERR_ARG, "null argument");
     Ctx &c = h->c;
-    const size_t nwarps = (size_t)c.lb_blocks * (LB_THREADS / 32);
+    const int nmb = ops(c.prec).mass(c);
+    if (nmb < 0) return fail(EKL_ERR_CUDA, "mass kernel failed");
+    const size_t nwarps = (size_t)nmb;
     std::vector<double> pm(nwarps * NS);
     int it = 0;
     long long tot = 0;

@@ -11,7 +11,7 @@ constexpr int Q = 19;
 constexpr int NS = 3;
 constexpr int MAX_BEADS = 256;
 constexpr int MAX_ENTRIES = 8 * MAX_BEADS;
-constexpr int LB_THREADS = 256;
+constexpr int LB_THREADS = 128;
 constexpr int CHARGE_THREADS = 256;
 constexpr int POIS_THREADS = 1024;
 constexpr int BEAD_THREADS = 256;
@@ -73,7 +73,7 @@ struct Ctx {
     void *b;           // PhiT[N]
     void *phi;         // PhiT[N]
     double *part_charge;  // [charge blocks]
-    double *part_mass;    // [lb blocks][3]
+    double *part_mass;    // [mass blocks][3] (filled on request)
     double *part_pois;    // [poisson blocks][2]
     unsigned *barrier;    // {count, generation, abort}
     int *status;          // device status word
@@ -174,6 +174,7 @@ int get_fields_f64(Ctx &c, double *d_n, double *d_j, double *d_phi);
 int get_state_f64(Ctx &c, double *d_f, double *d_phi);
 int set_state_f64(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_f64();
+int mass_f64(Ctx &c);
 int mg_blocks_f64(size_t smem);
 
 int init_populations_f32(Ctx &c, const double *d_n_init);
@@ -182,6 +183,7 @@ int get_fields_f32(Ctx &c, double *d_n, double *d_j, double *d_phi);
 int get_state_f32(Ctx &c, double *d_f, double *d_phi);
 int set_state_f32(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_f32();
+int mass_f32(Ctx &c);
 int mg_blocks_f32(size_t smem);
 
 int init_populations_bf16(Ctx &c, const double *d_n_init);
@@ -190,6 +192,7 @@ int get_fields_bf16(Ctx &c, double *d_n, double *d_j, double *d_phi);
 int get_state_bf16(Ctx &c, double *d_f, double *d_phi);
 int set_state_bf16(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_bf16();
+int mass_bf16(Ctx &c);
 int mg_blocks_bf16(size_t smem);
 
 int init_populations_fp16(Ctx &c, const double *d_n_init);
@@ -198,6 +201,7 @@ int get_fields_fp16(Ctx &c, double *d_n, double *d_j, double *d_phi);
 int get_state_fp16(Ctx &c, double *d_f, double *d_phi);
 int set_state_fp16(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_fp16();
+int mass_fp16(Ctx &c);
 int mg_blocks_fp16(size_t smem);
 
 size_t real_size(int prec);

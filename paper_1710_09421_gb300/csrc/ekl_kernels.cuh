@@ -1534,7 +1534,6 @@ __device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long
 {
     const Grid3 g = a.g;
     const long long i = blk * (long long)blockDim.x + threadIdx.x;
-    R msum[NS] = {R(0), R(0), R(0)};
     int bad = 0, cfl = 0;
     if (i < g.N) {
         const uint32_t m = a.mask[i];
@@ -1575,7 +1574,6 @@ __device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long
                 dn[s] = nn;
                 n[s] = DEV ? a.n_ref[s] + nn : nn;
                 if (!(n[s] > R(0)) || !isfinite(n[s])) bad = 1;
-                msum[s] = n[s];
                 h[s] = R(0.5) * a.wd[s];
                 ih[s] = R(1) / (R(1) + h[s]);
                 // reduced-precision paths multiply by reciprocals; the FP64
@@ -1659,22 +1657,16 @@ __device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(a.status, ST_UNSTABLE);
     if (__any_sync(0xffffffffu, cfl) && (threadIdx.x & 31) == 0) atomicOr(a.status, ST_CFL);
-    for (int s = 0; s < NS; s++) {
-        double t;
-        if constexpr (sizeof(R) == 8) t = warp_sum((double)msum[s]);
-        else t = warp_sum_ff((float)msum[s]);
-        if ((threadIdx.x & 31) == 0) a.part_mass[(i >> 5) * NS + s] = t;
-    }
 }
 
 template <typename S, typename R, typename PhiT, bool DEV>
-__global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 2 : 1) lb_fused_kernel(StepArgs<S, R, PhiT> a)
+__global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 4 : 1) lb_fused_kernel(StepArgs<S, R, PhiT> a)
 {
     lb_body<S, R, PhiT, DEV>(a, blockIdx.x);
 }
 
 template <typename S, typename R, typename PhiT, bool DEV>
-__global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 4 : 1)
     lb_fused_batch_kernel(const StepArgs<S, R, PhiT> *reps)
 {
     const StepArgs<S, R, PhiT> &a = reps[blockIdx.y];
@@ -1725,6 +1717,28 @@ __global__ void fields_kernel(StepArgs<S, R, PhiT> a, double *n_out, double *j_o
         if constexpr (((PhiT)0.5) != 0) v = (double)a.phi[i];
         else v = (double)a.phi[i] * PHI_INV;
         phi_out[i] = solid ? 0.0 : v;
+    }
+}
+
+// Per-species mass of the post-collision populations (the collision keeps
+// each node's density, so this is the total of the last step's densities),
+// one FP64 partial per block; computed only when statistics are requested.
+template <typename S, typename R, typename PhiT, bool DEV>
+__global__ void mass_kernel(StepArgs<S, R, PhiT> a)
+{
+    __shared__ double sh[256 / 32];
+    const Grid3 g = a.g;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double v[NS] = {0.0, 0.0, 0.0};
+    if (i < g.N && !(a.mask[i] & SOLID_BIT))
+        for (int s = 0; s < NS; s++) {
+            double t = 0.0;
+            for (int p = 0; p < Q; p++) t += (double)Store<S>::ld(a.fin + (long long)(s * Q + p) * g.N + i);
+            v[s] = DEV ? t + (double)a.n_ref[s] : t;
+        }
+    for (int s = 0; s < NS; s++) {
+        const double b = block_sum(v[s], sh);
+        if (threadIdx.x == 0) a.part_mass[(size_t)blockIdx.x * NS + s] = b;
     }
 }
 

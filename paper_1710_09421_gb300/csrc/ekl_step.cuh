@@ -266,6 +266,16 @@ int state_impl(Ctx &c, double *d_f, double *d_phi, int to_host)
     return cuda_ok(cudaGetLastError());
 }
 
+// per-block mass partials into c.part_mass; returns the block count (< 0 on error)
+template <typename S, typename R, typename PhiT, bool DEV> int mass_impl(Ctx &c)
+{
+    StepArgs<S, R, PhiT> a = make_args<S, R, PhiT>(c);
+    const int blocks = (int)((c.N + 255) / 256);
+    mass_kernel<S, R, PhiT, DEV><<<blocks, 256, 0, c.stream>>>(a);
+    c.launches++;
+    return cudaGetLastError() == cudaSuccess ? blocks : EKL_ERR_CUDA;
+}
+
 // ------------------------------------------------------------------ batch
 template <typename S, typename R, typename PhiT, bool DEV> int batch_tables(Batch &B)
 {
@@ -414,6 +424,7 @@ template <typename S, typename R, typename PhiT> int poisson_max_blocks_per_sm()
         return state_impl<S, R, PhiT, DEV>(c, (double *)f, (double *)p, 0);                      \
     }                                                                                            \
     int pois_blocks_##SUFFIX() { return poisson_max_blocks_per_sm<S, R, PhiT>(); }                \
+    int mass_##SUFFIX(Ctx &c) { return mass_impl<S, R, PhiT, DEV>(c); }                           \
     int mg_blocks_##SUFFIX(size_t smem) { return mg_max_blocks_per_sm<S, R, PhiT>(smem); }        \
     int run_batch_##SUFFIX(Batch &b, int n) { return batch_impl<S, R, PhiT, DEV>(b, n); }         \
     }
