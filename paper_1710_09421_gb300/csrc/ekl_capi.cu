@@ -718,7 +718,7 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
         if (!d_solid) { rc = fail(EKL_ERR_ALLOC, "device allocation failed"); break; }
         e = cudaMemcpyAsync(d_solid, solid, N, cudaMemcpyHostToDevice, c.stream);
         if (e != cudaSuccess) { rc = fail_cuda(e, "upload solid"); break; }
-        mask_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c.stream>>>(Grid3{c.nx, c.ny, c.nz, N}, c.per[0], c.per[1], c.per[2], d_solid, c.mask);
+        mask_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c.stream>>>(make_grid3(c.nx, c.ny, c.nz), c.per[0], c.per[1], c.per[2], d_solid, c.mask);
         c.launches++;
         if (charged) {
             if (c.prec == EKL_F64) {

@@ -60,15 +60,34 @@ template <> struct Store<__half> {
 struct Grid3 {
     int nx, ny, nz;
     long long N;
+    // i / nx and r / ny for 0 <= i, r < 2^31 as (i * m) >> s: with
+    // L = ceil(log2 d), s = 31 + L and m = ceil(2^s / d) (< 2^32), the error
+    // i (m d - 2^s) / (d 2^s) stays below 1/d, so the floor is exact
+    unsigned mx, my;
+    int sx, sy;
 };
+inline void grid_divisor(int d, unsigned &m, int &s)
+{
+    int L = 0;
+    while ((1ll << L) < (long long)d) L++;
+    s = 31 + L;
+    m = (unsigned)(((1ull << s) + (unsigned long long)d - 1) / (unsigned long long)d);
+}
+inline Grid3 make_grid3(int nx, int ny, int nz)
+{
+    Grid3 g{nx, ny, nz, (long long)nx * ny * nz, 0u, 0u, 0, 0};
+    grid_divisor(nx, g.mx, g.sx);
+    grid_divisor(ny, g.my, g.sy);
+    return g;
+}
 
 // node coordinates; node ids fit 32 bits (lattices are capped at 2^31/64 nodes)
 __device__ __forceinline__ void coords_of(const Grid3 &g, long long i64, int &x, int &y, int &z)
 {
     const int i = (int)i64;
-    const int r = i / g.nx;
+    const int r = (int)(((unsigned long long)(unsigned)i * g.mx) >> g.sx);
     x = i - r * g.nx;
-    z = r / g.ny;
+    z = (int)(((unsigned long long)(unsigned)r * g.my) >> g.sy);
     y = r - z * g.ny;
 }
 

@@ -16,7 +16,7 @@ static StepArgs<S, R, PhiT> make_args(Ctx &c, int parity = -1)
 {
     StepArgs<S, R, PhiT> a;
     const int cur = parity < 0 ? c.cur : parity;
-    a.g = Grid3{c.nx, c.ny, c.nz, c.N};
+    a.g = make_grid3(c.nx, c.ny, c.nz);
     for (int k = 0; k < 3; k++) a.per[k] = c.per[k];
     a.mask = c.mask;
     a.fin = (const S *)c.f[cur];
@@ -63,7 +63,7 @@ static StepArgs<S, R, PhiT> make_args(Ctx &c, int parity = -1)
 template <typename R> static BeadArgs<R> make_bead_args(Ctx &c)
 {
     BeadArgs<R> b;
-    b.g = Grid3{c.nx, c.ny, c.nz, c.N};
+    b.g = make_grid3(c.nx, c.ny, c.nz);
     for (int k = 0; k < 3; k++) b.per[k] = c.per[k];
     b.mask = c.mask;
     b.nb = c.nb;
@@ -143,7 +143,7 @@ static inline void phase_end(Ctx &c, int ph)
 template <typename S, typename R, typename PhiT, bool DEV> int init_impl(Ctx &c, const double *d_n)
 {
     int blocks = (int)((c.N + 255) / 256);
-    init_kernel<S, R, DEV><<<blocks, 256, 0, c.stream>>>(Grid3{c.nx, c.ny, c.nz, c.N}, c.mask, d_n,
+    init_kernel<S, R, DEV><<<blocks, 256, 0, c.stream>>>(make_grid3(c.nx, c.ny, c.nz), c.mask, d_n,
                                                          (S *)c.f[c.cur], (R)c.P.n_ref[0],
                                                          (R)c.P.n_ref[1], (R)c.P.n_ref[2]);
     c.launches++;
