@@ -143,6 +143,7 @@ void release(Ctx &c)
     dev_free(c, c.mg_p[1], 0);
     dev_free(c, c.mg_part, 0);
     dev_free(c, c.mg_dense, 0);
+    dev_free(c, c.mg_phi_prev, 0);
     warmstart_free(c);
     (void)rs;
     for (int k = 0; k < 2 * PH_COUNT; k++)
@@ -470,6 +471,8 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A)
     c.mg_p[0] = (float *)A(N * sizeof(float));
     c.mg_p[1] = (float *)A(N * sizeof(float));
     c.mg_part = (double *)A((size_t)4 * c.pois_blocks * sizeof(double));
+    c.mg_phi_prev = A(N * phi_size(c.prec));
+    c.mg_have_prev = 0;
     c.mg = 1;
     return nullptr;
 }
@@ -937,6 +940,7 @@ int ekl_set_state(ekl_handle *h, const double *fstar, const double *phi, int64_t
     dev_free(c, dp, 0);
     if (rc != EKL_OK || e != cudaSuccess) return fail_cuda(e, "set_state");
     c.step = step;
+    c.mg_have_prev = 0;  // the potential history no longer matches
     return EKL_OK;
 }
 

@@ -110,6 +110,8 @@ struct Ctx {
     MgLevel mg_lev[MG_MAXLEV];
     float *mg_r, *mg_z, *mg_q, *mg_p[2];  // lattice-level CG vectors
     float *mg_dense;         // pseudo-inverse of the coarsest operator, or null
+    void *mg_phi_prev;       // potential of the step before the last (starting-guess extrapolation)
+    int mg_have_prev;        // mg_phi_prev and phi hold two consecutive potentials
     double *mg_part;         // [4][pois_blocks] reduction partials
 
     // learned warm start of the Poisson solve (ekl_net.cu)

@@ -37,6 +37,8 @@ struct MgArgs {
     float *r, *z, *q, *p[2];
     double *part;         // [4][gridDim.x]
     const float *dense;   // pseudo-inverse of the coarsest operator [N][N], or null
+    void *phi_prev;       // potential of the step before the last (PhiT[N])
+    int have_prev;        // phi_prev holds phi(t-2) and phi holds phi(t-1)
     int nlev, cta_from, nu, nu_c, coarse_sweeps;  // smoothing sweeps: lattice level, coarse levels
     float inner_red;
     MgLevel lev[MG_MAXLEV];
@@ -665,6 +667,18 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_mg_kernel(StepArgs<S,
         return true;
     };
     if (blockIdx.x == 0 && !m.dense) mg_cta_load(m, mg_sm);
+    // starting guess: the linear extrapolation 2 phi(t-1) - phi(t-2) of the
+    // last two potentials (exact in the fixed-point type); phi(t-1) is kept
+    // for the next step
+    {
+        PhiT *prev = (PhiT *)m.phi_prev;
+        for (int i = tid; i < N; i += nthr) {
+            if (__ldg(a.mask + i) & SOLID_BIT) continue;
+            const PhiT cur = __ldcg(a.phi + i);
+            if (m.have_prev) __stcg(a.phi + i, (PhiT)2 * cur - __ldcg(prev + i));
+            __stcg(prev + i, cur);
+        }
+    }
     double bb;
     if (!reduce(form_source(a, tid, nthr, sh, bc), bb)) return;
     if (a.fixed_iter <= 0 && bb == 0.0) {

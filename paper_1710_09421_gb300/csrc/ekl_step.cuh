@@ -119,6 +119,9 @@ static inline MgArgs make_mg_args(const Ctx &c)
     m.p[1] = c.mg_p[1];
     m.part = c.mg_part;
     m.dense = c.mg_dense;
+    m.phi_prev = c.mg_phi_prev;
+    // with a learned warm start installed the network supplies the guess
+    m.have_prev = c.mg_have_prev && !c.net;
     m.nlev = c.mg_nlev;
     m.cta_from = c.mg_cta_from;
     m.nu = MG_NU;
@@ -191,6 +194,7 @@ template <typename S, typename R, typename PhiT, bool DEV> int steps_impl(Ctx &c
                                                         c.stream);
             c.launches++;
             if (e != cudaSuccess) return EKL_ERR_CUDA;
+            c.mg_have_prev = 1;
         } else if (c.pois_tiled) {
             TileGeom tg{c.tile_ty, c.tile_tz, c.tile_nty, c.tile_ntz};
             const size_t smem = tile_smem_bytes<PhiT>(c.nx, tg);
