@@ -232,6 +232,8 @@ def run_batch(args):
     torch.cuda.set_device(0)
     E.load()
     wls = W.replica_set(n_rep=args.replicas, precision=args.precision)
+    if args.poisson == "mg":
+        wls = [w.replace(flags=w.flags | W.FLAG_POISSON_MG) for w in wls]
     stream = torch.cuda.Stream()
     b = E.Batch(wls, stream=stream.cuda_stream)
     choice = b.autotune(1)
@@ -273,7 +275,8 @@ def run_batch(args):
         "config": {"workload": f"{len(wls)} uneven translocation replicas", "nodes": nodes,
                    "beads": int(sum(w.n_beads for w in wls)), "poisson_tol": wls[0].poisson_tol,
                    "autotune_choice": choice, "l2": "inputs larger than L2"},
-        "steps_per_s": round(steps_per_s, 3), "poisson_sweeps_last_step_mean": float(sweeps),
+        "poisson_solver": "multigrid-CG" if args.poisson == "mg" else "chebyshev-sor",
+        "steps_per_s": round(steps_per_s, 3), "poisson_iterations_last_step_mean": float(sweeps),
         "events_completed": events,
         "events_per_hour_projected": round(rate * steps_per_s * 3600, 2),
         "gpu_launches": launches, "clocks": clk.summary(), "status": rc,

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "ekl_kernels.cuh"
+#include "ekl_mg.cuh"
 
 using namespace ekl;
 
@@ -49,15 +50,16 @@ struct PrecOps {
     int (*pois_blocks)();
     int (*mg_blocks)(size_t);
     int (*mass)(Ctx &);
+    int (*mg_batch_blocks)(size_t);
 };
 
 const PrecOps &ops(int prec)
 {
     static const PrecOps t[4] = {
-        {init_populations_f64, run_steps_f64, get_fields_f64, get_state_f64, set_state_f64, pois_blocks_f64, mg_blocks_f64, mass_f64},
-        {init_populations_f32, run_steps_f32, get_fields_f32, get_state_f32, set_state_f32, pois_blocks_f32, mg_blocks_f32, mass_f32},
-        {init_populations_bf16, run_steps_bf16, get_fields_bf16, get_state_bf16, set_state_bf16, pois_blocks_bf16, mg_blocks_bf16, mass_bf16},
-        {init_populations_fp16, run_steps_fp16, get_fields_fp16, get_state_fp16, set_state_fp16, pois_blocks_fp16, mg_blocks_fp16, mass_fp16},
+        {init_populations_f64, run_steps_f64, get_fields_f64, get_state_f64, set_state_f64, pois_blocks_f64, mg_blocks_f64, mass_f64, mg_batch_blocks_f64},
+        {init_populations_f32, run_steps_f32, get_fields_f32, get_state_f32, set_state_f32, pois_blocks_f32, mg_blocks_f32, mass_f32, mg_batch_blocks_f32},
+        {init_populations_bf16, run_steps_bf16, get_fields_bf16, get_state_bf16, set_state_bf16, pois_blocks_bf16, mg_blocks_bf16, mass_bf16, mg_batch_blocks_bf16},
+        {init_populations_fp16, run_steps_fp16, get_fields_fp16, get_state_fp16, set_state_fp16, pois_blocks_fp16, mg_blocks_fp16, mass_fp16, mg_batch_blocks_fp16},
     };
     return t[prec];
 }
@@ -337,7 +339,7 @@ static std::vector<float> coarse_pinv(int nx, int ny, int nz, const std::vector<
 // sum of the level-l conductances crossing the aggregated face.  Returns an
 // error message, or null.
 template <typename Alloc>
-static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A)
+static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, bool allow_dense)
 {
     int d[MG_MAXLEV][3];
     d[0][0] = c.nx;
@@ -426,7 +428,7 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A)
         if (cudaMemset(ml.e, 0, NC * sizeof(float)) != cudaSuccess) return "multigrid setup failed";
         if (cudaMemcpy(ml.sig, h4.data(), NC * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess)
             return "multigrid upload failed";
-        if (l == nlev - 1 && NC <= MG_DENSE_CELLS) {
+        if (allow_dense && l == nlev - 1 && NC <= MG_DENSE_CELLS) {
             const std::vector<float> M = coarse_pinv(C[0], C[1], C[2], h4);
             if (M.empty()) return "coarsest multigrid operator is not semi-definite";
             c.mg_dense = (float *)A(M.size() * sizeof(float));
@@ -505,7 +507,10 @@ void ekl_lattice(int32_t *c, double *w, int32_t *opp)
     }
 }
 
-int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
+// replica: a handle created for a batch (its coarsest multigrid level is
+// smoothed by one block instead of solved by a host-built pseudo-inverse,
+// which would cost host time per replica)
+static int create_handle(const ekl_params *P, void *stream, ekl_handle **out, bool replica)
 {
     g_err[0] = 0;
     if (!out) return fail(EKL_ERR_ARG, "out is null");
@@ -702,7 +707,7 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
         return fail(EKL_ERR_ALLOC, "device allocation failed");
     }
     if (P->flags & EKL_POISSON_MG) {
-        const char *why = build_multigrid(c, solid, A);
+        const char *why = build_multigrid(c, solid, A, !replica);
         if (!why && !okall) why = "device allocation failed";
         if (why) {
             release(c);
@@ -769,6 +774,8 @@ int ekl_create(const ekl_params *P, void *stream, ekl_handle **out)
     *out = h;
     return EKL_OK;
 }
+
+int ekl_create(const ekl_params *P, void *stream, ekl_handle **out) { return create_handle(P, stream, out, false); }
 
 int ekl_set_beads(ekl_handle *h, int32_t n, const double *R, const double *V, const double *q,
                   const int32_t *chain)
@@ -1034,6 +1041,8 @@ void batch_release(Batch &B)
     dev_free(c0, B.d_rep_blocks, 0);
     dev_free(c0, B.barrier, 0);
     dev_free(c0, B.status, 0);
+    dev_free(c0, B.d_mgargs, 0);
+    dev_free(c0, B.mg_bars, 0);
 }
 
 }  // namespace
@@ -1058,7 +1067,7 @@ int ekl_batch_create(int32_t nrep, const ekl_params *params, void *stream, ekl_b
     int rc = EKL_OK;
     for (int r = 0; r < nrep && rc == EKL_OK; r++) {
         ekl_handle *h = nullptr;
-        rc = ekl_create(&params[r], stream, &h);
+        rc = create_handle(&params[r], stream, &h, true);
         if (rc == EKL_OK) {
             B.handles[r] = h;
             B.reps[r] = &h->c;
@@ -1103,6 +1112,21 @@ int ekl_batch_create(int32_t nrep, const ekl_params *params, void *stream, ekl_b
             B.pois_threads = POIS_THREADS;
             B.pois_blocks = sms;
             B.weight_fluid = 1;
+        }
+        // multigrid replicas (all or none)
+        if (rc == EKL_OK) {
+            B.mg = B.reps[0]->mg;
+            for (int r = 1; r < nrep; r++)
+                if (B.reps[r]->mg != B.mg) rc = fail(EKL_ERR_ARG, "replicas must share the Poisson solver");
+        }
+        if (rc == EKL_OK && B.mg) {
+            B.mg_smem = 0;
+            for (int r = 0; r < nrep; r++) B.mg_smem = std::max(B.mg_smem, B.reps[r]->mg_smem);
+            B.d_mgargs = A(nrep * sizeof(MgArgs));
+            B.mg_bars = (unsigned *)A(4 * sizeof(unsigned) * (size_t)nrep);
+            if (!ok) rc = fail(EKL_ERR_ALLOC, "device allocation failed");
+            else if (ops(B.prec).mg_batch_blocks(B.mg_smem) < 1)
+                rc = fail(EKL_ERR_CUDA, "batched multigrid kernel cannot be resident");
         }
     }
     if (rc != EKL_OK) {
@@ -1164,6 +1188,7 @@ int ekl_batch_autotune(ekl_batch *bh, int32_t trial_steps, int32_t *choice_out)
     float best = 1e30f;
     int bestc = 0;
     for (int choice = 0; choice < 4; choice++) {
+        if (B.mg && (choice & 1)) continue;  // the multigrid launch keeps one 1024-thread block per SM
         B.pois_threads = (choice & 1) ? 512 : 1024;
         B.pois_blocks = (choice & 1) ? 2 * sms : sms;
         B.weight_fluid = (choice >> 1) & 1;

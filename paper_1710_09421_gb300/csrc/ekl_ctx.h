@@ -150,6 +150,12 @@ struct Batch {
     int weight_fluid;        // split Poisson blocks by fluid nodes (1) or all nodes (0)
     int max_lb_blocks, max_charge_blocks, max_nb;
     long long launches;
+    // multigrid replicas: one cooperative launch, each replica on its own
+    // blocks with its own barrier words
+    int mg;
+    void *d_mgargs;          // MgArgs per replica
+    unsigned *mg_bars;       // [4 * nrep]
+    size_t mg_smem;          // largest replica's shared memory for its coarse levels
 };
 int run_batch_f64(Batch &b, int nsteps);
 int run_batch_f32(Batch &b, int nsteps);
@@ -178,6 +184,7 @@ int set_state_f64(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_f64();
 int mass_f64(Ctx &c);
 int mg_blocks_f64(size_t smem);
+int mg_batch_blocks_f64(size_t smem);
 
 int init_populations_f32(Ctx &c, const double *d_n_init);
 int run_steps_f32(Ctx &c, int nsteps);
@@ -187,6 +194,7 @@ int set_state_f32(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_f32();
 int mass_f32(Ctx &c);
 int mg_blocks_f32(size_t smem);
+int mg_batch_blocks_f32(size_t smem);
 
 int init_populations_bf16(Ctx &c, const double *d_n_init);
 int run_steps_bf16(Ctx &c, int nsteps);
@@ -196,6 +204,7 @@ int set_state_bf16(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_bf16();
 int mass_bf16(Ctx &c);
 int mg_blocks_bf16(size_t smem);
+int mg_batch_blocks_bf16(size_t smem);
 
 int init_populations_fp16(Ctx &c, const double *d_n_init);
 int run_steps_fp16(Ctx &c, int nsteps);
@@ -205,6 +214,7 @@ int set_state_fp16(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_fp16();
 int mass_fp16(Ctx &c);
 int mg_blocks_fp16(size_t smem);
+int mg_batch_blocks_fp16(size_t smem);
 
 size_t real_size(int prec);
 size_t store_size(int prec);

@@ -44,6 +44,15 @@ struct MgArgs {
     MgLevel lev[MG_MAXLEV];
 };
 
+// The blocks that solve one problem: all blocks of a single-handle launch, or
+// the blocks a batched launch assigns to one replica (each replica then runs
+// at its own pace with its own barrier).
+struct MgGrid {
+    int t0, nt;      // this thread's index and the thread count of the set
+    int nblk, blk;   // block count of the set and this block's index in it
+    unsigned *bar;   // the set's barrier words
+};
+
 __device__ __forceinline__ float mg_inv_deg(int d)
 {
     return d == 6 ? (1.f / 6.f) : d == 5 ? 0.2f : d == 4 ? 0.25f : d == 3 ? (1.f / 3.f) : d == 2 ? 0.5f : 1.f;
@@ -456,16 +465,15 @@ static __device__ void mg_dense_solve(const MgArgs &m, int t0, int nt)
 // already set to r / deg; returns this block's partial of r.z in thread 0
 // (through rz_block), or false on a barrier abort.
 template <typename S, typename R, typename PhiT>
-__device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, unsigned &bar_k, float *sm, double *sh,
-                          double *bc, double &rz_block)
+__device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const MgGrid &G, unsigned &bar_k,
+                          float *sm, double *sh, double *bc, double &rz_block)
 {
     const Grid3 g = a.g;
-    const unsigned nblk = gridDim.x;
-    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, nt = nblk * blockDim.x;
+    const int t0 = G.t0, nt = G.nt;
     float dummy = 0.f;
-#define MG_BAR()                                                     \
-    do {                                                             \
-        if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return false; \
+#define MG_BAR()                                                          \
+    do {                                                                  \
+        if (!grid_barrier(G.bar, (unsigned)G.nblk, bar_k, a.status)) return false; \
     } while (0)
     // lattice level: rest of the pre-smoothing, residual restricted to level 1
     for (int s = 1; s < 2 * m.nu; s++) {
@@ -486,7 +494,7 @@ __device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, unsign
         MG_BAR();
     }
     if (m.dense) mg_dense_solve(m, t0, nt);
-    else if (blockIdx.x == 0) mg_cta_cycle(m, sm, sh, bc);
+    else if (G.blk == 0) mg_cta_cycle(m, sm, sh, bc);
     MG_BAR();
     for (int l = m.cta_from - 1; l >= 1; l--) {
         coarse_half<false, true>(m.lev[l], m.lev[l + 1], 1, t0, nt);
@@ -644,15 +652,12 @@ __device__ float mg_update_pass(const Grid3 &g, const uint32_t *__restrict__ mas
 }
 
 template <typename S, typename R, typename PhiT>
-__global__ void __launch_bounds__(POIS_THREADS, 1) poisson_mg_kernel(StepArgs<S, R, PhiT> a, MgArgs m)
+__device__ void mg_solve(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const MgGrid &G, float *mg_sm, double *sh,
+                         double *bc)
 {
-    __shared__ double sh[POIS_THREADS / 32];
-    __shared__ double bc[1];
-    extern __shared__ float mg_sm[];  // block 0: e and f of the levels it handles alone
     const Grid3 g = a.g;
-    const unsigned nblk = gridDim.x;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nthr = nblk * blockDim.x;
+    const int nblk = G.nblk;
+    const int tid = G.t0, nthr = G.nt;
     const int N = (int)g.N;
     unsigned bar_k = 0;
     int slot = 0;
@@ -661,12 +666,12 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_mg_kernel(StepArgs<S,
     auto reduce = [&](double block_value, double &out) -> bool {
         double *p = m.part + (size_t)(slot & 3) * nblk;
         slot++;
-        if (threadIdx.x == 0) p[blockIdx.x] = block_value;
-        if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return false;
-        out = sum_partials(p, (int)nblk, bc);
+        if (threadIdx.x == 0) p[G.blk] = block_value;
+        if (!grid_barrier(G.bar, (unsigned)nblk, bar_k, a.status)) return false;
+        out = sum_partials(p, nblk, bc);
         return true;
     };
-    if (blockIdx.x == 0 && !m.dense) mg_cta_load(m, mg_sm);
+    if (G.blk == 0 && !m.dense) mg_cta_load(m, mg_sm);
     // starting guess: the linear extrapolation 2 phi(t-1) - phi(t-2) of the
     // last two potentials (exact in the fixed-point type); phi(t-1) is kept
     // for the next step
@@ -700,7 +705,7 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_mg_kernel(StepArgs<S,
     double rz_old = 1.0;
     while (!converged && it < limit) {
         double rzb = 0.0, rz;
-        if (!mg_vcycle(a, m, bar_k, mg_sm, sh, bc, rzb)) return;
+        if (!mg_vcycle(a, m, G, bar_k, mg_sm, sh, bc, rzb)) return;
         if (!reduce(rzb, rz)) return;
         if (!(rz > 0.0)) break;
         const float beta = fresh ? 0.f : (float)(rz / rz_old);
@@ -744,6 +749,33 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_mg_kernel(StepArgs<S,
         *a.pois_res = sqrt(rr_true / bb);
         if (a.fixed_iter <= 0 && !(converged || rr_true <= tol2)) atomicOr(a.status, ST_NOCONV);
     }
+}
+
+template <typename S, typename R, typename PhiT>
+__global__ void __launch_bounds__(POIS_THREADS, 1) poisson_mg_kernel(StepArgs<S, R, PhiT> a, MgArgs m)
+{
+    __shared__ double sh[POIS_THREADS / 32];
+    __shared__ double bc[1];
+    extern __shared__ float mg_sm[];  // block 0: the levels it handles alone
+    const MgGrid G{(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x), (int)gridDim.x,
+                   (int)blockIdx.x, a.barrier};
+    mg_solve(a, m, G, mg_sm, sh, bc);
+}
+
+// Batched form: block b solves replica block_rep[b] together with the other
+// rep_blocks[r] blocks of that replica (local index block_local[b]); each
+// replica has its own barrier words bars[4 r ..] and converges on its own.
+template <typename S, typename R, typename PhiT>
+__global__ void __launch_bounds__(POIS_THREADS, 1)
+    poisson_mg_batch_kernel(const StepArgs<S, R, PhiT> *reps, const MgArgs *mgs, PoisBatch pb, unsigned *bars)
+{
+    __shared__ double sh[POIS_THREADS / 32];
+    __shared__ double bc[1];
+    extern __shared__ float mg_sm[];
+    const int r = pb.block_rep[blockIdx.x];
+    const int lb = pb.block_local[blockIdx.x], nb = pb.rep_blocks[r];
+    const MgGrid G{(int)(lb * blockDim.x + threadIdx.x), (int)(nb * blockDim.x), nb, lb, bars + 4 * r};
+    mg_solve(reps[r], mgs[r], G, mg_sm, sh, bc);
 }
 
 }  // namespace ekl

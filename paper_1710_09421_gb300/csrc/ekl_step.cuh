@@ -281,6 +281,16 @@ template <typename S, typename R, typename PhiT, bool DEV> int mass_impl(Ctx &c)
 }
 
 // ------------------------------------------------------------------ batch
+static inline int mg_batch_tables(Batch &B)
+{
+    std::vector<MgArgs> t(B.nrep);
+    for (int r = 0; r < B.nrep; r++) t[r] = make_mg_args(*B.reps[r]);
+    if (cudaMemcpyAsync(B.d_mgargs, t.data(), t.size() * sizeof(MgArgs), cudaMemcpyHostToDevice, B.stream) !=
+        cudaSuccess)
+        return EKL_ERR_CUDA;
+    return cudaStreamSynchronize(B.stream) == cudaSuccess ? EKL_OK : EKL_ERR_CUDA;
+}
+
 template <typename S, typename R, typename PhiT, bool DEV> int batch_tables(Batch &B)
 {
     const int n = B.nrep;
@@ -332,6 +342,7 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_tables(Batc
         cudaMemcpyAsync(B.d_rep_blocks, k.data(), n * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess)
         return EKL_ERR_CUDA;
     if (cudaStreamSynchronize(B.stream) != cudaSuccess) return EKL_ERR_CUDA;
+    if (B.mg && mg_batch_tables(B) != EKL_OK) return EKL_ERR_CUDA;
     B.max_nb = 0;
     B.max_lb_blocks = B.max_charge_blocks = 0;
     for (int r = 0; r < n; r++) {
@@ -361,7 +372,33 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_impl(Batch 
             (const StepArgs<S, R, PhiT> *)B.d_args[q]);
         B.launches++;
         cudaMemsetAsync(B.barrier, 0, 4 * sizeof(unsigned), B.stream);
-        {
+        if (B.mg) {
+            cudaMemsetAsync(B.mg_bars, 0, 4 * sizeof(unsigned) * (size_t)n, B.stream);
+            PoisBatch pb{n, B.d_block_rep, B.d_block_local, B.d_rep_blocks, B.barrier, B.status};
+            const StepArgs<S, R, PhiT> *reps = (const StepArgs<S, R, PhiT> *)B.d_args[q];
+            const MgArgs *mgs = (const MgArgs *)B.d_mgargs;
+            unsigned *bars = B.mg_bars;
+            static size_t attr_bytes = 0;
+            if (B.mg_smem > attr_bytes) {
+                cudaFuncSetAttribute(poisson_mg_batch_kernel<S, R, PhiT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.mg_smem);
+                attr_bytes = B.mg_smem;
+            }
+            void *args[] = {&reps, &mgs, &pb, &bars};
+            cudaError_t e = cudaLaunchCooperativeKernel((const void *)poisson_mg_batch_kernel<S, R, PhiT>,
+                                                        dim3(B.pois_blocks), dim3(POIS_THREADS), args, B.mg_smem,
+                                                        B.stream);
+            B.launches++;
+            if (e != cudaSuccess) return EKL_ERR_CUDA;
+            // from now on every replica extrapolates its starting guess
+            bool changed = false;
+            for (int r = 0; r < n; r++)
+                if (!B.reps[r]->mg_have_prev) {
+                    B.reps[r]->mg_have_prev = 1;
+                    changed = true;
+                }
+            if (changed && mg_batch_tables(B) != EKL_OK) return EKL_ERR_CUDA;
+        } else {
             PoisBatch pb{n, B.d_block_rep, B.d_block_local, B.d_rep_blocks, B.barrier, B.status};
             const StepArgs<S, R, PhiT> *reps = (const StepArgs<S, R, PhiT> *)B.d_args[q];
             void *args[] = {&reps, &pb};
@@ -405,6 +442,16 @@ template <typename S, typename R, typename PhiT> int mg_max_blocks_per_sm(size_t
     return nb;
 }
 
+template <typename S, typename R, typename PhiT> int mg_batch_max_blocks_per_sm(size_t smem)
+{
+    if (cudaFuncSetAttribute(poisson_mg_batch_kernel<S, R, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, poisson_mg_batch_kernel<S, R, PhiT>, POIS_THREADS, smem);
+    return nb;
+}
+
 template <typename S, typename R, typename PhiT> int poisson_max_blocks_per_sm()
 {
     int nb = 0;
@@ -430,5 +477,6 @@ template <typename S, typename R, typename PhiT> int poisson_max_blocks_per_sm()
     int pois_blocks_##SUFFIX() { return poisson_max_blocks_per_sm<S, R, PhiT>(); }                \
     int mass_##SUFFIX(Ctx &c) { return mass_impl<S, R, PhiT, DEV>(c); }                           \
     int mg_blocks_##SUFFIX(size_t smem) { return mg_max_blocks_per_sm<S, R, PhiT>(smem); }        \
+    int mg_batch_blocks_##SUFFIX(size_t smem) { return mg_batch_max_blocks_per_sm<S, R, PhiT>(smem); } \
     int run_batch_##SUFFIX(Batch &b, int n) { return batch_impl<S, R, PhiT, DEV>(b, n); }         \
     }

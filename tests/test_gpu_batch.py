@@ -52,3 +52,40 @@ def test_batch_tolerance_and_autotune():
     batch.step(3)
     assert batch.launches() - l0 == 3 * 5
     batch.close()
+
+
+def test_batch_multigrid_replicas():
+    """Batched multigrid: each replica solves on its own blocks with its own
+    barrier and converges on its own.  Every replica meets its tolerance; its
+    FP64 potential meets it under the oracle's operator and source too; and it
+    agrees with a single-handle multigrid run (whose coarsest level is solved
+    exactly instead of smoothed) within the bound two tolerance-converged
+    solves allow."""
+    import oracle
+    from helpers import rel
+
+    tol = 1e-10
+    wls = _uneven(0)
+    wls[2] = W.small_pore(nx=16, ny=16, nz=20, membrane=(8, 11), radius=3.0, n_beads=3, seed_init=9)
+    wls = [w.replace(poisson_tol=tol, flags=W.FLAG_POISSON_MG, precision="f64") for w in wls]
+    batch = E.Batch(wls, precision="f64")
+    assert batch.step(1) >= 0
+    for r, wl in enumerate(wls):
+        ref = oracle.Sim(wl.replace(poisson_tol=1e-13), threads=8)
+        assert ref.step(1) >= 0
+        _, phi, _ = batch.reps[r].get_state()
+        assert ref.poisson_residual(ref.last_rho(), phi) <= tol * 1.001, r
+    l0 = batch.launches()
+    assert batch.step(9) >= 0
+    assert batch.launches() - l0 == 9 * 5
+    for r, wl in enumerate(wls):
+        st = batch.reps[r].stats()
+        assert st["poisson_res"] <= tol and st["poisson_iters"] > 0, (r, st)
+        sim = E.Simulation(wl, precision="f64")
+        sim.step(10)
+        a, b = sim.fields(), batch.reps[r].fields()
+        fluid = wl.solid.ravel() == 0
+        assert max(rel(b["n"][s][fluid], a["n"][s][fluid]) for s in range(3)) < 1e-10, r
+        assert rel(b["phi"][fluid], a["phi"][fluid]) < 1e-7, r
+        sim.close()
+    batch.close()
