@@ -339,7 +339,7 @@ static std::vector<float> coarse_pinv(int nx, int ny, int nz, const std::vector<
 // sum of the level-l conductances crossing the aggregated face.  Returns an
 // error message, or null.
 template <typename Alloc>
-static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, bool allow_dense)
+static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long long coarsest_cells)
 {
     int d[MG_MAXLEV][3];
     d[0][0] = c.nx;
@@ -348,7 +348,7 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, bool 
     int nlev = 1;
     while (nlev < MG_MAXLEV) {
         const int *p = d[nlev - 1];
-        if ((long long)p[0] * p[1] * p[2] <= MG_COARSEST_CELLS) break;
+        if ((long long)p[0] * p[1] * p[2] <= coarsest_cells) break;
         bool ok = true;
         for (int a = 0; a < 3; a++)
             if (p[a] < 2 || (c.per[a] && p[a] % 4)) ok = false;
@@ -428,7 +428,7 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, bool 
         if (cudaMemset(ml.e, 0, NC * sizeof(float)) != cudaSuccess) return "multigrid setup failed";
         if (cudaMemcpy(ml.sig, h4.data(), NC * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess)
             return "multigrid upload failed";
-        if (allow_dense && l == nlev - 1 && NC <= MG_DENSE_CELLS) {
+        if (l == nlev - 1 && NC <= MG_DENSE_CELLS) {
             const std::vector<float> M = coarse_pinv(C[0], C[1], C[2], h4);
             if (M.empty()) return "coarsest multigrid operator is not semi-definite";
             c.mg_dense = (float *)A(M.size() * sizeof(float));
@@ -507,9 +507,9 @@ void ekl_lattice(int32_t *c, double *w, int32_t *opp)
     }
 }
 
-// replica: a handle created for a batch (its coarsest multigrid level is
-// smoothed by one block instead of solved by a host-built pseudo-inverse,
-// which would cost host time per replica)
+// replica: a handle created for a batch (its multigrid hierarchy goes one
+// level deeper, so that the host-built pseudo-inverse of each replica's
+// coarsest level stays small to build and to read)
 static int create_handle(const ekl_params *P, void *stream, ekl_handle **out, bool replica)
 {
     g_err[0] = 0;
@@ -707,7 +707,7 @@ static int create_handle(const ekl_params *P, void *stream, ekl_handle **out, bo
         return fail(EKL_ERR_ALLOC, "device allocation failed");
     }
     if (P->flags & EKL_POISSON_MG) {
-        const char *why = build_multigrid(c, solid, A, !replica);
+        const char *why = build_multigrid(c, solid, A, replica ? MG_COARSEST_CELLS_REPLICA : MG_COARSEST_CELLS);
         if (!why && !okall) why = "device allocation failed";
         if (why) {
             release(c);

@@ -35,6 +35,7 @@ constexpr int MG_NU_COARSE = 2;          // the same on the coarse levels
 constexpr int MG_COARSE_SWEEPS = 8;      // (R B)^k R half sweeps on the coarsest level
 constexpr float MG_INNER_RED = 1e-4f;    // CG residual reduction before the true residual is formed
 constexpr int MG_COARSEST_CELLS = 1024;  // stop coarsening at or below this many cells
+constexpr int MG_COARSEST_CELLS_REPLICA = 512;  // the same for the replicas of a batch
 constexpr int MG_DENSE_CELLS = 1024;     // coarsest levels this small are solved exactly (dense pseudo-inverse)
 constexpr int MG_CTA_CELLS = 2048;       // levels this small are handled by one block
 struct MgLevel {
