@@ -155,24 +155,30 @@ static __device__ void fine_half(const Grid3 &g, const uint32_t *__restrict__ ma
     for (int h = t0; h < np; h += nt) {
         const Pair p = mg_pair(h, hx, g.ny, c);
         if (p.x < g.nx) {
+            // every load is issued before the link word is known (neighbour
+            // indices are always valid; closed faces are masked afterwards),
+            // so a node costs one memory round trip, not two
             const int i = p.x + g.nx * p.row;
+            int nb[6];
+            face_nbrs(g, p.x, p.y, p.z, i, nb);
+            float zn[6];
+#pragma unroll
+            for (int f = 0; f < 6; f++) {
+                zn[f] = __ldcg(z + nb[f]);
+                if (PRO) {
+                    int X, Y, Z;
+                    mg_face_coord(g.nx, g.ny, g.nz, p.x, p.y, p.z, f, X, Y, Z);
+                    zn[f] += __ldcg(C.e + mg_parent(C, X, Y, Z));
+                }
+            }
+            const float ri = __ldcg(r + i);
             const uint32_t m = __ldg(mask + i);
             const unsigned o = mg_open(m);
             if (!(m & SOLID_BIT) && o) {
-                int nb[6];
-                face_nbrs(g, p.x, p.y, p.z, i, nb);
-                const float ri = __ldcg(r + i);
                 float v = ri;
 #pragma unroll
                 for (int f = 0; f < 6; f++)
-                    if ((o >> f) & 1u) {
-                        v += __ldcg(z + nb[f]);
-                        if (PRO) {
-                            int X, Y, Z;
-                            mg_face_coord(g.nx, g.ny, g.nz, p.x, p.y, p.z, f, X, Y, Z);
-                            v += __ldcg(C.e + mg_parent(C, X, Y, Z));
-                        }
-                    }
+                    if ((o >> f) & 1u) v += zn[f];
                 v *= mg_inv_deg(__popc(o));
                 __stcg(z + i, v);
                 if (RZ) rz += ri * v;
@@ -180,8 +186,9 @@ static __device__ void fine_half(const Grid3 &g, const uint32_t *__restrict__ ma
         }
         if (RZ && p.xo < g.nx) {
             const int io = p.xo + g.nx * p.row;
+            const float ro = __ldcg(r + io), zo = __ldcg(z + io);
             const uint32_t m = __ldg(mask + io);
-            if (!(m & SOLID_BIT) && mg_open(m)) rz += __ldcg(r + io) * __ldcg(z + io);
+            if (!(m & SOLID_BIT) && mg_open(m)) rz += ro * zo;
         }
     }
 }
@@ -203,15 +210,19 @@ __device__ __forceinline__ float fine_resid(const Grid3 &g, const uint32_t *__re
 {
     if (x >= g.nx || y >= g.ny || zz >= g.nz) return 0.f;
     const int i = x + g.nx * (y + g.ny * zz);
+    int nb[6];
+    face_nbrs(g, x, y, zz, i, nb);
+    float zn[6];
+#pragma unroll
+    for (int f = 0; f < 6; f++) zn[f] = __ldcg(z + nb[f]);
+    const float ri = __ldcg(r + i), zi = __ldcg(z + i);
     const uint32_t m = __ldg(mask + i);
     const unsigned o = mg_open(m);
     if ((m & SOLID_BIT) || !o) return 0.f;
-    int nb[6];
-    face_nbrs(g, x, y, zz, i, nb);
-    float acc = __ldcg(r + i) - (float)__popc(o) * __ldcg(z + i);
+    float acc = ri - (float)__popc(o) * zi;
 #pragma unroll
     for (int f = 0; f < 6; f++)
-        if ((o >> f) & 1u) acc += __ldcg(z + nb[f]);
+        if ((o >> f) & 1u) acc += zn[f];
     return acc;
 }
 
@@ -531,19 +542,23 @@ __device__ double mg_true_residual(const Grid3 &g, const uint32_t *__restrict__ 
     float rr = 0.f;
     const int N = (int)g.N;
     for (int i = t0; i < N; i += nt) {
+        const int x = i % g.nx, t = i / g.nx, y = t % g.ny, zz = t / g.ny;
+        int nb[6];
+        face_nbrs(g, x, y, zz, i, nb);
+        PhiT pn[6];
+#pragma unroll
+        for (int f = 0; f < 6; f++) pn[f] = __ldcg(phi + nb[f]);
+        const PhiT bi = __ldcg(b + i), phii = __ldcg(phi + i);
         const uint32_t m = __ldg(mask + i);
         if (m & SOLID_BIT) continue;
         const unsigned o = mg_open(m);
         float rv = 0.f;
         if (o) {
-            const int x = i % g.nx, t = i / g.nx, y = t % g.ny, zz = t / g.ny;
-            int nb[6];
-            face_nbrs(g, x, y, zz, i, nb);
-            PhiT acc = __ldcg(b + i);
+            PhiT acc = bi;
 #pragma unroll
             for (int f = 0; f < 6; f++)
-                if ((o >> f) & 1u) acc += __ldcg(phi + nb[f]);
-            acc -= (PhiT)__popc(o) * __ldcg(phi + i);
+                if ((o >> f) & 1u) acc += pn[f];
+            acc -= (PhiT)__popc(o) * phii;
             if constexpr (((PhiT)0.5) != 0) rv = (float)acc;
             else rv = ll_to_float(acc) * (float)PHI_INV;
             if (!((x + y + zz) & 1)) __stcg(z + i, rv * mg_inv_deg(__popc(o)));
@@ -563,19 +578,23 @@ __device__ __forceinline__ void mg_pq_node(const Grid3 &g, const uint32_t *__res
                                            const float *pold, float beta, int x, int y, int zz, int i, float &pn,
                                            float &qv, bool &live)
 {
+    int nb[6];
+    face_nbrs(g, x, y, zz, i, nb);
+    float pj[6];
+#pragma unroll
+    for (int f = 0; f < 6; f++) pj[f] = FRESH ? __ldcg(z + nb[f]) : __ldcg(z + nb[f]) + beta * __ldcg(pold + nb[f]);
+    const float pi_ = FRESH ? __ldcg(z + i) : __ldcg(z + i) + beta * __ldcg(pold + i);
     const uint32_t mk = __ldg(mask + i);
     const unsigned o = mg_open(mk);
     live = !(mk & SOLID_BIT);
     pn = 0.f;
     qv = 0.f;
     if (!live || !o) return;
-    int nb[6];
-    face_nbrs(g, x, y, zz, i, nb);
-    pn = FRESH ? __ldcg(z + i) : __ldcg(z + i) + beta * __ldcg(pold + i);
+    pn = pi_;
     float acc = 0.f;
 #pragma unroll
     for (int f = 0; f < 6; f++)
-        if ((o >> f) & 1u) acc += FRESH ? __ldcg(z + nb[f]) : __ldcg(z + nb[f]) + beta * __ldcg(pold + nb[f]);
+        if ((o >> f) & 1u) acc += pj[f];
     qv = (float)__popc(o) * pn - acc;
 }
 
@@ -628,12 +647,15 @@ __device__ float mg_update_pass(const Grid3 &g, const uint32_t *__restrict__ mas
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             mk[k] = SOLID_BIT;
-            if (k < nk) mk[k] = __ldg(mask + i0 + k);
-            const bool live = !(mk[k] & SOLID_BIT) && mg_open(mk[k]);
-            pv[k] = live ? __ldcg(p + i0 + k) : 0.f;
-            qv[k] = live ? __ldcg(q + i0 + k) : 0.f;
-            rv[k] = live ? __ldcg(r + i0 + k) : 0.f;
-            ph[k] = live ? __ldcg(phi + i0 + k) : (PhiT)0;
+            pv[k] = qv[k] = rv[k] = 0.f;
+            ph[k] = (PhiT)0;
+            if (k < nk) {
+                mk[k] = __ldg(mask + i0 + k);
+                pv[k] = __ldcg(p + i0 + k);
+                qv[k] = __ldcg(q + i0 + k);
+                rv[k] = __ldcg(r + i0 + k);
+                ph[k] = __ldcg(phi + i0 + k);
+            }
         }
 #pragma unroll
         for (int k = 0; k < 2; k++) {
