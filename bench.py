@@ -285,6 +285,65 @@ def run_batch(args):
     b.close()
 
 
+def run_precision(args):
+    """Storage-precision sweep on the 256x256x512 pore (membrane 16 thick,
+    radius 8, N = 128): the same run in FP64 and in FP32 / BF16 / FP16
+    deviation storage (FP32 arithmetic), errors against the FP64 run per
+    observable, and each format's throughput."""
+    import numpy as np
+    import torch
+
+    import paper_1710_09421_gb300 as E
+    from paper_1710_09421_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    E.load()
+    base = W.config_precision_sweep()
+    if args.poisson == "mg":
+        base = base.replace(flags=base.flags | W.FLAG_POISSON_MG)
+    fluid = base.solid.ravel() == 0
+    every = max(1, args.steps // 20)
+    out = {}
+    ref = None
+    for prec in ("f64", "f32", "bf16", "fp16"):
+        sim = E.Simulation(base, precision=prec)
+        zs = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(0, args.steps, every):
+            sim.step(min(every, args.steps - k))
+            zs.append(float(sim.fields(("R",))["R"][:, 2].mean()))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        F = sim.fields(("n", "j", "phi"))
+        st = sim.stats()
+        sim.close()
+        u = F["j"] / np.where(F["n"] > 0, F["n"], 1.0)[:, None, :]
+        rec = {"steps_per_s": round(args.steps / dt, 3), "poisson_iters_last": st["poisson_iters"],
+               "status": st["status"]}
+        if ref is None:
+            ref = (F, u, np.array(zs))
+        else:
+            F0, u0, z0 = ref
+            scale = max(np.linalg.norm(u0[a][:, fluid]) for a in range(3))
+            rec["err_n_ions"] = float(max(np.linalg.norm(F["n"][a][fluid] - F0["n"][a][fluid]) /
+                                          np.linalg.norm(F0["n"][a][fluid]) for a in (1, 2)))
+            rec["err_u_flow"] = float(max(np.linalg.norm(u[a][:, fluid] - u0[a][:, fluid]) / scale
+                                          for a in range(3)))
+            rec["err_phi"] = float(np.linalg.norm(F["phi"][fluid] - F0["phi"][fluid]) /
+                                   np.linalg.norm(F0["phi"][fluid]))
+            dz = np.array(zs) - z0
+            rec["err_bead_z_max"] = float(np.abs(dz).max())
+            rec["bead_z_drift_f64"] = float(z0[-1] - z0[0])
+        out[prec] = rec
+        del F, u
+    line = {"metric": "storage-precision error vs the FP64 run", "unit": "relative / lattice units",
+            "steps": args.steps, "config": {"workload": base.name, "nodes": base.n_nodes, "beads": base.n_beads,
+                                            "poisson_tol": base.poisson_tol},
+            "data": "synthetic", "precisions": out}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     world, rank, local = dist_setup(args)
     if rank != 0:
@@ -514,6 +573,8 @@ def main():
         run_reference(args)
     elif args.workload == "replicas":
         run_batch(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 
