@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "ekl_kernels.cuh"
@@ -231,6 +232,24 @@ void dev_free(Ctx &c, void *p, size_t bytes)
 
 namespace {
 
+// fn(t) for t in [0, count) on the host's cores (interleaved, so that rows of
+// growing length spread evenly); runs inline when count is small
+template <typename Fn> static void host_parallel(int count, Fn fn)
+{
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int T = std::max(1, std::min({hw, 32, count / 16}));
+    if (T <= 1) {
+        for (int t = 0; t < count; t++) fn(t);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int w = 0; w < T; w++)
+        pool.emplace_back([&, w]() {
+            for (int t = w; t < count; t += T) fn(t);
+        });
+    for (auto &th : pool) th.join();
+}
+
 // Pseudo-inverse of the coarsest multigrid operator A (cells with conductances
 // sig: +x, +y, +z faces, 1/diag; inactive cells have none).  A is the graph
 // Laplacian of the active cells, symmetric positive semi-definite with the
@@ -290,23 +309,54 @@ static std::vector<float> coarse_pinv(int nx, int ny, int nz, const std::vector<
         for (int j = 0; j < n; j++)
             if (act[j] && part[j] == part[i]) at(i, j) += 1.0 / count[part[i]];
     }
-    // Cholesky B = L L^T (lower triangle in place)
-    for (int j = 0; j < n; j++) {
-        double d = at(j, j);
-        for (int k = 0; k < j; k++) d -= at(j, k) * at(j, k);
-        if (!(d > 0.0)) return {};
-        d = sqrt(d);
-        at(j, j) = d;
-        for (int i = j + 1; i < n; i++) {
-            double v = at(i, j);
-            const double *ri = &B[(size_t)i * n], *rj = &B[(size_t)j * n];
-            for (int k = 0; k < j; k++) v -= ri[k] * rj[k];
-            at(i, j) = v / d;
+    // Cholesky B = L L^T (lower triangle in place), blocked right-looking:
+    // per block column, factor the diagonal block, solve the panel below it,
+    // update the trailing matrix; panel and update rows go to host threads
+    const int NB = 64;
+    bool spd = true;
+    for (int kb = 0; kb < n && spd; kb += NB) {
+        const int e = std::min(kb + NB, n);
+        for (int j = kb; j < e && spd; j++) {
+            double d = at(j, j);
+            for (int k = kb; k < j; k++) d -= at(j, k) * at(j, k);
+            if (!(d > 0.0)) {
+                spd = false;
+                break;
+            }
+            d = sqrt(d);
+            at(j, j) = d;
+            for (int i = j + 1; i < e; i++) {
+                double v = at(i, j);
+                for (int k = kb; k < j; k++) v -= at(i, k) * at(j, k);
+                at(i, j) = v / d;
+            }
         }
+        if (!spd) break;
+        host_parallel(n - e, [&](int t) {
+            const int i = e + t;
+            double *ri = &B[(size_t)i * n];
+            for (int j = kb; j < e; j++) {
+                const double *rj = &B[(size_t)j * n];
+                double v = ri[j];
+                for (int k = kb; k < j; k++) v -= ri[k] * rj[k];
+                ri[j] = v / rj[j];
+            }
+        });
+        host_parallel(n - e, [&](int t) {
+            const int i = e + t;
+            double *ri = &B[(size_t)i * n];
+            for (int j = e; j <= i; j++) {
+                const double *rj = &B[(size_t)j * n];
+                double v = 0.0;
+                for (int k = kb; k < e; k++) v += ri[k] * rj[k];
+                ri[j] -= v;
+            }
+        });
     }
+    if (!spd) return {};
     // Wt = (L^-1)^T (upper, row j = column j of L^-1), then B^-1 = Wt Wt^T
     std::vector<double> Wt((size_t)n * n, 0.0);
-    for (int j = 0; j < n; j++) {
+    host_parallel(n, [&](int j) {
         double *w = &Wt[(size_t)j * n];
         w[j] = 1.0 / at(j, j);
         for (int i = j + 1; i < n; i++) {
@@ -315,10 +365,10 @@ static std::vector<float> coarse_pinv(int nx, int ny, int nz, const std::vector<
             for (int k = j; k < i; k++) v -= ri[k] * w[k];
             w[i] = v / ri[i];
         }
-    }
+    });
     std::vector<float> M((size_t)n * n, 0.f);
-    for (int i = 0; i < n; i++) {
-        if (!act[i]) continue;
+    host_parallel(n, [&](int i) {
+        if (!act[i]) return;
         const double *wi = &Wt[(size_t)i * n];
         for (int j = 0; j <= i; j++) {
             if (!act[j]) continue;
@@ -328,7 +378,7 @@ static std::vector<float> coarse_pinv(int nx, int ny, int nz, const std::vector<
             if (part[i] == part[j]) v -= 1.0 / count[part[i]];
             M[(size_t)i * n + j] = M[(size_t)j * n + i] = (float)v;
         }
-    }
+    });
     return M;
 }
 
