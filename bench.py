@@ -37,8 +37,8 @@ FALLBACK_HBM_GBS = 6800.0
 # each valid only while the source files it was taken on are unchanged
 PROFILED = {
     # kernel: (sha256 prefix of its source files, dram read + write bytes per launch)
-    "lb_fused_kernel": ("0dbea948a5c7d63c", 119344896 + 67133184),
-    "poisson_mg_kernel": ("5bfbe8cea0638c11", 16019968 + 563712),
+    "lb_fused_kernel": ("049e687f3a099360", 119373824 + 66732288),
+    "poisson_mg_kernel": ("c8ea034c12e05bea", 20793856 + 771072),
 }
 KERNEL_SOURCES = {
     "lb_fused_kernel": ("ekl_kernels.cuh", "ekl_dev.cuh"),
