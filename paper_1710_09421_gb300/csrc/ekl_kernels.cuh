@@ -1012,9 +1012,17 @@ __device__ __forceinline__ void wca_add(R eps, R sig, const R d[3], R F[3])
     // 2^(1/3) sigma^2 is the squared WCA cut-off
     R rc2 = (R)1.2599210498948732 * sig * sig;
     if (r2 >= rc2) return;
-    R sr2 = sig * sig / r2;
-    R sr6 = sr2 * sr2 * sr2;
-    R mag = R(24) * eps * (R(2) * sr6 * sr6 - sr6) / r2;
+    R mag;
+    if constexpr (sizeof(R) == 8) {  // FP64: divisions as the oracle writes them
+        R sr2 = sig * sig / r2;
+        R sr6 = sr2 * sr2 * sr2;
+        mag = R(24) * eps * (R(2) * sr6 * sr6 - sr6) / r2;
+    } else {
+        const R inv = R(1) / r2;
+        R sr2 = sig * sig * inv;
+        R sr6 = sr2 * sr2 * sr2;
+        mag = R(24) * eps * (R(2) * sr6 * sr6 - sr6) * inv;
+    }
     for (int c = 0; c < 3; c++) F[c] += mag * d[c];
 }
 
@@ -1074,6 +1082,14 @@ __device__ __forceinline__ bool wall_solid(const Grid3 &g, const int per[3], con
                                            int x, int y, int z, const int *org, const uint32_t *bits,
                                            bool &in)
 {
+    // inside the cached block the bit already encodes the wrap and the box
+    // faces (a node beyond a closed face was cached as fluid)
+    const int ox = x - org[0], oy = y - org[1], oz = z - org[2];
+    if (ox >= 0 && ox < WALL_BOX && oy >= 0 && oy < WALL_BOX && oz >= 0 && oz < WALL_BOX) {
+        in = true;
+        const int bit = (oz * WALL_BOX + oy) * WALL_BOX + ox;
+        return (bits[bit >> 5] >> (bit & 31)) & 1u;
+    }
     int q[3] = {x, y, z};
     const int dims[3] = {g.nx, g.ny, g.nz};
     in = true;
@@ -1086,11 +1102,6 @@ __device__ __forceinline__ bool wall_solid(const Grid3 &g, const int per[3], con
         }
     }
     if (!in) return false;
-    int ox = x - org[0], oy = y - org[1], oz = z - org[2];
-    if (ox >= 0 && ox < WALL_BOX && oy >= 0 && oy < WALL_BOX && oz >= 0 && oz < WALL_BOX) {
-        int bit = (oz * WALL_BOX + oy) * WALL_BOX + ox;
-        return (bits[bit >> 5] >> (bit & 31)) & 1u;
-    }
     long long id = (long long)q[0] + (long long)g.nx * (q[1] + (long long)g.ny * q[2]);
     return mask[id] & SOLID_BIT;
 }
