@@ -30,7 +30,7 @@ constexpr int ST_TIMEOUT = 16;
 // lattice itself).  Cell (X, Y, Z) of level l+1 aggregates the cells
 // (2X + {0,1}, 2Y + {0,1}, 2Z + {0,1}) of level l.
 constexpr int MG_MAXLEV = 12;
-constexpr int MG_NU = 3;                 // red-black smoothing sweeps on the lattice before and after the coarse correction
+constexpr int MG_NU = 2;                 // red-black smoothing sweeps on the lattice before and after the coarse correction
 constexpr int MG_NU_COARSE = 2;          // the same on the coarse levels
 constexpr int MG_COARSE_SWEEPS = 8;      // (R B)^k R half sweeps on the coarsest level
 constexpr float MG_INNER_RED = 1e-4f;    // CG residual reduction before the true residual is formed
