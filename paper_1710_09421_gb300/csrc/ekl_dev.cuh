@@ -51,9 +51,14 @@ template <> struct Store<__nv_bfloat16> {
     __device__ static float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     __device__ static void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
+// FP16 deviations are stored times 2^12: the ion deviations (about 1e-6 to
+// 1e-4 at salt 0.01) would otherwise sit below FP16's normal range (6.1e-5)
+// and lose bits as subnormals; scaled, deviations from 1.5e-8 to 16 are
+// normal numbers.  The power of two makes the scaling exact.
+constexpr float FP16_DEV_SCALE = 4096.0f;
 template <> struct Store<__half> {
-    __device__ static float ld(const __half *p) { return __half2float(__ldg(p)); }
-    __device__ static void st(__half *p, float v) { *p = __float2half_rn(v); }
+    __device__ static float ld(const __half *p) { return __half2float(__ldg(p)) * (1.0f / FP16_DEV_SCALE); }
+    __device__ static void st(__half *p, float v) { *p = __float2half_rn(v * FP16_DEV_SCALE); }
 };
 
 // ---------------------------------------------------------------- indexing
