@@ -63,6 +63,7 @@ class Params(C.Structure):
         ("seed", C.c_uint64),
         ("bead_kT", C.c_double),
         ("flags", C.c_int32),
+        ("fluct_mass", C.c_double),
     ]
 
 
@@ -95,6 +96,7 @@ def lib():
             L.eko_poisson_residual.argtypes = [vp, vp, vp]
             L.eko_poisson_residual.restype = C.c_double
             L.eko_last_rho.argtypes = [vp, vp]
+            L.eko_basis.argtypes = [vp]
             L.eko_bead_stencil.argtypes = [vp, vp, vp, vp]
             L.eko_bead_stencil.restype = C.c_int
             L.eko_philox4x32_10.argtypes = [vp, vp, vp]
@@ -116,6 +118,13 @@ def lattice():
     opp = np.zeros(Q, np.int32)
     lib().eko_lattice(_ptr(c), _ptr(w), _ptr(opp))
     return c, w, opp
+
+
+def basis():
+    """Moment basis of the fluctuating term, chi[k][p] (Eq. 14)."""
+    out = np.zeros((19, 19))
+    lib().eko_basis(_ptr(out))
+    return out
 
 
 def philox4x32_10(ctr, key):
@@ -154,6 +163,7 @@ def _params(wl) -> Params:
     P.seed = wl.seed
     P.bead_kT = wl.bead_kT
     P.flags = wl.flags
+    P.fluct_mass = wl.fluct_mass
     return P
 
 

@@ -73,7 +73,57 @@ static const int CV[EKO_Q][3] = {
     {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
 static double WV[EKO_Q];
 static int OPPV[EKO_Q];
+/* Moment basis of the fluctuating term (Eq. 14): CHI[k][p], orthonormal in
+ * sum_p w_p CHI[k][p] CHI[l][p]; k = 0 density, 1-3 current, 4-9 momentum
+ * flux, 10-18 the remaining moments.  Built by Gram-Schmidt, in that
+ * scalar product, of the monomials 1, cx, cy, cz, cx^2, cy^2, cz^2, cx cy,
+ * cx cz, cy cz, cx^2 cy, cx cy^2, cx^2 cz, cx cz^2, cy^2 cz, cy cz^2,
+ * cx^2 cy^2, cx^2 cz^2, cy^2 cz^2 in this order. */
+static double CHI[EKO_Q][EKO_Q];
 static int lattice_ready = 0;
+
+static double monomial(int k, const int c[3])
+{
+    const double x = c[0], y = c[1], z = c[2];
+    switch (k) {
+    case 0: return 1.0;
+    case 1: return x;
+    case 2: return y;
+    case 3: return z;
+    case 4: return x * x;
+    case 5: return y * y;
+    case 6: return z * z;
+    case 7: return x * y;
+    case 8: return x * z;
+    case 9: return y * z;
+    case 10: return x * x * y;
+    case 11: return x * y * y;
+    case 12: return x * x * z;
+    case 13: return x * z * z;
+    case 14: return y * y * z;
+    case 15: return y * z * z;
+    case 16: return x * x * y * y;
+    case 17: return x * x * z * z;
+    default: return y * y * z * z;
+    }
+}
+
+static void basis_init(void)
+{
+    for (int k = 0; k < EKO_Q; k++) {
+        double v[EKO_Q];
+        for (int p = 0; p < EKO_Q; p++) v[p] = monomial(k, CV[p]);
+        for (int l = 0; l < k; l++) {
+            double d = 0.0;
+            for (int p = 0; p < EKO_Q; p++) d += WV[p] * v[p] * CHI[l][p];
+            for (int p = 0; p < EKO_Q; p++) v[p] -= d * CHI[l][p];
+        }
+        double nrm = 0.0;
+        for (int p = 0; p < EKO_Q; p++) nrm += WV[p] * v[p] * v[p];
+        nrm = sqrt(nrm);
+        for (int p = 0; p < EKO_Q; p++) CHI[k][p] = v[p] / nrm;
+    }
+}
 
 static void lattice_init(void)
 {
@@ -85,6 +135,7 @@ static void lattice_init(void)
             if (CV[q][0] == -CV[p][0] && CV[q][1] == -CV[p][1] && CV[q][2] == -CV[p][2])
                 OPPV[p] = q;
     }
+    basis_init();
     lattice_ready = 1;
 }
 
@@ -112,6 +163,7 @@ typedef struct {
     uint64_t seed;
     double bead_kT;
     int32_t flags;
+    double fluct_mass;   /* thermal mass m of the fluctuating term (Eq. 14); 0 = none */
 } eko_params;
 
 typedef struct {
@@ -880,6 +932,26 @@ static int collide(eko_sim *s)
                 size_t k = ((size_t)a * EKO_Q + p) * N + i;
                 s->fstar[k] = s->f[k] - om * (s->f[k] - feq) + (1.0 - 0.5 * om) * S;
             }
+            if (P->fluct_mass > 0.0) {
+                /* Eq. 14: Delta_p = sqrt(m n omega (2 - omega)) sum_{k=4}^{18}
+                 * w_p CHI_kp N_k, N_k zero mean and unit variance, drawn
+                 * from Philox with counter (node, 2^25 | species << 4 | call,
+                 * step) and the run's seed as key */
+                double Nk[16];
+                for (int call = 0; call < 4; call++) {
+                    uint32_t ctr[4] = {(uint32_t)i, (2u << 24) | ((uint32_t)a << 4) | (uint32_t)call,
+                                       (uint32_t)s->step, (uint32_t)((uint64_t)s->step >> 32)};
+                    uint32_t key[2] = {(uint32_t)P->seed, (uint32_t)(P->seed >> 32)}, out[4];
+                    eko_philox4x32_10(ctr, key, out);
+                    for (int j = 0; j < 4; j++) Nk[4 * call + j] = unit_variate(out[j]);
+                }
+                double amp = sqrt(P->fluct_mass * n[a] * om * (2.0 - om));
+                for (int p = 0; p < EKO_Q; p++) {
+                    double d = 0.0;
+                    for (int k = 4; k < EKO_Q; k++) d += CHI[k][p] * Nk[k - 4];
+                    s->fstar[((size_t)a * EKO_Q + p) * N + i] += amp * WV[p] * d;
+                }
+            }
         }
     }
     if (cfl) s->status |= EKO_WARN_CFL;
@@ -1012,6 +1084,12 @@ void eko_link_mask(const eko_sim *s, uint32_t *mask)
 }
 
 void eko_wall_source(const eko_sim *s, double *out) { memcpy(out, s->src_wall, sizeof(double) * s->N); }
+
+void eko_basis(double *chi)
+{
+    lattice_init();
+    memcpy(chi, CHI, sizeof(CHI));
+}
 
 void eko_lattice(int32_t *c, double *w, int32_t *opp)
 {

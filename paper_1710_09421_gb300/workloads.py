@@ -78,6 +78,7 @@ class Workload:
     seed: int = 2
     bead_kT: float = 1e-3                   # bead thermostat temperature (lattice units)
     flags: int = 0
+    fluct_mass: float = 0.0                 # thermal mass of the fluctuating LB term (0 = none)
     R: Optional[np.ndarray] = None          # float64 [nb,3]
     V: Optional[np.ndarray] = None          # float64 [nb,3]
     charge: Optional[np.ndarray] = None     # float64 [nb]
