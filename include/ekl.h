@@ -116,6 +116,10 @@ typedef struct ekl_params {
     double bead_kT;               /* bead thermostat temperature (Eq. 8) */
     int32_t flags;                /* EKL_EQ_BARYCENTRIC | EKL_GAMMA_LITERAL | EKL_NO_BEAD_NOISE */
     int32_t precision;            /* EKL_F64 / EKL_F32 / EKL_BF16DEV / EKL_FP16DEV */
+    double fluct_mass;            /* thermal mass m of the fluctuating term of Eq. 14 (Landau-Lifshitz
+                                     noise on the momentum flux and higher moments,
+                                     Delta_p = sqrt(m n omega (2 - omega)) sum_{k>=4} w_p chi_kp N_k,
+                                     N_k from Philox keyed by `seed`); 0 = no fluctuations */
 } ekl_params;
 
 typedef struct ekl_stats {

@@ -68,6 +68,7 @@ class ekl_params(C.Structure):
         ("bead_kT", C.c_double),
         ("flags", C.c_int32),
         ("precision", C.c_int32),
+        ("fluct_mass", C.c_double),
     ]
 
 
@@ -243,6 +244,7 @@ def make_params(wl, precision=None):
     P.bead_kT = wl.bead_kT
     P.flags = wl.flags
     P.precision = PRECISION[precision or wl.precision]
+    P.fluct_mass = wl.fluct_mass
     return P, keep
 
 

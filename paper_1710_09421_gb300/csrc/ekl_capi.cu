@@ -120,6 +120,7 @@ void release(Ctx &c)
     dev_free(c, c.pois_total, 0);
     dev_free(c, c.pois_res, 0);
     dev_free(c, c.omegas, 0);
+    dev_free(c, c.wchi, 0);
     dev_free(c, c.R, 0);
     dev_free(c, c.V, 0);
     dev_free(c, c.q, 0);
@@ -231,6 +232,38 @@ void dev_free(Ctx &c, void *p, size_t bytes)
 }  // namespace ekl
 
 namespace {
+
+// Moment basis of the fluctuating term (Eq. 14), returned as w_p chi_kp:
+// the monomials 1, cx, cy, cz, cx^2, cy^2, cz^2, cx cy, cx cz, cy cz,
+// cx^2 cy, cx cy^2, cx^2 cz, cx cz^2, cy^2 cz, cy cz^2, cx^2 cy^2, cx^2 cz^2,
+// cy^2 cz^2 on the 19 velocities, made orthonormal in order (classical
+// Gram-Schmidt) in the scalar product sum_p w_p a_p b_p; rows 0-3 then span
+// density and current, 4-9 the momentum flux, 10-18 the rest.
+static void fluct_basis(double wchi[Q][Q])
+{
+    double chi[Q][Q];
+    for (int k = 0; k < Q; k++) {
+        double v[Q];
+        for (int p = 0; p < Q; p++) {
+            const double x = cx_(p), y = cy_(p), z = cz_(p);
+            const double mono[Q] = {1.0,       x,         y,         z,         x * x,     y * y,     z * z,
+                                    x * y,     x * z,     y * z,     x * x * y, x * y * y, x * x * z, x * z * z,
+                                    y * y * z, y * z * z, x * x * y * y, x * x * z * z, y * y * z * z};
+            v[p] = mono[k];
+        }
+        for (int l = 0; l < k; l++) {
+            double dot = 0.0;
+            for (int p = 0; p < Q; p++) dot += w_(p) * v[p] * chi[l][p];
+            for (int p = 0; p < Q; p++) v[p] -= dot * chi[l][p];
+        }
+        double norm2 = 0.0;
+        for (int p = 0; p < Q; p++) norm2 += w_(p) * v[p] * v[p];
+        const double inv = 1.0 / sqrt(norm2);
+        for (int p = 0; p < Q; p++) chi[k][p] = v[p] * inv;
+    }
+    for (int k = 0; k < Q; k++)
+        for (int p = 0; p < Q; p++) wchi[k][p] = w_(p) * chi[k][p];
+}
 
 // fn(t) for t in [0, count) on the host's cores (interleaved, so that rows of
 // growing length spread evenly); runs inline when count is small
@@ -574,6 +607,7 @@ static int create_handle(const ekl_params *P, void *stream, ekl_handle **out, bo
     for (int s = 0; s < NS; s++)
         if (!(P->tau[s] > 0.5)) return fail(EKL_ERR_ARG, "tau must exceed 1/2");
     if (!(P->diffusivity[1] > 0.0)) return fail(EKL_ERR_ARG, "cation diffusivity must be positive");
+    if (!(P->fluct_mass >= 0.0) || !isfinite(P->fluct_mass)) return fail(EKL_ERR_ARG, "fluct_mass must be finite and >= 0");
     long long N = (long long)P->nx * P->ny * P->nz;
     if (N > (1ll << 31) / 64) return fail(EKL_ERR_ARG, "lattice too large for 32-bit node ids");
 
@@ -737,6 +771,7 @@ static int create_handle(const ekl_params *P, void *stream, ekl_handle **out, bo
         om[k] = k == 0 ? 1.0 : (k == 1 ? 1.0 / (1.0 - 0.5 * rJ * rJ) : 1.0 / (1.0 - 0.25 * rJ * rJ * om[k - 1]));
     std::vector<float> omf(om.begin(), om.end());
     c.omegas = A(om.size() * (c.prec == EKL_F64 ? sizeof(double) : sizeof(float)));
+    if (P->fluct_mass > 0.0) c.wchi = A((size_t)Q * Q * rs);
     c.patch_count = (int *)A(sizeof(int));
     c.patch_bits = (uint32_t *)A(((size_t)N / 32 + 1) * sizeof(uint32_t));
     c.patch_node = (int *)A(MAX_ENTRIES * sizeof(int));
@@ -810,6 +845,18 @@ static int create_handle(const ekl_params *P, void *stream, ekl_handle **out, bo
         cudaMemsetAsync(c.pois_res, 0, sizeof(double), c.stream);
         if (c.prec == EKL_F64) cudaMemcpyAsync(c.omegas, om.data(), om.size() * 8, cudaMemcpyHostToDevice, c.stream);
         else cudaMemcpyAsync(c.omegas, omf.data(), omf.size() * 4, cudaMemcpyHostToDevice, c.stream);
+        if (c.wchi) {
+            double wchi[Q][Q];
+            fluct_basis(wchi);
+            if (c.prec == EKL_F64) {
+                e = cudaMemcpy(c.wchi, wchi, sizeof(wchi), cudaMemcpyHostToDevice);
+            } else {
+                float wf[Q * Q];
+                for (int k = 0; k < Q * Q; k++) wf[k] = (float)(&wchi[0][0])[k];
+                e = cudaMemcpy(c.wchi, wf, sizeof(wf), cudaMemcpyHostToDevice);
+            }
+            if (e != cudaSuccess) { rc = fail_cuda(e, "upload basis"); break; }
+        }
 
         e = cudaStreamSynchronize(c.stream);
         if (e != cudaSuccess) { rc = fail_cuda(e, "create"); break; }

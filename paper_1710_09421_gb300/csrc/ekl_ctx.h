@@ -82,6 +82,7 @@ struct Ctx {
     long long *pois_total;  // sweeps summed over all steps
     double *pois_res;     // last step's relative residual
     void *omegas;         // Chebyshev relaxation factor per half sweep
+    void *wchi;           // Real[19][19] w_p chi_kp of the fluctuating term, or null
     int charge_blocks;
     int lb_blocks;
     int pois_blocks;
@@ -150,6 +151,7 @@ struct Batch {
     int pois_threads, pois_blocks;  // schedule of the batched Poisson launch
     int weight_fluid;        // split Poisson blocks by fluid nodes (1) or all nodes (0)
     int max_lb_blocks, max_charge_blocks, max_nb;
+    int fluct;               // some replica has the fluctuating term on
     long long launches;
     // multigrid replicas: one cooperative launch, each replica on its own
     // blocks with its own barrier words

@@ -64,6 +64,11 @@ template <typename S, typename R, typename PhiT> struct StepArgs {
     double rJ;
     double n_fluid;  // number of fluid nodes (mean charge divisor)
     int nblocks_charge;
+    // fluctuating term (Eq. 14)
+    const R *wchi;   // w_p chi_kp, [19][19] row k (k = 4..18 used)
+    R fluct_m;       // thermal mass m (0: off)
+    uint32_t key0, key1;
+    long long step;
 };
 
 // pull of the 19 populations of species s at node i (bounce-back on set bits)
@@ -1540,8 +1545,17 @@ __global__ void __launch_bounds__(MdThreads<R>::value)
 //   a^a = j^a/n^a + G^a/2, h^a = omega_d^a/2,
 //   u* = sum n a/(1+h) / sum n/(1+h), u^a* = (a^a + h^a u*)/(1+h^a),
 //   Phi^a = G^a - omega_d^a (u^a* - u*).
-template <typename S, typename R, typename PhiT, bool DEV>
-__device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long blk)
+// Zero-mean, unit-variance variate of the fluid noise in FP32 arithmetic:
+// sqrt(3) (2U - 1) with U = (x + 1/2) / 2^32, i.e. (x - 2^31 + 1/2) 2^-31
+// (the 32-bit conversion rounds to FP32; no 64-bit conversion).
+__device__ __forceinline__ float unit_variate_f32(uint32_t x)
+{
+    const float t = __int2float_rn((int)(x ^ 0x80000000u)) * 4.656612873077393e-10f + 2.3283064365386963e-10f;
+    return 1.7320508f * t;
+}
+
+template <typename S, typename R, typename PhiT, bool DEV, bool FLUCT>
+__device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long blk, long long step)
 {
     const Grid3 g = a.g;
     const long long i = blk * (long long)blockDim.x + threadIdx.x;
@@ -1629,6 +1643,34 @@ __device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long
                 const R Fu = Ph[0] * ue[0] + Ph[1] * ue[1] + Ph[2] * ue[2];
                 const R cS = R(1) - R(0.5) * om;
                 S *out = a.fout + (long long)(s * Q) * g.N + i;
+                // fluctuating term (Eq. 14): 15 zero-mean unit-variance N_k
+                // from Philox (counter: node, 2^25 | species << 4 | call, step)
+                R Nk[FLUCT ? 16 : 1];
+                R amp = R(0);
+                if constexpr (FLUCT) {
+#pragma unroll
+                    for (int call = 0; call < 4; call++) {
+                        uint32_t ctr[4] = {(uint32_t)i, (2u << 24) | ((uint32_t)s << 4) | (uint32_t)call,
+                                           (uint32_t)step, (uint32_t)((uint64_t)step >> 32)};
+                        philox4x32_10(ctr, a.key0, a.key1);
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            if constexpr (sizeof(R) == 8) Nk[4 * call + j] = unit_variate<R>(ctr[j]);
+                            else Nk[4 * call + j] = unit_variate_f32(ctr[j]);
+                        }
+                    }
+                    amp = sqrt(a.fluct_m * n[s] * om * (R(2) - om));
+                }
+                // v plus the noise of population p (v itself without the term)
+                auto noisy = [&](R v, int p) -> R {
+                    if constexpr (!FLUCT) return v;
+                    else {
+                        R d = R(0);
+#pragma unroll
+                        for (int k = 4; k < Q; k++) d += __ldg(a.wchi + k * Q + p) * Nk[k - 4];
+                        return v + amp * d;
+                    }
+                };
                 if constexpr (!DEV) {
 #pragma unroll
                     for (int p = 0; p < Q; p++) {
@@ -1639,7 +1681,7 @@ __device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long
                         R feq = w * n[s] * (R(1) + cu / VT2 + (cu * cu - VT2 * u2) / (R(2) * VT2 * VT2));
                         R Sp = w * n[s] * (cF / VT2 + (cu * cF - VT2 * Fu) / (VT2 * VT2));
                         R fs = f[s][p] - om * (f[s][p] - feq) + cS * Sp;
-                        Store<S>::st(out + (long long)p * g.N, fs);
+                        Store<S>::st(out + (long long)p * g.N, noisy(fs, p));
                     }
                 } else {
                     // deviation form, s_eq = f_eq - w n_ref:
@@ -1648,7 +1690,7 @@ __device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long
                     // a velocity and its opposite share the parts even in c
                     const R keep = R(1) - om;
                     const R w0 = (R)w_(0);
-                    Store<S>::st(out, keep * f[s][0] + w0 * (om * (dn[s] - R(1.5) * n[s] * u2) - cS * R(3) * n[s] * Fu));
+                    Store<S>::st(out, noisy(keep * f[s][0] + w0 * (om * (dn[s] - R(1.5) * n[s] * u2) - cS * R(3) * n[s] * Fu), 0));
 #pragma unroll
                     for (int p = 1; p < Q; p += 2) {
                         const int q = p + 1;  // opposite of p
@@ -1659,8 +1701,8 @@ __device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long
                         const R even = om * (R(4.5) * cu * cu - R(1.5) * u2) + cS * (R(9) * cu * cF - R(3) * Fu);
                         const R odd = R(3) * (om * cu + cS * cF);
                         const R base = om * w * dn[s];
-                        Store<S>::st(out + (long long)p * g.N, keep * f[s][p] + (base + wn * (even + odd)));
-                        Store<S>::st(out + (long long)q * g.N, keep * f[s][q] + (base + wn * (even - odd)));
+                        Store<S>::st(out + (long long)p * g.N, noisy(keep * f[s][p] + (base + wn * (even + odd)), p));
+                        Store<S>::st(out + (long long)q * g.N, noisy(keep * f[s][q] + (base + wn * (even - odd)), q));
                     }
                 }
             }
@@ -1670,19 +1712,19 @@ __device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long
     if (__any_sync(0xffffffffu, cfl) && (threadIdx.x & 31) == 0) atomicOr(a.status, ST_CFL);
 }
 
-template <typename S, typename R, typename PhiT, bool DEV>
+template <typename S, typename R, typename PhiT, bool DEV, bool FLUCT>
 __global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 4 : 1) lb_fused_kernel(StepArgs<S, R, PhiT> a)
 {
-    lb_body<S, R, PhiT, DEV>(a, blockIdx.x);
+    lb_body<S, R, PhiT, DEV, FLUCT>(a, blockIdx.x, a.step);
 }
 
-template <typename S, typename R, typename PhiT, bool DEV>
+template <typename S, typename R, typename PhiT, bool DEV, bool FLUCT>
 __global__ void __launch_bounds__(LB_THREADS, sizeof(R) == 4 ? 4 : 1)
-    lb_fused_batch_kernel(const StepArgs<S, R, PhiT> *reps)
+    lb_fused_batch_kernel(const StepArgs<S, R, PhiT> *reps, long long step)
 {
     const StepArgs<S, R, PhiT> &a = reps[blockIdx.y];
     if ((long long)blockIdx.x * blockDim.x >= a.g.N) return;
-    lb_body<S, R, PhiT, DEV>(a, blockIdx.x);
+    lb_body<S, R, PhiT, DEV, FLUCT>(a, blockIdx.x, step);
 }
 
 // ============================================================== outputs

@@ -56,6 +56,11 @@ static StepArgs<S, R, PhiT> make_args(Ctx &c, int parity = -1)
     a.rJ = c.rJ;
     a.omegas = c.omegas;
     a.n_fluid = (double)c.n_fluid;
+    a.wchi = (const R *)c.wchi;
+    a.fluct_m = (R)c.P.fluct_mass;
+    a.key0 = (uint32_t)c.P.seed;
+    a.key1 = (uint32_t)(c.P.seed >> 32);
+    a.step = c.step;
     a.nblocks_charge = c.charge_blocks * (CHARGE_THREADS / 32);  // one partial per warp
     return a;
 }
@@ -239,7 +244,10 @@ template <typename S, typename R, typename PhiT, bool DEV> int steps_impl(Ctx &c
         phase_end(c, PH_MD);
         // 5. fused pull-collide-stream
         phase_begin(c, PH_LB);
-        lb_fused_kernel<S, R, PhiT, DEV><<<c.lb_blocks, LB_THREADS, 0, c.stream>>>(a);
+        if (c.P.fluct_mass > 0.0)
+            lb_fused_kernel<S, R, PhiT, DEV, true><<<c.lb_blocks, LB_THREADS, 0, c.stream>>>(a);
+        else
+            lb_fused_kernel<S, R, PhiT, DEV, false><<<c.lb_blocks, LB_THREADS, 0, c.stream>>>(a);
         c.launches++;
         phase_end(c, PH_LB);
         cudaError_t e = cudaGetLastError();
@@ -344,6 +352,9 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_tables(Batc
     if (cudaStreamSynchronize(B.stream) != cudaSuccess) return EKL_ERR_CUDA;
     if (B.mg && mg_batch_tables(B) != EKL_OK) return EKL_ERR_CUDA;
     B.max_nb = 0;
+    B.fluct = 0;
+    for (int r = 0; r < n; r++)
+        if (B.reps[r]->P.fluct_mass > 0.0) B.fluct = 1;
     B.max_lb_blocks = B.max_charge_blocks = 0;
     for (int r = 0; r < n; r++) {
         B.max_nb = std::max(B.max_nb, B.reps[r]->nb);
@@ -419,8 +430,12 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_impl(Batch 
                 (const MdArgs<S, R, PhiT, DEV> *)B.d_mdargs[q], step);
             B.launches++;
         }
-        lb_fused_batch_kernel<S, R, PhiT, DEV><<<dim3(B.max_lb_blocks, n), LB_THREADS, 0, B.stream>>>(
-            (const StepArgs<S, R, PhiT> *)B.d_args[q]);
+        if (B.fluct)
+            lb_fused_batch_kernel<S, R, PhiT, DEV, true><<<dim3(B.max_lb_blocks, n), LB_THREADS, 0, B.stream>>>(
+                (const StepArgs<S, R, PhiT> *)B.d_args[q], step);
+        else
+            lb_fused_batch_kernel<S, R, PhiT, DEV, false><<<dim3(B.max_lb_blocks, n), LB_THREADS, 0, B.stream>>>(
+                (const StepArgs<S, R, PhiT> *)B.d_args[q], step);
         B.launches++;
         if (cudaGetLastError() != cudaSuccess) return EKL_ERR_CUDA;
         for (int r = 0; r < n; r++) {
