@@ -173,6 +173,19 @@ int ekl_step_async(ekl_handle *h, int32_t nsteps);
 int ekl_get_fields(ekl_handle *h, double *n_out, double *j_out, double *phi_out,
                    double *R_out, double *V_out);
 
+/* Replace the applied field E_app (k_B T / (e dx)) from the next step on,
+ * e.g. to relax a chain at zero field before driving it (Sec. IV.A).
+ * Errors: EKL_ERR_ARG (null or non-finite). */
+int ekl_set_field(ekl_handle *h, const double E[3]);
+
+/* Flux of each species through the lattice plane {coordinate `axis` ==
+ * `plane`} (axis 0/1/2 = x/y/z): out[s] = sum over the plane's fluid nodes of
+ * the current component sum_p c_p,axis f^s_p of the streamed populations
+ * (Eq. 16, the populations the next step starts from); out[3] = sum_s z^s
+ * out[s], the ionic current in e per time step (the conductance observable
+ * of Sec. IV.B: G = out[3] / potential difference).  Errors: EKL_ERR_ARG. */
+int ekl_get_current(ekl_handle *h, int32_t axis, int32_t plane, double out[4]);
+
 /* Checkpoint: post-collision populations as FP64 f values [3][19][N] and the
  * raw potential [N] (no gauge shift), plus the step counter. */
 int ekl_get_state(ekl_handle *h, double *fstar, double *phi, int64_t *step);

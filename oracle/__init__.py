@@ -97,6 +97,7 @@ def lib():
             L.eko_poisson_residual.restype = C.c_double
             L.eko_last_rho.argtypes = [vp, vp]
             L.eko_basis.argtypes = [vp]
+            L.eko_set_field.argtypes = [vp, vp]
             L.eko_bead_stencil.argtypes = [vp, vp, vp, vp]
             L.eko_bead_stencil.restype = C.c_int
             L.eko_philox4x32_10.argtypes = [vp, vp, vp]
@@ -256,6 +257,10 @@ class Sim:
         it = lib().eko_poisson_solve(self.h, _ptr(rho), _ptr(phi), tol, max_iter, check_every,
                                      fixed_iter, C.byref(res))
         return phi, it, res.value
+
+    def set_field(self, E):
+        E = np.ascontiguousarray(E, np.float64)
+        lib().eko_set_field(self.h, _ptr(E))
 
     def poisson_residual(self, rho, phi):
         """||b - A phi|| / ||b|| of phi for the charge density rho."""

@@ -1039,6 +1039,12 @@ void eko_get_state(const eko_sim *s, double *fstar, double *phi, int64_t *step)
     if (step) *step = s->step;
 }
 
+/* replace the applied field from the next step on */
+void eko_set_field(eko_sim *s, const double E[3])
+{
+    for (int a = 0; a < 3; a++) s->P.E_app[a] = E[a];
+}
+
 void eko_set_state(eko_sim *s, const double *fstar, const double *phi, int64_t step)
 {
     if (fstar) memcpy(s->fstar, fstar, sizeof(double) * EKO_NS * EKO_Q * s->N);

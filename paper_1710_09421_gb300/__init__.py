@@ -116,6 +116,8 @@ def load(build_if_missing: bool = True):
         L.ekl_set_state.argtypes = [vp, vp, vp, C.c_int64]
         L.ekl_get_stats.argtypes = [vp, C.POINTER(ekl_stats)]
         L.ekl_set_timing.argtypes = [vp, C.c_int32]
+        L.ekl_set_field.argtypes = [vp, vp]
+        L.ekl_get_current.argtypes = [vp, C.c_int32, C.c_int32, vp]
         L.ekl_get_link_mask.argtypes = [vp, vp]
         L.ekl_lattice.argtypes = [vp, vp, vp]
         L.ekl_lattice.restype = None
@@ -306,6 +308,18 @@ def ekl_get_stats(h):
                 poisson_sweeps=s.poisson_sweeps)
 
 
+def ekl_set_field(h, E):
+    E = np.ascontiguousarray(E, np.float64)
+    return _check(load().ekl_set_field(h, _ptr(E)), "ekl_set_field")
+
+
+def ekl_get_current(h, axis, plane):
+    """Species fluxes through a lattice plane and the ionic current (4 values)."""
+    out = np.zeros(4)
+    _check(load().ekl_get_current(h, int(axis), int(plane), _ptr(out)), "ekl_get_current")
+    return out
+
+
 def ekl_set_timing(h, on):
     return _check(load().ekl_set_timing(h, 1 if on else 0), "ekl_set_timing")
 
@@ -373,6 +387,15 @@ class Simulation:
 
     def set_timing(self, on=True):
         return ekl_set_timing(self.h, on)
+
+    def set_field(self, E):
+        return ekl_set_field(self.h, E)
+
+    def current(self, axis=2, plane=None):
+        """out[0:3] species fluxes, out[3] ionic current through the plane
+        (default: the middle plane along `axis`)."""
+        L = (self.wl.nx, self.wl.ny, self.wl.nz)[axis]
+        return ekl_get_current(self.h, axis, L // 2 if plane is None else plane)
 
     def set_warmstart(self, w, scales=(1.0, 1.0, 1.0)):
         return ekl_set_warmstart(self.h, w, scales)

@@ -52,15 +52,16 @@ struct PrecOps {
     int (*mg_blocks)(size_t);
     int (*mass)(Ctx &);
     int (*mg_batch_blocks)(size_t);
+    int (*current)(Ctx &, int, int, double *);
 };
 
 const PrecOps &ops(int prec)
 {
     static const PrecOps t[4] = {
-        {init_populations_f64, run_steps_f64, get_fields_f64, get_state_f64, set_state_f64, pois_blocks_f64, mg_blocks_f64, mass_f64, mg_batch_blocks_f64},
-        {init_populations_f32, run_steps_f32, get_fields_f32, get_state_f32, set_state_f32, pois_blocks_f32, mg_blocks_f32, mass_f32, mg_batch_blocks_f32},
-        {init_populations_bf16, run_steps_bf16, get_fields_bf16, get_state_bf16, set_state_bf16, pois_blocks_bf16, mg_blocks_bf16, mass_bf16, mg_batch_blocks_bf16},
-        {init_populations_fp16, run_steps_fp16, get_fields_fp16, get_state_fp16, set_state_fp16, pois_blocks_fp16, mg_blocks_fp16, mass_fp16, mg_batch_blocks_fp16},
+        {init_populations_f64, run_steps_f64, get_fields_f64, get_state_f64, set_state_f64, pois_blocks_f64, mg_blocks_f64, mass_f64, mg_batch_blocks_f64, current_f64},
+        {init_populations_f32, run_steps_f32, get_fields_f32, get_state_f32, set_state_f32, pois_blocks_f32, mg_blocks_f32, mass_f32, mg_batch_blocks_f32, current_f32},
+        {init_populations_bf16, run_steps_bf16, get_fields_bf16, get_state_bf16, set_state_bf16, pois_blocks_bf16, mg_blocks_bf16, mass_bf16, mg_batch_blocks_bf16, current_bf16},
+        {init_populations_fp16, run_steps_fp16, get_fields_fp16, get_state_fp16, set_state_fp16, pois_blocks_fp16, mg_blocks_fp16, mass_fp16, mg_batch_blocks_fp16, current_fp16},
     };
     return t[prec];
 }
@@ -1079,6 +1080,43 @@ int ekl_get_stats(ekl_handle *h, ekl_stats *out)
     for (int k = 0; k < PH_COUNT; k++) out->ms_phase[k] = c.ms_phase[k];
     out->launches = c.launches;
     out->poisson_sweeps = tot;
+    return EKL_OK;
+}
+
+int ekl_set_field(ekl_handle *h, const double E[3])
+{
+    if (!h || !E) return fail(EKL_ERR_ARG, "null argument");
+    for (int a = 0; a < 3; a++)
+        if (!isfinite(E[a])) return fail(EKL_ERR_ARG, "field must be finite");
+    for (int a = 0; a < 3; a++) h->c.P.E_app[a] = E[a];
+    return EKL_OK;
+}
+
+int ekl_get_current(ekl_handle *h, int32_t axis, int32_t plane, double out[4])
+{
+    if (!h || !out) return fail(EKL_ERR_ARG, "null argument");
+    Ctx &c = h->c;
+    const int L[3] = {c.nx, c.ny, c.nz};
+    if (axis < 0 || axis > 2 || plane < 0 || plane >= L[axis]) return fail(EKL_ERR_ARG, "axis or plane out of range");
+    const int n1 = axis == 0 ? c.ny : c.nx, n2 = axis == 2 ? c.ny : c.nz;
+    const int blocks = (n1 * n2 + 255) / 256;
+    double *part = (double *)dev_alloc(c, (size_t)blocks * NS * sizeof(double));
+    if (!part) return fail(EKL_ERR_ALLOC, "device allocation failed");
+    const int nb = ops(c.prec).current(c, axis, plane, part);
+    std::vector<double> h_part((size_t)blocks * NS);
+    cudaError_t e = nb < 0 ? cudaErrorLaunchFailure
+                           : cudaMemcpyAsync(h_part.data(), part, h_part.size() * 8, cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    dev_free(c, part, 0);
+    if (e != cudaSuccess) return fail_cuda(e, "get_current");
+    double total = 0.0;
+    for (int s = 0; s < NS; s++) {
+        double t = 0.0;
+        for (int b = 0; b < blocks; b++) t += h_part[(size_t)b * NS + s];
+        out[s] = t;
+        total += (double)c.P.valence[s] * t;
+    }
+    out[3] = total;
     return EKL_OK;
 }
 

@@ -186,6 +186,7 @@ int get_state_f64(Ctx &c, double *d_f, double *d_phi);
 int set_state_f64(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_f64();
 int mass_f64(Ctx &c);
+int current_f64(Ctx &c, int axis, int plane, double *part);
 int mg_blocks_f64(size_t smem);
 int mg_batch_blocks_f64(size_t smem);
 
@@ -196,6 +197,7 @@ int get_state_f32(Ctx &c, double *d_f, double *d_phi);
 int set_state_f32(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_f32();
 int mass_f32(Ctx &c);
+int current_f32(Ctx &c, int axis, int plane, double *part);
 int mg_blocks_f32(size_t smem);
 int mg_batch_blocks_f32(size_t smem);
 
@@ -206,6 +208,7 @@ int get_state_bf16(Ctx &c, double *d_f, double *d_phi);
 int set_state_bf16(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_bf16();
 int mass_bf16(Ctx &c);
+int current_bf16(Ctx &c, int axis, int plane, double *part);
 int mg_blocks_bf16(size_t smem);
 int mg_batch_blocks_bf16(size_t smem);
 
@@ -216,6 +219,7 @@ int get_state_fp16(Ctx &c, double *d_f, double *d_phi);
 int set_state_fp16(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_fp16();
 int mass_fp16(Ctx &c);
+int current_fp16(Ctx &c, int axis, int plane, double *part);
 int mg_blocks_fp16(size_t smem);
 int mg_batch_blocks_fp16(size_t smem);
 

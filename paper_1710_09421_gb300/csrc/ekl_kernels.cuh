@@ -1773,6 +1773,48 @@ __global__ void fields_kernel(StepArgs<S, R, PhiT> a, double *n_out, double *j_o
     }
 }
 
+// Species fluxes through the lattice plane {coordinate `axis` == plane}:
+// per fluid node of the plane the bare current component sum_p c_p,axis f_p
+// of the streamed populations (Eq. 16), summed in FP64; one partial per
+// block and species.
+template <typename S, typename R, typename PhiT, bool DEV>
+__global__ void current_kernel(StepArgs<S, R, PhiT> a, int axis, int plane, double *part)
+{
+    __shared__ double sh[256 / 32];
+    const Grid3 g = a.g;
+    const int n1 = axis == 0 ? g.ny : g.nx, n2 = axis == 2 ? g.ny : g.nz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[NS] = {0.0, 0.0, 0.0};
+    if (t < n1 * n2) {
+        const int u = t % n1, v = t / n1;
+        int x, y, z;
+        if (axis == 0) { x = plane; y = u; z = v; }
+        else if (axis == 1) { x = u; y = plane; z = v; }
+        else { x = u; y = v; z = plane; }
+        const long long i = x + (long long)g.nx * (y + (long long)g.ny * z);
+        const uint32_t m = a.mask[i];
+        if (!(m & SOLID_BIT)) {
+            const Nbr nb = make_nbr(g, x, y, z);
+            for (int s = 0; s < NS; s++) {
+                R v19[Q];
+                pull19<S, R>(a.fin, g.N, s, i, m, nb, v19);
+                double j = 0.0;
+#pragma unroll
+                for (int p = 0; p < Q; p++) {
+                    const int c = axis == 0 ? cx_(p) : (axis == 1 ? cy_(p) : cz_(p));
+                    if (c == 1) j += (double)v19[p];
+                    if (c == -1) j -= (double)v19[p];
+                }
+                acc[s] = j;
+            }
+        }
+    }
+    for (int s = 0; s < NS; s++) {
+        const double b = block_sum(acc[s], sh);
+        if (threadIdx.x == 0) part[(size_t)blockIdx.x * NS + s] = b;
+    }
+}
+
 // Per-species mass of the post-collision populations (the collision keeps
 // each node's density, so this is the total of the last step's densities),
 // one FP64 partial per block; computed only when statistics are requested.

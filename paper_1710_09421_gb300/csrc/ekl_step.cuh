@@ -278,6 +278,17 @@ int state_impl(Ctx &c, double *d_f, double *d_phi, int to_host)
     return cuda_ok(cudaGetLastError());
 }
 
+// per-block plane-current partials into `part`; returns the block count (< 0 on error)
+template <typename S, typename R, typename PhiT, bool DEV> int current_impl(Ctx &c, int axis, int plane, double *part)
+{
+    StepArgs<S, R, PhiT> a = make_args<S, R, PhiT>(c);
+    const int n1 = axis == 0 ? c.ny : c.nx, n2 = axis == 2 ? c.ny : c.nz;
+    const int blocks = (n1 * n2 + 255) / 256;
+    current_kernel<S, R, PhiT, DEV><<<blocks, 256, 0, c.stream>>>(a, axis, plane, part);
+    c.launches++;
+    return cudaGetLastError() == cudaSuccess ? blocks : EKL_ERR_CUDA;
+}
+
 // per-block mass partials into c.part_mass; returns the block count (< 0 on error)
 template <typename S, typename R, typename PhiT, bool DEV> int mass_impl(Ctx &c)
 {
@@ -491,6 +502,7 @@ template <typename S, typename R, typename PhiT> int poisson_max_blocks_per_sm()
     }                                                                                            \
     int pois_blocks_##SUFFIX() { return poisson_max_blocks_per_sm<S, R, PhiT>(); }                \
     int mass_##SUFFIX(Ctx &c) { return mass_impl<S, R, PhiT, DEV>(c); }                           \
+    int current_##SUFFIX(Ctx &c, int ax, int pl, double *p) { return current_impl<S, R, PhiT, DEV>(c, ax, pl, p); } \
     int mg_blocks_##SUFFIX(size_t smem) { return mg_max_blocks_per_sm<S, R, PhiT>(smem); }        \
     int mg_batch_blocks_##SUFFIX(size_t smem) { return mg_batch_max_blocks_per_sm<S, R, PhiT>(smem); } \
     int run_batch_##SUFFIX(Batch &b, int n) { return batch_impl<S, R, PhiT, DEV>(b, n); }         \

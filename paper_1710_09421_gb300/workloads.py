@@ -239,6 +239,43 @@ def threaded_chain(n, center, bond, solid, periodic, rng, straight_zone, wall_cl
 # densities
 # ----------------------------------------------------------------------------
 
+def random_walk_chain(n, start, bond, solid, periodic, rng, z_min, wall_clear=1.2, bead_clear=1.6):
+    """A chain grown from `start` (bead 0, e.g. at a pore mouth) by a seeded
+    random walk of fixed bond length (Sec. IV.A: generated in the cis chamber
+    starting from the pore entrance): every new bead takes a uniformly random
+    direction and is rejected when it falls below z_min, comes within
+    `wall_clear` of a wall node or within `bead_clear` of any earlier bead."""
+    dims = (solid.shape[2], solid.shape[1], solid.shape[0])
+    R = np.zeros((n, 3))
+    R[0] = start
+    for k in range(1, n):
+        for attempt in range(5000):
+            d = rng.standard_normal(3)
+            d /= np.linalg.norm(d)
+            cand = R[k - 1] + bond * d
+            if cand[2] < z_min:
+                continue
+            w = np.array([cand[a] % dims[a] if periodic[a] else cand[a] for a in range(3)])
+            if any((not periodic[a]) and (w[a] < 1 or w[a] > dims[a] - 2) for a in range(3)):
+                continue
+            if _min_dist_to_solid(w, solid, periodic) < wall_clear:
+                continue
+            diff = cand[None, :] - R[:k]
+            for a in range(3):
+                if periodic[a]:
+                    diff[:, a] -= dims[a] * np.round(diff[:, a] / dims[a])
+            if k > 1 and np.min(np.linalg.norm(diff[:-1], axis=1)) < bead_clear:
+                continue
+            R[k] = cand
+            break
+        else:
+            raise RuntimeError("chain generation failed")
+    for a in range(3):
+        if periodic[a]:
+            R[:, a] %= dims[a]
+    return R
+
+
 def ion_densities(solid, salt, n_solvent, counter_charge, noise, seed):
     """Solvent + 1:1 salt with a uniform counter-ion excess that neutralises
     `counter_charge` (the sum of wall and bead charges); each ion density gets
@@ -315,6 +352,49 @@ def translocation(nx=64, ny=64, nz=128, membrane=(60, 67), radius=4.0, salt=0.00
         periodic=periodic, solid=solid, surface_charge=sc, n_init=n,
         n_ref=(n_solvent, salt, salt), E_app=tuple(E), poisson_tol=tol, precision=precision,
         seed=seed_noise, R=R, V=None if R is None else np.zeros_like(R), charge=q,
+        chain=None if R is None else np.zeros(n_beads, np.int32))
+
+
+def paper_pore(nx=64, ny=64, nz=160, membrane=(60, 99), radius=6.0, salt_mM=100.0, n_beads=100,
+               bead_charge=-0.1, bjerrum=1.4, E=(0.0, 0.0, 0.05), pore_line_charge=-0.18, dx_nm=0.5,
+               precision="f32", seed_init=1, seed_chain=3, seed_noise=2, tol=1e-8):
+    """The paper's translocation set-up (Sec. IV.A) in lattice units, dx = 0.5 nm:
+    pore diameter 12, membrane 40 thick, chain of 100 beads of charge 0.1 e
+    with 1 nm (2 dx) bonds and sigma = 1 nm, Bjerrum length 0.7 nm = 1.4 dx,
+    field 0.05 k_B T/(e dx), 1:1 salt (100 or 10 mM: salt_mM * N_A * dx^3 per
+    node).  The pore wall carries the paper's -0.36 e per nm of pore length
+    (the printed unit "C/nm" read as e/nm): -0.18 e per dx slice, spread
+    evenly over the wall nodes lining the pore in that slice.  The chain is a
+    random walk in the cis chamber (high z; negative beads drift to -z) from
+    the pore entrance; the freely jointed bonds are stiff harmonic springs.
+    Fully periodic box."""
+    periodic = (1, 1, 1)
+    solid = pore_solid(nx, ny, nz, membrane[0], membrane[1], radius)
+    # wall nodes lining the pore: wall nodes touching fluid inside the membrane
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cx, cy = (nx - 1) / 2.0, (ny - 1) / 2.0
+    lining = wall_nodes_touching_fluid(solid, periodic) & (z >= membrane[0]) & (z <= membrane[1]) & \
+        ((x - cx) ** 2 + (y - cy) ** 2 < (radius + 2.0) ** 2)
+    sc = np.zeros(solid.shape)
+    for zz in range(membrane[0], membrane[1] + 1):
+        sl = lining[zz]
+        if sl.any():
+            sc[zz][sl] = pore_line_charge / sl.sum()
+    salt = salt_mM * 6.02214076e23 * (dx_nm * 1e-9) ** 3
+    rng = np.random.default_rng(seed_chain)
+    sigma = 2.0
+    start = np.array([cx, cy, membrane[1] + 1.5])
+    R = random_walk_chain(n_beads, start, 2.0, solid, periodic, rng, z_min=membrane[1] + 1.5,
+                          wall_clear=1.2, bead_clear=0.9 * sigma) if n_beads else None
+    q = np.full(n_beads, bead_charge) if n_beads else None
+    total = sc.sum() + (q.sum() if n_beads else 0.0)
+    n = ion_densities(solid, salt, 1.0, total, 0.0, seed_init)
+    return Workload(
+        name=f"paper_pore_{nx}x{ny}x{nz}_d{2 * radius:g}_{salt_mM:g}mM_N{n_beads}", nx=nx, ny=ny, nz=nz,
+        periodic=periodic, solid=solid, surface_charge=sc, n_init=n, n_ref=(1.0, salt, salt),
+        E_app=tuple(E), bjerrum=bjerrum, poisson_tol=tol, precision=precision, seed=seed_noise,
+        bond_kind=BOND_HARMONIC, bond_k=100.0 * KT / sigma ** 2, bond_l0=2.0, wca_sigma=sigma,
+        R=R, V=None if R is None else np.zeros_like(R), charge=q,
         chain=None if R is None else np.zeros(n_beads, np.int32))
 
 
