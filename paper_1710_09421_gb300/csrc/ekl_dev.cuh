@@ -347,7 +347,7 @@ __device__ __forceinline__ double sum_partials(const double *p, int n, double *s
 
 // Residual test of an iteration: warp 0 sums the block partials (fixed
 // order), thread 0 compares sqrt(sum) with tol * bnorm and broadcasts the
-// verdict; every thread of the block must call it.
+// result; every thread of the block must call it.
 __device__ __forceinline__ bool test_partials(const double *p, int n, double tolb, double *sh,
                                               int *flag, double &sum_out)
 {
