@@ -948,27 +948,53 @@ template <typename R> __device__ void bead_bin_body(const BeadArgs<R> &a)
             __syncthreads();
         }
     }
-    for (int t = threadIdx.x; t < npow; t += blockDim.x) {
-        unsigned long long u = key[t];
-        flag[t] = (u != ~0ull) && (t == 0 || (key[t - 1] >> 20) != (u >> 20));
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int c = 0, nvalid = 0;
-        for (int t = 0; t < npow; t++) {
-            if (key[t] == ~0ull) {
+    // slots: an entry starts a slot when its node differs from the previous
+    // entry's; slot index = inclusive prefix count of starts - 1 (block scan:
+    // each thread takes a contiguous chunk, warps scan their chunk totals by
+    // shuffles, warp totals are scanned once); unused keys (~0) sort last
+    {
+        __shared__ int wtot[BEAD_THREADS / 32];
+        __shared__ int s_nvalid;
+        const int per = (npow + blockDim.x - 1) / blockDim.x;
+        const int t0 = threadIdx.x * per, t1 = min(t0 + per, npow);
+        int local = 0;
+        for (int t = t0; t < t1; t++) {
+            const unsigned long long u = key[t];
+            local += (u != ~0ull) && (t == 0 || (key[t - 1] >> 20) != (u >> 20));
+        }
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int incl = local;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wtot[wid] = incl;
+        if (threadIdx.x == 0) s_nvalid = npow;
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < wid; w++) before += wtot[w];
+        int run = before + incl - local;  // starts before this thread's chunk
+        for (int t = t0; t < t1; t++) {
+            const unsigned long long u = key[t];
+            if (u == ~0ull) {
                 flag[t] = -1;
+                if (t == 0 || key[t - 1] != ~0ull) s_nvalid = t;  // first unused key
                 continue;
             }
-            nvalid++;
-            if (flag[t]) {
-                a.slot_first[c] = t;
-                c++;
+            if (t == 0 || (key[t - 1] >> 20) != (u >> 20)) {
+                a.slot_first[run] = t;
+                run++;
             }
-            flag[t] = c - 1;
+            flag[t] = run - 1;
         }
-        a.slot_first[c] = nvalid;
-        *a.patch_count = c;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) {
+            int c = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) c += wtot[w];
+            a.slot_first[c] = s_nvalid;
+            *a.patch_count = c;
+        }
     }
     __syncthreads();
     for (int t = threadIdx.x; t < ne; t += blockDim.x) a.entry_slot[t] = -1;
