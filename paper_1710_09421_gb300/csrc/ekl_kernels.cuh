@@ -869,27 +869,40 @@ __device__ bool bead_stencil(const Grid3 &g, const int per[3], const uint32_t *m
         base[c] = (int)fl;
         fr[c] = (R)(Rb[c] - fl);
     }
-    R W = R(0);
+    // node ids first (a position in [0, L) on a periodic axis puts every
+    // corner within one period, so a single add or subtract wraps it), then
+    // all eight link words are loaded together
+    uint32_t mk[8];
+#pragma unroll
     for (int k = 0; k < 8; k++) {
-        int o[3] = {k & 1, (k >> 1) & 1, (k >> 2) & 1};
-        R wk = R(1);
-        for (int c = 0; c < 3; c++) wk *= o[c] ? fr[c] : R(1) - fr[c];
+        const int o[3] = {k & 1, (k >> 1) & 1, (k >> 2) & 1};
         int q[3];
         bool in = true;
         for (int c = 0; c < 3; c++) {
             int v = base[c] + o[c];
             if (per[c]) {
-                v %= dims[c];
-                if (v < 0) v += dims[c];
+                if (v >= dims[c]) v -= dims[c];
+                else if (v < 0) v += dims[c];
+                if (v < 0 || v >= dims[c]) {  // far outside the box: the general wrap
+                    v %= dims[c];
+                    if (v < 0) v += dims[c];
+                }
             } else if (v < 0 || v >= dims[c]) {
                 in = false;
             }
             q[c] = v;
         }
-        long long id = in ? (long long)q[0] + (long long)g.nx * (q[1] + (long long)g.ny * q[2]) : -1;
-        bool fl = in && !(mask[id] & SOLID_BIT);
-        nodes[k] = id;
-        w[k] = fl ? wk : R(0);
+        nodes[k] = in ? (long long)q[0] + (long long)g.nx * (q[1] + (long long)g.ny * q[2]) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) mk[k] = nodes[k] >= 0 ? mask[nodes[k]] : SOLID_BIT;
+    R W = R(0);
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const int o[3] = {k & 1, (k >> 1) & 1, (k >> 2) & 1};
+        R wk = R(1);
+        for (int c = 0; c < 3; c++) wk *= o[c] ? fr[c] : R(1) - fr[c];
+        w[k] = (mk[k] & SOLID_BIT) ? R(0) : wk;
         W += w[k];
     }
     if (!(W > R(0))) return false;
@@ -1413,8 +1426,13 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
             bool in = true;
             for (int c = 0; c < 3; c++) {
                 if (B.per[c]) {
-                    q[c] %= dims[c];
-                    if (q[c] < 0) q[c] += dims[c];
+                    // the block reaches at most WALL_BOX nodes beyond the box
+                    if (q[c] >= dims[c]) q[c] -= dims[c];
+                    else if (q[c] < 0) q[c] += dims[c];
+                    if (q[c] < 0 || q[c] >= dims[c]) {
+                        q[c] %= dims[c];
+                        if (q[c] < 0) q[c] += dims[c];
+                    }
                 } else if (q[c] < 0 || q[c] >= dims[c]) {
                     in = false;
                 }
