@@ -161,6 +161,14 @@ template <> __device__ __forceinline__ double unit_variate<double>(uint32_t x)
     double t = ((double)(2.0 * (double)x + 1.0) - 4294967296.0) * (1.0 / 4294967296.0);
     return 1.7320508075688772 * t;
 }
+// The same variate in FP32 arithmetic without a 64-bit conversion (GB300 runs
+// those at the FP64 rate): (x - 2^31 + 1/2) 2^-31 = 2U - 1, the 32-bit
+// conversion rounding to FP32.  Used by the reduced-precision paths.
+__device__ __forceinline__ float unit_variate_f32(uint32_t x)
+{
+    const float t = __int2float_rn((int)(x ^ 0x80000000u)) * 4.656612873077393e-10f + 2.3283064365386963e-10f;
+    return 1.7320508f * t;
+}
 template <> __device__ __forceinline__ float unit_variate<float>(uint32_t x)
 {
     // exact: 2x + 1 - 2^32 is an odd integer below 2^33 in magnitude

@@ -1490,7 +1490,10 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
                 uint32_t ctr[4] = {(uint32_t)b, (uint32_t)sub | (1u << 24), (uint32_t)A.step,
                                    (uint32_t)((uint64_t)A.step >> 32)};
                 philox4x32_10(ctr, A.key0, A.key1);
-                for (int c = 0; c < 3; c++) xi_[c] = unit_variate<R>(ctr[c]);
+                for (int c = 0; c < 3; c++) {
+                    if constexpr (SERIAL) xi_[c] = unit_variate<R>(ctr[c]);
+                    else xi_[c] = unit_variate_f32(ctr[c]);
+                }
             }
             const R *gam = &sGam[3 * b];
             R gtot = gam[0] + gam[1] + gam[2];
@@ -1589,15 +1592,6 @@ __global__ void __launch_bounds__(MdThreads<R>::value)
 //   a^a = j^a/n^a + G^a/2, h^a = omega_d^a/2,
 //   u* = sum n a/(1+h) / sum n/(1+h), u^a* = (a^a + h^a u*)/(1+h^a),
 //   Phi^a = G^a - omega_d^a (u^a* - u*).
-// Zero-mean, unit-variance variate of the fluid noise in FP32 arithmetic:
-// sqrt(3) (2U - 1) with U = (x + 1/2) / 2^32, i.e. (x - 2^31 + 1/2) 2^-31
-// (the 32-bit conversion rounds to FP32; no 64-bit conversion).
-__device__ __forceinline__ float unit_variate_f32(uint32_t x)
-{
-    const float t = __int2float_rn((int)(x ^ 0x80000000u)) * 4.656612873077393e-10f + 2.3283064365386963e-10f;
-    return 1.7320508f * t;
-}
-
 template <typename S, typename R, typename PhiT, bool DEV, bool FLUCT>
 __device__ __forceinline__ void lb_body(const StepArgs<S, R, PhiT> &a, long long blk, long long step)
 {
