@@ -14,7 +14,8 @@ constexpr int MAX_ENTRIES = 8 * MAX_BEADS;
 constexpr int LB_THREADS = 128;
 constexpr int CHARGE_THREADS = 256;
 constexpr int POIS_THREADS = 1024;
-constexpr int MG_THREADS = 512;     // multigrid launch: one block per SM
+constexpr int MG_THREADS = 512;     // multigrid launch: one block per SM (latency-bound solve)
+constexpr int MG_BATCH_THREADS = 1024;  // batched multigrid: each block sweeps large replica volumes
 constexpr int BEAD_THREADS = 256;
 // fixed-point scale of the potential in the reduced-precision paths: 2^40
 constexpr double PHI_SCALE = 1099511627776.0;

@@ -788,10 +788,10 @@ __global__ void __launch_bounds__(MG_THREADS, 1) poisson_mg_kernel(StepArgs<S, R
 // rep_blocks[r] blocks of that replica (local index block_local[b]); each
 // replica has its own barrier words bars[4 r ..] and converges on its own.
 template <typename S, typename R, typename PhiT>
-__global__ void __launch_bounds__(MG_THREADS, 1)
+__global__ void __launch_bounds__(MG_BATCH_THREADS, 1)
     poisson_mg_batch_kernel(const StepArgs<S, R, PhiT> *reps, const MgArgs *mgs, PoisBatch pb, unsigned *bars)
 {
-    __shared__ double sh[MG_THREADS / 32];
+    __shared__ double sh[MG_BATCH_THREADS / 32];
     __shared__ double bc[1];
     extern __shared__ float mg_sm[];
     const int r = pb.block_rep[blockIdx.x];

@@ -408,7 +408,7 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_impl(Batch 
             }
             void *args[] = {&reps, &mgs, &pb, &bars};
             cudaError_t e = cudaLaunchCooperativeKernel((const void *)poisson_mg_batch_kernel<S, R, PhiT>,
-                                                        dim3(B.pois_blocks), dim3(MG_THREADS), args, B.mg_smem,
+                                                        dim3(B.pois_blocks), dim3(MG_BATCH_THREADS), args, B.mg_smem,
                                                         B.stream);
             B.launches++;
             if (e != cudaSuccess) return EKL_ERR_CUDA;
@@ -474,7 +474,7 @@ template <typename S, typename R, typename PhiT> int mg_batch_max_blocks_per_sm(
                              (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, poisson_mg_batch_kernel<S, R, PhiT>, MG_THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, poisson_mg_batch_kernel<S, R, PhiT>, MG_BATCH_THREADS, smem);
     return nb;
 }
 
