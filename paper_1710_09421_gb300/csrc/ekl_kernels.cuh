@@ -194,11 +194,14 @@ __device__ __forceinline__ void charge_body(const StepArgs<S, R, PhiT> &a, long 
         }
         a.rho[i] = rho;
     }
-    // one FP64 partial per warp (fixed shuffle tree), no block barrier
+    // one FP64 partial per block (fixed shuffle tree per warp, warps in
+    // order), so that the Poisson launch sums few partials
+    __shared__ double csh[CHARGE_THREADS / 32];
     double t;
     if constexpr (sizeof(R) == 8) t = warp_sum((double)mine);
-    else t = warp_sum_ff((float)mine);
-    if ((threadIdx.x & 31) == 0) a.part_charge[i >> 5] = t;
+    else t = warp_sum_ff_lane0((float)mine);
+    t = block_sum_lanes0(t, csh);
+    if (threadIdx.x == 0) a.part_charge[blk] = t;
 }
 
 template <typename S, typename R, typename PhiT, bool DEV>
@@ -299,6 +302,7 @@ __device__ double form_source(const StepArgs<S, R, PhiT> &a, int tid, int nthr, 
     const double csum = sum_partials(a.part_charge, a.nblocks_charge, bc);
     const double nfl = a.n_fluid;
     const double mean = nfl > 0 ? csum / nfl : 0.0;
+    const long long mean_q = __double2ll_rn(mean * PHI_SCALE);
     double bl = 0.0;
     float blf = 0.f;
     for (long long i = tid; i < a.g.N; i += nthr) {
@@ -311,14 +315,23 @@ __device__ double form_source(const StepArgs<S, R, PhiT> &a, int tid, int nthr, 
             bv = (PhiT)v;
             bl += v * v;
         } else {
-            // The source is formed in FP64 once per step: most fluid nodes carry
-            // nearly the same small charge, so FP32 rounding of c4 (rho - mean)
-            // is correlated over the lattice and leaves a net source that a
-            // periodic or all-Neumann problem cannot absorb (it floors the
-            // residual near 1e-8 on the 64x64x128 pore).
-            const double vd = (double)a.c4 * ((double)a.rho[i] - mean);
-            bv = __double2ll_rn(vd * PHI_SCALE);
-            const float v = (float)vd;
+            // Fixed point throughout, without FP64 per node: rho * 2^40 is
+            // exact (a power-of-two scaling of an FP32 value; rounded to the
+            // nearest 2^-40 below 2^-17), the mean is subtracted as an integer,
+            // and c4 d is formed as an unevaluated float pair (the product's
+            // rounding error recovered by an FMA) and rounded to the nearest
+            // integer.  Most fluid nodes carry nearly the same small charge, so
+            // an FP32 rounding of c4 (rho - mean) would be correlated over the
+            // lattice and leave a net source that a periodic or all-Neumann
+            // problem cannot absorb (it floored the residual near 1e-8).
+            const long long d = float_to_ll((float)a.rho[i] * (float)PHI_SCALE) - mean_q;
+            const float d_hi = ll_to_float(d);
+            const float d_lo = ll_to_float(d - float_to_ll(d_hi));  // exact remainder
+            const float c4f = (float)a.c4;
+            const float p = c4f * d_hi;
+            const float lo = fmaf(c4f, d_hi, -p) + c4f * d_lo;
+            bv = float_to_ll(p) + float_to_ll(lo);
+            const float v = ll_to_float(bv) * (float)PHI_INV;
             blf += v * v;
         }
         __stcg(a.b + i, bv);
@@ -511,31 +524,7 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_tiled_kernel(StepArgs
     const int by = blockIdx.x % tg.nty, bz = blockIdx.x / tg.nty;
     const int y0 = by * tg.ty - 2, z0 = bz * tg.tz - 2;  // global coordinates of the extended origin
     // --- source (grid-wide, as in the global kernel)
-    const double csum = sum_partials(a.part_charge, a.nblocks_charge, bc);
-    const double nfl = a.n_fluid;
-    const double mean = nfl > 0 ? csum / nfl : 0.0;
-    double bl = 0.0;
-    float blf = 0.f;
-    for (long long i = tid; i < g.N; i += nthr) {
-        uint32_t m = a.mask[i];
-        PhiT bv;
-        if (m & SOLID_BIT) {
-            bv = (PhiT)0;
-        } else if constexpr (((PhiT)0.5) != 0) {
-            double v = (double)a.c4 * ((double)a.rho[i] - mean);
-            bv = (PhiT)v;
-            bl += v * v;
-        } else {
-            const double vd = (double)a.c4 * ((double)a.rho[i] - mean);
-            bv = __double2ll_rn(vd * PHI_SCALE);
-            const float v = (float)vd;
-            blf += v * v;
-        }
-        __stcg(a.b + i, bv);
-    }
-    double t;
-    if constexpr (((PhiT)0.5) != 0) t = block_sum(bl, sh);
-    else t = block_sum_lanes0(warp_sum_ff_lane0(blf), sh);
+    const double t = form_source(a, tid, nthr, sh, bc);
     if (threadIdx.x == 0) a.part_pois[blockIdx.x] = t;
     if (!grid_barrier(a.barrier, nblk, bar_k, a.status)) return;
     const double bn2 = sum_partials(a.part_pois, (int)nblk, bc);
@@ -700,30 +689,7 @@ __global__ void __launch_bounds__(POIS_THREADS, 1) poisson_batch_kernel(const St
     unsigned bar_k = 0;
     // --- source of this replica (mean over its fluid nodes)
     __shared__ double bc[1];
-    const double csum = sum_partials(a.part_charge, a.nblocks_charge, bc);
-    const double mean = a.n_fluid > 0 ? csum / a.n_fluid : 0.0;
-    double bl = 0.0;
-    float blf = 0.f;
-    for (long long i = tid; i < g.N; i += nthr) {
-        const uint32_t m = a.mask[i];
-        PhiT bv;
-        if (m & SOLID_BIT) {
-            bv = (PhiT)0;
-        } else if constexpr (((PhiT)0.5) != 0) {
-            const double v = (double)a.c4 * ((double)a.rho[i] - mean);
-            bv = (PhiT)v;
-            bl += v * v;
-        } else {
-            const double vd = (double)a.c4 * ((double)a.rho[i] - mean);
-            bv = __double2ll_rn(vd * PHI_SCALE);
-            const float v = (float)vd;
-            blf += v * v;
-        }
-        __stcg(a.b + i, bv);
-    }
-    double t;
-    if constexpr (((PhiT)0.5) != 0) t = block_sum(bl, sh);
-    else t = block_sum_lanes0(warp_sum_ff_lane0(blf), sh);
+    const double t = form_source(a, tid, nthr, sh, bc);
     if (threadIdx.x == 0) a.part_pois[lb] = t;
     if (!grid_barrier(pb.barrier, gridDim.x, bar_k, pb.status)) return;
     // every replica's source norm and activity, in every block

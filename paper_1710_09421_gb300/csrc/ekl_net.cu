@@ -567,7 +567,7 @@ int warmstart_before_poisson(Ctx &c)
 {
     WarmStart &ws = *(WarmStart *)c.net;
     const int N = (int)c.N;
-    mean_k<<<1, 1024, 0, c.stream>>>(c.part_charge, c.charge_blocks * (CHARGE_THREADS / 32), (double)c.n_fluid, ws.mean);
+    mean_k<<<1, 1024, 0, c.stream>>>(c.part_charge, c.charge_blocks, (double)c.n_fluid, ws.mean);
     const int bn = (N + 255) / 256;
     const int have = ws.have_prev;
     if (c.prec == EKL_F64)

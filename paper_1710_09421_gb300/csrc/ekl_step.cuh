@@ -61,7 +61,7 @@ static StepArgs<S, R, PhiT> make_args(Ctx &c, int parity = -1)
     a.key0 = (uint32_t)c.P.seed;
     a.key1 = (uint32_t)(c.P.seed >> 32);
     a.step = c.step;
-    a.nblocks_charge = c.charge_blocks * (CHARGE_THREADS / 32);  // one partial per warp
+    a.nblocks_charge = c.charge_blocks;  // one partial per block
     return a;
 }
 
