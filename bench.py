@@ -37,8 +37,8 @@ FALLBACK_HBM_GBS = 6800.0
 # each valid only while the source files it was taken on are unchanged
 PROFILED = {
     # kernel: (sha256 prefix of its source files, dram read + write bytes per launch)
-    "lb_fused_kernel": ("f9878bc4dbd41ef2", 119378688 + 66883840),
-    "poisson_mg_kernel": ("c8ea034c12e05bea", 20793856 + 771072),
+    "lb_fused_kernel": ("07c290b5cbb6be0e", 119373568 + 66508288),
+    "poisson_mg_kernel": ("8b85dc4d2cdb1702", 20677376 + 772608),
 }
 KERNEL_SOURCES = {
     "lb_fused_kernel": ("ekl_kernels.cuh", "ekl_dev.cuh"),
