@@ -173,6 +173,13 @@ int ekl_step_async(ekl_handle *h, int32_t nsteps);
 int ekl_get_fields(ekl_handle *h, double *n_out, double *j_out, double *phi_out,
                    double *R_out, double *V_out);
 
+/* Self-test of the library's bounded device-side wait (no counterpart in
+ * the paper): one block waits at a grid barrier that another block never
+ * reaches; the wait gives up after about 2 s and raises the timeout status,
+ * as every spin in the library's kernels does.  Returns EKL_ERR_TIMEOUT when
+ * the bound works (the expected result), EKL_ERR_CUDA on a CUDA error. */
+int ekl_selftest_wait(void);
+
 /* Replace the applied field E_app (k_B T / (e dx)) from the next step on,
  * e.g. to relax a chain at zero field before driving it (Sec. IV.A).
  * Errors: EKL_ERR_ARG (null or non-finite). */

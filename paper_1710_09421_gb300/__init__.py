@@ -117,6 +117,7 @@ def load(build_if_missing: bool = True):
         L.ekl_get_stats.argtypes = [vp, C.POINTER(ekl_stats)]
         L.ekl_set_timing.argtypes = [vp, C.c_int32]
         L.ekl_set_field.argtypes = [vp, vp]
+        L.ekl_selftest_wait.argtypes = []
         L.ekl_get_current.argtypes = [vp, C.c_int32, C.c_int32, vp]
         L.ekl_get_link_mask.argtypes = [vp, vp]
         L.ekl_lattice.argtypes = [vp, vp, vp]

@@ -68,6 +68,15 @@ const PrecOps &ops(int prec)
 
 // Link bits of every node (integer work, bit-exact against the oracle):
 // bit p set when x - c_p is a wall node or beyond a closed face; bit 31 on walls.
+// Self-test of the bounded device-side wait: block 1 never reaches the
+// barrier, so block 0's wait has to give up on its own.
+__global__ void wait_selftest_kernel(unsigned *bar, int *status)
+{
+    if (blockIdx.x != 0) return;
+    unsigned k = 0;
+    grid_barrier(bar, gridDim.x, k, status);
+}
+
 __global__ void mask_kernel(Grid3 g, int px, int py, int pz, const uint8_t *__restrict__ solid,
                             uint32_t *__restrict__ mask)
 {
@@ -1080,6 +1089,28 @@ int ekl_get_stats(ekl_handle *h, ekl_stats *out)
     for (int k = 0; k < PH_COUNT; k++) out->ms_phase[k] = c.ms_phase[k];
     out->launches = c.launches;
     out->poisson_sweeps = tot;
+    return EKL_OK;
+}
+
+int ekl_selftest_wait(void)
+{
+    unsigned *bar = nullptr;
+    int *status = nullptr;
+    cudaError_t e = cudaMalloc(&bar, 4 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(bar, 0, 4 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(status, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        wait_selftest_kernel<<<2, 32>>>(bar, status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int st = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(bar);
+    cudaFree(status);
+    if (e != cudaSuccess) return fail_cuda(e, "selftest_wait");
+    if (st & ST_TIMEOUT) return fail(EKL_ERR_TIMEOUT, "a device-side wait timed out");
     return EKL_OK;
 }
 
