@@ -37,8 +37,8 @@ FALLBACK_HBM_GBS = 6800.0
 # each valid only while the source files it was taken on are unchanged
 PROFILED = {
     # kernel: (sha256 prefix of its source files, dram read + write bytes per launch)
-    "lb_fused_kernel": ("07c290b5cbb6be0e", 119373568 + 66508288),
-    "poisson_mg_kernel": ("8b85dc4d2cdb1702", 20677376 + 772608),
+    "lb_fused_kernel": ("9e03f41f3a4eef12", 119364608 + 65307904),
+    "poisson_mg_kernel": ("6dca54ffcc0e69af", 20425984 + 953856),
 }
 KERNEL_SOURCES = {
     "lb_fused_kernel": ("ekl_kernels.cuh", "ekl_dev.cuh"),

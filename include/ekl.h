@@ -67,7 +67,8 @@ extern "C" {
 #define EKL_EQ_BARYCENTRIC 1   /* f_eq and S use the barycentric velocity (printed Eq. 10) */
 #define EKL_GAMMA_LITERAL 2    /* bead drag gamma^a = xi for every species (literal Sec. II.B) */
 #define EKL_NO_BEAD_NOISE 4    /* no Langevin noise on the beads */
-#define EKL_POISSON_GLOBAL 8   /* always use the global-memory SOR kernel (no shared-memory tiles) */
+#define EKL_POISSON_GLOBAL 8   /* no shared-memory tiles: the global-memory SOR kernel, or (with
+                                  EKL_POISSON_MG) coarse-level half sweeps one grid-wide phase each */
 /* Solve the Poisson equation of each step by conjugate gradients
  * preconditioned with one geometric multigrid V-cycle (2x2x2 aggregation,
  * red-black Gauss-Seidel smoothing) instead of the Chebyshev SOR of
@@ -76,8 +77,10 @@ extern "C" {
  * residual met during a sweep).  poisson_max_iter and poisson_fixed_iter
  * then count CG iterations, poisson_check_every and rho_jacobi are unused,
  * and ekl_stats.poisson_iters / poisson_sweeps report CG iterations.
- * ekl_create fails with EKL_ERR_ARG when no coarser level exists (a
- * periodic extent that is not a multiple of 4). */
+ * Coarse levels small enough per block are smoothed in shared-memory tiles
+ * with redundant halos (same results, fewer grid-wide barriers) unless
+ * EKL_POISSON_GLOBAL is set.  ekl_create fails with EKL_ERR_ARG when no
+ * coarser level exists (a periodic extent that is not a multiple of 4). */
 #define EKL_POISSON_MG 16
 
 #define EKL_BOND_FENE 0
@@ -223,10 +226,14 @@ int64_t ekl_sizeof_params(void);
  * paper runs 100 such events, Sec. IV.A) stepped together: each phase of
  * the step is one launch for all replicas, the Poisson solve one persistent
  * cooperative launch whose blocks are shared out among the replicas (each
- * with its own schedule, tolerance and convergence).  All replicas share the
- * precision of params[0] and the stream.  Replicas are ordinary handles
- * (ekl_batch_replica) for set-up and read-back, but must only be advanced
- * through ekl_batch_step. */
+ * with its own schedule, tolerance and convergence).  With EKL_POISSON_MG
+ * (every replica or none) each replica runs its multigrid-CG solve on its own
+ * blocks with its own barrier, at its own pace, and its hierarchy goes one
+ * level deeper (coarsest level <= 512 cells, solved exactly).  All replicas
+ * share the precision of params[0] and the stream.  Replicas are ordinary
+ * handles (ekl_batch_replica) for set-up and read-back, but must only be
+ * advanced through ekl_batch_step; ekl_set_field on a replica takes effect
+ * from the next ekl_batch_step. */
 typedef struct ekl_batch ekl_batch;
 
 /* nrep parameter blocks (params[r]); errors as ekl_create, plus
@@ -247,8 +254,10 @@ ekl_handle *ekl_batch_replica(ekl_batch *b, int32_t rep);
 /* Autotuner: time each Poisson schedule (1024-thread blocks one per SM or
  * 512-thread blocks two per SM; blocks shared by all nodes or by fluid
  * nodes) over trial_steps steps of the live batch (the steps are real: the
- * batch advances by 4 * trial_steps) and keep the fastest; *choice_out gets
- * its index (bit 0: 512-thread blocks, bit 1: fluid weighting). */
+ * batch advances by trial_steps per schedule tried) and keep the fastest;
+ * *choice_out gets its index (bit 0: 512-thread blocks, bit 1: fluid
+ * weighting).  A multigrid batch keeps one 1024-thread block per SM and
+ * tunes the weighting only. */
 int ekl_batch_autotune(ekl_batch *b, int32_t trial_steps, int32_t *choice_out);
 
 /* kernels launched by the batch itself since creation */

@@ -442,7 +442,8 @@ def ekl_batch_destroy(b):
 
 
 class _Replica:
-    """Read-back view of one replica of a Batch."""
+    """Read-back view of one replica of a Batch (plus the applied field,
+    which takes effect from the batch's next step)."""
 
     def __init__(self, h, wl, nb):
         self.h, self.wl, self.N, self.nb = h, wl, wl.n_nodes, nb
@@ -455,6 +456,9 @@ class _Replica:
 
     def get_state(self):
         return ekl_get_state(self.h, self.N)
+
+    def set_field(self, E):
+        return ekl_set_field(self.h, E)
 
 
 class Batch:

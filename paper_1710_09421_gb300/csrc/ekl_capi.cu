@@ -149,6 +149,7 @@ void release(Ctx &c)
         dev_free(c, c.mg_lev[l].sig, 0);
         dev_free(c, c.mg_lev[l].e, 0);
         dev_free(c, c.mg_lev[l].f, 0);
+        dev_free(c, c.mg_lev[l].t, 0);
     }
     dev_free(c, c.mg_r, 0);
     dev_free(c, c.mg_z, 0);
@@ -425,14 +426,45 @@ static std::vector<float> coarse_pinv(int nx, int ny, int nz, const std::vector<
     return M;
 }
 
+// Tile of a coarse level for the shared-memory smoothing (even extents up to
+// tmax; halo H; region within max_bytes):
+// minimises the rounds of tiles over the launch's blocks times a tile's cost,
+// taken as a fixed part (load latency and the block-wide barriers, worth
+// about 6000 region cells) plus its region's cell count.
+static void mg_pick_tile(const int ex[3], int H, int nblk, int tmax, size_t max_bytes, int T[3], size_t &words)
+{
+    int lim[3];
+    for (int a = 0; a < 3; a++) lim[a] = std::min(tmax, std::max(2, (ex[a] + 1) & ~1));
+    double best = 1e300;
+    size_t wbest = 0;
+    for (int tx = 2; tx <= lim[0]; tx += 2)
+        for (int ty = 2; ty <= lim[1]; ty += 2)
+            for (int tz = 2; tz <= lim[2]; tz += 2) {
+                const size_t w = mg_tile_words(tx + 2 * H, ty + 2 * H, tz + 2 * H);
+                if (w * sizeof(float) > max_bytes) continue;
+                const long long nt = (long long)((ex[0] + tx - 1) / tx) * ((ex[1] + ty - 1) / ty) * ((ex[2] + tz - 1) / tz);
+                const double rounds = (double)((nt + nblk - 1) / nblk);
+                const double cost = rounds * (6000.0 + (double)(tx + 2 * H) * (ty + 2 * H) * (tz + 2 * H));
+                if (cost < best) {
+                    best = cost;
+                    T[0] = tx;
+                    T[1] = ty;
+                    T[2] = tz;
+                    wbest = w;
+                }
+            }
+    words = std::max(words, wbest);
+}
+
 // Multigrid hierarchy of the Poisson operator (EKL_POISSON_MG): levels halve
 // every extent (rounding up) while each periodic extent stays even, down to
 // MG_COARSEST_CELLS cells.  Face conductances: 1 on the lattice's open faces
 // (fluid to fluid, inside or across a periodic side); on level l+1, half the
-// sum of the level-l conductances crossing the aggregated face.  Returns an
-// error message, or null.
+// sum of the level-l conductances crossing the aggregated face.  `tiles`:
+// smooth the grid-wide coarse levels of at most MG_TILE_CELLS_PER_BLOCK cells
+// per block in shared-memory tiles.  Returns an error message, or null.
 template <typename Alloc>
-static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long long coarsest_cells)
+static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long long coarsest_cells, bool tiles)
 {
     int d[MG_MAXLEV][3];
     d[0][0] = c.nx;
@@ -516,9 +548,12 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long 
         ml.sig = (float4 *)A(NC * sizeof(float4));
         ml.e = (float *)A(NC * sizeof(float));
         ml.f = (float *)A(NC * sizeof(float));
-        if (!ml.sig || !ml.e || !ml.f) return nullptr;
+        ml.t = (float *)A(NC * sizeof(float));
+        if (!ml.sig || !ml.e || !ml.f || !ml.t) return nullptr;
         // inactive cells are never written and must read as 0
-        if (cudaMemset(ml.e, 0, NC * sizeof(float)) != cudaSuccess) return "multigrid setup failed";
+        if (cudaMemset(ml.e, 0, NC * sizeof(float)) != cudaSuccess ||
+            cudaMemset(ml.t, 0, NC * sizeof(float)) != cudaSuccess)
+            return "multigrid setup failed";
         if (cudaMemcpy(ml.sig, h4.data(), NC * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess)
             return "multigrid upload failed";
         if (l == nlev - 1 && NC <= MG_DENSE_CELLS) {
@@ -558,6 +593,18 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long 
         c.mg_cta_from = nlev - 1;
         c.mg_smem = 0;
     }
+    // tiled smoothing from the first grid-wide coarse level small enough per
+    // block; its region follows block 0's levels in the dynamic shared memory
+    c.mg_tile_from = c.mg_cta_from;
+    c.mg_tile_off = c.mg_smem / sizeof(float);
+    size_t tile_words = 0;
+    for (int l = 1; tiles && l < c.mg_cta_from; l++) {
+        if ((long long)c.mg_lev[l].N > (long long)MG_TILE_CELLS_PER_BLOCK * c.pois_blocks) continue;
+        if (c.mg_tile_from == c.mg_cta_from) c.mg_tile_from = l;
+        const int ex[3] = {c.mg_lev[l].nx, c.mg_lev[l].ny, c.mg_lev[l].nz};
+        mg_pick_tile(ex, 2 * MG_NU_COARSE, c.pois_blocks, 16, MG_TILE_BYTES, c.mg_tile[l], tile_words);
+    }
+    c.mg_smem += tile_words * sizeof(float);
     if (c.mg_smem + 4096 > (size_t)maxdyn) return "coarsest multigrid level too large for shared memory";
     if (ops(c.prec).mg_blocks(c.mg_smem) < 1) return "multigrid kernel cannot be resident";
     c.mg_r = (float *)A(N * sizeof(float));
@@ -802,7 +849,8 @@ static int create_handle(const ekl_params *P, void *stream, ekl_handle **out, bo
         return fail(EKL_ERR_ALLOC, "device allocation failed");
     }
     if (P->flags & EKL_POISSON_MG) {
-        const char *why = build_multigrid(c, solid, A, replica ? MG_COARSEST_CELLS_REPLICA : MG_COARSEST_CELLS);
+        const bool tiles = !replica && !(P->flags & EKL_POISSON_GLOBAL);
+        const char *why = build_multigrid(c, solid, A, replica ? MG_COARSEST_CELLS_REPLICA : MG_COARSEST_CELLS, tiles);
         if (!why && !okall) why = "device allocation failed";
         if (why) {
             release(c);
@@ -1120,6 +1168,7 @@ int ekl_set_field(ekl_handle *h, const double E[3])
     for (int a = 0; a < 3; a++)
         if (!isfinite(E[a])) return fail(EKL_ERR_ARG, "field must be finite");
     for (int a = 0; a < 3; a++) h->c.P.E_app[a] = E[a];
+    if (h->c.batch_ready) *h->c.batch_ready = 0;  // the batch's descriptor tables carry the field
     return EKL_OK;
 }
 
@@ -1237,6 +1286,7 @@ int ekl_batch_create(int32_t nrep, const ekl_params *params, void *stream, ekl_b
         if (rc == EKL_OK) {
             B.handles[r] = h;
             B.reps[r] = &h->c;
+            h->c.batch_ready = &B.ready;
         }
     }
     int sms = rc == EKL_OK ? B.reps[0]->num_sms : 0;

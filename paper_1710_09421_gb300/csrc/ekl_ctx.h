@@ -40,11 +40,18 @@ constexpr int MG_COARSEST_CELLS = 1024;  // stop coarsening at or below this man
 constexpr int MG_COARSEST_CELLS_REPLICA = 512;  // the same for the replicas of a batch
 constexpr int MG_DENSE_CELLS = 1024;     // coarsest levels this small are solved exactly (dense pseudo-inverse)
 constexpr int MG_CTA_CELLS = 2048;       // levels this small are handled by one block
+// Coarse levels with at most this many cells per block of the launch are
+// smoothed in shared-memory tiles with redundant halos (one grid barrier per
+// smoothing pass instead of one per half sweep); a tile's region (cells plus
+// halo) takes at most MG_TILE_BYTES of shared memory.
+constexpr int MG_TILE_CELLS_PER_BLOCK = 1024;
+constexpr size_t MG_TILE_BYTES = 100 * 1024;
 struct MgLevel {
     int nx, ny, nz, N;
     float4 *sig;  // conductances of the +x, +y, +z faces and 1 / diagonal (0: inactive cell)
     float *e;     // correction
     float *f;     // right-hand side (restricted residual)
+    float *t;     // pre-smoothed correction of a tiled level (read by its post-smoothing)
 };
 
 enum Phase { PH_BIN = 0, PH_CHARGE, PH_POISSON, PH_MD, PH_LB, PH_OTHER, PH_COUNT };
@@ -59,6 +66,7 @@ struct Ctx {
     cudaStream_t stream;
     int device;
     int num_sms;
+    int *batch_ready;  // replica of a batch: its descriptor-table flag, cleared on set-up changes
 
     // constants (FP64, derived exactly as the paper's formulas state)
     double c4;        // 4 pi l_B
@@ -110,6 +118,9 @@ struct Ctx {
     int mg;                  // solver in use
     int mg_nlev;             // levels including the lattice
     int mg_cta_from;         // first level handled by one block alone
+    int mg_tile_from;        // first level smoothed in shared-memory tiles (mg_cta_from: none)
+    int mg_tile[MG_MAXLEV][3];  // owned cells per tile of each tiled level
+    size_t mg_tile_off;      // offset (floats) of the tile region in the dynamic shared memory
     size_t mg_smem;          // dynamic shared memory of the multigrid launch
     MgLevel mg_lev[MG_MAXLEV];
     float *mg_r, *mg_z, *mg_q, *mg_p[2];  // lattice-level CG vectors

@@ -177,12 +177,17 @@ template <> __device__ __forceinline__ float unit_variate<float>(uint32_t x)
 }
 
 // ---------------------------------------------------------------- sync
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *p)
 {
     unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ uint64_t globaltimer_ns()
 {
     uint64_t t;
@@ -193,9 +198,12 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
 // Grid-wide barrier of a cooperative launch with a bounded wait.  bar[0]
 // counts arrivals monotonically within a launch (reset by the host before
 // the launch); barrier number k (k = 1, 2, ...) is passed when the count
-// reaches k * nblocks.  A block that waits more than ~2 s raises ST_TIMEOUT
-// and the abort word bar[2]; every waiter also leaves as soon as the abort
-// word is set.  Returns false on abort.
+// reaches k * nblocks.  Arrival is a release reduction (it publishes the
+// block's writes, ordered before it by __syncthreads); the wait polls with
+// relaxed loads, one load per poll, and the fence after the last poll makes
+// it an acquire.  A block that waits more than ~2 s raises ST_TIMEOUT and
+// the abort word bar[2]; every waiter also leaves soon after the abort word
+// is set (it is read every 64 polls).  Returns false on abort.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, unsigned &k, int *status)
 {
     __shared__ int ok_s;
@@ -204,16 +212,15 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, un
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned target = k * nblocks;
-        __threadfence();
-        atomicAdd(&bar[0], 1u);
+        red_release_add(&bar[0], 1u);
         uint64_t t0 = 0;
         unsigned spins = 0;
-        while ((int)(ld_acquire(&bar[0]) - target) < 0) {
-            if (ld_acquire(&bar[2])) {
-                ok = 0;
-                break;
-            }
-            if ((++spins & 255u) == 0) {
+        while ((int)(ld_relaxed(&bar[0]) - target) < 0) {
+            if ((++spins & 63u) == 0) {
+                if (ld_relaxed(&bar[2])) {
+                    ok = 0;
+                    break;
+                }
                 uint64_t t = globaltimer_ns();
                 if (t0 == 0) t0 = t;
                 else if (t - t0 > 2000000000ull) {
@@ -224,7 +231,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, un
                 }
             }
         }
-        __threadfence();
+        fence_acq_rel_gpu();
         ok_s = ok;
     }
     __syncthreads();

@@ -24,10 +24,14 @@
 //     tol ||b||, and CG restarts from it when needed (iterative refinement).
 //
 // One cooperative launch runs the whole solve: lattice-sized phases are
-// spread over the grid and separated by the bounded grid barrier; levels at
-// and below `cta_from` are handled by block 0 alone while the other blocks
-// wait at the next barrier.  Every load of data written inside the launch
-// goes through L2 (__ldcg): L1 is not coherent across SMs.
+// spread over the grid and separated by the bounded grid barrier; coarse
+// levels from `tile_from` on are smoothed in shared-memory tiles (one barrier
+// per smoothing pass); levels at and below `cta_from` are handled by block 0
+// alone while the other blocks wait at the next barrier.  Every load of data written inside the launch
+// goes through L2 (__ldcg: L1 is not coherent across SMs) or, for data
+// that no block writes during the current phase, through L1 (mg_ldl): the
+// acquire fence of the grid barrier that opens the phase discards stale L1
+// lines, and the phase itself never rewrites what it reads.
 #pragma once
 #include "ekl_kernels.cuh"
 
@@ -41,8 +45,20 @@ struct MgArgs {
     int have_prev;        // phi_prev holds phi(t-2) and phi holds phi(t-1)
     int nlev, cta_from, nu, nu_c, coarse_sweeps;  // smoothing sweeps: lattice level, coarse levels
     float inner_red;
+    int tile_from;                // first tiled coarse level (cta_from: none)
+    int tile_off;                 // tile region offset (floats) in the dynamic shared memory
+    int tile[MG_MAXLEV][3];       // owned cells per tile, per level
     MgLevel lev[MG_MAXLEV];
 };
+
+// 4-byte words of shared memory for a tile region of Rx x Ry x Rz cells:
+// e and f (each padded to 16 bytes), the float4 conductances, and the
+// wrapped level coordinates of the region's columns, rows and planes
+__host__ __device__ inline size_t mg_tile_words(int Rx, int Ry, int Rz)
+{
+    const size_t RN = (size_t)Rx * Ry * Rz, RN4 = (RN + 3) & ~(size_t)3;
+    return 2 * RN4 + 4 * RN + (size_t)Rx + Ry + Rz;
+}
 
 // The blocks that solve one problem: all blocks of a single-handle launch, or
 // the blocks a batched launch assigns to one replica (each replica then runs
@@ -78,10 +94,13 @@ __device__ __forceinline__ Pair mg_pair(int h, int hx, int ny, int c)
     return p;
 }
 
+// load of a value no block writes during the current phase (L1-cached)
+template <typename T> __device__ __forceinline__ T mg_ldl(const T *p) { return __ldca(p); }
+
 template <bool SH> __device__ __forceinline__ float mg_ld(const float *p)
 {
     if constexpr (SH) return *p;
-    else return __ldcg(p);
+    else return mg_ldl(p);
 }
 template <bool SH> __device__ __forceinline__ void mg_st(float *p, float v)
 {
@@ -164,14 +183,14 @@ static __device__ void fine_half(const Grid3 &g, const uint32_t *__restrict__ ma
             float zn[6];
 #pragma unroll
             for (int f = 0; f < 6; f++) {
-                zn[f] = __ldcg(z + nb[f]);
+                zn[f] = mg_ldl(z + nb[f]);
                 if (PRO) {
                     int X, Y, Z;
                     mg_face_coord(g.nx, g.ny, g.nz, p.x, p.y, p.z, f, X, Y, Z);
-                    zn[f] += __ldcg(C.e + mg_parent(C, X, Y, Z));
+                    zn[f] += mg_ldl(C.e + mg_parent(C, X, Y, Z));
                 }
             }
-            const float ri = __ldcg(r + i);
+            const float ri = mg_ldl(r + i);
             const uint32_t m = __ldg(mask + i);
             const unsigned o = mg_open(m);
             if (!(m & SOLID_BIT) && o) {
@@ -186,7 +205,7 @@ static __device__ void fine_half(const Grid3 &g, const uint32_t *__restrict__ ma
         }
         if (RZ && p.xo < g.nx) {
             const int io = p.xo + g.nx * p.row;
-            const float ro = __ldcg(r + io), zo = __ldcg(z + io);
+            const float ro = mg_ldl(r + io), zo = mg_ldl(z + io);
             const uint32_t m = __ldg(mask + io);
             if (!(m & SOLID_BIT) && mg_open(m)) rz += ro * zo;
         }
@@ -214,8 +233,8 @@ __device__ __forceinline__ float fine_resid(const Grid3 &g, const uint32_t *__re
     face_nbrs(g, x, y, zz, i, nb);
     float zn[6];
 #pragma unroll
-    for (int f = 0; f < 6; f++) zn[f] = __ldcg(z + nb[f]);
-    const float ri = __ldcg(r + i), zi = __ldcg(z + i);
+    for (int f = 0; f < 6; f++) zn[f] = mg_ldl(z + nb[f]);
+    const float ri = mg_ldl(r + i), zi = mg_ldl(z + i);
     const uint32_t m = __ldg(mask + i);
     const unsigned o = mg_open(m);
     if ((m & SOLID_BIT) || !o) return 0.f;
@@ -281,6 +300,31 @@ __device__ __forceinline__ float coarse_val(const MgLevel &L, const MgLevel &C, 
     return v;
 }
 
+// The coarse-level update e_i = (f_i + sum_j sigma_ij e_j) / diag_i and the
+// residual f_i - (A e)_i from the cell's own conductances s (+x, +y, +z
+// faces, 1/diag), those of its -x, -y, -z faces and the six neighbour
+// values; one definition serves the global and the tiled sweeps, so both
+// round identically.
+__device__ __forceinline__ float mg_relax(float f, float4 s, float sxm, float sym, float szm, float vxp,
+                                          float vxm, float vyp, float vym, float vzp, float vzm)
+{
+    float acc = f;
+    acc += s.x * vxp + sxm * vxm;
+    acc += s.y * vyp + sym * vym;
+    acc += s.z * vzp + szm * vzm;
+    return acc * s.w;
+}
+__device__ __forceinline__ float mg_cresid(float f, float e, float4 s, float sxm, float sym, float szm, float exp_,
+                                           float exm, float eyp, float eym, float ezp, float ezm)
+{
+    const float diag = s.x + s.y + s.z + sxm + sym + szm;
+    float acc = f - diag * e;
+    acc += s.x * exp_ + sxm * exm;
+    acc += s.y * eyp + sym * eym;
+    acc += s.z * ezp + szm * ezm;
+    return acc;
+}
+
 // Half sweep of colour c of e <- (f + sum sigma e_j) / diag.  Faces beyond a
 // closed side carry sigma = 0 and inactive cells keep e = 0, so wrapped or
 // inactive neighbours contribute nothing.
@@ -298,14 +342,14 @@ static __device__ void coarse_half(const MgLevel &L, const MgLevel &C, int c, in
         const int xm = p.x == 0 ? L.nx - 1 : p.x - 1, xp = p.x == L.nx - 1 ? 0 : p.x + 1;
         const int ym = p.y == 0 ? L.ny - 1 : p.y - 1, yp = p.y == L.ny - 1 ? 0 : p.y + 1;
         const int zm = p.z == 0 ? L.nz - 1 : p.z - 1, zp = p.z == L.nz - 1 ? 0 : p.z + 1;
-        float acc = mg_ld<SH>(L.f + i);
-        acc += s.x * coarse_val<SH, PRO>(L, C, n.xp, xp, p.y, p.z) +
-               mg_sx<SH>(L.sig + n.xm) * coarse_val<SH, PRO>(L, C, n.xm, xm, p.y, p.z);
-        acc += s.y * coarse_val<SH, PRO>(L, C, n.yp, p.x, yp, p.z) +
-               mg_sy<SH>(L.sig + n.ym) * coarse_val<SH, PRO>(L, C, n.ym, p.x, ym, p.z);
-        acc += s.z * coarse_val<SH, PRO>(L, C, n.zp, p.x, p.y, zp) +
-               mg_sz<SH>(L.sig + n.zm) * coarse_val<SH, PRO>(L, C, n.zm, p.x, p.y, zm);
-        mg_st<SH>(L.e + i, acc * s.w);
+        const float v = mg_relax(mg_ld<SH>(L.f + i), s, mg_sx<SH>(L.sig + n.xm), mg_sy<SH>(L.sig + n.ym),
+                                 mg_sz<SH>(L.sig + n.zm), coarse_val<SH, PRO>(L, C, n.xp, xp, p.y, p.z),
+                                 coarse_val<SH, PRO>(L, C, n.xm, xm, p.y, p.z),
+                                 coarse_val<SH, PRO>(L, C, n.yp, p.x, yp, p.z),
+                                 coarse_val<SH, PRO>(L, C, n.ym, p.x, ym, p.z),
+                                 coarse_val<SH, PRO>(L, C, n.zp, p.x, p.y, zp),
+                                 coarse_val<SH, PRO>(L, C, n.zm, p.x, p.y, zm));
+        mg_st<SH>(L.e + i, v);
     }
 }
 
@@ -318,13 +362,9 @@ __device__ __forceinline__ float coarse_resid(const MgLevel &L, int x, int y, in
     const float4 sg = mg_sig<SH>(L.sig + i);
     if (sg.w == 0.f) return 0.f;
     const CNbr n = coarse_nbrs(L, x, y, z, i);
-    const float sxm = mg_sx<SH>(L.sig + n.xm), sym = mg_sy<SH>(L.sig + n.ym), szm = mg_sz<SH>(L.sig + n.zm);
-    const float diag = sg.x + sg.y + sg.z + sxm + sym + szm;
-    float acc = mg_ld<SH>(L.f + i) - diag * mg_ld<SH>(L.e + i);
-    acc += sg.x * mg_ld<SH>(L.e + n.xp) + sxm * mg_ld<SH>(L.e + n.xm);
-    acc += sg.y * mg_ld<SH>(L.e + n.yp) + sym * mg_ld<SH>(L.e + n.ym);
-    acc += sg.z * mg_ld<SH>(L.e + n.zp) + szm * mg_ld<SH>(L.e + n.zm);
-    return acc;
+    return mg_cresid(mg_ld<SH>(L.f + i), mg_ld<SH>(L.e + i), sg, mg_sx<SH>(L.sig + n.xm), mg_sy<SH>(L.sig + n.ym),
+                     mg_sz<SH>(L.sig + n.zm), mg_ld<SH>(L.e + n.xp), mg_ld<SH>(L.e + n.xm), mg_ld<SH>(L.e + n.yp),
+                     mg_ld<SH>(L.e + n.ym), mg_ld<SH>(L.e + n.zp), mg_ld<SH>(L.e + n.zm));
 }
 
 // C.f = sum over the children of each cell of level l+1 of (f - A e) on
@@ -350,6 +390,263 @@ static __device__ void coarse_restrict(const MgLevel &L, const MgLevel &C, int t
             mg_st<SH>(C.f + I, sum);
             if (FIRST && !((X + Y + Z) & 1)) mg_st<SH>(C.e + I, sum * mg_sw<SH>(C.sig + I));
         }
+    }
+}
+
+// ------------------------------------------------------------ tiled coarse smoothing
+// A block takes whole tiles of a level (tx x ty x tz owned cells, even, tile
+// origins even) and runs a complete smoothing pass on the tile plus a halo of
+// H = 2 nu_c cells held in shared memory: the k-th half sweep updates the
+// cells within H - k (pre) or H - 1 - k (post) layers of the tile, so each
+// half sweep reads only values already final for that stage, and the halo
+// is recomputed by every tile that needs it.  The region is indexed by
+// wrapped level coordinates (a region larger than the level simply repeats
+// cells, which all take the same values), and every update and residual
+// uses mg_relax / mg_cresid on the same inputs as the global sweeps: results
+// are identical, at one grid barrier per smoothing pass.
+constexpr int TILE_LOADS = 4;  // region cells a thread loads per round
+struct TileSm {
+    float *e, *f;
+    float4 *s;
+    int *wx, *wy, *wz;
+    int Rx, Ry, Rz;
+};
+__device__ __forceinline__ TileSm tile_sm(float *sm, int Rx, int Ry, int Rz)
+{
+    TileSm T;
+    const int RN = Rx * Ry * Rz, RN4 = (RN + 3) & ~3;
+    T.e = sm;
+    T.f = sm + RN4;
+    T.s = (float4 *)(sm + 2 * RN4);
+    T.wx = (int *)(T.s + RN);
+    T.wy = T.wx + Rx;
+    T.wz = T.wy + Ry;
+    T.Rx = Rx;
+    T.Ry = Ry;
+    T.Rz = Rz;
+    return T;
+}
+
+// n / d for 0 <= n < 2^21 from inv = 1/d (rounded): (n + 1/2) / d lies at
+// least 1/(2d) from an integer and the two roundings move it by less than
+// 2^-23 (n + 1/2) / d, so truncation gives the floor
+__device__ __forceinline__ int tdiv(int n, float inv) { return (int)(((float)n + 0.5f) * inv); }
+// region index k -> (a, b, c) for rows of nx cells and planes of ny rows
+__device__ __forceinline__ void tsplit(int k, int nx, int ny, float inx, float iny, int &a, int &b, int &c)
+{
+    const int r = tdiv(k, inx);
+    a = k - r * nx;
+    c = tdiv(r, iny);
+    b = r - c * ny;
+}
+__device__ __forceinline__ int mg_wrap(int v, int n)
+{
+    while (v < 0) v += n;
+    while (v >= n) v -= n;
+    return v;
+}
+
+// wrapped level coordinates of the region that starts at (x0, y0, z0)
+__device__ __forceinline__ void tile_coords(const TileSm &T, const MgLevel &L, int x0, int y0, int z0)
+{
+    for (int a = threadIdx.x; a < T.Rx + T.Ry + T.Rz; a += blockDim.x) {
+        if (a < T.Rx) T.wx[a] = mg_wrap(x0 + a, L.nx);
+        else if (a < T.Rx + T.Ry) T.wy[a - T.Rx] = mg_wrap(y0 + a - T.Rx, L.ny);
+        else T.wz[a - T.Rx - T.Ry] = mg_wrap(z0 + a - T.Rx - T.Ry, L.nz);
+    }
+}
+
+// Half sweep of colour col over the region cells at least `lo` layers from
+// the region's faces.  Colours follow the region coordinates (parity base at
+// the region origin): they equal the level's colours everywhere the owned
+// cells' results depend on, since periodic extents are even and a closed
+// side decouples the wrapped cells beyond it (zero conductance).  A thread
+// takes an x-pair and updates its colour-col cell.
+static __device__ void tile_half(const TileSm &T, int lo, int col, int base)
+{
+    const int bx = T.Rx - 2 * lo, by = T.Ry - 2 * lo, bz = T.Rz - 2 * lo;
+    const int bxh = (bx + 1) >> 1, np = bxh * by * bz;
+    const float ibxh = 1.f / (float)bxh, iby = 1.f / (float)by;
+    const int sy = T.Rx, sz = T.Rx * T.Ry, amax = T.Rx - lo;
+    for (int h = threadIdx.x; h < np; h += blockDim.x) {
+        int xh, b, c;
+        tsplit(h, bxh, by, ibxh, iby, xh, b, c);
+        b += lo;
+        c += lo;
+        const int a0 = lo + 2 * xh;
+        const int a = a0 + ((a0 + b + c + base + col) & 1);
+        if (a >= amax) continue;
+        const int k = a + sy * b + sz * c;
+        const float4 s = T.s[k];
+        if (s.w == 0.f) continue;
+        T.e[k] = mg_relax(T.f[k], s, T.s[k - 1].x, T.s[k - sy].y, T.s[k - sz].z, T.e[k + 1], T.e[k - 1],
+                          T.e[k + sy], T.e[k - sy], T.e[k + sz], T.e[k - sz]);
+    }
+}
+
+// tile origin (owned cells) of tile number t of a level
+__device__ __forceinline__ void tile_origin(const MgLevel &L, const int *tdim, int t, int &x0, int &y0, int &z0)
+{
+    const int ntx = (L.nx + tdim[0] - 1) / tdim[0], nty = (L.ny + tdim[1] - 1) / tdim[1];
+    const int tz = t / (ntx * nty), rem = t - tz * ntx * nty, ty = rem / ntx;
+    x0 = (rem - ty * ntx) * tdim[0];
+    y0 = ty * tdim[1];
+    z0 = tz * tdim[2];
+}
+__device__ __forceinline__ int tile_count(const MgLevel &L, const int *tdim)
+{
+    return ((L.nx + tdim[0] - 1) / tdim[0]) * ((L.ny + tdim[1] - 1) / tdim[1]) * ((L.nz + tdim[2] - 1) / tdim[2]);
+}
+
+// Pre-smoothing of level L from its right-hand side (colour 0 from zero, then
+// 2 nu_c - 1 half sweeps), the smoothed correction of the owned cells into
+// L.t, and the restricted residual of the owned parents into C.f.
+static __device__ void coarse_pre_tiles(const MgLevel &L, const MgLevel &C, const int *tdim, int H, int blk,
+                                        int nblk, float *sm)
+{
+    const int tx = tdim[0], ty = tdim[1], tz = tdim[2];
+    const TileSm T = tile_sm(sm, tx + 2 * H, ty + 2 * H, tz + 2 * H);
+    const int RN = T.Rx * T.Ry * T.Rz, sy = T.Rx, sz = T.Rx * T.Ry;
+    const float iRx = 1.f / (float)T.Rx, iRy = 1.f / (float)T.Ry, itx = 1.f / (float)tx, ity = 1.f / (float)ty;
+    const int px = tx >> 1, py = ty >> 1, pz = tz >> 1;
+    const float ipx = 1.f / (float)px, ipy = 1.f / (float)py;
+    const int ntiles = tile_count(L, tdim);
+    for (int t = blk; t < ntiles; t += nblk) {
+        int x0, y0, z0;
+        tile_origin(L, tdim, t, x0, y0, z0);
+        const int base = (x0 + y0 + z0 - 3 * H) & 1;
+        tile_coords(T, L, x0 - H, y0 - H, z0 - H);
+        __syncthreads();
+        // TILE_LOADS cells per thread in flight at once (the loads of one
+        // round are independent: one L2 round trip per round, not per cell)
+        for (int k0 = threadIdx.x; k0 < RN; k0 += TILE_LOADS * blockDim.x) {
+            float4 sv[TILE_LOADS];
+            float fv[TILE_LOADS];
+            int col[TILE_LOADS];
+#pragma unroll
+            for (int j = 0; j < TILE_LOADS; j++) {
+                const int k = k0 + j * blockDim.x;
+                if (k < RN) {
+                    int a, b, c;
+                    tsplit(k, T.Rx, T.Ry, iRx, iRy, a, b, c);
+                    const int i = T.wx[a] + L.nx * (T.wy[b] + L.ny * T.wz[c]);
+                    sv[j] = __ldg(L.sig + i);
+                    fv[j] = __ldcg(L.f + i);
+                    col[j] = (a + b + c + base) & 1;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < TILE_LOADS; j++) {
+                const int k = k0 + j * blockDim.x;
+                if (k < RN) {
+                    T.s[k] = sv[j];
+                    T.f[k] = fv[j];
+                    T.e[k] = col[j] ? 0.f : fv[j] * sv[j].w;
+                }
+            }
+        }
+        __syncthreads();
+        for (int h = 1; h < H; h++) {
+            tile_half(T, h, h & 1, base);
+            __syncthreads();
+        }
+        // residual of the owned cells (in place of f), and their correction
+        for (int k = threadIdx.x; k < tx * ty * tz; k += blockDim.x) {
+            int a, b, c;
+            tsplit(k, tx, ty, itx, ity, a, b, c);
+            const int X = x0 + a, Y = y0 + b, Z = z0 + c;
+            const int q = (a + H) + sy * (b + H) + sz * (c + H);
+            float res = 0.f;
+            if (X < L.nx && Y < L.ny && Z < L.nz) {
+                const float4 s = T.s[q];
+                if (s.w != 0.f)
+                    res = mg_cresid(T.f[q], T.e[q], s, T.s[q - 1].x, T.s[q - sy].y, T.s[q - sz].z, T.e[q + 1],
+                                    T.e[q - 1], T.e[q + sy], T.e[q - sy], T.e[q + sz], T.e[q - sz]);
+                __stcg(L.t + X + L.nx * (Y + L.ny * Z), T.e[q]);
+            }
+            T.f[q] = res;
+        }
+        __syncthreads();
+        // children summed as the global restriction does: each (dy, dz) row's
+        // two x-children, then rows (0 + 1) + (2 + 3) with row = dy + 2 dz
+        for (int k = threadIdx.x; k < px * py * pz; k += blockDim.x) {
+            int a, b, c;
+            tsplit(k, px, py, ipx, ipy, a, b, c);
+            const int X = (x0 >> 1) + a, Y = (y0 >> 1) + b, Z = (z0 >> 1) + c;
+            if (X >= C.nx || Y >= C.ny || Z >= C.nz) continue;
+            const int q = (2 * a + H) + sy * (2 * b + H) + sz * (2 * c + H);
+            const float r0 = T.f[q] + T.f[q + 1], r1 = T.f[q + sy] + T.f[q + sy + 1];
+            const float r2 = T.f[q + sz] + T.f[q + sz + 1], r3 = T.f[q + sz + sy] + T.f[q + sz + sy + 1];
+            __stcg(C.f + X + C.nx * (Y + C.ny * Z), (r0 + r1) + (r2 + r3));
+        }
+        __syncthreads();
+    }
+}
+
+// Post-smoothing of level L: colour-0 cells start from their pre-smoothed
+// correction plus the coarser correction C.e of their parent (what the first
+// global post half sweep reads), then 2 nu_c half sweeps; the owned active
+// cells' result goes to L.e.
+static __device__ void coarse_post_tiles(const MgLevel &L, const MgLevel &C, const int *tdim, int H, int blk,
+                                         int nblk, float *sm)
+{
+    const int tx = tdim[0], ty = tdim[1], tz = tdim[2];
+    const TileSm T = tile_sm(sm, tx + 2 * H, ty + 2 * H, tz + 2 * H);
+    const int RN = T.Rx * T.Ry * T.Rz, sy = T.Rx, sz = T.Rx * T.Ry;
+    const float iRx = 1.f / (float)T.Rx, iRy = 1.f / (float)T.Ry, itx = 1.f / (float)tx, ity = 1.f / (float)ty;
+    const int ntiles = tile_count(L, tdim);
+    for (int t = blk; t < ntiles; t += nblk) {
+        int x0, y0, z0;
+        tile_origin(L, tdim, t, x0, y0, z0);
+        const int base = (x0 + y0 + z0 - 3 * H) & 1;
+        tile_coords(T, L, x0 - H, y0 - H, z0 - H);
+        __syncthreads();
+        for (int k0 = threadIdx.x; k0 < RN; k0 += TILE_LOADS * blockDim.x) {
+            float4 sv[TILE_LOADS];
+            float fv[TILE_LOADS], tv[TILE_LOADS], cv[TILE_LOADS];
+#pragma unroll
+            for (int j = 0; j < TILE_LOADS; j++) {
+                const int k = k0 + j * blockDim.x;
+                if (k < RN) {
+                    int a, b, c;
+                    tsplit(k, T.Rx, T.Ry, iRx, iRy, a, b, c);
+                    const int gx = T.wx[a], gy = T.wy[b], gz = T.wz[c];
+                    const int i = gx + L.nx * (gy + L.ny * gz);
+                    sv[j] = __ldg(L.sig + i);
+                    fv[j] = __ldcg(L.f + i);
+                    tv[j] = 0.f;
+                    cv[j] = 0.f;
+                    if (!((a + b + c + base) & 1)) {
+                        tv[j] = __ldcg(L.t + i);
+                        cv[j] = __ldcg(C.e + mg_parent(C, gx, gy, gz));
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < TILE_LOADS; j++) {
+                const int k = k0 + j * blockDim.x;
+                if (k < RN) {
+                    T.s[k] = sv[j];
+                    T.f[k] = fv[j];
+                    float v = tv[j];
+                    v += cv[j];
+                    T.e[k] = v;
+                }
+            }
+        }
+        __syncthreads();
+        for (int h = 0; h < H; h++) {
+            tile_half(T, h + 1, (h & 1) ^ 1, base);
+            __syncthreads();
+        }
+        for (int k = threadIdx.x; k < tx * ty * tz; k += blockDim.x) {
+            int a, b, c;
+            tsplit(k, tx, ty, itx, ity, a, b, c);
+            const int X = x0 + a, Y = y0 + b, Z = z0 + c;
+            const int q = (a + H) + sy * (b + H) + sz * (c + H);
+            if (X < L.nx && Y < L.ny && Z < L.nz && T.s[q].w != 0.f) __stcg(L.e + X + L.nx * (Y + L.ny * Z), T.e[q]);
+        }
+        __syncthreads();
     }
 }
 
@@ -465,7 +762,7 @@ static __device__ void mg_dense_solve(const MgArgs &m, int t0, int nt)
     for (int I = t0 >> 5; I < n; I += nt >> 5) {
         const float *row = m.dense + (size_t)I * n;
         float acc = 0.f;
-        for (int J = lane; J < n; J += 32) acc += __ldg(row + J) * __ldcg(L.f + J);
+        for (int J = lane; J < n; J += 32) acc += __ldg(row + J) * mg_ldl(L.f + J);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) __stcg(L.e + I, acc);
@@ -475,7 +772,7 @@ static __device__ void mg_dense_solve(const MgArgs &m, int t0, int nt)
 // One V-cycle z = M^-1 r over the grid, entered with z's colour-0 nodes
 // already set to r / deg; returns this block's partial of r.z in thread 0
 // (through rz_block), or false on a barrier abort.
-template <typename S, typename R, typename PhiT>
+template <typename S, typename R, typename PhiT, bool TILES>
 __device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const MgGrid &G, unsigned &bar_k,
                           float *sm, double *sh, double *bc, double &rz_block)
 {
@@ -486,6 +783,7 @@ __device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const 
     do {                                                                  \
         if (!grid_barrier(G.bar, (unsigned)G.nblk, bar_k, a.status)) return false; \
     } while (0)
+    float *tsm = sm + m.tile_off;  // coarse tile regions
     // lattice level: rest of the pre-smoothing, residual restricted to level 1
     for (int s = 1; s < 2 * m.nu; s++) {
         fine_half<false, false>(g, a.mask, m.r, m.z, m.lev[1], s & 1, t0, nt, dummy);
@@ -496,6 +794,11 @@ __device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const 
     MG_BAR();
     // grid-wide coarse levels
     for (int l = 1; l < m.cta_from; l++) {
+        if (TILES && l >= m.tile_from) {
+            coarse_pre_tiles(m.lev[l], m.lev[l + 1], m.tile[l], 2 * m.nu_c, G.blk, G.nblk, tsm);
+            MG_BAR();
+            continue;
+        }
         for (int s = 1; s < 2 * m.nu_c; s++) {
             coarse_half<false, false>(m.lev[l], m.lev[l], s & 1, t0, nt);
             MG_BAR();
@@ -508,6 +811,11 @@ __device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const 
     else if (G.blk == 0) mg_cta_cycle(m, sm, sh, bc);
     MG_BAR();
     for (int l = m.cta_from - 1; l >= 1; l--) {
+        if (TILES && l >= m.tile_from) {
+            coarse_post_tiles(m.lev[l], m.lev[l + 1], m.tile[l], 2 * m.nu_c, G.blk, G.nblk, tsm);
+            MG_BAR();
+            continue;
+        }
         coarse_half<false, true>(m.lev[l], m.lev[l + 1], 1, t0, nt);
         MG_BAR();
         for (int s = 1; s < 2 * m.nu_c; s++) {
@@ -547,8 +855,8 @@ __device__ double mg_true_residual(const Grid3 &g, const uint32_t *__restrict__ 
         face_nbrs(g, x, y, zz, i, nb);
         PhiT pn[6];
 #pragma unroll
-        for (int f = 0; f < 6; f++) pn[f] = __ldcg(phi + nb[f]);
-        const PhiT bi = __ldcg(b + i), phii = __ldcg(phi + i);
+        for (int f = 0; f < 6; f++) pn[f] = mg_ldl(phi + nb[f]);
+        const PhiT bi = mg_ldl(b + i), phii = mg_ldl(phi + i);
         const uint32_t m = __ldg(mask + i);
         if (m & SOLID_BIT) continue;
         const unsigned o = mg_open(m);
@@ -582,8 +890,8 @@ __device__ __forceinline__ void mg_pq_node(const Grid3 &g, const uint32_t *__res
     face_nbrs(g, x, y, zz, i, nb);
     float pj[6];
 #pragma unroll
-    for (int f = 0; f < 6; f++) pj[f] = FRESH ? __ldcg(z + nb[f]) : __ldcg(z + nb[f]) + beta * __ldcg(pold + nb[f]);
-    const float pi_ = FRESH ? __ldcg(z + i) : __ldcg(z + i) + beta * __ldcg(pold + i);
+    for (int f = 0; f < 6; f++) pj[f] = FRESH ? mg_ldl(z + nb[f]) : mg_ldl(z + nb[f]) + beta * mg_ldl(pold + nb[f]);
+    const float pi_ = FRESH ? mg_ldl(z + i) : mg_ldl(z + i) + beta * mg_ldl(pold + i);
     const uint32_t mk = __ldg(mask + i);
     const unsigned o = mg_open(mk);
     live = !(mk & SOLID_BIT);
@@ -673,7 +981,7 @@ __device__ float mg_update_pass(const Grid3 &g, const uint32_t *__restrict__ mas
     return rr;
 }
 
-template <typename S, typename R, typename PhiT>
+template <typename S, typename R, typename PhiT, bool TILES>
 __device__ void mg_solve(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const MgGrid &G, float *mg_sm, double *sh,
                          double *bc)
 {
@@ -727,7 +1035,7 @@ __device__ void mg_solve(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const M
     double rz_old = 1.0;
     while (!converged && it < limit) {
         double rzb = 0.0, rz;
-        if (!mg_vcycle(a, m, G, bar_k, mg_sm, sh, bc, rzb)) return;
+        if (!mg_vcycle<S, R, PhiT, TILES>(a, m, G, bar_k, mg_sm, sh, bc, rzb)) return;
         if (!reduce(rzb, rz)) return;
         if (!(rz > 0.0)) break;
         const float beta = fresh ? 0.f : (float)(rz / rz_old);
@@ -781,7 +1089,7 @@ __global__ void __launch_bounds__(MG_THREADS, 1) poisson_mg_kernel(StepArgs<S, R
     extern __shared__ float mg_sm[];  // block 0: the levels it handles alone
     const MgGrid G{(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x), (int)gridDim.x,
                    (int)blockIdx.x, a.barrier};
-    mg_solve(a, m, G, mg_sm, sh, bc);
+    mg_solve<S, R, PhiT, true>(a, m, G, mg_sm, sh, bc);
 }
 
 // Batched form: block b solves replica block_rep[b] together with the other
@@ -797,7 +1105,7 @@ __global__ void __launch_bounds__(MG_BATCH_THREADS, 1)
     const int r = pb.block_rep[blockIdx.x];
     const int lb = pb.block_local[blockIdx.x], nb = pb.rep_blocks[r];
     const MgGrid G{(int)(lb * blockDim.x + threadIdx.x), (int)(nb * blockDim.x), nb, lb, bars + 4 * r};
-    mg_solve(reps[r], mgs[r], G, mg_sm, sh, bc);
+    mg_solve<S, R, PhiT, false>(reps[r], mgs[r], G, mg_sm, sh, bc);  // replicas are not tiled
 }
 
 }  // namespace ekl

@@ -133,7 +133,12 @@ static inline MgArgs make_mg_args(const Ctx &c)
     m.nu_c = MG_NU_COARSE;
     m.coarse_sweeps = MG_COARSE_SWEEPS;
     m.inner_red = MG_INNER_RED;
-    for (int l = 0; l < MG_MAXLEV; l++) m.lev[l] = c.mg_lev[l];
+    m.tile_from = c.mg_tile_from;
+    m.tile_off = (int)c.mg_tile_off;
+    for (int l = 0; l < MG_MAXLEV; l++) {
+        m.lev[l] = c.mg_lev[l];
+        for (int k = 0; k < 3; k++) m.tile[l][k] = c.mg_tile[l][k];
+    }
     return m;
 }
 
