@@ -86,6 +86,11 @@ inline Grid3 make_grid3(int nx, int ny, int nz)
     return g;
 }
 
+// n / d for 0 <= n < 2^21 from inv = 1/d (rounded): (n + 1/2) / d lies at
+// least 1/(2d) from an integer and the two roundings move it by less than
+// 2^-23 (n + 1/2) / d, so truncation gives the floor
+__device__ __forceinline__ int tdiv(int n, float inv) { return (int)(((float)n + 0.5f) * inv); }
+
 // node coordinates; node ids fit 32 bits (lattices are capped at 2^31/64 nodes)
 __device__ __forceinline__ void coords_of(const Grid3 &g, long long i64, int &x, int &y, int &z)
 {

@@ -1118,11 +1118,11 @@ __device__ __forceinline__ bool wall_solid(const Grid3 &g, const int per[3], con
 
 // bond force on bead b from the pair (lo, lo+1); side 0: b = lo+1, side 1: b = lo
 template <typename S, typename R, typename PhiT, bool DEV, typename P>
-__device__ __forceinline__ bool bond_add(const MdArgs<S, R, PhiT, DEV> &A, const P *Rs, int b,
+__device__ __forceinline__ bool bond_add(const MdArgs<S, R, PhiT, DEV> &A, const P *Rs, const int *chain, int b,
                                          int side, R F[3])
 {
     const int lo = side == 0 ? b - 1 : b;
-    if (lo < 0 || lo + 1 >= A.b.nb || A.b.chain[lo] != A.b.chain[lo + 1]) return true;
+    if (lo < 0 || lo + 1 >= A.b.nb || chain[lo] != chain[lo + 1]) return true;
     R d[3];
     separation(A.b.g, A.b.per, &Rs[3 * lo], &Rs[3 * (lo + 1)], d);
     R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -1154,8 +1154,8 @@ __device__ bool bead_force_serial(const MdArgs<S, R, PhiT, DEV> &A, const double
     const Grid3 &g = A.b.g;
     const int nb = A.b.nb;
     F[0] = F[1] = F[2] = R(0);
-    bool ok = bond_add(A, Rs, b, 0, F);
-    ok = bond_add(A, Rs, b, 1, F) && ok;
+    bool ok = bond_add(A, Rs, A.b.chain, b, 0, F);
+    ok = bond_add(A, Rs, A.b.chain, b, 1, F) && ok;
     for (int c2 = 0; c2 < nb; c2++) {
         if (c2 == b) continue;
         int lo = c2 < b ? c2 : b, hi = c2 < b ? b : c2;
@@ -1194,7 +1194,7 @@ __device__ bool bead_force_serial(const MdArgs<S, R, PhiT, DEV> &A, const double
 // is valid in every lane.
 template <typename S, typename R, typename PhiT, bool DEV>
 __device__ bool bead_force_warp(const MdArgs<S, R, PhiT, DEV> &A, const long long *Rq, const float *Rf,
-                                const float *Rloc, const int *wlo, const int *wn, int b, R F[3],
+                                const float *Rloc, const int *wlo, const int *wn, const int *chain, int b, R F[3],
                                 const int *org, const uint32_t *bits)
 {
     const Grid3 &g = A.b.g;
@@ -1202,17 +1202,14 @@ __device__ bool bead_force_warp(const MdArgs<S, R, PhiT, DEV> &A, const long lon
     const int lane = threadIdx.x & 31;
     R f[3] = {R(0), R(0), R(0)};
     bool ok = true;
-    if (lane == 0) {
-        ok = bond_add(A, Rq, b, 0, f);
-        ok = bond_add(A, Rq, b, 1, f) && ok;
-    }
+    // the bond with b - 1 in lane 0, with b + 1 in lane 1 (one pass)
+    if (lane < 2) ok = bond_add(A, Rq, chain, b, lane, f);
     const float Lf[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
     const float cut2 = 1.2599210498948732f * (float)A.wca_sigma * (float)A.wca_sigma;
     for (int c2 = lane; c2 < nb; c2 += 32) {
         if (c2 == b) continue;
         int lo = c2 < b ? c2 : b, hi = c2 < b ? b : c2;
-        if (A.bond_kind == EKL_BOND_HARMONIC && A.b.chain[lo] == A.b.chain[hi] && hi - lo <= 1)
-            continue;
+        if (A.bond_kind == EKL_BOND_HARMONIC && chain[lo] == chain[hi] && hi - lo <= 1) continue;
         // float screen, FP64 separation only for pairs near the cut-off
         float q2 = 0.f;
         for (int c = 0; c < 3; c++) {
@@ -1236,8 +1233,10 @@ __device__ bool bead_force_warp(const MdArgs<S, R, PhiT, DEV> &A, const long lon
     // wall nodes in the scan box; coordinates relative to the cached box origin
     const int n0 = wn[3 * b], n1 = wn[3 * b + 1], n2 = wn[3 * b + 2];
     const int cells = n0 * n1 * n2;
+    const float i0 = 1.f / (float)n0, i1 = 1.f / (float)n1;
     for (int t = lane; t < cells; t += 32) {
-        const int x = wlo[3 * b] + t % n0, y = wlo[3 * b + 1] + (t / n0) % n1, z = wlo[3 * b + 2] + t / (n0 * n1);
+        const int r = tdiv(t, i0), zz = tdiv(r, i1);
+        const int x = wlo[3 * b] + t - r * n0, y = wlo[3 * b + 1] + r - zz * n1, z = wlo[3 * b + 2] + zz;
         bool in;
         if (!wall_solid(g, A.b.per, A.b.mask, x, y, z, org, bits, in)) continue;
         R d[3] = {(R)(Rloc[3 * b] - (float)(x - org[0])), (R)(Rloc[3 * b + 1] - (float)(y - org[1])),
@@ -1292,7 +1291,7 @@ __device__ __forceinline__ void scan_bounds_q(long long rq, long long rcq, int o
 // Reduced-precision instantiations: one warp per bead.
 template <typename R> inline size_t md_smem_bytes(int nb)
 {
-    return (size_t)nb * (3 * sizeof(double) + 27 * sizeof(R) + 6 * sizeof(float) + 9 * sizeof(int) +
+    return (size_t)nb * (3 * sizeof(double) + 27 * sizeof(R) + 6 * sizeof(float) + 10 * sizeof(int) +
                          WALL_WORDS * sizeof(uint32_t));
 }
 
@@ -1323,18 +1322,21 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
     int *worg = (int *)(Rloc + 3 * nb);
     int *wlo = worg + 3 * nb;
     int *wn = wlo + 3 * nb;
-    uint32_t *wbits = (uint32_t *)(wn + 3 * nb);
+    int *sChain = wn + 3 * nb;  // chain ids (read every sub-step)
+    uint32_t *wbits = (uint32_t *)(sChain + nb);
     __shared__ int sBad;
     if (threadIdx.x == 0) sBad = 0;
-    // moments at the patch nodes
-    for (int k = threadIdx.x; k < pc; k += blockDim.x) {
+    // moments at the patch nodes: thread (k, s) takes species s of node k,
+    // thread (k, 3) the potential gradient (one memory round trip each)
+    for (int t = threadIdx.x; t < 4 * pc; t += blockDim.x) {
+        const int k = t >> 2, s = t & 3;
         long long i = B.patch_node[k];
         uint32_t m = a.mask[i];
         int x, y, z;
         coords_of(g, i, x, y, z);
         Nbr nbr = make_nbr(g, x, y, z);
         R *out = B.patch_mom + (long long)k * 15;
-        for (int s = 0; s < NS; s++) {
+        if (s < NS) {
             R v[Q];
             pull19<S, R>(a.fin, g.N, s, i, m, nbr, v);
             R n = R(0), jx = R(0), jy = R(0), jz = R(0);
@@ -1353,14 +1355,15 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
             out[3 + 3 * s + 0] = jx / n;
             out[3 + 3 * s + 1] = jy / n;
             out[3 + 3 * s + 2] = jz / n;
+        } else {
+            R gr[3];
+            int olo[3], ohi[3];
+            closed_faces(g, a.per, x, y, z, olo, ohi);
+            node_gradient<R, PhiT>(a.phi, a.wall_share, a.c4, i, m, nbr, olo, ohi, gr);
+            out[12] = gr[0];
+            out[13] = gr[1];
+            out[14] = gr[2];
         }
-        R gr[3];
-        int olo[3], ohi[3];
-        closed_faces(g, a.per, x, y, z, olo, ohi);
-        node_gradient<R, PhiT>(a.phi, a.wall_share, a.c4, i, m, nbr, olo, ohi, gr);
-        out[12] = gr[0];
-        out[13] = gr[1];
-        out[14] = gr[2];
     }
     for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
         const double r = B.Rb[t];
@@ -1369,7 +1372,7 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
         Rf[t] = (float)r;
         sV[t] = B.Vb[t];
     }
-    for (int t = threadIdx.x; t < WALL_WORDS * nb; t += blockDim.x) wbits[t] = 0u;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) sChain[t] = B.chain[t];
     for (int t = threadIdx.x; t < 9 * nb; t += blockDim.x) sAcc[t] = R(0);
     __syncthreads();
     const double rcw = 1.122462048309373 * (double)A.wall_sigma;  // 2^(1/6) sigma
@@ -1383,28 +1386,45 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
     }
     __syncthreads();
     {
+        // one word (32 cells of one bead's block) per warp and round, built by
+        // a ballot; WALL_ROUNDS rounds' link words are loaded before any is used
+        constexpr int WALL_ROUNDS = 8;
         const int dims[3] = {g.nx, g.ny, g.nz};
         const int cells = WALL_BOX * WALL_BOX * WALL_BOX;
-        for (int t = threadIdx.x; t < nb * cells; t += blockDim.x) {
-            int bb = t / cells, cell = t - bb * cells;
-            int ox = cell % WALL_BOX, oy = (cell / WALL_BOX) % WALL_BOX, oz = cell / (WALL_BOX * WALL_BOX);
-            int q[3] = {worg[3 * bb] + ox, worg[3 * bb + 1] + oy, worg[3 * bb + 2] + oz};
-            bool in = true;
-            for (int c = 0; c < 3; c++) {
-                if (B.per[c]) {
-                    // the block reaches at most WALL_BOX nodes beyond the box
-                    if (q[c] >= dims[c]) q[c] -= dims[c];
-                    else if (q[c] < 0) q[c] += dims[c];
-                    if (q[c] < 0 || q[c] >= dims[c]) {
-                        q[c] %= dims[c];
-                        if (q[c] < 0) q[c] += dims[c];
+        const int words = nb * WALL_WORDS;
+        const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int w0 = wid; w0 < words; w0 += WALL_ROUNDS * nw) {
+            bool solid[WALL_ROUNDS];
+#pragma unroll
+            for (int u = 0; u < WALL_ROUNDS; u++) {
+                const int w = w0 + u * nw;
+                solid[u] = false;
+                const int bb = w / WALL_WORDS, cell = (w - bb * WALL_WORDS) * 32 + ln;
+                if (w >= words || cell >= cells) continue;
+                const int ox = cell % WALL_BOX, oy = (cell / WALL_BOX) % WALL_BOX, oz = cell / (WALL_BOX * WALL_BOX);
+                int q[3] = {worg[3 * bb] + ox, worg[3 * bb + 1] + oy, worg[3 * bb + 2] + oz};
+                bool in = true;
+                for (int c = 0; c < 3; c++) {
+                    if (B.per[c]) {
+                        // the block reaches at most WALL_BOX nodes beyond the box
+                        if (q[c] >= dims[c]) q[c] -= dims[c];
+                        else if (q[c] < 0) q[c] += dims[c];
+                        if (q[c] < 0 || q[c] >= dims[c]) {
+                            q[c] %= dims[c];
+                            if (q[c] < 0) q[c] += dims[c];
+                        }
+                    } else if (q[c] < 0 || q[c] >= dims[c]) {
+                        in = false;
                     }
-                } else if (q[c] < 0 || q[c] >= dims[c]) {
-                    in = false;
                 }
+                if (in) solid[u] = a.mask[(long long)q[0] + (long long)g.nx * (q[1] + (long long)g.ny * q[2])] & SOLID_BIT;
             }
-            if (in && (a.mask[(long long)q[0] + (long long)g.nx * (q[1] + (long long)g.ny * q[2])] & SOLID_BIT))
-                atomicOr(&wbits[bb * WALL_WORDS + (cell >> 5)], 1u << (cell & 31));
+#pragma unroll
+            for (int u = 0; u < WALL_ROUNDS; u++) {
+                const int w = w0 + u * nw;  // warp-uniform
+                const unsigned word = __ballot_sync(0xffffffffu, solid[u]);
+                if (ln == 0 && w < words) wbits[w] = word;
+            }
         }
     }
     // interpolation: one thread per bead, entries in slot order k
@@ -1439,6 +1459,17 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
     const R dt = R(1) / (R)nsub;
     const bool noise = A.bead_kT > R(0) && !(a.flags & EKL_NO_BEAD_NOISE);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    // Reduced-precision instantiations: with one bead per warp and at most
+    // 32 sub-steps, lane s draws the sub-step-s noise of its warp's bead up
+    // front (the draws are independent of the dynamics)
+    const bool pre = !SERIAL && noise && nb <= nwarps && nsub <= 32;
+    float xpre[3] = {0.f, 0.f, 0.f};
+    if (pre && warp < nb && lane < nsub) {
+        uint32_t ctr[4] = {(uint32_t)warp, (uint32_t)lane | (1u << 24), (uint32_t)A.step,
+                           (uint32_t)((uint64_t)A.step >> 32)};
+        philox4x32_10(ctr, A.key0, A.key1);
+        for (int c = 0; c < 3; c++) xpre[c] = unit_variate_f32(ctr[c]);
+    }
     for (int sub = 0; sub < nsub; sub++) {
         // force from the positions at the start of the sub-step, then the
         // bead's own velocity and drag update (positions move after the barrier)
@@ -1448,28 +1479,37 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
             R F[3];
             bool okf;
             if constexpr (SERIAL) okf = bead_force_serial(A, Rs, b, F, &worg[3 * b], &wbits[b * WALL_WORDS]);
-            else okf = bead_force_warp(A, Rq, Rf, Rloc, wlo, wn, b, F, &worg[3 * b], &wbits[b * WALL_WORDS]);
+            else okf = bead_force_warp(A, Rq, Rf, Rloc, wlo, wn, sChain, b, F, &worg[3 * b], &wbits[b * WALL_WORDS]);
             if (!okf) sBad = 1;
-            if (!SERIAL && lane != 0) continue;
             R xi_[3] = {R(0), R(0), R(0)};
             if (noise) {
-                uint32_t ctr[4] = {(uint32_t)b, (uint32_t)sub | (1u << 24), (uint32_t)A.step,
-                                   (uint32_t)((uint64_t)A.step >> 32)};
-                philox4x32_10(ctr, A.key0, A.key1);
-                for (int c = 0; c < 3; c++) {
-                    if constexpr (SERIAL) xi_[c] = unit_variate<R>(ctr[c]);
-                    else xi_[c] = unit_variate_f32(ctr[c]);
+                if (pre) {
+                    for (int c = 0; c < 3; c++) xi_[c] = __shfl_sync(0xffffffffu, xpre[c], sub);
+                } else {
+                    uint32_t ctr[4] = {(uint32_t)b, (uint32_t)sub | (1u << 24), (uint32_t)A.step,
+                                       (uint32_t)((uint64_t)A.step >> 32)};
+                    philox4x32_10(ctr, A.key0, A.key1);
+                    for (int c = 0; c < 3; c++) {
+                        if constexpr (SERIAL) xi_[c] = unit_variate<R>(ctr[c]);
+                        else xi_[c] = unit_variate_f32(ctr[c]);
+                    }
                 }
             }
+            // the serial instantiation updates the three components in turn;
+            // the warp instantiation updates component `lane` in lanes 0-2
+            const int c0 = SERIAL ? 0 : lane, c1 = SERIAL ? 3 : lane + 1;
+            if (c0 >= 3) continue;
             const R *gam = &sGam[3 * b];
             R gtot = gam[0] + gam[1] + gam[2];
             R amp = noise ? sqrt(R(2) * gtot * A.bead_kT / dt) : R(0);
             R qb = B.qb[b];
-            for (int c = 0; c < 3; c++) {
+            for (int c = c0; c < c1; c++) {
+                const R Fc = c == 0 ? F[0] : c == 1 ? F[1] : F[2];
+                const R xc = c == 0 ? xi_[0] : c == 1 ? xi_[1] : xi_[2];
                 R Fe = -qb * Consts<R>::KT * sG[3 * b + c] + qb * Consts<R>::KT * a.E[c];
                 R num = A.mass * sV[3 * b + c] / dt;
                 for (int s2 = 0; s2 < NS; s2++) num += gam[s2] * sU[9 * b + 3 * s2 + c];
-                num += F[c] + Fe + amp * xi_[c];
+                num += Fc + Fe + amp * xc;
                 R Vn = num / (A.mass / dt + gtot);
                 for (int s2 = 0; s2 < NS; s2++)
                     sAcc[9 * b + 3 * s2 + c] += dt * (-gam[s2] * (sU[9 * b + 3 * s2 + c] - Vn));

@@ -427,10 +427,6 @@ __device__ __forceinline__ TileSm tile_sm(float *sm, int Rx, int Ry, int Rz)
     return T;
 }
 
-// n / d for 0 <= n < 2^21 from inv = 1/d (rounded): (n + 1/2) / d lies at
-// least 1/(2d) from an integer and the two roundings move it by less than
-// 2^-23 (n + 1/2) / d, so truncation gives the floor
-__device__ __forceinline__ int tdiv(int n, float inv) { return (int)(((float)n + 0.5f) * inv); }
 // region index k -> (a, b, c) for rows of nx cells and planes of ny rows
 __device__ __forceinline__ void tsplit(int k, int nx, int ny, float inx, float iny, int &a, int &b, int &c)
 {
