@@ -1374,17 +1374,18 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
     }
     for (int t = threadIdx.x; t < nb; t += blockDim.x) sChain[t] = B.chain[t];
     for (int t = threadIdx.x; t < 9 * nb; t += blockDim.x) sAcc[t] = R(0);
-    __syncthreads();
     const double rcw = 1.122462048309373 * (double)A.wall_sigma;  // 2^(1/6) sigma
     const long long rcq = rcw < 16.0 ? __double2ll_rn(rcw * PHI_SCALE) : (16ll << 40);
+    int bad0 = 0;  // raised into sBad after the barrier that orders its reset
     for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
         const double r = B.Rb[t];
         worg[t] = fabs(r) < 1e6 ? (int)floor(r) - WALL_BOX / 2 + 1 : 0;
         int bad = 0;
         scan_bounds(r, rcw, worg[t], wlo[t], wn[t], Rloc[t], bad);
-        if (bad) sBad = 1;
+        bad0 |= bad;
     }
     __syncthreads();
+    if (bad0) sBad = 1;
     {
         // one word (32 cells of one bead's block) per warp and round, built by
         // a ballot; WALL_ROUNDS rounds' link words are loaded before any is used
@@ -1427,31 +1428,54 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
             }
         }
     }
-    // interpolation: one thread per bead, entries in slot order k
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        R nR[NS] = {R(0), R(0), R(0)}, uR[NS][3], gR[3] = {R(0), R(0), R(0)};
-        for (int s = 0; s < NS; s++)
-            for (int c = 0; c < 3; c++) uR[s][c] = R(0);
-        for (int k = 0; k < 8; k++) {
-            R w = B.entry_w[b * 8 + k];
-            if (w == R(0)) continue;
-            int slot = B.entry_slot[b * 8 + k];
-            const R *mo = B.patch_mom + (long long)slot * 15;
-            for (int s = 0; s < NS; s++) {
-                nR[s] += w * mo[s];
-                for (int c = 0; c < 3; c++) uR[s][c] += w * mo[3 + 3 * s + c];
-            }
-            for (int c = 0; c < 3; c++) gR[c] += w * mo[12 + c];
-        }
-        R ntot = nR[0] + nR[1] + nR[2];
+    // interpolation.  FP64: one thread per bead, entries in slot order k (the
+    // oracle's order).  Reduced precision: eight lanes per bead, one entry
+    // each (all loads in flight at once), summed over the lanes by shuffles.
+    auto interp_out = [&](int b, const R *v) {  // v: n^a (3), u^a (9), grad phi (3)
+        const R ntot = v[0] + v[1] + v[2];
         for (int s = 0; s < NS; s++) {
-            sGam[3 * b + s] = (a.flags & EKL_GAMMA_LITERAL) ? A.xi : A.xi * nR[s] / ntot;
-            for (int c = 0; c < 3; c++) sU[9 * b + 3 * s + c] = uR[s][c];
+            sGam[3 * b + s] = (a.flags & EKL_GAMMA_LITERAL) ? A.xi : A.xi * v[s] / ntot;
+            for (int c = 0; c < 3; c++) sU[9 * b + 3 * s + c] = v[3 + 3 * s + c];
         }
-        R qb = B.qb[b];
+        const R qb = B.qb[b];
         for (int c = 0; c < 3; c++) {
-            sG[3 * b + c] = gR[c];
-            if (fabs(qb * gR[c]) >= R(1)) atomicOr(a.status, ST_CFL);
+            sG[3 * b + c] = v[12 + c];
+            if (fabs(qb * v[12 + c]) >= R(1)) atomicOr(a.status, ST_CFL);
+        }
+    };
+    if constexpr (SERIAL) {
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            R v[15];
+            for (int j = 0; j < 15; j++) v[j] = R(0);
+            for (int k = 0; k < 8; k++) {
+                R w = B.entry_w[b * 8 + k];
+                if (w == R(0)) continue;
+                int slot = B.entry_slot[b * 8 + k];
+                const R *mo = B.patch_mom + (long long)slot * 15;
+                for (int j = 0; j < 15; j++) v[j] += w * mo[j];
+            }
+            interp_out(b, v);
+        }
+    } else {
+        const int total = (8 * nb + 31) & ~31;  // whole warps: the shuffles below are warp-wide
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            const int b = t >> 3, k = t & 7;
+            R v[15];
+#pragma unroll
+            for (int j = 0; j < 15; j++) v[j] = R(0);
+            if (b < nb) {
+                const R w = B.entry_w[b * 8 + k];
+                if (w != R(0)) {
+                    const R *mo = B.patch_mom + (long long)B.entry_slot[b * 8 + k] * 15;
+#pragma unroll
+                    for (int j = 0; j < 15; j++) v[j] = w * mo[j];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 15; j++)
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+            if (k == 0 && b < nb) interp_out(b, v);
         }
     }
     __syncthreads();
@@ -1557,12 +1581,22 @@ __device__ void bead_md_body(const MdArgs<S, R, PhiT, DEV> &A)
     for (int k = threadIdx.x; k < pc; k += blockDim.x) {
         R acc[9];
         for (int t = 0; t < 9; t++) acc[t] = R(0);
-        for (int t = B.slot_first[k]; t < B.slot_first[k + 1]; t++) {
-            int e = B.sorted_entry[t];
-            R w = B.entry_w[e];
-            if (w == R(0)) continue;
-            int bb = e >> 3;
-            for (int u = 0; u < 9; u++) acc[u] += sAcc[bb * 9 + u] * w;
+        const int t0 = B.slot_first[k], t1 = B.slot_first[k + 1];
+        // entries in rounds of eight: their ids, then their weights, loaded
+        // before any is summed (in the same order as one at a time)
+        for (int tb = t0; tb < t1; tb += 8) {
+            int e[8];
+            R w[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) e[j] = tb + j < t1 ? B.sorted_entry[tb + j] : -1;
+#pragma unroll
+            for (int j = 0; j < 8; j++) w[j] = e[j] >= 0 ? B.entry_w[e[j]] : R(0);
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                if (w[j] == R(0)) continue;
+                const int bb = e[j] >> 3;
+                for (int u = 0; u < 9; u++) acc[u] += sAcc[bb * 9 + u] * w[j];
+            }
         }
         const R *mo = B.patch_mom + (long long)k * 15;
         for (int s = 0; s < NS; s++)
