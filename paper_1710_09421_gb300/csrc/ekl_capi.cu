@@ -122,6 +122,7 @@ void release(Ctx &c)
     dev_free(c, c.b, 0);
     dev_free(c, c.phi, 0);
     dev_free(c, c.part_charge, 0);
+    dev_free(c, c.part_charge_q, 0);
     dev_free(c, c.part_mass, 0);
     dev_free(c, c.part_pois, 0);
     dev_free(c, c.barrier, 0);
@@ -812,6 +813,7 @@ static int create_handle(const ekl_params *P, void *stream, ekl_handle **out, bo
     c.b = A(N * ps);
     c.phi = A(N * ps);
     c.part_charge = (double *)A((size_t)c.charge_blocks * (CHARGE_THREADS / 32) * sizeof(double));
+    c.part_charge_q = (long long *)A((size_t)c.charge_blocks * sizeof(long long));
     c.part_mass = (double *)A((size_t)((N + 255) / 256) * NS * sizeof(double));
     c.part_pois = (double *)A((size_t)c.pois_blocks * sizeof(double));
     c.barrier = (unsigned *)A(4 * sizeof(unsigned));

@@ -84,6 +84,7 @@ struct Ctx {
     void *b;           // PhiT[N]
     void *phi;         // PhiT[N]
     double *part_charge;  // [charge blocks]
+    long long *part_charge_q;  // [charge blocks] fixed-point paths: exact sum of rho * 2^40
     double *part_mass;    // [mass blocks][3] (filled on request)
     double *part_pois;    // [poisson blocks][2]
     unsigned *barrier;    // {count, generation, abort}

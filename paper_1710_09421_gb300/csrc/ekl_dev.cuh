@@ -365,6 +365,35 @@ __device__ __forceinline__ double sum_partials(const double *p, int n, double *s
     return sh[0];
 }
 
+// The same for 64-bit integer partials (exact).
+__device__ __forceinline__ long long sum_partials_ll(const long long *p, int n)
+{
+    __shared__ long long s_ll;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        long long v = 0;
+        for (int k = threadIdx.x; k < n; k += 32) v += __ldcg(p + k);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) s_ll = v;
+    }
+    __syncthreads();
+    return s_ll;
+}
+
+// A uniform number in [0, 1) fixed per node index (integer hash: multiply by
+// the golden-ratio constant, then xor-shift / multiply mixing rounds)
+__device__ __forceinline__ float node_uniform(long long i)
+{
+    uint32_t h = (uint32_t)i * 0x9E3779B1u;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return (float)(h >> 8) * (1.0f / 16777216.0f);
+}
+
 // Residual test of an iteration: warp 0 sums the block partials (fixed
 // order), thread 0 compares sqrt(sum) with tol * bnorm and broadcasts the
 // result; every thread of the block must call it.

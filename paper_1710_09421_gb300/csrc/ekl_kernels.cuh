@@ -50,6 +50,7 @@ template <typename S, typename R, typename PhiT> struct StepArgs {
     const R *patch_f;
     // reductions / status
     double *part_charge;
+    long long *part_charge_q;  // fixed-point paths: exact sum of rho * 2^40 per block
     double *part_mass;
     double *part_pois;
     unsigned *barrier;
@@ -202,6 +203,21 @@ __device__ __forceinline__ void charge_body(const StepArgs<S, R, PhiT> &a, long 
     else t = warp_sum_ff_lane0((float)mine);
     t = block_sum_lanes0(t, csh);
     if (threadIdx.x == 0) a.part_charge[blk] = t;
+    if constexpr (!(((PhiT)0.5) != 0)) {
+        // the fixed-point source's exact total: sum of rho * 2^40 as the
+        // Poisson launch rounds it (integer, order-independent)
+        __shared__ long long qsh[CHARGE_THREADS / 32];
+        long long qv = (i < g.N) ? float_to_ll((float)mine * (float)PHI_SCALE) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) qv += __shfl_xor_sync(0xffffffffu, qv, o);
+        if ((threadIdx.x & 31) == 0) qsh[threadIdx.x >> 5] = qv;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long s = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += qsh[w];
+            a.part_charge_q[blk] = s;
+        }
+    }
 }
 
 template <typename S, typename R, typename PhiT, bool DEV>
@@ -302,7 +318,26 @@ __device__ double form_source(const StepArgs<S, R, PhiT> &a, int tid, int nthr, 
     const double csum = sum_partials(a.part_charge, a.nblocks_charge, bc);
     const double nfl = a.n_fluid;
     const double mean = nfl > 0 ? csum / nfl : 0.0;
-    const long long mean_q = __double2ll_rn(mean * PHI_SCALE);
+    // fixed point: the exact total S of rho * 2^40 over the fluid nodes,
+    // S / n = mean_lo + frac with 0 <= frac < 1, and C = c4 frac split into
+    // integer and fraction
+    long long mean_lo = 0, C_int = 0;
+    float C_frac = 0.f;
+    if constexpr (!(((PhiT)0.5) != 0)) {
+        const long long S = sum_partials_ll(a.part_charge_q, a.nblocks_charge);
+        const long long n = (long long)nfl;
+        if (n > 0) {
+            mean_lo = S / n;
+            long long rem = S - mean_lo * n;
+            if (rem < 0) {
+                mean_lo -= 1;
+                rem += n;
+            }
+            const double C = (double)(float)a.c4 * ((double)rem / (double)n);
+            C_int = (long long)floor(C);
+            C_frac = (float)(C - (double)C_int);
+        }
+    }
     double bl = 0.0;
     float blf = 0.f;
     for (long long i = tid; i < a.g.N; i += nthr) {
@@ -315,22 +350,30 @@ __device__ double form_source(const StepArgs<S, R, PhiT> &a, int tid, int nthr, 
             bv = (PhiT)v;
             bl += v * v;
         } else {
-            // Fixed point throughout, without FP64 per node: rho * 2^40 is
+            // Fixed point throughout, without FP64 per node.  rho * 2^40 is
             // exact (a power-of-two scaling of an FP32 value; rounded to the
-            // nearest 2^-40 below 2^-17), the mean is subtracted as an integer,
-            // and c4 d is formed as an unevaluated float pair (the product's
-            // rounding error recovered by an FMA) and rounded to the nearest
-            // integer.  Most fluid nodes carry nearly the same small charge, so
-            // an FP32 rounding of c4 (rho - mean) would be correlated over the
-            // lattice and leave a net source that a periodic or all-Neumann
-            // problem cannot absorb (it floored the residual near 1e-8).
-            const long long d = float_to_ll((float)a.rho[i] * (float)PHI_SCALE) - mean_q;
+            // nearest 2^-40 below 2^-17) and its total S over the fluid nodes
+            // comes exactly from the charge pass; d = q - floor(S / n) is an
+            // integer, c4 d is formed as an unevaluated float pair (the
+            // product's rounding error recovered by an FMA), the fractional
+            // mean enters as C = c4 frac, and x = c4 d - C is rounded to an
+            // integer stochastically, floor(x + u) with u uniform per node.
+            // The source then sums to zero up to a random walk of unit
+            // roundings.  Any rounding shared by many nodes (the mean rounded
+            // once, or the same rounding of c4 d on the many nodes that carry
+            // the same charge) would instead leave a net source of up to half
+            // a unit per node, which a periodic or all-Neumann problem cannot
+            // absorb: on 33.5 M nodes it stalled CG near a relative residual
+            // of 1e-6.
+            const long long d = float_to_ll((float)a.rho[i] * (float)PHI_SCALE) - mean_lo;
             const float d_hi = ll_to_float(d);
             const float d_lo = ll_to_float(d - float_to_ll(d_hi));  // exact remainder
             const float c4f = (float)a.c4;
             const float p = c4f * d_hi;
             const float lo = fmaf(c4f, d_hi, -p) + c4f * d_lo;
-            bv = float_to_ll(p) + float_to_ll(lo);
+            const float fp = floorf(p), fl = floorf(lo);
+            const float F = (p - fp) + (lo - fl) - C_frac + node_uniform(i);
+            bv = float_to_ll(fp) + float_to_ll(fl) - C_int + (long long)floorf(F);
             const float v = ll_to_float(bv) * (float)PHI_INV;
             blf += v * v;
         }

@@ -42,6 +42,7 @@ static StepArgs<S, R, PhiT> make_args(Ctx &c, int parity = -1)
     a.patch_q = (const R *)c.patch_q;
     a.patch_f = (const R *)c.patch_f;
     a.part_charge = c.part_charge;
+    a.part_charge_q = c.part_charge_q;
     a.part_mass = c.part_mass;
     a.part_pois = c.part_pois;
     a.barrier = c.barrier;

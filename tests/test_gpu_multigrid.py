@@ -145,3 +145,32 @@ def test_mg_tiled_coarse_smoothing_equals_grid_wide(case):
     assert sa["poisson_iters"] == sb["poisson_iters"] and sa["poisson_res"] == sb["poisson_res"]
     for k in ("n", "phi"):
         assert np.array_equal(fa[k], fb[k]), k
+
+
+@pytest.mark.parametrize("flags", [MG, 0], ids=["multigrid", "sor"])
+def test_fixed_point_source_has_no_net_charge(flags):
+    """A periodic 64^3 box whose only charge is one node's cation excess of
+    610349 * 2^17 fixed-point units (2^-40 e; 0.073 e), so that the
+    neutralising mean is an odd number of half units: the source carries
+    minus that on 262 143 nodes with the same charge.  Rounding the mean, or
+    the product c4 (rho - mean), the same way on all of them leaves a net
+    source of up to half a unit per node, a null-space component that no
+    solver on a periodic box can remove: that form stalled at a relative
+    residual of 3e-4.  (The excess is large enough for the 2^-40 resolution
+    of the potential: a 0.001 e excess floors near 2e-7 either way.)  The
+    FP32 path must converge, and its potential must meet the FP64 oracle's
+    equation to the tolerance plus the FP32 rounding of 4 pi l_B."""
+    n = 64
+    wl = box(n, n, n, n=(1.0, 0.01, 0.01), poisson_tol=1e-8, precision="f32", flags=flags,
+             poisson_max_iter=400 if flags else 20000)
+    wl.n_init[1][17, 33, 9] += 610349 * 2.0 ** -23
+    sim = E.Simulation(wl)
+    rc = sim.step(1)
+    st = sim.stats()
+    assert rc >= 0 and not (rc & E.EKL_WARN_NOCONV), (rc, st)
+    assert st["poisson_res"] <= 1e-8, st
+    _, phi, _ = sim.get_state()
+    sim.close()
+    ref = oracle.Sim(wl.replace(precision="f64", poisson_tol=1e-12, flags=0), threads=8)
+    assert ref.step(1) >= 0
+    assert ref.poisson_residual(ref.last_rho(), phi) <= 1e-7
