@@ -498,27 +498,18 @@ def run_ours(args):
 
 
 def learned_vs_plain(E, wl, args, sraw, collect_steps=60, ncrops=8, crop=16, train_iters=400,
-                     compare_steps=40):
-    """Train the warm-start network on crops the solver records on this
-    workload (a separate run with another seed), then time the same steps
-    with and without it from identical states.  Both runs iterate to the same
+                     compare_steps=40, train_wl=None, trained=None):
+    """Train the warm-start network on crops the solver records on train_wl
+    (default: this workload; a separate run with another seed), or take a
+    trained (weights, scales, info), then time the same steps with and
+    without it from identical states.  Both runs iterate to the same
     residual tolerance; only sweeps and time are compared."""
-    import numpy as np
     import torch
-    from paper_1710_09421_gb300 import warmstart as WS
 
-    t0 = time.perf_counter()
-    src = E.Simulation(wl.replace(seed=wl.seed + 101), precision=args.precision, stream=sraw)
-    src.step(args.warmup)
-    crops = src.collect(collect_steps, crop=crop, ncrops=ncrops, seed=7)
-    src.close()
-    t1 = time.perf_counter()
-    w, scales, curve = WS.train(crops, iters=train_iters, batch=8, lr=2e-3, seed=0)
-    t2 = time.perf_counter()
-    out = {"crops": int(len(crops)), "crop": crop, "collect_s": round(t1 - t0, 3),
-           "train_s": round(t2 - t1, 3), "train_iters": train_iters,
-           "rel_loss_first": round(float(np.mean(curve[:20])), 4),
-           "rel_loss_last": round(float(np.mean(curve[-20:])), 4)}
+    if trained is None:
+        trained = train_warmstart(E, train_wl or wl, args, sraw, collect_steps, ncrops, crop, train_iters)
+    w, scales, info = trained
+    out = dict(info)
     for name, use in (("plain", False), ("learned", True)):
         sim = E.Simulation(wl, precision=args.precision, stream=sraw)
         sim.step(args.warmup)
@@ -545,6 +536,56 @@ def learned_vs_plain(E, wl, args, sraw, collect_steps=60, ncrops=8, crop=16, tra
     out["sweeps_saved_frac"] = round(1 - out["learned"]["poisson_sweeps_per_step"]
                                      / max(out["plain"]["poisson_sweeps_per_step"], 1e-9), 4)
     return out
+
+
+def train_warmstart(E, wl, args, sraw, collect_steps, ncrops, crop, train_iters):
+    """Crops recorded by the solver on wl with another seed, and the network
+    trained on them: (weights, scales, info)."""
+    import numpy as np
+    from paper_1710_09421_gb300 import warmstart as WS
+
+    t0 = time.perf_counter()
+    src = E.Simulation(wl.replace(seed=wl.seed + 101), precision=args.precision, stream=sraw)
+    src.step(args.warmup)
+    crops = src.collect(collect_steps, crop=crop, ncrops=ncrops, seed=7)
+    src.close()
+    t1 = time.perf_counter()
+    w, scales, curve = WS.train(crops, iters=train_iters, batch=8, lr=2e-3, seed=0)
+    t2 = time.perf_counter()
+    info = {"crops": int(len(crops)), "crop": crop, "collect_s": round(t1 - t0, 3),
+            "train_s": round(t2 - t1, 3), "train_iters": train_iters,
+            "rel_loss_first": round(float(np.mean(curve[:20])), 4),
+            "rel_loss_last": round(float(np.mean(curve[-20:])), 4)}
+    return w, scales, info
+
+
+def run_learned(args):
+    """The learned warm start on the 128x128x256 pore (radius 6, N = 64,
+    salt 0.005): the network is trained on 20 000 crops that the solver
+    records on the 64x64x128 pore (radius 4, N = 32) under another seed,
+    then the same steps run with and without it from identical states, to
+    the same residual, with the paper's Chebyshev SOR and with multigrid."""
+    import torch
+
+    import paper_1710_09421_gb300 as E
+    from paper_1710_09421_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    E.load()
+    stream = torch.cuda.Stream()
+    sraw = stream.cuda_stream
+    wl = W.config_learned(args.precision)
+    train_wl = W.config_pore_fp32().replace(flags=W.FLAG_POISSON_MG)
+    trained = train_warmstart(E, train_wl, args, sraw, collect_steps=250, ncrops=80, crop=16,
+                              train_iters=800)
+    line = {"metric": "learned vs plain Poisson: iterations and steps/s at the same residual",
+            "unit": "steps/s", "data": "synthetic", "dtype": args.precision,
+            "config": {"workload": "pore_128x128x256_r6_N64", "nodes": wl.n_nodes,
+                       "poisson_tol": wl.poisson_tol, "trained_on": "pore_64x64x128_r4_N32, seed + 101"}}
+    for name, flags in (("chebyshev-sor", 0), ("multigrid-CG", W.FLAG_POISSON_MG)):
+        line[name] = learned_vs_plain(E, wl.replace(flags=wl.flags | flags), args, sraw,
+                                      compare_steps=max(10, args.steps // 10), trained=trained)
+    print(json.dumps(line))
 
 
 def main():
@@ -575,6 +616,8 @@ def main():
         run_batch(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

@@ -411,6 +411,14 @@ def config_pore_fp32():
     return translocation().replace(rho_jacobi=0.9999, poisson_check_every=4)
 
 
+def config_learned(precision="f32"):
+    """128x128x256 pore of radius 6 (12 nodes across, as in the paper), N = 64,
+    salt 0.005, membrane 8 thick centred, E_z = 5e-3: the learned warm-start
+    comparison."""
+    return translocation(nx=128, ny=128, nz=256, membrane=(124, 131), radius=6.0, salt=0.005,
+                         n_beads=64, precision=precision)
+
+
 def config_precision_sweep(precision="f32"):
     """256x256x512 box, membrane 16 thick centred at z=256, pore radius 8,
     salt 0.01, E_z = 2e-3, N = 128."""
