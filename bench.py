@@ -37,8 +37,8 @@ FALLBACK_HBM_GBS = 6800.0
 # each valid only while the source files it was taken on are unchanged
 PROFILED = {
     # kernel: (sha256 prefix of its source files, dram read + write bytes per launch)
-    "lb_fused_kernel": ("9e03f41f3a4eef12", 119364608 + 65307904),
-    "poisson_mg_kernel": ("6dca54ffcc0e69af", 20425984 + 953856),
+    "lb_fused_kernel": ("64c6980a96cc13dc", 119372032 + 65814272),
+    "poisson_mg_kernel": ("18df217dc0e82b21", 20447744 + 888320),
 }
 KERNEL_SOURCES = {
     "lb_fused_kernel": ("ekl_kernels.cuh", "ekl_dev.cuh"),
