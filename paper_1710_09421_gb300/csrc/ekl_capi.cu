@@ -49,7 +49,7 @@ struct PrecOps {
     int (*get_state)(Ctx &, double *, double *);
     int (*set_state)(Ctx &, const double *, const double *);
     int (*pois_blocks)();
-    int (*mg_blocks)(size_t);
+    int (*mg_blocks)(size_t, int);
     int (*mass)(Ctx &);
     int (*mg_batch_blocks)(size_t);
     int (*current)(Ctx &, int, int, double *);
@@ -607,7 +607,11 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long 
     }
     c.mg_smem += tile_words * sizeof(float);
     if (c.mg_smem + 4096 > (size_t)maxdyn) return "coarsest multigrid level too large for shared memory";
-    if (ops(c.prec).mg_blocks(c.mg_smem) < 1) return "multigrid kernel cannot be resident";
+    // large lattices per SM make the lattice passes bandwidth-bound: twice the
+    // warps in flight (1024-thread blocks) then beat the 512-thread launch
+    // that keeps 128 registers a thread for the latency-bound small solve
+    c.mg_wide = N >= (long long)MG_WIDE_NODES_PER_SM * c.num_sms;  // (replicas use the batched kernel)
+    if (ops(c.prec).mg_blocks(c.mg_smem, c.mg_wide) < 1) return "multigrid kernel cannot be resident";
     c.mg_r = (float *)A(N * sizeof(float));
     c.mg_z = (float *)A(N * sizeof(float));
     c.mg_q = (float *)A(N * sizeof(float));

@@ -15,6 +15,8 @@ constexpr int LB_THREADS = 128;
 constexpr int CHARGE_THREADS = 256;
 constexpr int POIS_THREADS = 1024;
 constexpr int MG_THREADS = 512;     // multigrid launch: one block per SM (latency-bound solve)
+constexpr int MG_WIDE_THREADS = 1024;  // the same for lattices of at least MG_WIDE_NODES_PER_SM nodes per SM
+constexpr int MG_WIDE_NODES_PER_SM = 16384;
 constexpr int MG_BATCH_THREADS = 1024;  // batched multigrid: each block sweeps large replica volumes
 constexpr int BEAD_THREADS = 256;
 // fixed-point scale of the potential in the reduced-precision paths: 2^40
@@ -119,6 +121,7 @@ struct Ctx {
     int mg;                  // solver in use
     int mg_nlev;             // levels including the lattice
     int mg_cta_from;         // first level handled by one block alone
+    int mg_wide;             // launch the solve with MG_WIDE_THREADS-thread blocks
     int mg_tile_from;        // first level smoothed in shared-memory tiles (mg_cta_from: none)
     int mg_tile[MG_MAXLEV][3];  // owned cells per tile of each tiled level
     size_t mg_tile_off;      // offset (floats) of the tile region in the dynamic shared memory
@@ -201,7 +204,7 @@ int set_state_f64(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_f64();
 int mass_f64(Ctx &c);
 int current_f64(Ctx &c, int axis, int plane, double *part);
-int mg_blocks_f64(size_t smem);
+int mg_blocks_f64(size_t smem, int wide);
 int mg_batch_blocks_f64(size_t smem);
 
 int init_populations_f32(Ctx &c, const double *d_n_init);
@@ -212,7 +215,7 @@ int set_state_f32(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_f32();
 int mass_f32(Ctx &c);
 int current_f32(Ctx &c, int axis, int plane, double *part);
-int mg_blocks_f32(size_t smem);
+int mg_blocks_f32(size_t smem, int wide);
 int mg_batch_blocks_f32(size_t smem);
 
 int init_populations_bf16(Ctx &c, const double *d_n_init);
@@ -223,7 +226,7 @@ int set_state_bf16(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_bf16();
 int mass_bf16(Ctx &c);
 int current_bf16(Ctx &c, int axis, int plane, double *part);
-int mg_blocks_bf16(size_t smem);
+int mg_blocks_bf16(size_t smem, int wide);
 int mg_batch_blocks_bf16(size_t smem);
 
 int init_populations_fp16(Ctx &c, const double *d_n_init);
@@ -234,7 +237,7 @@ int set_state_fp16(Ctx &c, const double *d_f, const double *d_phi);
 int pois_blocks_fp16();
 int mass_fp16(Ctx &c);
 int current_fp16(Ctx &c, int axis, int plane, double *part);
-int mg_blocks_fp16(size_t smem);
+int mg_blocks_fp16(size_t smem, int wide);
 int mg_batch_blocks_fp16(size_t smem);
 
 size_t real_size(int prec);

@@ -115,6 +115,23 @@ static MdArgs<S, R, PhiT, DEV> make_md_args(Ctx &c, const StepArgs<S, R, PhiT> &
     return md;
 }
 
+// The multigrid solve of poisson_mg_kernel with 1024-thread blocks (64
+// registers a thread), for lattices of at least MG_WIDE_NODES_PER_SM nodes
+// per SM: their lattice passes are bound by memory throughput and gain from
+// twice the warps in flight (17 against 23 ms per step on a 256x256x512
+// pore), where a small lattice is bound by barrier latency and runs faster
+// at 512 threads with 128 registers (0.68 against 0.75 ms on 64x64x128).
+template <typename S, typename R, typename PhiT>
+__global__ void __launch_bounds__(MG_WIDE_THREADS, 1) poisson_mg_wide_kernel(StepArgs<S, R, PhiT> a, MgArgs m)
+{
+    __shared__ double sh[MG_WIDE_THREADS / 32];
+    __shared__ double bc[1];
+    extern __shared__ float mg_sm[];
+    const MgGrid G{(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x), (int)gridDim.x,
+                   (int)blockIdx.x, a.barrier};
+    mg_solve<S, R, PhiT, true>(a, m, G, mg_sm, sh, bc);
+}
+
 static inline MgArgs make_mg_args(const Ctx &c)
 {
     MgArgs m;
@@ -194,15 +211,16 @@ template <typename S, typename R, typename PhiT, bool DEV> int steps_impl(Ctx &c
         if (c.mg) {
             MgArgs m = make_mg_args(c);
             void *args[] = {&a, &m};
-            static size_t attr_bytes = 0;
-            if (c.mg_smem > attr_bytes) {
-                cudaFuncSetAttribute(poisson_mg_kernel<S, R, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)c.mg_smem);
-                attr_bytes = c.mg_smem;
+            const void *kern = c.mg_wide ? (const void *)poisson_mg_wide_kernel<S, R, PhiT>
+                                         : (const void *)poisson_mg_kernel<S, R, PhiT>;
+            static size_t attr_bytes[2] = {0, 0};
+            if (c.mg_smem > attr_bytes[c.mg_wide]) {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.mg_smem);
+                attr_bytes[c.mg_wide] = c.mg_smem;
             }
-            cudaError_t e = cudaLaunchCooperativeKernel((const void *)poisson_mg_kernel<S, R, PhiT>,
-                                                        dim3(c.pois_blocks), dim3(MG_THREADS), args, c.mg_smem,
-                                                        c.stream);
+            cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(c.pois_blocks),
+                                                        dim3(c.mg_wide ? MG_WIDE_THREADS : MG_THREADS), args,
+                                                        c.mg_smem, c.stream);
             c.launches++;
             if (e != cudaSuccess) return EKL_ERR_CUDA;
             c.mg_have_prev = 1;
@@ -464,13 +482,14 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_impl(Batch 
 }
 
 // occupancy of the cooperative Poisson kernel for this instantiation
-template <typename S, typename R, typename PhiT> int mg_max_blocks_per_sm(size_t smem)
+template <typename S, typename R, typename PhiT> int mg_max_blocks_per_sm(size_t smem, int wide)
 {
-    if (cudaFuncSetAttribute(poisson_mg_kernel<S, R, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    const void *kern = wide ? (const void *)poisson_mg_wide_kernel<S, R, PhiT>
+                            : (const void *)poisson_mg_kernel<S, R, PhiT>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, poisson_mg_kernel<S, R, PhiT>, MG_THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, wide ? MG_WIDE_THREADS : MG_THREADS, smem);
     return nb;
 }
 
@@ -509,7 +528,7 @@ template <typename S, typename R, typename PhiT> int poisson_max_blocks_per_sm()
     int pois_blocks_##SUFFIX() { return poisson_max_blocks_per_sm<S, R, PhiT>(); }                \
     int mass_##SUFFIX(Ctx &c) { return mass_impl<S, R, PhiT, DEV>(c); }                           \
     int current_##SUFFIX(Ctx &c, int ax, int pl, double *p) { return current_impl<S, R, PhiT, DEV>(c, ax, pl, p); } \
-    int mg_blocks_##SUFFIX(size_t smem) { return mg_max_blocks_per_sm<S, R, PhiT>(smem); }        \
+    int mg_blocks_##SUFFIX(size_t smem, int wide) { return mg_max_blocks_per_sm<S, R, PhiT>(smem, wide); } \
     int mg_batch_blocks_##SUFFIX(size_t smem) { return mg_batch_max_blocks_per_sm<S, R, PhiT>(smem); } \
     int run_batch_##SUFFIX(Batch &b, int n) { return batch_impl<S, R, PhiT, DEV>(b, n); }         \
     }

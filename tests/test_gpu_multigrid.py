@@ -174,3 +174,27 @@ def test_fixed_point_source_has_no_net_charge(flags):
     ref = oracle.Sim(wl.replace(precision="f64", poisson_tol=1e-12, flags=0), threads=8)
     assert ref.step(1) >= 0
     assert ref.poisson_residual(ref.last_rho(), phi) <= 1e-7
+
+
+def test_mg_wide_launch_large_lattice_agrees_with_sor():
+    """A lattice of at least 16 384 nodes per SM (3.3 M nodes here) is solved
+    by the 1024-thread launch: it converges to the tolerance every step and
+    its potential agrees with the SOR solve of the same steps."""
+    wl = W.translocation(nx=160, ny=160, nz=128, membrane=(60, 67), radius=5.0, salt=0.005, n_beads=16,
+                         precision="f32")
+    assert wl.n_nodes >= 16384 * 152
+    mg = E.Simulation(wl.replace(flags=MG))
+    sor = E.Simulation(wl.replace(rho_jacobi=0.9999, poisson_check_every=4, poisson_max_iter=20000))
+    for _ in range(3):
+        rc = mg.step(1)
+        st = mg.stats()
+        assert rc >= 0 and not (rc & E.EKL_WARN_NOCONV), (rc, st)
+        assert st["poisson_res"] <= wl.poisson_tol and 0 < st["poisson_iters"] <= 30, st
+        assert sor.step(1) >= 0
+    fluid = wl.solid.ravel() == 0
+    pm, ps = mg.fields(("phi",))["phi"], sor.fields(("phi",))["phi"]
+    d = rel(pm[fluid], ps[fluid])
+    print("phi mg vs sor", d)
+    assert d < 1e-4
+    mg.close()
+    sor.close()
