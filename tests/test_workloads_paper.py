@@ -35,3 +35,39 @@ def test_observable_helpers():
     assert list(O.crossing_times(z, 4.5)) == [1, 3]
     assert O.conductance(2.0, 0.5, 8) == 0.5
     assert abs(O.g0(40) - 3 ** 0.5 / 40) < 1e-15
+
+
+def test_benchmark_workload_geometries():
+    """The timed, precision-sweep and learned-warm-start pores have the sizes
+    the benchmarks name: box, membrane slab, pore radius, chain length, salt,
+    neutrality, and the chain threaded through the pore."""
+    cases = [(W.config_pore_fp32(), (64, 64, 128), (60, 67), 4.0, 32, 0.005),
+             (W.config_learned(), (128, 128, 256), (124, 131), 6.0, 64, 0.005),
+             (W.config_precision_sweep(), (256, 256, 512), (248, 263), 8.0, 128, 0.01)]
+    for wl, dims, (z0, z1), radius, nb, salt in cases:
+        assert (wl.nx, wl.ny, wl.nz) == dims and wl.n_beads == nb
+        solid = wl.solid
+        # membrane: every node of the slab outside the pore is solid, none outside the slab
+        z = np.arange(wl.nz)
+        slab = (z >= z0) & (z <= z1)
+        assert not solid[~slab].any()
+        cx, cy = (wl.nx - 1) / 2.0, (wl.ny - 1) / 2.0
+        yy, xx = np.meshgrid(np.arange(wl.ny), np.arange(wl.nx), indexing="ij")
+        r = np.hypot(xx - cx, yy - cy)
+        for k in (z0, (z0 + z1) // 2, z1):
+            open_ = solid[k] == 0
+            assert open_.any() and r[open_].max() <= radius + 1e-9
+            assert np.all(solid[k][r > radius + 1.5])
+        # salt, and neutrality up to the seeded U(-1e-4, 1e-4) density noise
+        # (the counter-ions compensate the chain; six standard deviations)
+        assert abs(wl.n_ref[2] - salt) < 1e-12
+        fl = solid == 0
+        net = (wl.n_init[1] - wl.n_init[2])[fl].sum() + wl.charge.sum()
+        if wl.surface_charge is not None:
+            net += wl.surface_charge.sum()
+        assert abs(net) < 6 * 1e-4 * np.sqrt(2 * fl.sum() / 3), net
+        # some bead inside the pore, every bead in fluid
+        R = wl.R
+        assert np.any((R[:, 2] >= z0) & (R[:, 2] <= z1 + 1))
+        idx = np.floor(R).astype(int)
+        assert not solid[idx[:, 2] % wl.nz, idx[:, 1] % wl.ny, idx[:, 0] % wl.nx].any()
