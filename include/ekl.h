@@ -215,6 +215,15 @@ void ekl_lattice(int32_t *c, double *w, int32_t *opp);
 
 void ekl_destroy(ekl_handle *h);
 
+/* Every call that takes a handle runs with the handle's device (the device
+ * that was current at ekl_create) made current, and restores the caller's
+ * device before it returns; a call whose handle device cannot be made
+ * current fails with EKL_ERR_ARG and queues no work.
+ * Test support (no counterpart in the paper): record `device` as the
+ * handle's device without moving anything, so that a one-GPU test can check
+ * that refusal.  Not for use by programs. */
+int ekl_test_set_device(ekl_handle *h, int32_t device);
+
 /* Message of the last error on this thread ("" if none). */
 const char *ekl_last_error(void);
 
@@ -309,7 +318,9 @@ int ekl_warmstart_collect(ekl_handle *h, int32_t nsteps, int32_t crop, int32_t n
  * running between capture and replay of a CUDA graph on a pool-allocated
  * stream, a real-time loop that reserved all device memory up front, a host
  * framework whose allocator is locked during a solver callback).  It returns
- * the same fields as ekl_get_fields, staged through one fixed device array of
+ * the fields of ekl_get_fields (n, j, R and V bit for bit; phi to the
+ * round-off of its mean subtraction, which sums in another order), staged
+ * through one fixed device array of
  * EKL_NOALLOC_MAX_DOUBLES doubles (16 MiB) that the library reserves on every
  * GPU that loads it, instead of per-call device buffers; it calls no
  * cudaMalloc/cudaFree and no allocator.  A request needing more staging than

@@ -123,6 +123,8 @@ def load(build_if_missing: bool = True):
         L.ekl_lattice.argtypes = [vp, vp, vp]
         L.ekl_lattice.restype = None
         L.ekl_destroy.argtypes = [vp]
+        L.ekl_test_set_device.argtypes = [vp, C.c_int32]
+        L.ekl_get_fields_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
         L.ekl_destroy.restype = None
         L.ekl_last_error.restype = C.c_char_p
         L.ekl_sizeof_params.restype = C.c_int64

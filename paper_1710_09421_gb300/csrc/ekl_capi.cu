@@ -942,6 +942,8 @@ int ekl_set_beads(ekl_handle *h, int32_t n, const double *R, const double *V, co
                   const int32_t *chain)
 {
     if (!h) return fail(EKL_ERR_ARG, "null handle");
+    DeviceScope dscope(h->c.device);
+    if (!dscope.ok()) return fail(EKL_ERR_ARG, "the handle's device cannot be made current");
     if (n < 0 || n > MAX_BEADS) return fail(EKL_ERR_ARG, "bead count out of range (max 256)");
     if (n > 0 && (!R || !q)) return fail(EKL_ERR_ARG, "positions and charges are required");
     Ctx &c = h->c;
@@ -984,6 +986,8 @@ int ekl_set_beads(ekl_handle *h, int32_t n, const double *R, const double *V, co
 int ekl_step_async(ekl_handle *h, int32_t nsteps)
 {
     if (!h) return fail(EKL_ERR_ARG, "null handle");
+    DeviceScope dscope(h->c.device);
+    if (!dscope.ok()) return fail(EKL_ERR_ARG, "the handle's device cannot be made current");
     if (nsteps < 0) return fail(EKL_ERR_ARG, "negative step count");
     int rc = ops(h->c.prec).run(h->c, nsteps);
     if (rc != EKL_OK) return fail(rc, "kernel launch failed");
@@ -993,6 +997,8 @@ int ekl_step_async(ekl_handle *h, int32_t nsteps)
 int ekl_step(ekl_handle *h, int32_t nsteps)
 {
     if (!h) return fail(EKL_ERR_ARG, "null handle");
+    DeviceScope dscope(h->c.device);
+    if (!dscope.ok()) return fail(EKL_ERR_ARG, "the handle's device cannot be made current");
     Ctx &c = h->c;
     cudaMemsetAsync(c.status, 0, sizeof(int), c.stream);
     int rc = ekl_step_async(h, nsteps);
@@ -1010,6 +1016,8 @@ int ekl_get_fields(ekl_handle *h, double *n_out, double *j_out, double *phi_out,
                    double *V_out)
 {
     if (!h) return fail(EKL_ERR_ARG, "null handle");
+    DeviceScope dscope(h->c.device);
+    if (!dscope.ok()) return fail(EKL_ERR_ARG, "the handle's device cannot be made current");
     Ctx &c = h->c;
     const long long N = c.N;
     double *dn = n_out ? (double *)dev_alloc(c, (size_t)NS * N * 8) : nullptr;
@@ -1068,6 +1076,8 @@ int ekl_get_fields(ekl_handle *h, double *n_out, double *j_out, double *phi_out,
 int ekl_get_state(ekl_handle *h, double *fstar, double *phi, int64_t *step)
 {
     if (!h) return fail(EKL_ERR_ARG, "null handle");
+    DeviceScope dscope(h->c.device);
+    if (!dscope.ok()) return fail(EKL_ERR_ARG, "the handle's device cannot be made current");
     Ctx &c = h->c;
     double *df = fstar ? (double *)dev_alloc(c, (size_t)NS * Q * c.N * 8) : nullptr;
     double *dp = phi ? (double *)dev_alloc(c, (size_t)c.N * 8) : nullptr;
@@ -1092,6 +1102,8 @@ int ekl_get_state(ekl_handle *h, double *fstar, double *phi, int64_t *step)
 int ekl_set_state(ekl_handle *h, const double *fstar, const double *phi, int64_t step)
 {
     if (!h || !fstar) return fail(EKL_ERR_ARG, "null handle or populations");
+    DeviceScope dscope(h->c.device);
+    if (!dscope.ok()) return fail(EKL_ERR_ARG, "the handle's device cannot be made current");
     Ctx &c = h->c;
     double *df = (double *)dev_alloc(c, (size_t)NS * Q * c.N * 8);
     double *dp = phi ? (double *)dev_alloc(c, (size_t)c.N * 8) : nullptr;
@@ -1115,6 +1127,8 @@ int ekl_set_state(ekl_handle *h, const double *fstar, const double *phi, int64_t
 int ekl_get_stats(ekl_handle *h, ekl_stats *out)
 {
     if (!h || !out) return fail(EKL_ERR_ARG, "null argument");
+    DeviceScope dscope(h->c.device);
+    if (!dscope.ok()) return fail(EKL_ERR_ARG, "the handle's device cannot be made current");
     Ctx &c = h->c;
     const int nmb = ops(c.prec).mass(c);
     if (nmb < 0) return fail(EKL_ERR_CUDA, "mass kernel failed");
@@ -1181,6 +1195,8 @@ int ekl_set_field(ekl_handle *h, const double E[3])
 int ekl_get_current(ekl_handle *h, int32_t axis, int32_t plane, double out[4])
 {
     if (!h || !out) return fail(EKL_ERR_ARG, "null argument");
+    DeviceScope dscope(h->c.device);
+    if (!dscope.ok()) return fail(EKL_ERR_ARG, "the handle's device cannot be made current");
     Ctx &c = h->c;
     const int L[3] = {c.nx, c.ny, c.nz};
     if (axis < 0 || axis > 2 || plane < 0 || plane >= L[axis]) return fail(EKL_ERR_ARG, "axis or plane out of range");
@@ -1209,6 +1225,8 @@ int ekl_get_current(ekl_handle *h, int32_t axis, int32_t plane, double out[4])
 int ekl_set_timing(ekl_handle *h, int32_t on)
 {
     if (!h) return fail(EKL_ERR_ARG, "null handle");
+    DeviceScope dscope(h->c.device);
+    if (!dscope.ok()) return fail(EKL_ERR_ARG, "the handle's device cannot be made current");
     cudaStreamSynchronize(h->c.stream);
     timing_flush(h->c);
     h->c.timing = on ? 1 : 0;
@@ -1219,6 +1237,8 @@ int ekl_set_timing(ekl_handle *h, int32_t on)
 int ekl_get_link_mask(ekl_handle *h, uint32_t *mask_out)
 {
     if (!h || !mask_out) return fail(EKL_ERR_ARG, "null argument");
+    DeviceScope dscope(h->c.device);
+    if (!dscope.ok()) return fail(EKL_ERR_ARG, "the handle's device cannot be made current");
     cudaError_t e = cudaMemcpyAsync(mask_out, h->c.mask, h->c.N * 4, cudaMemcpyDeviceToHost, h->c.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->c.stream);
     if (e != cudaSuccess) return fail_cuda(e, "get_link_mask");
@@ -1228,9 +1248,17 @@ int ekl_get_link_mask(ekl_handle *h, uint32_t *mask_out)
 void ekl_destroy(ekl_handle *h)
 {
     if (!h) return;
+    DeviceScope dscope(h->c.device);
     cudaStreamSynchronize(h->c.stream);
     release(h->c);
     delete h;
+}
+
+int ekl_test_set_device(ekl_handle *h, int32_t device)
+{
+    if (!h) return fail(EKL_ERR_ARG, "null handle");
+    h->c.device = device;
+    return EKL_OK;
 }
 
 }  // extern "C"
@@ -1381,6 +1409,8 @@ ekl_handle *ekl_batch_replica(ekl_batch *bh, int32_t rep)
 int ekl_batch_step(ekl_batch *bh, int32_t nsteps)
 {
     if (!bh || nsteps < 0) return fail(EKL_ERR_ARG, "bad batch or step count");
+    DeviceScope dscope(bh->b.reps[0]->device);
+    if (!dscope.ok()) return fail(EKL_ERR_ARG, "the batch's device cannot be made current");
     Batch &B = bh->b;
     for (int r = 0; r < B.nrep; r++) cudaMemsetAsync(B.reps[r]->status, 0, sizeof(int), B.stream);
     cudaMemsetAsync(B.status, 0, sizeof(int), B.stream);
@@ -1402,6 +1432,8 @@ int ekl_batch_step(ekl_batch *bh, int32_t nsteps)
 int ekl_batch_autotune(ekl_batch *bh, int32_t trial_steps, int32_t *choice_out)
 {
     if (!bh || trial_steps < 1) return fail(EKL_ERR_ARG, "bad batch or trial length");
+    DeviceScope dscope(bh->b.reps[0]->device);
+    if (!dscope.ok()) return fail(EKL_ERR_ARG, "the batch's device cannot be made current");
     Batch &B = bh->b;
     const int sms = B.reps[0]->num_sms;
     cudaEvent_t e0, e1;
@@ -1447,6 +1479,7 @@ void ekl_batch_destroy(ekl_batch *bh)
 {
     if (!bh) return;
     Batch &B = bh->b;
+    DeviceScope dscope(B.nrep > 0 && B.reps[0] ? B.reps[0]->device : 0);
     cudaStreamSynchronize(B.stream);
     batch_release(B);
     for (int r = 0; r < B.nrep; r++)

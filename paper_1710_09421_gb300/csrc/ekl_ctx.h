@@ -188,6 +188,39 @@ int warmstart_before_poisson(Ctx &c);
 int warmstart_after_poisson(Ctx &c);
 void warmstart_free(Ctx &c);
 
+// Makes a handle's device current for the duration of one C-ABI call and
+// restores the caller's device when the call returns, so that every kernel,
+// copy and symbol lookup of the call lands on the device the handle's memory
+// lives on, whatever device the calling thread had current.  ok() is false
+// when that device cannot be made current; the call then fails.
+struct DeviceScope {
+    int prev = -1;
+    bool switched = false;
+    bool good = true;
+    explicit DeviceScope(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            good = false;
+            return;
+        }
+        if (prev == dev) return;
+        if (cudaSetDevice(dev) != cudaSuccess) {
+            cudaGetLastError();
+            good = false;
+            return;
+        }
+        switched = true;
+    }
+    ~DeviceScope()
+    {
+        if (switched) cudaSetDevice(prev);
+    }
+    DeviceScope(const DeviceScope &) = delete;
+    DeviceScope &operator=(const DeviceScope &) = delete;
+    bool ok() const { return good; }
+};
+
 // message returned by ekl_last_error() on this thread
 void set_last_error(const char *msg);
 

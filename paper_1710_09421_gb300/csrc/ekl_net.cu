@@ -773,6 +773,11 @@ extern "C" {
 int ekl_set_warmstart(ekl_handle *h, const float *w, const float scales[3])
 {
     if (!h) return EKL_ERR_ARG;
+    ekl::DeviceScope dscope(h->c.device);
+    if (!dscope.ok()) {
+        ekl::set_last_error("the handle's device cannot be made current");
+        return EKL_ERR_ARG;
+    }
     ekl::Ctx &c = h->c;
     if (!w) {
         if (c.net) ((WarmStart *)c.net)->enabled = 0;
@@ -795,6 +800,11 @@ int ekl_warmstart_collect(ekl_handle *h, int32_t nsteps, int32_t crop, int32_t n
                           int64_t *n_out)
 {
     if (!h || nsteps < 1 || crop < 4 || ncrops < 1 || !out) return EKL_ERR_ARG;
+    ekl::DeviceScope dscope(h->c.device);
+    if (!dscope.ok()) {
+        ekl::set_last_error("the handle's device cannot be made current");
+        return EKL_ERR_ARG;
+    }
     ekl::Ctx &c = h->c;
     if (c.nb == 0) return EKL_ERR_ARG;
     int rc = ekl::warmstart_ensure(c);

@@ -41,10 +41,18 @@ double *g_stage_addr[MAX_DEVICES] = {nullptr};
 std::mutex g_stage_mu;
 
 
-// device address of the staging array for the current device (set-up once)
+// device address of the staging array on device dev (set-up once per
+// device); dev must be the current device, which the check below enforces so
+// that no other device's address is ever cached under dev
 int stage_address(int dev, double **out)
 {
     if (dev < 0 || dev >= MAX_DEVICES) return EKL_ERR_ARG;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != dev) {
+        cudaGetLastError();
+        ekl::set_last_error("the staging array is looked up with another device current");
+        return EKL_ERR_ARG;
+    }
     std::lock_guard<std::mutex> lk(g_stage_mu);
     if (!g_stage_addr[dev]) {
         void *p = nullptr;
@@ -108,6 +116,13 @@ extern "C" int ekl_get_fields_noalloc(ekl_handle *h, double *n_out, double *j_ou
 {
     if (!h) {
         ekl::set_last_error("null handle");
+        return EKL_ERR_ARG;
+    }
+    // the staging array's address is looked up, and cached, for the handle's
+    // device with that device current
+    ekl::DeviceScope dscope(h->c.device);
+    if (!dscope.ok()) {
+        ekl::set_last_error("the handle's device cannot be made current");
         return EKL_ERR_ARG;
     }
     ekl::Ctx &c = h->c;

@@ -47,7 +47,7 @@ def _close(a, b):
     return np.linalg.norm(a - b) <= TOL * max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "bf16", "fp16"])
 def test_noalloc_matches_get_fields_twice(precision):
     lib = E.load()
     f = _noalloc(lib)
@@ -81,4 +81,35 @@ def test_noalloc_rejects_requests_beyond_its_array():
     # the potential alone fits
     assert f(sim.h, None, None, p(phi), None, None) == E.EKL_OK
     assert _close(phi, sim.fields(("phi",))["phi"])
+    sim.close()
+
+
+def test_noalloc_refuses_a_handle_whose_device_is_unavailable():
+    """The staging array's address is looked up for the handle's device with
+    that device current; a handle whose device cannot be made current is
+    refused (EKL_ERR_ARG) before any lookup or work, and nothing is cached
+    for it: restored to its real device, the same handle reads back exactly
+    what ekl_get_fields returns."""
+    import torch
+
+    lib = E.load()
+    f = _noalloc(lib)
+    wl = W.small_pore(nx=16, ny=16, nz=20, membrane=(8, 11), radius=3.0, n_beads=4, precision="f32")
+    sim = E.Simulation(wl)
+    sim.step(3)
+    ref = sim.fields()
+    dev = torch.cuda.current_device()
+    assert lib.ekl_test_set_device(sim.h, torch.cuda.device_count()) == E.EKL_OK
+    N, nb = sim.N, sim.nb
+    n = np.zeros((3, N))
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    assert f(sim.h, p(n), None, None, None, None) == E.EKL_ERR_ARG
+    assert b"device cannot be made current" in lib.ekl_last_error()
+    assert lib.ekl_step(sim.h, 1) == E.EKL_ERR_ARG
+    assert torch.cuda.current_device() == dev
+    assert lib.ekl_test_set_device(sim.h, dev) == E.EKL_OK
+    got = _fields_noalloc(f, sim)
+    for k in ("n", "j", "R", "V"):
+        assert np.array_equal(got[k], ref[k]), k
+    assert _close(got["phi"], ref["phi"])
     sim.close()
