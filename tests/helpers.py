@@ -32,3 +32,11 @@ def rel(a, b):
     b = np.asarray(b, np.float64).ravel()
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def pointwise(a, b):
+    """max |a - b| / max |b|: the worst node against the field's scale."""
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    mb = np.abs(b).max()
+    return np.abs(a - b).max() / (mb if mb > 0 else 1.0)

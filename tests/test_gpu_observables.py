@@ -70,3 +70,50 @@ def test_paper_pore_relax_then_drive():
     print("mid-pore fluxes and current", I)
     assert np.isfinite(I).all() and I[3] > 0
     sim.close()
+
+
+def test_paper_pore_fp64_matches_oracle_across_field_switch():
+    """The paper's own set-up (Sec. IV.A) at a size the oracle finishes in
+    seconds: a 16 x 16 x 40 box, membrane z = 15..24 pierced by a pore of
+    radius 3, the pore lining charged with -0.18 e per lattice slice, six
+    beads of -0.1 e on stiff harmonic bonds of 2 dx with WCA sigma = 2 dx,
+    Bjerrum length 1.4 dx, 100 mM salt, Chebyshev SOR to 1e-12.  Relaxed at
+    zero field for 25 steps, then driven at E_z = 0.05 for 25 more (the
+    relax-then-drive protocol): FP64 on the GPU against the oracle within
+    1e-12 normwise and pointwise on densities, velocities, potential and
+    bead displacements, and the plane current through the pore's mid-plane
+    against the oracle's plane sum."""
+    from helpers import pointwise
+
+    wl = W.paper_pore(nx=16, ny=16, nz=40, membrane=(15, 24), radius=3.0, n_beads=6,
+                      precision="f64", tol=1e-12)
+    assert wl.surface_charge is not None and wl.surface_charge.min() < 0
+    sim = E.Simulation(wl.replace(E_app=(0.0, 0.0, 0.0)))
+    ref = oracle.Sim(wl.replace(E_app=(0.0, 0.0, 0.0)), threads=8)
+    R0 = np.array(wl.R)
+    assert sim.step(25) >= 0 and ref.step(25) >= 0
+    E_drive = np.array(wl.E_app)
+    sim.set_field(E_drive)
+    ref.set_field(E_drive)
+    assert sim.step(25) >= 0 and ref.step(25) >= 0
+    G, O_ = sim.fields(), ref.fields()
+    fluid = wl.solid.ravel() == 0
+    vel = lambda F: F["j"] / np.where(F["n"] > 0, F["n"], 1.0)[:, None, :]
+    ug, uo = vel(G), vel(O_)
+    errs = {
+        "n": max(rel(G["n"][a][fluid], O_["n"][a][fluid]) for a in range(3)),
+        "u": max(rel(ug[a][:, fluid], uo[a][:, fluid]) for a in range(3)),
+        "phi": rel(G["phi"][fluid], O_["phi"][fluid]),
+        "R": rel(G["R"] - R0, O_["R"] - R0),
+        "n_max": max(pointwise(G["n"][a][fluid], O_["n"][a][fluid]) for a in range(3)),
+        "u_max": max(pointwise(ug[a][:, fluid], uo[a][:, fluid]) for a in range(3)),
+        "phi_max": pointwise(G["phi"][fluid], O_["phi"][fluid]),
+    }
+    print(errs, sim.stats()["poisson_iters"], ref.stats()["poisson_iters"])
+    assert all(v < 1e-12 for v in errs.values()), errs
+    zmid = (15 + 24) // 2
+    jz = O_["j"][:, 2].reshape(3, wl.nz, wl.ny, wl.nx)[:, zmid]
+    out = sim.current(axis=2, plane=zmid)
+    scale = np.abs(jz).sum(axis=(1, 2)) + 1e-300
+    assert np.all(np.abs(out[:3] - jz.sum(axis=(1, 2))) <= 1e-12 * scale), (out, jz.sum(axis=(1, 2)))
+    sim.close()

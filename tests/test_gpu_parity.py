@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import paper_1710_09421_gb300 as E
-from helpers import box, rel
+from helpers import box, pointwise, rel
 from paper_1710_09421_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -51,6 +51,13 @@ def _compare(wl, steps, tol, precision=None, check_phi=True, check_beads=True, t
         dg = G["R"] - R0
         do = O["R"] - R0
         errs["R"] = rel(dg, do)
+    # pointwise: the largest node error against the field's largest value
+    # (a single node far off cannot hide in a norm over the lattice)
+    errs["n_max"] = max(pointwise(G["n"][a][fluid], O["n"][a][fluid]) for a in range(3))
+    errs["u_flow_max"] = max(np.abs(ug[a][:, fluid] - uo[a][:, fluid]).max() for a in range(3)) / max(
+        np.abs(uo[a][:, fluid]).max() for a in range(3))
+    if check_phi:
+        errs["phi_max"] = pointwise(G["phi"][fluid], O["phi"][fluid])
     sg, so = sim.stats(), ref.stats()
     sim.close()
     return errs, sg, so
@@ -101,6 +108,7 @@ def test_fp32_small_pore_1000_steps():
     errs, sg, so = _compare(wl, 1000, TOL32, precision="f32", check_beads=False)
     assert errs["n"] < TOL32 and errs["u_flow"] < TOL32 and errs["u_ions"] < TOL32, errs
     assert errs["phi"] < TOL32, errs
+    assert errs["n_max"] < TOL32 and errs["u_flow_max"] < TOL32 and errs["phi_max"] < TOL32, errs
 
 
 def test_fp32_small_pore_with_chain_1000_steps():
@@ -110,7 +118,45 @@ def test_fp32_small_pore_with_chain_1000_steps():
     wl = W.small_pore(nx=20, ny=16, nz=24, membrane=(10, 13), radius=3.0, n_beads=4,
                       precision="f32").replace(poisson_fixed_iter=60, flags=W.FLAG_NO_BEAD_NOISE)
     errs, sg, so = _compare(wl, 1000, TOL32, precision="f32", check_beads=True)
-    assert errs["n"] < TOL32 and errs["u_flow"] < TOL32, errs
+    print(errs)
+    assert errs["n"] < TOL32 and errs["u_flow"] < TOL32 and errs["u_ions"] < TOL32, errs
+    assert errs["R"] < TOL32, errs
+    assert errs["n_max"] < TOL32 and errs["u_flow_max"] < TOL32, errs
+
+
+def test_fp32_multigrid_small_pore_with_chain_1000_steps():
+    """The benchmarked configuration of the solver -- FP32 storage and
+    arithmetic, multigrid-CG stopped on its true residual -- over 1000 steps
+    against the oracle's Chebyshev SOR.  Both stop on a tolerance (1e-10 on
+    the GPU, 1e-13 in the oracle), so their potentials differ by at most
+    about cond(A) x 1e-10 ~ 1e-7 relative per step; FP32 rounding must keep
+    densities, velocities, potential and bead displacements within 1e-5."""
+    wl = W.small_pore(nx=20, ny=16, nz=24, membrane=(10, 13), radius=3.0, n_beads=4,
+                      precision="f32").replace(poisson_tol=1e-10, flags=W.FLAG_NO_BEAD_NOISE | W.FLAG_POISSON_MG)
+    sim = E.Simulation(wl)
+    ref = oracle.Sim(wl.replace(poisson_tol=1e-13, flags=W.FLAG_NO_BEAD_NOISE), threads=8)
+    R0 = np.array(wl.R, np.float64)
+    for _ in range(10):
+        st = sim.step(100)
+        assert st >= 0 and not (st & E.EKL_WARN_NOCONV), st
+        assert sim.stats()["poisson_res"] <= 1e-10
+        assert ref.step(100) >= 0
+    G, O = sim.fields(), ref.fields()
+    sim.close()
+    fluid = wl.solid.ravel() == 0
+    ug, uo = _vel(G), _vel(O)
+    scale = max(np.linalg.norm(uo[a][:, fluid]) for a in range(3))
+    errs = {
+        "n": max(rel(G["n"][a][fluid], O["n"][a][fluid]) for a in range(3)),
+        "u_flow": max(np.linalg.norm(ug[a][:, fluid] - uo[a][:, fluid]) / scale for a in range(3)),
+        "u_ions": max(rel(ug[a][:, fluid], uo[a][:, fluid]) for a in (1, 2)),
+        "phi": rel(G["phi"][fluid], O["phi"][fluid]),
+        "R": rel(G["R"] - R0, O["R"] - R0),
+        "n_max": max(pointwise(G["n"][a][fluid], O["n"][a][fluid]) for a in range(3)),
+        "phi_max": pointwise(G["phi"][fluid], O["phi"][fluid]),
+    }
+    print(errs)
+    assert all(v < TOL32 for v in errs.values()), errs
 
 
 def test_fp32_charged_slit_fixed_point_poisson():
