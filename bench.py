@@ -43,6 +43,10 @@ PROFILED = {
     # (kernel, workload): (sha256 prefix of its source files, dram read + write bytes per launch)
     ("lb_fused_kernel", "pore_64x64x128_r4_N32"): ("64c6980a96cc13dc", 119372032 + 65814272),
     ("poisson_mg_kernel", "pore_64x64x128_r4_N32"): ("18df217dc0e82b21", 20447744 + 888320),
+    ("lb_fused_kernel", "pore_256x256x512_r8_N128"): ("64c6980a96cc13dc", 7823804928 + 7367143680),
+    ("poisson_mg_wide_kernel", "pore_256x256x512_r8_N128"): ("18df217dc0e82b21", 33757597440 + 12620104960),
+    ("lb_fused_kernel", "pore_128x128x256_r6_N64"): ("64c6980a96cc13dc", 978504960 + 877521408),
+    ("poisson_mg_wide_kernel", "pore_128x128x256_r6_N64"): ("18df217dc0e82b21", 1022712832 + 978288384),
 }
 KERNEL_SOURCES = {
     "lb_fused_kernel": ("ekl_kernels.cuh", "ekl_dev.cuh"),
