@@ -598,34 +598,33 @@ def run_ours(args):
     if small is not None:
         line["pore_64x64x128"] = small
     if world == 1 and not args.no_learned:
-        line["learned_vs_plain"] = learned_vs_plain(E, workload_for("pore", 0, args), args, sraw)
-        line["learned_vs_plain"]["workload"] = "pore_64x64x128_r4_N32"
+        line["learned_vs_plain"] = learned_summary(E, W, args, sraw)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, workload_for("pore", 0, args), budget_s=args.cpu_budget)
     print(json.dumps(line))
 
 
 def learned_vs_plain(E, wl, args, sraw, collect_steps=60, ncrops=8, crop=16, train_iters=400,
-                     compare_steps=40, train_wl=None, trained=None):
-    """Train the warm-start network on crops the solver records on train_wl
+                     compare_steps=40, train_wl=None, trained=None, level=0):
+    """Train the warm-start network on samples the solver records on train_wl
     (default: this workload; a separate run with another seed), or take a
     trained (weights, scales, info), then time the same steps with and
     without it from identical states.  Both runs iterate to the same
-    residual tolerance; only sweeps and time are compared."""
+    residual tolerance; only sweeps and time are compared.  level: the
+    lattice level the network runs on (0: the lattice, crops near the beads;
+    L >= 1: whole grids of 2^L-node cells)."""
     import torch
 
     if trained is None:
-        trained = train_warmstart(E, train_wl or wl, args, sraw, collect_steps, ncrops, crop, train_iters)
+        trained = train_warmstart(E, train_wl or wl, args, sraw, collect_steps, ncrops, crop, train_iters, level)
     w, scales, info = trained
     out = dict(info)
     for name, use in (("plain", False), ("learned", True)):
         sim = E.Simulation(wl, precision=args.precision, stream=sraw)
         sim.step(args.warmup)
         if use:
-            sim.set_warmstart(w, scales)
-            sim.step(2)   # the network needs the previous source
-        else:
-            sim.step(2)
+            sim.set_warmstart(w, scales, level=level)
+        sim.step(2)   # the network needs the previous source
         s0 = sim.stats()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -643,36 +642,69 @@ def learned_vs_plain(E, wl, args, sraw, collect_steps=60, ncrops=8, crop=16, tra
                      "poisson_res_last": s1["poisson_res"]}
     out["sweeps_saved_frac"] = round(1 - out["learned"]["poisson_sweeps_per_step"]
                                      / max(out["plain"]["poisson_sweeps_per_step"], 1e-9), 4)
+    out["speedup"] = round(out["learned"]["steps_per_s"] / max(out["plain"]["steps_per_s"], 1e-9), 4)
     return out
 
 
-def train_warmstart(E, wl, args, sraw, collect_steps, ncrops, crop, train_iters):
-    """Crops recorded by the solver on wl with another seed, and the network
-    trained on them: (weights, scales, info)."""
+def train_warmstart(E, wl, args, sraw, collect_steps, ncrops, crop, train_iters, level=0):
+    """Samples recorded by the solver on wl with another seed, and the
+    network trained on them: (weights, scales, info)."""
     import numpy as np
     from paper_1710_09421_gb300 import warmstart as WS
 
     t0 = time.perf_counter()
     src = E.Simulation(wl.replace(seed=wl.seed + 101), precision=args.precision, stream=sraw)
     src.step(args.warmup)
-    crops = src.collect(collect_steps, crop=crop, ncrops=ncrops, seed=7)
+    if level:
+        src.warmstart_level(level)
+        data = src.collect(collect_steps + 1, seed=7)[1:]  # the first step has no previous source
+    else:
+        data = src.collect(collect_steps, crop=crop, ncrops=ncrops, seed=7)
     src.close()
     t1 = time.perf_counter()
-    w, scales, curve = WS.train(crops, iters=train_iters, batch=8, lr=2e-3, seed=0)
+    if level:
+        w, scales, curve = WS.train_fields(data, wl.periodic, iters=train_iters, batch=8, lr=2e-3, seed=0)
+    else:
+        w, scales, curve = WS.train(data, iters=train_iters, batch=8, lr=2e-3, seed=0)
     t2 = time.perf_counter()
-    info = {"crops": int(len(crops)), "crop": crop, "collect_s": round(t1 - t0, 3),
+    info = {"samples": int(len(data)), "level": level, "collect_s": round(t1 - t0, 3),
             "train_s": round(t2 - t1, 3), "train_iters": train_iters,
             "rel_loss_first": round(float(np.mean(curve[:20])), 4),
             "rel_loss_last": round(float(np.mean(curve[-20:])), 4)}
+    if not level:
+        info["crop"] = crop
     return w, scales, info
+
+
+def learned_summary(E, W, args, sraw, samples=2000, iters=600):
+    """The learned warm start in the benchmark line: trained on the
+    64x64x128 pore (another seed) at network level --ws-level, compared on
+    the 128x128x256 pore with the paper's SOR and with multigrid, at the same
+    residual (the full-size training of BASELINE's 20 000 snapshots is
+    `--workload learned`)."""
+    wl = W.config_learned(args.precision)
+    train_wl = W.config_pore_fp32().replace(flags=W.FLAG_POISSON_MG)
+    L = args.ws_level
+    trained = train_warmstart(E, train_wl, args, sraw, collect_steps=samples, ncrops=1, crop=0,
+                              train_iters=iters, level=L)
+    out = {"workload": "pore_128x128x256_r6_N64", "trained_on": "pore_64x64x128_r4_N32, seed + 101",
+           "network_level": L}
+    sor = wl.replace(rho_jacobi=0.9999, poisson_check_every=4, poisson_max_iter=20000)
+    for name, w_ in (("chebyshev-sor", sor), ("multigrid-CG", wl.replace(flags=wl.flags | W.FLAG_POISSON_MG))):
+        r = learned_vs_plain(E, w_, args, sraw, compare_steps=12, trained=trained, level=L)
+        out[name] = {k: r[k] for k in ("plain", "learned", "sweeps_saved_frac", "speedup")}
+        out["training"] = {k: r[k] for k in ("samples", "train_iters", "rel_loss_first", "rel_loss_last",
+                                             "collect_s", "train_s")}
+    return out
 
 
 def run_learned(args):
     """The learned warm start on the 128x128x256 pore (radius 6, N = 64,
-    salt 0.005): the network is trained on 20 000 crops that the solver
-    records on the 64x64x128 pore (radius 4, N = 32) under another seed,
-    then the same steps run with and without it from identical states, to
-    the same residual, with the paper's Chebyshev SOR and with multigrid."""
+    salt 0.005): the network is trained on samples that the solver records
+    on the 64x64x128 pore (radius 4, N = 32) under another seed, then the
+    same steps run with and without it from identical states, to the same
+    residual, with the paper's Chebyshev SOR and with multigrid.  The
+    network runs on cells of 2^level nodes (--ws-level)."""
     import torch
 
     import paper_1710_09421_gb300 as E
@@ -684,15 +716,22 @@ def run_learned(args):
     sraw = stream.cuda_stream
     wl = W.config_learned(args.precision)
     train_wl = W.config_pore_fp32().replace(flags=W.FLAG_POISSON_MG)
-    trained = train_warmstart(E, train_wl, args, sraw, collect_steps=250, ncrops=80, crop=16,
-                              train_iters=800)
+    L = args.ws_level
+    if L:
+        trained = train_warmstart(E, train_wl, args, sraw, collect_steps=args.ws_samples, ncrops=1, crop=0,
+                                  train_iters=args.ws_iters, level=L)
+    else:
+        trained = train_warmstart(E, train_wl, args, sraw, collect_steps=250, ncrops=80, crop=16,
+                                  train_iters=800)
     line = {"metric": "learned vs plain Poisson: iterations and steps/s at the same residual",
             "unit": "steps/s", "data": "synthetic", "dtype": args.precision,
             "config": {"workload": "pore_128x128x256_r6_N64", "nodes": wl.n_nodes,
-                       "poisson_tol": wl.poisson_tol, "trained_on": "pore_64x64x128_r4_N32, seed + 101"}}
-    for name, flags in (("chebyshev-sor", 0), ("multigrid-CG", W.FLAG_POISSON_MG)):
-        line[name] = learned_vs_plain(E, wl.replace(flags=wl.flags | flags), args, sraw,
-                                      compare_steps=max(10, args.steps // 10), trained=trained)
+                       "poisson_tol": wl.poisson_tol, "trained_on": "pore_64x64x128_r4_N32, seed + 101",
+                       "network_level": L}}
+    sor = wl.replace(rho_jacobi=0.9999, poisson_check_every=4, poisson_max_iter=20000)
+    for name, w_ in (("chebyshev-sor", sor), ("multigrid-CG", wl.replace(flags=wl.flags | W.FLAG_POISSON_MG))):
+        line[name] = learned_vs_plain(E, w_, args, sraw, compare_steps=max(10, args.steps // 10), trained=trained,
+                                      level=L)
     print(json.dumps(line))
 
 
@@ -712,6 +751,11 @@ def main():
                     help="Poisson residual test interval (0: workload default)")
     ap.add_argument("--poisson", default="mg", choices=["mg", "sor"],
                     help="Poisson solver: multigrid-preconditioned CG or Chebyshev red-black SOR")
+    ap.add_argument("--ws-level", type=int, default=2,
+                    help="lattice level of the learned warm start (--workload learned; 0: the lattice)")
+    ap.add_argument("--ws-samples", type=int, default=20000,
+                    help="solver snapshots the warm-start network is trained on (--workload learned)")
+    ap.add_argument("--ws-iters", type=int, default=2000, help="training iterations (--workload learned)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-vs-plain warm-start comparison")

@@ -306,11 +306,36 @@ int ekl_net_train(int32_t nsamples, const int32_t dims[3], const float *x, const
  * and starts from phi(t-1). */
 int ekl_set_warmstart(ekl_handle *h, const float *w, const float scales[3]);
 
-/* Run nsteps plain steps and record ncrops training crops per step, cubes of
- * crop^3 nodes centred near the beads: out[k][3][crop^3] = (b(t) - b(t-1),
- * phi(t-1), phi(t) - phi(t-1)), unscaled; *n_out crops written.  Needs beads. */
+/* Run nsteps plain steps and record training samples.  Network on the
+ * lattice (level 0): ncrops crops per step, cubes of crop^3 nodes centred near
+ * the beads, out[k][3][crop^3] = (b(t) - b(t-1), phi(t-1), phi(t) - phi(t-1)),
+ * unscaled; needs beads.  Network on level L >= 1 (ekl_warmstart_level): one
+ * sample per step, the whole coarse grid, out[k][3][NL] = (b(t) - b(t-1)
+ * summed over each cell, phi(t-1) and phi(t) - phi(t-1) averaged over the
+ * cell's fluid nodes), NL = nx ny nz / 8^L; crop is unused.  *n_out samples
+ * written. */
 int ekl_warmstart_collect(ekl_handle *h, int32_t nsteps, int32_t crop, int32_t ncrops, uint64_t seed,
                           float *out, int64_t *n_out);
+
+/* The level the warm-start network runs on (not in the paper; the error
+ * that sets the solver's iteration count is smooth and box-wide, while the
+ * network sees 4 cells around each output).  0: the lattice (default).
+ * L >= 1 (at most 4): cells of 2^L x 2^L x 2^L nodes, cell (X, Y, Z) covering
+ * nodes 2^L (X, Y, Z) + [0, 2^L)^3; the inputs are the change of the Poisson
+ * source summed over each cell (times scales[0]) and phi(t-1) averaged over
+ * its fluid nodes (times scales[1]); the output times scales[2] is added to
+ * the potential of every fluid node of the cell (piecewise-constant
+ * prolongation) before the solve, which still runs to poisson_tol.  Every
+ * extent must be a multiple of 2^L.  Changing the level discards the
+ * installed parameters; install them (ekl_set_warmstart) afterwards.
+ * Errors: EKL_ERR_ARG. */
+int ekl_warmstart_level(ekl_handle *h, int32_t level);
+
+/* ekl_net_train on a grid whose periodic axes wrap (whole coarse fields of
+ * a periodic box); ekl_net_train is this with every axis closed. */
+int ekl_net_train_grid(int32_t nsamples, const int32_t dims[3], const int32_t periodic[3], const float *x,
+                       const float *target, const uint8_t *mask, float *w, int32_t iters, int32_t batch, float lr,
+                       uint64_t seed, float *loss_out);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free field read-back.  The paper has no counterpart: this entry

@@ -144,6 +144,9 @@ def load(build_if_missing: bool = True):
         L.ekl_warmstart_collect.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, vp,
                                             C.POINTER(C.c_int64)]
         L.ekl_net_loss_grad.argtypes = [vp, vp, vp, vp, vp, vp, C.POINTER(C.c_double), vp]
+        L.ekl_warmstart_level.argtypes = [vp, C.c_int32]
+        L.ekl_net_train_grid.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, C.c_int32, C.c_int32, C.c_float,
+                                         C.c_uint64, vp]
         L.ekl_net_train.argtypes = [C.c_int32, vp, vp, vp, vp, vp, C.c_int32, C.c_int32, C.c_float,
                                     C.c_uint64, vp]
         if L.ekl_sizeof_params() != C.sizeof(ekl_params):
@@ -400,10 +403,20 @@ class Simulation:
         L = (self.wl.nx, self.wl.ny, self.wl.nz)[axis]
         return ekl_get_current(self.h, axis, L // 2 if plane is None else plane)
 
-    def set_warmstart(self, w, scales=(1.0, 1.0, 1.0)):
+    def set_warmstart(self, w, scales=(1.0, 1.0, 1.0), level=None):
+        if level is not None:
+            ekl_warmstart_level(self.h, level)
         return ekl_set_warmstart(self.h, w, scales)
 
+    def warmstart_level(self, level):
+        self._ws_level = int(level)
+        return ekl_warmstart_level(self.h, level)
+
     def collect(self, nsteps, crop=16, ncrops=8, seed=0):
+        L = getattr(self, "_ws_level", 0)
+        if L:
+            dims = (self.wl.nz >> L, self.wl.ny >> L, self.wl.nx >> L)
+            return ekl_warmstart_collect_level(self.h, nsteps, dims, seed)
         return ekl_warmstart_collect(self.h, nsteps, crop, ncrops, seed)
 
 
@@ -551,6 +564,34 @@ def ekl_set_warmstart(h, w, scales=(1.0, 1.0, 1.0)):
     wp = None if w is None else np.ascontiguousarray(w, np.float32)
     sc = np.ascontiguousarray(scales, np.float32)
     return _check(load().ekl_set_warmstart(h, _ptr(wp), _ptr(sc)), "ekl_set_warmstart")
+
+
+def ekl_warmstart_level(h, level):
+    return _check(load().ekl_warmstart_level(h, int(level)), "ekl_warmstart_level")
+
+
+def ekl_warmstart_collect_level(h, nsteps, dims_zyx, seed=0):
+    """Coarse-level samples[k][3][nzL][nyL][nxL] = (db summed per cell,
+    phi_prev and dphi averaged per cell)."""
+    out = np.zeros((nsteps, 3) + tuple(dims_zyx), np.float32)
+    n = C.c_int64(0)
+    _check(load().ekl_warmstart_collect(h, int(nsteps), 0, 1, int(seed), _ptr(out), C.byref(n)),
+           "ekl_warmstart_collect")
+    return out[: n.value]
+
+
+def ekl_net_train_grid(dims, periodic, x, target, mask, w, iters, batch=4, lr=1e-3, seed=0):
+    """ekl_net_train on a grid with periodic axes; returns (trained w, loss curve)."""
+    d = _i3(dims)
+    p = _i3(periodic)
+    x = np.ascontiguousarray(x, np.float32)
+    t = np.ascontiguousarray(target, np.float32)
+    m = None if mask is None else np.ascontiguousarray(mask, np.uint8)
+    w = np.ascontiguousarray(w, np.float32).copy()
+    curve = np.zeros(iters, np.float32)
+    _check(load().ekl_net_train_grid(len(x), _ptr(d), _ptr(p), _ptr(x), _ptr(t), _ptr(m), _ptr(w), int(iters),
+                                     int(batch), float(lr), int(seed), _ptr(curve)), "ekl_net_train_grid")
+    return w, curve
 
 
 def ekl_warmstart_collect(h, nsteps, crop=16, ncrops=8, seed=0):

@@ -464,11 +464,14 @@ NetGrid make_grid(const int32_t dims[3], const int32_t periodic[3])
 
 // ---------------------------------------------------------------- in-step warm start
 struct WarmStart {
-    NetWork W;
+    NetWork W;               // on the lattice (level 0) or on cubes of 2^level nodes
     float s_db = 1.f, s_phi = 1.f, s_out = 1.f;
     int enabled = 0;
     int have_prev = 0;
+    int level = 0;
+    NetGrid fine;            // the lattice
     float *bprev = nullptr, *bcur = nullptr, *phiprev = nullptr;
+    float *dbf = nullptr, *phf = nullptr;  // level > 0: the lattice's inputs before restriction
     double *mean = nullptr;
     int collect = 0, crop = 0, ncrops = 0;
     float *crops = nullptr;  // [cap][3][crop^3]: dB, phi_prev, dphi
@@ -485,11 +488,12 @@ __global__ void mean_k(const double *part, int n, double nfl, double *mean)
     if (threadIdx.x == 0) *mean = nfl > 0 ? t / nfl : 0.0;
 }
 
-// network inputs: x0 = s_db (b(t) - b(t-1)), x1 = s_phi phi(t-1); b = 4 pi l_B (rho - mean)
+// network inputs on the lattice: x0 = s_db (b(t) - b(t-1)), x1 = s_phi phi(t-1);
+// b = 4 pi l_B (rho - mean)
 template <typename R, typename PhiT>
 __global__ void ws_inputs(int N, const uint32_t *mask, const R *rho, const double *mean, double c4, const PhiT *phi,
-                          const float *bprev, int have_prev, float s_db, float s_phi, float *x, float *bcur,
-                          float *phiprev)
+                          const float *bprev, int have_prev, float s_db, float s_phi, float *x0, float *x1,
+                          float *bcur, float *phiprev)
 {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
@@ -501,8 +505,77 @@ __global__ void ws_inputs(int N, const uint32_t *mask, const R *rho, const doubl
     if (solid) p = 0.f;
     bcur[n] = b;
     if (phiprev) phiprev[n] = p;
-    x[n] = solid ? 0.f : s_db * (b - (have_prev ? bprev[n] : b));
-    x[N + n] = s_phi * p;
+    x0[n] = solid ? 0.f : s_db * (b - (have_prev ? bprev[n] : b));
+    x1[n] = s_phi * p;
+}
+
+// The network on a coarse level: cell (X, Y, Z) of level L covers the cube
+// of 2^L nodes starting at 2^L (X, Y, Z).  Inputs: x0 = s_db times the sum of
+// the change of the source over the cube (the source a coarse Poisson
+// operator sees), x1 = s_phi times the mean of phi(t-1) over its fluid nodes.
+__global__ void ws_restrict(NetGrid f, NetGrid c, int L, const uint32_t *mask, const float *db, const float *ph,
+                            float s_db, float s_phi, float *x)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= c.N) return;
+    int X, Y, Z;
+    xyz_of(c, I, X, Y, Z);
+    const int B = 1 << L;
+    double sd = 0.0, sp = 0.0;
+    int cnt = 0;
+    for (int dz = 0; dz < B; dz++)
+        for (int dy = 0; dy < B; dy++)
+            for (int dx = 0; dx < B; dx++) {
+                const int n = (X * B + dx) + f.nx * ((Y * B + dy) + f.ny * (Z * B + dz));
+                if (mask[n] & SOLID_BIT) continue;
+                sd += (double)db[n];
+                sp += (double)ph[n];
+                cnt++;
+            }
+    x[I] = (float)(s_db * sd);
+    x[c.N + I] = cnt ? (float)(s_phi * (sp / cnt)) : 0.f;
+}
+
+// mean over the fluid nodes of each cube of phi(t) - phi(t-1): the training
+// target of the coarse network
+template <typename PhiT>
+__global__ void ws_coarse_target(NetGrid f, NetGrid c, int L, const uint32_t *mask, const PhiT *phi,
+                                 const float *phiprev, float *out)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= c.N) return;
+    int X, Y, Z;
+    xyz_of(c, I, X, Y, Z);
+    const int B = 1 << L;
+    double s = 0.0;
+    int cnt = 0;
+    for (int dz = 0; dz < B; dz++)
+        for (int dy = 0; dy < B; dy++)
+            for (int dx = 0; dx < B; dx++) {
+                const int n = (X * B + dx) + f.nx * ((Y * B + dy) + f.ny * (Z * B + dz));
+                if (mask[n] & SOLID_BIT) continue;
+                float pn;
+                if constexpr (((PhiT)0.5) != 0) pn = (float)phi[n];
+                else pn = ll_to_float(phi[n]) * (float)PHI_INV;
+                s += (double)(pn - phiprev[n]);
+                cnt++;
+            }
+    out[I] = cnt ? (float)(s / cnt) : 0.f;
+}
+
+// phi += s_out y(cube of the node) on the fluid nodes (piecewise-constant
+// prolongation of the coarse network's output)
+template <typename PhiT>
+__global__ void ws_apply_coarse(NetGrid f, NetGrid c, int L, const uint32_t *mask, const float *y, float s_out,
+                                PhiT *phi)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= f.N || (mask[n] & SOLID_BIT)) return;
+    int x, yy, z;
+    xyz_of(f, n, x, yy, z);
+    const float d = s_out * y[(x >> L) + c.nx * ((yy >> L) + c.ny * (z >> L))];
+    if constexpr (((PhiT)0.5) != 0) phi[n] += (double)d;
+    else phi[n] += float_to_ll(d * (float)PHI_SCALE);
 }
 
 template <typename PhiT>
@@ -570,21 +643,39 @@ int warmstart_before_poisson(Ctx &c)
     mean_k<<<1, 1024, 0, c.stream>>>(c.part_charge, c.charge_blocks, (double)c.n_fluid, ws.mean);
     const int bn = (N + 255) / 256;
     const int have = ws.have_prev;
+    const int L = ws.level;
+    // level 0: the inputs go straight to the network; level > 0: unscaled
+    // into the lattice buffers, then restricted (and scaled) per cube
+    float *x0 = L ? ws.dbf : ws.W.x, *x1 = L ? ws.phf : ws.W.x + N;
+    const float sdb = L ? 1.f : ws.s_db, sph = L ? 1.f : ws.s_phi;
     if (c.prec == EKL_F64)
         ws_inputs<double, double><<<bn, 256, 0, c.stream>>>(N, c.mask, (const double *)c.rho, ws.mean, c.c4,
-                                                           (const double *)c.phi, ws.bprev, have, ws.s_db, ws.s_phi,
-                                                           ws.W.x, ws.bcur, ws.collect ? ws.phiprev : nullptr);
+                                                           (const double *)c.phi, ws.bprev, have, sdb, sph, x0, x1,
+                                                           ws.bcur, ws.collect ? ws.phiprev : nullptr);
     else
         ws_inputs<float, long long><<<bn, 256, 0, c.stream>>>(N, c.mask, (const float *)c.rho, ws.mean, c.c4,
-                                                             (const long long *)c.phi, ws.bprev, have, ws.s_db,
-                                                             ws.s_phi, ws.W.x, ws.bcur, ws.collect ? ws.phiprev : nullptr);
+                                                             (const long long *)c.phi, ws.bprev, have, sdb, sph, x0,
+                                                             x1, ws.bcur, ws.collect ? ws.phiprev : nullptr);
     c.launches += 2;
+    if (L) {
+        ws_restrict<<<(ws.W.g.N + 255) / 256, 256, 0, c.stream>>>(ws.fine, ws.W.g, L, c.mask, ws.dbf, ws.phf,
+                                                                  ws.s_db, ws.s_phi, ws.W.x);
+        c.launches++;
+    }
     if (ws.enabled && have) {
         net_forward(ws.W, c.stream);
-        const int bm = bn;
-        if (c.prec == EKL_F64) ws_apply<double><<<bm, 256, 0, c.stream>>>(N, c.mask, ws.W.y, ws.s_out, (double *)c.phi);
-        else ws_apply<long long><<<bm, 256, 0, c.stream>>>(N, c.mask, ws.W.y, ws.s_out, (long long *)c.phi);
-        c.launches += 8;
+        if (L) {
+            if (c.prec == EKL_F64)
+                ws_apply_coarse<double><<<bn, 256, 0, c.stream>>>(ws.fine, ws.W.g, L, c.mask, ws.W.y, ws.s_out,
+                                                                  (double *)c.phi);
+            else
+                ws_apply_coarse<long long><<<bn, 256, 0, c.stream>>>(ws.fine, ws.W.g, L, c.mask, ws.W.y, ws.s_out,
+                                                                     (long long *)c.phi);
+        } else {
+            if (c.prec == EKL_F64) ws_apply<double><<<bn, 256, 0, c.stream>>>(N, c.mask, ws.W.y, ws.s_out, (double *)c.phi);
+            else ws_apply<long long><<<bn, 256, 0, c.stream>>>(N, c.mask, ws.W.y, ws.s_out, (long long *)c.phi);
+        }
+        c.launches += 7;
     }
     std::swap(ws.bprev, ws.bcur);
     ws.have_prev = 1;
@@ -594,7 +685,22 @@ int warmstart_before_poisson(Ctx &c)
 int warmstart_after_poisson(Ctx &c)
 {
     WarmStart &ws = *(WarmStart *)c.net;
-    if (!ws.collect || c.nb == 0 || ws.used + ws.ncrops > ws.cap) return EKL_OK;
+    if (ws.collect && ws.level && ws.used < ws.cap) {
+        // one sample per step: the whole coarse grid (inputs as fed, target)
+        const size_t NL = (size_t)ws.W.g.N;
+        float *dst = ws.crops + (size_t)ws.used * 3 * NL;
+        cudaMemcpyAsync(dst, ws.W.x, 2 * NL * 4, cudaMemcpyDeviceToDevice, c.stream);
+        if (c.prec == EKL_F64)
+            ws_coarse_target<double><<<(ws.W.g.N + 255) / 256, 256, 0, c.stream>>>(
+                ws.fine, ws.W.g, ws.level, c.mask, (const double *)c.phi, ws.phiprev, dst + 2 * NL);
+        else
+            ws_coarse_target<long long><<<(ws.W.g.N + 255) / 256, 256, 0, c.stream>>>(
+                ws.fine, ws.W.g, ws.level, c.mask, (const long long *)c.phi, ws.phiprev, dst + 2 * NL);
+        c.launches++;
+        ws.used++;
+        return cudaGetLastError() == cudaSuccess ? EKL_OK : EKL_ERR_CUDA;
+    }
+    if (!ws.collect || ws.level || c.nb == 0 || ws.used + ws.ncrops > ws.cap) return EKL_OK;
     const size_t c3 = (size_t)ws.crop * ws.crop * ws.crop;
     float *dst = ws.crops + (size_t)ws.used * 3 * c3;
     if (c.prec == EKL_F64)
@@ -618,25 +724,36 @@ void warmstart_free(Ctx &c)
     cudaFree(ws->bprev);
     cudaFree(ws->bcur);
     cudaFree(ws->phiprev);
+    cudaFree(ws->dbf);
+    cudaFree(ws->phf);
     cudaFree(ws->mean);
     cudaFree(ws->crops);
     delete ws;
     c.net = nullptr;
 }
 
-static int warmstart_ensure(Ctx &c)
+// the warm start's state on the network level `level` (recreated when the
+// level changes; the parameters are installed afterwards)
+static int warmstart_ensure(Ctx &c, int level = -1)
 {
-    if (c.net) return EKL_OK;
+    if (c.net && (level < 0 || ((WarmStart *)c.net)->level == level)) return EKL_OK;
+    if (c.net) warmstart_free(c);
+    if (level < 0) level = 0;
     WarmStart *ws = new (std::nothrow) WarmStart();
     if (!ws) return EKL_ERR_ALLOC;
     const int32_t dims[3] = {c.nx, c.ny, c.nz};
-    ws->W.g = make_grid(dims, c.per);
+    ws->fine = make_grid(dims, c.per);
+    ws->level = level;
+    const int32_t cdims[3] = {c.nx >> level, c.ny >> level, c.nz >> level};
+    ws->W.g = make_grid(cdims, c.per);
     const int N = (int)c.N;
-    int rc = work_alloc(ws->W, N);
+    int rc = work_alloc(ws->W, ws->W.g.N);
     cudaError_t e = rc == EKL_OK ? cudaSuccess : cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = cudaMalloc(&ws->bprev, (size_t)N * 4);
     if (e == cudaSuccess) e = cudaMalloc(&ws->bcur, (size_t)N * 4);
     if (e == cudaSuccess) e = cudaMalloc(&ws->phiprev, (size_t)N * 4);
+    if (e == cudaSuccess && level) e = cudaMalloc(&ws->dbf, (size_t)N * 4);
+    if (e == cudaSuccess && level) e = cudaMalloc(&ws->phf, (size_t)N * 4);
     if (e == cudaSuccess) e = cudaMalloc(&ws->mean, sizeof(double));
     c.net = ws;
     if (e != cudaSuccess) {
@@ -702,14 +819,13 @@ int ekl_net_loss_grad(const int32_t dims[3], const int32_t periodic[3], const fl
     return cuda_err(e);
 }
 
-int ekl_net_train(int32_t nsamples, const int32_t dims[3], const float *x, const float *target,
-                  const uint8_t *mask, float *w, int32_t iters, int32_t batch, float lr, uint64_t seed,
-                  float *loss_out)
+int ekl_net_train_grid(int32_t nsamples, const int32_t dims[3], const int32_t periodic[3], const float *x,
+                       const float *target, const uint8_t *mask, float *w, int32_t iters, int32_t batch, float lr,
+                       uint64_t seed, float *loss_out)
 {
     if (nsamples < 1 || !dims || !x || !target || !w || iters < 0 || batch < 1) return EKL_ERR_ARG;
     NetWork W;
-    const int32_t closed[3] = {0, 0, 0};
-    W.g = make_grid(dims, closed);
+    W.g = make_grid(dims, periodic);
     const int N = W.g.N;
     int rc = work_alloc(W, N);
     if (rc != EKL_OK) { work_free(W); return rc; }
@@ -766,9 +882,34 @@ int ekl_net_train(int32_t nsamples, const int32_t dims[3], const float *x, const
     return cuda_err(e);
 }
 
+int ekl_net_train(int32_t nsamples, const int32_t dims[3], const float *x, const float *target,
+                  const uint8_t *mask, float *w, int32_t iters, int32_t batch, float lr, uint64_t seed,
+                  float *loss_out)
+{
+    const int32_t closed[3] = {0, 0, 0};
+    return ekl_net_train_grid(nsamples, dims, closed, x, target, mask, w, iters, batch, lr, seed, loss_out);
+}
+
 }  // extern "C"
 
 extern "C" {
+
+int ekl_warmstart_level(ekl_handle *h, int32_t level)
+{
+    if (!h || level < 0 || level > 4) return EKL_ERR_ARG;
+    ekl::DeviceScope dscope(h->c.device);
+    if (!dscope.ok()) {
+        ekl::set_last_error("the handle's device cannot be made current");
+        return EKL_ERR_ARG;
+    }
+    ekl::Ctx &c = h->c;
+    const int B = 1 << level;
+    if (c.nx % B || c.ny % B || c.nz % B) {
+        ekl::set_last_error("every extent must be a multiple of 2^level");
+        return EKL_ERR_ARG;
+    }
+    return ekl::warmstart_ensure(c, level);
+}
 
 int ekl_set_warmstart(ekl_handle *h, const float *w, const float scales[3])
 {
@@ -799,17 +940,17 @@ int ekl_set_warmstart(ekl_handle *h, const float *w, const float scales[3])
 int ekl_warmstart_collect(ekl_handle *h, int32_t nsteps, int32_t crop, int32_t ncrops, uint64_t seed, float *out,
                           int64_t *n_out)
 {
-    if (!h || nsteps < 1 || crop < 4 || ncrops < 1 || !out) return EKL_ERR_ARG;
+    if (!h || nsteps < 1 || ncrops < 1 || !out) return EKL_ERR_ARG;
     ekl::DeviceScope dscope(h->c.device);
     if (!dscope.ok()) {
         ekl::set_last_error("the handle's device cannot be made current");
         return EKL_ERR_ARG;
     }
     ekl::Ctx &c = h->c;
-    if (c.nb == 0) return EKL_ERR_ARG;
     int rc = ekl::warmstart_ensure(c);
     if (rc != EKL_OK) return rc;
     WarmStart &ws = *(WarmStart *)c.net;
+    if (!ws.level && (c.nb == 0 || crop < 4)) return EKL_ERR_ARG;  // bead-centred crops
     const int en = ws.enabled;
     const float s0 = ws.s_db, s1 = ws.s_phi, s2 = ws.s_out;
     ws.enabled = 0;
@@ -818,9 +959,10 @@ int ekl_warmstart_collect(ekl_handle *h, int32_t nsteps, int32_t crop, int32_t n
     ws.crop = crop;
     ws.ncrops = ncrops;
     ws.seed = seed;
-    ws.cap = (long long)nsteps * ncrops;
+    // level > 0: one sample per step, the whole coarse grid
+    ws.cap = ws.level ? (long long)nsteps : (long long)nsteps * ncrops;
     ws.used = 0;
-    const size_t c3 = (size_t)crop * crop * crop;
+    const size_t c3 = ws.level ? (size_t)ws.W.g.N : (size_t)crop * crop * crop;
     if (cudaMalloc(&ws.crops, (size_t)ws.cap * 3 * c3 * 4) != cudaSuccess) {
         ws.collect = 0;
         return EKL_ERR_ALLOC;

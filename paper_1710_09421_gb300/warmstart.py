@@ -1,18 +1,21 @@
 """Training and evaluation of the learned Poisson warm start.
 
-Data: crops recorded by the library during plain steps (ekl_warmstart_collect):
-the change of the Poisson source, the previous potential and the change of
-the converged potential, near the beads.  Inputs and target are scaled by
-their standard deviations; the target's crop mean is removed (a constant does
+Data recorded by the library during plain steps (ekl_warmstart_collect): the
+change of the Poisson source, the previous potential and the change of the
+converged potential -- as crops near the beads when the network runs on the
+lattice, or as whole coarse grids when it runs on a coarse level
+(ekl_warmstart_level).  Inputs and target are scaled by their standard
+deviations; the target's mean over each sample is removed (a constant does
 not change the residual) and the previous potential gets a random constant
-per crop so the network learns not to depend on the potential's level.
-Training runs on the GPU (ekl_net_train); nothing here touches the oracle.
+per sample so the network learns not to depend on the potential's level.
+Training runs on the GPU (ekl_net_train, ekl_net_train_grid); nothing here
+touches the oracle.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import EKL_NET_PARAMS, ekl_net_train
+from . import EKL_NET_PARAMS, ekl_net_train, ekl_net_train_grid
 
 CHANNELS = (2, 16, 16, 16, 1)
 
@@ -44,6 +47,29 @@ def prepare(crops, seed=0):
     mask = np.zeros((c, c, c), np.uint8)
     mask[4:c - 4, 4:c - 4, 4:c - 4] = 1   # receptive field inside the crop
     return x, t, mask, (s_db, s_phi, s_out)
+
+
+def prepare_fields(samples, seed=0):
+    """(x, t, scales) from whole coarse-grid samples[k][3][nz][ny][nx]."""
+    rng = np.random.default_rng(seed)
+    db, ph, dp = samples[:, 0], samples[:, 1], samples[:, 2]
+    s_db = 1.0 / max(float(db.std()), 1e-30)
+    s_phi = 1.0 / max(float(ph.std()), 1e-30)
+    tgt = dp - dp.mean(axis=(1, 2, 3), keepdims=True)
+    s_out = max(float(tgt.std()), 1e-30)
+    phc = ph - ph.mean(axis=(1, 2, 3), keepdims=True) + rng.normal(0, 2 * ph.std(), (len(ph), 1, 1, 1))
+    x = np.stack([db * s_db, phc * s_phi], axis=1).astype(np.float32)
+    t = (tgt / s_out).astype(np.float32)
+    return x, t, (s_db, s_phi, s_out)
+
+
+def train_fields(samples, periodic, iters=1000, batch=8, lr=2e-3, seed=0):
+    """Train the network on whole coarse grids of a box with the given
+    periodic axes; returns (weights, scales, loss curve)."""
+    x, t, scales = prepare_fields(samples, seed)
+    nz, ny, nx = samples.shape[-3:]
+    w, curve = ekl_net_train_grid((nx, ny, nz), periodic, x, t, None, init_params(seed), iters, batch, lr, seed)
+    return w, scales, curve
 
 
 def train(crops, iters=600, batch=8, lr=2e-3, seed=0):
