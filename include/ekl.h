@@ -331,6 +331,13 @@ int ekl_warmstart_collect(ekl_handle *h, int32_t nsteps, int32_t crop, int32_t n
  * Errors: EKL_ERR_ARG. */
 int ekl_warmstart_level(ekl_handle *h, int32_t level);
 
+/* Tensor-core path of the two 16 -> 16 layers (no counterpart in the paper):
+ * 1 = tcgen05.mma implicit GEMM, 128 nodes per block, FP32 accumulator in
+ * tensor memory (default); 0 = the warp-level mma.sync form; other values
+ * leave it unchanged.  Returns the previous path.  Process-wide; the network
+ * calls return EKL_ERR_TIMEOUT if a block gave up waiting for its MMAs. */
+int ekl_net_tensor_path(int32_t path);
+
 /* ekl_net_train on a grid whose periodic axes wrap (whole coarse fields of
  * a periodic box); ekl_net_train is this with every axis closed. */
 int ekl_net_train_grid(int32_t nsamples, const int32_t dims[3], const int32_t periodic[3], const float *x,

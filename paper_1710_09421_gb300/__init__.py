@@ -145,6 +145,7 @@ def load(build_if_missing: bool = True):
                                             C.POINTER(C.c_int64)]
         L.ekl_net_loss_grad.argtypes = [vp, vp, vp, vp, vp, vp, C.POINTER(C.c_double), vp]
         L.ekl_warmstart_level.argtypes = [vp, C.c_int32]
+        L.ekl_net_tensor_path.argtypes = [C.c_int32]
         L.ekl_net_train_grid.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, C.c_int32, C.c_int32, C.c_float,
                                          C.c_uint64, vp]
         L.ekl_net_train.argtypes = [C.c_int32, vp, vp, vp, vp, vp, C.c_int32, C.c_int32, C.c_float,

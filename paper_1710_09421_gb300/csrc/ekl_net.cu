@@ -10,10 +10,12 @@
 // beyond closed ones.
 //
 // The two 16 -> 16 layers (about 93 % of the arithmetic) are implicit GEMMs
-// on the tensor cores: per warp 16 nodes x 16 output channels, K = 27 offsets
-// x 16 input channels, BF16 operands, FP32 accumulation (mma.sync m16n8k16);
-// the data gradient of those layers is the same kernel with flipped offsets
-// and transposed channels.  The 2 -> 16 and 16 -> 1 layers, the weight
+// on the tensor cores, K = 27 offsets x 16 input channels, BF16 operands,
+// FP32 accumulation: by default on tcgen05 (128 nodes per block, the
+// accumulator in tensor memory, operands staged in shared memory), or with
+// the warp-level mma.sync m16n8k16 (16 nodes per warp); the data gradient of
+// those layers is the same kernel with flipped offsets and transposed
+// channels.  The 2 -> 16 and 16 -> 1 layers, the weight
 // gradients (per-block partial sums reduced in a fixed order) and Adam run on
 // the CUDA cores in FP32.
 #include <cuda_bf16.h>
@@ -184,6 +186,175 @@ __global__ void __launch_bounds__(256) conv16_mma(NetGrid g, const __nv_bfloat16
             if (na < g.N) *(__nv_bfloat162 *)(o + (size_t)na * 16 + co) = __floats2bfloat162_rn(v[0], v[1]);
             if (nb < g.N) *(__nv_bfloat162 *)(o + (size_t)nb * 16 + co) = __floats2bfloat162_rn(v[2], v[3]);
         }
+    }
+}
+
+// ---------------------------------------------------------------- 16 -> 16 on tcgen05
+// The same layer as an implicit GEMM on the fifth-generation tensor cores:
+// a block takes 128 consecutive nodes (M = 128), N = 16 output channels, and
+// K = 27 offsets x 16 input channels as 27 MMAs of K = 16 (one per offset),
+// BF16 operands from shared memory, FP32 accumulation in tensor memory.
+//   * A (per offset): the 16 input channels of each node's neighbour, 128 x 16
+//     BF16, K-major without swizzle: core matrices of 8 rows x 16 bytes,
+//     row-group g and K-half h at byte g * 256 + h * 128 (LBO = 128 between
+//     the K-halves, SBO = 256 between row groups);
+//   * B (per offset): W[co][ci], 16 x 16 BF16, the same layout;
+//   * D: TMEM lanes 0..127 = nodes, columns 0..15 = output channels; warp w
+//     reads lanes 32w..32w+31 back with tcgen05.ld (32x32b, 16 columns).
+// One thread issues the 27 MMAs and commits them to an mbarrier; the wait is
+// bounded (on giving up the block raises tc_status and skips the epilogue),
+// and the block frees its tensor memory on every path.
+constexpr int TC_M = 128;
+constexpr int TC_A_BYTES = TC_M * 32;           // one offset's A tile
+constexpr int TC_B_BYTES = 16 * 32;             // one offset's B tile
+constexpr int TC_SMEM = K27 * (TC_A_BYTES + TC_B_BYTES) + 64;
+
+__device__ int tc_status;  // nonzero after a bounded wait gave up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: no swizzle, K-major core matrices
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor: D FP32, A and B BF16, both K-major, N = 16, M = 128
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+// byte offset of element (row, k) (k < 16) in a no-swizzle K-major tile
+__device__ __forceinline__ int tc_off(int row, int k) { return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2; }
+
+// wait (bounded, about a second at most) for phase 0 of the mbarrier
+__device__ __forceinline__ uint32_t tc_wait(uint64_t *mbar)
+{
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 20) && !done; it++) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(mbar)));
+    }
+    return done;
+}
+
+template <bool RELU>
+__global__ void __launch_bounds__(TC_M) conv16_tc(NetGrid g, const __nv_bfloat16 *__restrict__ in,
+                                                  const __nv_bfloat16 *__restrict__ Wt,
+                                                  const float *__restrict__ bias, int flip,
+                                                  __nv_bfloat16 *__restrict__ out,
+                                                  const __nv_bfloat16 *__restrict__ relu_mask_src)
+{
+    extern __shared__ __align__(1024) uint8_t tc_sm[];
+    uint8_t *sA = tc_sm;                              // [27][TC_A_BYTES]
+    uint8_t *sB = tc_sm + K27 * TC_A_BYTES;           // [27][TC_B_BYTES]
+    uint64_t *mbar = (uint64_t *)(sB + K27 * TC_B_BYTES);
+    uint32_t *tmem_slot = (uint32_t *)(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n = blockIdx.x * TC_M + tid;
+    const bool valid = n < g.N;
+
+    // tensor memory: 32 columns (the smallest allocation) for the 16 of D
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;\n" ::"r"(smem_u32(tmem_slot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)));
+    }
+    // operands: B tiles (weights of every offset), A tiles (this thread's
+    // node's neighbour at every offset, zero beyond a closed face)
+    for (int t = tid; t < K27 * 16 * 2; t += TC_M) {
+        const int k = t >> 5, co = (t >> 1) & 15, h = t & 1;
+        const uint4 v = *(const uint4 *)(Wt + ((size_t)k * 16 + co) * 16 + 8 * h);
+        *(uint4 *)(sB + k * TC_B_BYTES + tc_off(co, 8 * h)) = v;
+    }
+    int X = 0, Y = 0, Z = 0;
+    if (valid) xyz_of(g, n, X, Y, Z);
+    for (int k = 0; k < K27; k++) {
+        const int j = valid ? nbr_off(g, X, Y, Z, flip ? 26 - k : k) : -1;
+        uint4 v0 = make_uint4(0u, 0u, 0u, 0u), v1 = v0;
+        if (j >= 0) {
+            const uint4 *src = (const uint4 *)(in + (size_t)j * 16);
+            v0 = src[0];
+            v1 = src[1];
+        }
+        *(uint4 *)(sA + k * TC_A_BYTES + tc_off(tid, 0)) = v0;
+        *(uint4 *)(sA + k * TC_A_BYTES + tc_off(tid, 8)) = v1;
+    }
+    // make the generic-proxy writes visible to the tensor cores' async proxy
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    if (tid == 0) {
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        for (int k = 0; k < K27; k++) {
+            const uint64_t ad = tc_desc(a0 + k * TC_A_BYTES, 128, 256);
+            const uint64_t bd = tc_desc(b0 + k * TC_B_BYTES, 128, 256);
+            const uint32_t acc = k > 0;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_u32(mbar)));
+    }
+    // bounded wait for the MMAs (phase 0 of the mbarrier)
+    uint32_t done = tc_wait(mbar);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (!done) {
+        // give up: raise the status, wait once more (bounded) for the MMAs
+        // still in flight, then free the tensor memory below
+        if (lane == 0) atomicExch(&tc_status, 1);
+        done = tc_wait(mbar);
+    } else {
+        uint32_t d[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];\n"
+            : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7]),
+              "=r"(d[8]), "=r"(d[9]), "=r"(d[10]), "=r"(d[11]), "=r"(d[12]), "=r"(d[13]), "=r"(d[14]), "=r"(d[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (valid) {
+            float v[16];
+#pragma unroll
+            for (int co = 0; co < 16; co++) {
+                v[co] = __uint_as_float(d[co]) + (bias ? bias[co] : 0.f);
+                if (RELU) v[co] = fmaxf(v[co], 0.f);
+                // gradient through the ReLU of the layer that produced relu_mask_src
+                if (relu_mask_src && !(__bfloat162float(relu_mask_src[(size_t)n * 16 + co]) > 0.f)) v[co] = 0.f;
+            }
+            __nv_bfloat162 *o = (__nv_bfloat162 *)(out + (size_t)n * 16);
+#pragma unroll
+            for (int c = 0; c < 8; c++) o[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;\n" ::"r"(tmem));
+}
+
+// which kernel runs the 16 -> 16 layers: 1 = tcgen05 (default), 0 = mma.sync
+int g_tensor_path = 1;
+
+template <bool RELU>
+void conv16(const NetGrid &g, const __nv_bfloat16 *in, const __nv_bfloat16 *Wt, const float *bias, int flip,
+            __nv_bfloat16 *out, const __nv_bfloat16 *relu_mask_src, cudaStream_t s)
+{
+    if (g_tensor_path) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(conv16_tc<RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+            attr = true;
+        }
+        conv16_tc<RELU><<<(g.N + TC_M - 1) / TC_M, TC_M, TC_SMEM, s>>>(g, in, Wt, bias, flip, out, relu_mask_src);
+    } else {
+        conv16_mma<RELU, false><<<(g.N + 127) / 128, 256, 0, s>>>(g, in, Wt, bias, flip, out, relu_mask_src);
     }
 }
 
@@ -409,10 +580,9 @@ void net_forward(NetWork &W, cudaStream_t s)
     prep_w16<<<27, 256, 0, s>>>(W.w, OW2, W.W2f, W.W2b);
     prep_w16<<<27, 256, 0, s>>>(W.w, OW3, W.W3f, W.W3b);
     const int bn = (g.N + NT - 1) / NT;
-    const int bm = (g.N + 127) / 128;  // 8 warps x 16 nodes per block
     l1_fwd<<<bn, NT, 0, s>>>(g, W.x, W.w, W.a1);
-    conv16_mma<true, false><<<bm, 256, 0, s>>>(g, W.a1, W.W2f, W.w + OB2, 0, W.a2, nullptr);
-    conv16_mma<true, false><<<bm, 256, 0, s>>>(g, W.a2, W.W3f, W.w + OB3, 0, W.a3, nullptr);
+    conv16<true>(g, W.a1, W.W2f, W.w + OB2, 0, W.a2, nullptr, s);
+    conv16<true>(g, W.a2, W.W3f, W.w + OB3, 0, W.a3, nullptr, s);
     l4_fwd<<<bn, NT, 0, s>>>(g, W.a3, W.w, W.y);
 }
 
@@ -421,7 +591,6 @@ int net_backward(NetWork &W, const float *d_t, const uint8_t *d_mask, float inv_
 {
     const NetGrid &g = W.g;
     const int bn = (g.N + NT - 1) / NT;
-    const int bm = (g.N + 127) / 128;
     const int bw = (g.N + 511) / 512;
     loss_grad_k<<<bn, NT, 0, s>>>(g.N, W.y, d_t, d_mask, inv_cnt, W.gy, W.lpart);
     // layer 4
@@ -431,11 +600,11 @@ int net_backward(NetWork &W, const float *d_t, const uint8_t *d_mask, float inv_
     // layer 3: dz holds d z3 (through relu of a3)
     wgrad_partial<16, 16><<<bw, NT, 0, s>>>(g, W.a2, 1, W.dz, 1, W.part);
     reduce_partials<<<(16 * 16 * 27 + 16 + 255) / 256, 256, 0, s>>>(W.part, bw, 16 * 16 * 27 + 16, W.grad, OW3);
-    conv16_mma<false, false><<<bm, 256, 0, s>>>(g, W.dz, W.W3b, nullptr, 1, W.dz2, W.a2);
+    conv16<false>(g, W.dz, W.W3b, nullptr, 1, W.dz2, W.a2, s);
     // layer 2
     wgrad_partial<16, 16><<<bw, NT, 0, s>>>(g, W.a1, 1, W.dz2, 1, W.part);
     reduce_partials<<<(16 * 16 * 27 + 16 + 255) / 256, 256, 0, s>>>(W.part, bw, 16 * 16 * 27 + 16, W.grad, OW2);
-    conv16_mma<false, false><<<bm, 256, 0, s>>>(g, W.dz2, W.W2b, nullptr, 1, W.dz, W.a1);
+    conv16<false>(g, W.dz2, W.W2b, nullptr, 1, W.dz, W.a1, s);
     // layer 1
     wgrad_partial<2, 16><<<bw, NT, 0, s>>>(g, W.x, 0, W.dz, 1, W.part);
     reduce_partials<<<(16 * 2 * 27 + 16 + 255) / 256, 256, 0, s>>>(W.part, bw, 16 * 2 * 27 + 16, W.grad, OW1);
@@ -765,7 +934,26 @@ static int warmstart_ensure(Ctx &c, int level = -1)
 
 }  // namespace ekl
 
+// EKL_ERR_TIMEOUT when a tensor-core block gave up waiting for its MMAs
+// (the flag is cleared on reading)
+static int tc_check()
+{
+    int st = 0;
+    if (cudaMemcpyFromSymbol(&st, tc_status, sizeof(int)) != cudaSuccess) return EKL_ERR_CUDA;
+    if (!st) return EKL_OK;
+    const int zero = 0;
+    cudaMemcpyToSymbol(tc_status, &zero, sizeof(int));
+    return EKL_ERR_TIMEOUT;
+}
+
 extern "C" {
+
+int ekl_net_tensor_path(int32_t path)
+{
+    const int prev = g_tensor_path;
+    if (path == 0 || path == 1) g_tensor_path = path;
+    return prev;
+}
 
 int ekl_net_eval(const int32_t dims[3], const int32_t periodic[3], const float *x, const float *w, float *y)
 {
@@ -781,6 +969,7 @@ int ekl_net_eval(const int32_t dims[3], const int32_t periodic[3], const float *
         e = cudaMemcpy(y, W.y, (size_t)W.g.N * 4, cudaMemcpyDeviceToHost);
     }
     work_free(W);
+    if (e == cudaSuccess) return tc_check();
     return cuda_err(e);
 }
 
@@ -816,6 +1005,7 @@ int ekl_net_loss_grad(const int32_t dims[3], const int32_t periodic[3], const fl
     cudaFree(dm);
     work_free(W);
     if (rc != EKL_OK) return rc;
+    if (e == cudaSuccess) return tc_check();
     return cuda_err(e);
 }
 
@@ -879,6 +1069,7 @@ int ekl_net_train_grid(int32_t nsamples, const int32_t dims[3], const int32_t pe
     cudaFree(dx); cudaFree(dt); cudaFree(m1); cudaFree(m2); cudaFree(dm);
     work_free(W);
     if (rc != EKL_OK) return rc;
+    if (e == cudaSuccess) return tc_check();
     return cuda_err(e);
 }
 

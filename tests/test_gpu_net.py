@@ -1,7 +1,9 @@
 """Warm-start network kernels (BF16 tensor-core implicit GEMMs, FP32
 accumulation) against the FP64 numpy oracle: forward output, loss and every
-parameter gradient within BF16-level tolerances, and GPU training lowers the
-loss on a learnable mapping."""
+parameter gradient within BF16-level tolerances, on both tensor paths of the
+16 -> 16 layers (tcgen05 with the accumulator in tensor memory, and the
+warp-level mma.sync form), the two paths against each other, and GPU
+training lowers the loss on a learnable mapping."""
 import numpy as np
 import pytest
 
@@ -18,16 +20,43 @@ def _case(seed, shape=(12, 10, 14)):
     return rng, x, w
 
 
+@pytest.fixture(params=[1, 0], ids=["tcgen05", "mma_sync"])
+def tensor_path(request):
+    lib = E.load()
+    prev = lib.ekl_net_tensor_path(request.param)
+    yield request.param
+    lib.ekl_net_tensor_path(prev)
+
+
 @pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (1, 0, 1)])
-def test_forward_matches_oracle(periodic):
+def test_forward_matches_oracle(periodic, tensor_path):
     rng, x, w = _case(0)
     nz, ny, nx = x.shape[1:]
     y = E.ekl_net_eval((nx, ny, nz), periodic, x, w)
     ref = net.forward(x.astype(np.float64), w.astype(np.float64), periodic)
-    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 2e-2
+    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    print(tensor_path, periodic, err)
+    assert err < 1e-2
 
 
-def test_loss_and_gradient_match_oracle():
+def test_tcgen05_matches_mma_sync_on_a_ragged_grid():
+    """1190 nodes: nine full 128-node tiles and a ragged one.  The two paths
+    differ only in the order of the FP32 accumulation inside an MMA, which
+    can move a BF16 activation by one unit between layers."""
+    rng, x, w = _case(3, (7, 10, 17))
+    nz, ny, nx = x.shape[1:]
+    lib = E.load()
+    prev = lib.ekl_net_tensor_path(1)
+    y1 = E.ekl_net_eval((nx, ny, nz), (1, 0, 1), x, w)
+    lib.ekl_net_tensor_path(0)
+    y0 = E.ekl_net_eval((nx, ny, nz), (1, 0, 1), x, w)
+    lib.ekl_net_tensor_path(prev)
+    d = np.linalg.norm(y1 - y0) / np.linalg.norm(y0)
+    print("tcgen05 vs mma.sync", d)
+    assert d < 5e-3
+
+
+def test_loss_and_gradient_match_oracle(tensor_path):
     rng, x, w = _case(1)
     nz, ny, nx = x.shape[1:]
     t = rng.standard_normal(x.shape[1:]).astype(np.float32)
@@ -41,7 +70,8 @@ def test_loss_and_gradient_match_oracle():
     for ci, co in zip(net.CHANNELS[:-1], net.CHANNELS[1:]):
         for n in (co * ci * 27, co):
             seg, ref = g[o:o + n], gref[o:o + n]
-            assert np.linalg.norm(seg - ref) <= 5e-2 * np.linalg.norm(ref) + 1e-7, (ci, co, n)
+            print(tensor_path, ci, co, n, np.linalg.norm(seg - ref) / np.linalg.norm(ref))
+            assert np.linalg.norm(seg - ref) <= 2e-2 * np.linalg.norm(ref) + 1e-7, (ci, co, n)
             o += n
 
 
