@@ -47,3 +47,11 @@ def test_clock_summary():
     assert c.summary()["reasons"] == ["hw_slowdown"]
     c.rows = []
     assert c.summary()["reasons"] == ["unsampled"]
+
+
+def test_translocation_progress_step():
+    """Samples every 10 steps (the first at step 10): the centre of mass
+    falls 2 units below the first sample between the samples at steps 40
+    (8.2) and 50 (7.5): step 40 + 10 * 0.2 / 0.7."""
+    assert abs(bench.progress_step([10, 9.5, 9.0, 8.2, 7.5], 10) - (40 + 10 * 0.2 / 0.7)) < 0.01
+    assert bench.progress_step([10, 9.9, 9.8], 10) is None
