@@ -309,78 +309,106 @@ __device__ __forceinline__ void sor_apply(PhiT *phi, int i, uint32_t m, PhiT bi,
 constexpr int POIS_KMAX = 2;  // nodes per colour a thread keeps in registers
 
 // Poisson source of the step, b = 4 pi l_B (rho - <rho>_fluid) on fluid
-// nodes and 0 on walls (Eqs. 2-3 with the neutralising mean of Sec. III),
-// written to a.b; returns this block's sum of b^2 (valid in thread 0).
-// Every thread of the block must call it.
+// nodes and 0 on walls (Eqs. 2-3 with the neutralising mean of Sec. III).
+// SrcMean holds the mean in the forms the per-node formula needs.
+struct SrcMean {
+    double mean;             // FP64 path: the mean charge over the fluid nodes
+    long long mean_lo, C_int;  // fixed-point path: see source_value
+    float C_frac;
+};
+
+// Every thread of the block must call it (the charge pass's block partials
+// are summed by the block).
 template <typename S, typename R, typename PhiT>
-__device__ double form_source(const StepArgs<S, R, PhiT> &a, int tid, int nthr, double *sh, double *bc)
+__device__ SrcMean source_mean(const StepArgs<S, R, PhiT> &a, double *bc)
 {
+    SrcMean sm{0.0, 0, 0, 0.f};
     const double csum = sum_partials(a.part_charge, a.nblocks_charge, bc);
     const double nfl = a.n_fluid;
-    const double mean = nfl > 0 ? csum / nfl : 0.0;
+    sm.mean = nfl > 0 ? csum / nfl : 0.0;
     // fixed point: the exact total S of rho * 2^40 over the fluid nodes,
     // S / n = mean_lo + frac with 0 <= frac < 1, and C = c4 frac split into
     // integer and fraction
-    long long mean_lo = 0, C_int = 0;
-    float C_frac = 0.f;
     if constexpr (!(((PhiT)0.5) != 0)) {
         const long long S = sum_partials_ll(a.part_charge_q, a.nblocks_charge);
         const long long n = (long long)nfl;
         if (n > 0) {
-            mean_lo = S / n;
+            long long mean_lo = S / n;
             long long rem = S - mean_lo * n;
             if (rem < 0) {
                 mean_lo -= 1;
                 rem += n;
             }
             const double C = (double)(float)a.c4 * ((double)rem / (double)n);
-            C_int = (long long)floor(C);
-            C_frac = (float)(C - (double)C_int);
+            sm.mean_lo = mean_lo;
+            sm.C_int = (long long)floor(C);
+            sm.C_frac = (float)(C - (double)sm.C_int);
         }
     }
+    return sm;
+}
+
+// b of one fluid node i with charge density rho; adds b^2 to bl (FP64 path)
+// or blf (fixed-point path, in units of the potential)
+template <typename R, typename PhiT>
+__device__ __forceinline__ PhiT source_value(R rho, long long i, R c4, const SrcMean &sm, double &bl, float &blf)
+{
+    if constexpr (((PhiT)0.5) != 0) {
+        const double v = (double)c4 * ((double)rho - sm.mean);
+        bl += v * v;
+        return (PhiT)v;
+    } else {
+        // Fixed point throughout, without FP64 per node.  rho * 2^40 is
+        // exact (a power-of-two scaling of an FP32 value; rounded to the
+        // nearest 2^-40 below 2^-17) and its total S over the fluid nodes
+        // comes exactly from the charge pass; d = q - floor(S / n) is an
+        // integer, c4 d is formed as an unevaluated float pair (the
+        // product's rounding error recovered by an FMA), the fractional
+        // mean enters as C = c4 frac, and x = c4 d - C is rounded to an
+        // integer stochastically, floor(x + u) with u uniform per node.
+        // The source then sums to zero up to a random walk of unit
+        // roundings.  Any rounding shared by many nodes (the mean rounded
+        // once, or the same rounding of c4 d on the many nodes that carry
+        // the same charge) would instead leave a net source of up to half
+        // a unit per node, which a periodic or all-Neumann problem cannot
+        // absorb: on 33.5 M nodes it stalled CG near a relative residual
+        // of 1e-6.
+        const long long d = float_to_ll((float)rho * (float)PHI_SCALE) - sm.mean_lo;
+        const float d_hi = ll_to_float(d);
+        const float d_lo = ll_to_float(d - float_to_ll(d_hi));  // exact remainder
+        const float c4f = (float)c4;
+        const float p = c4f * d_hi;
+        const float lo = fmaf(c4f, d_hi, -p) + c4f * d_lo;
+        const float fp = floorf(p), fl = floorf(lo);
+        const float F = (p - fp) + (lo - fl) - sm.C_frac + node_uniform(i);
+        const PhiT bv = float_to_ll(fp) + float_to_ll(fl) - sm.C_int + (long long)floorf(F);
+        const float v = ll_to_float(bv) * (float)PHI_INV;
+        blf += v * v;
+        return bv;
+    }
+}
+
+// block total of the per-thread b^2 sums (valid in thread 0)
+template <typename PhiT> __device__ __forceinline__ double source_norm(double bl, float blf, double *sh)
+{
+    if constexpr (((PhiT)0.5) != 0) return block_sum(bl, sh);
+    else return block_sum_lanes0(warp_sum_ff_lane0(blf), sh);
+}
+
+// Writes the source to a.b; returns this block's sum of b^2 (valid in
+// thread 0).  Every thread of the block must call it.
+template <typename S, typename R, typename PhiT>
+__device__ double form_source(const StepArgs<S, R, PhiT> &a, int tid, int nthr, double *sh, double *bc)
+{
+    const SrcMean sm = source_mean(a, bc);
     double bl = 0.0;
     float blf = 0.f;
     for (long long i = tid; i < a.g.N; i += nthr) {
-        uint32_t m = a.mask[i];
-        PhiT bv;
-        if (m & SOLID_BIT) {
-            bv = (PhiT)0;
-        } else if constexpr (((PhiT)0.5) != 0) {
-            double v = (double)a.c4 * ((double)a.rho[i] - mean);
-            bv = (PhiT)v;
-            bl += v * v;
-        } else {
-            // Fixed point throughout, without FP64 per node.  rho * 2^40 is
-            // exact (a power-of-two scaling of an FP32 value; rounded to the
-            // nearest 2^-40 below 2^-17) and its total S over the fluid nodes
-            // comes exactly from the charge pass; d = q - floor(S / n) is an
-            // integer, c4 d is formed as an unevaluated float pair (the
-            // product's rounding error recovered by an FMA), the fractional
-            // mean enters as C = c4 frac, and x = c4 d - C is rounded to an
-            // integer stochastically, floor(x + u) with u uniform per node.
-            // The source then sums to zero up to a random walk of unit
-            // roundings.  Any rounding shared by many nodes (the mean rounded
-            // once, or the same rounding of c4 d on the many nodes that carry
-            // the same charge) would instead leave a net source of up to half
-            // a unit per node, which a periodic or all-Neumann problem cannot
-            // absorb: on 33.5 M nodes it stalled CG near a relative residual
-            // of 1e-6.
-            const long long d = float_to_ll((float)a.rho[i] * (float)PHI_SCALE) - mean_lo;
-            const float d_hi = ll_to_float(d);
-            const float d_lo = ll_to_float(d - float_to_ll(d_hi));  // exact remainder
-            const float c4f = (float)a.c4;
-            const float p = c4f * d_hi;
-            const float lo = fmaf(c4f, d_hi, -p) + c4f * d_lo;
-            const float fp = floorf(p), fl = floorf(lo);
-            const float F = (p - fp) + (lo - fl) - C_frac + node_uniform(i);
-            bv = float_to_ll(fp) + float_to_ll(fl) - C_int + (long long)floorf(F);
-            const float v = ll_to_float(bv) * (float)PHI_INV;
-            blf += v * v;
-        }
+        const uint32_t m = a.mask[i];
+        const PhiT bv = (m & SOLID_BIT) ? (PhiT)0 : source_value<R, PhiT>(a.rho[i], i, a.c4, sm, bl, blf);
         __stcg(a.b + i, bv);
     }
-    if constexpr (((PhiT)0.5) != 0) return block_sum(bl, sh);
-    else return block_sum_lanes0(warp_sum_ff_lane0(blf), sh);
+    return source_norm<PhiT>(bl, blf, sh);
 }
 
 template <typename S, typename R, typename PhiT>

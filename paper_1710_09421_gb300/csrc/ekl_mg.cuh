@@ -165,49 +165,67 @@ __device__ __forceinline__ int mg_parent(const MgLevel &C, int x, int y, int z)
 // Half sweep of colour c of z <- (r + sum_open z_j) / deg.  PRO: the
 // neighbours' values include the level-1 correction C.e(parent).  RZ: add
 // r_i z_i of both nodes of each pair (the last half sweep of a V-cycle, when
-// the other colour is final).
-template <bool RZ, bool PRO>
+// the other colour is final).  A thread takes U pairs per trip (h, h + nt,
+// ...) and issues the loads of all of them before the first update, so
+// their memory round trips overlap; the updates, and the order of the r.z
+// sum, are those of one pair per trip.
+constexpr int MG_FINE_U = 1;
+template <bool RZ, bool PRO, int U = MG_FINE_U>
 static __device__ void fine_half(const Grid3 &g, const uint32_t *__restrict__ mask, const float *r, float *z,
                                  const MgLevel &C, int c, int t0, int nt, float &rz)
 {
     const int hx = (g.nx + 1) >> 1, np = hx * g.ny * g.nz;
-    for (int h = t0; h < np; h += nt) {
-        const Pair p = mg_pair(h, hx, g.ny, c);
-        if (p.x < g.nx) {
-            // every load is issued before the link word is known (neighbour
-            // indices are always valid; closed faces are masked afterwards),
-            // so a node costs one memory round trip, not two
-            const int i = p.x + g.nx * p.row;
-            int nb[6];
-            face_nbrs(g, p.x, p.y, p.z, i, nb);
-            float zn[6];
+    for (int h0 = t0; h0 < np; h0 += U * nt) {
+        float zn[U][6], ri[U], ro[U], zo[U];
+        uint32_t mk[U], mo[U];
+        int ii[U];
 #pragma unroll
-            for (int f = 0; f < 6; f++) {
-                zn[f] = mg_ldl(z + nb[f]);
-                if (PRO) {
-                    int X, Y, Z;
-                    mg_face_coord(g.nx, g.ny, g.nz, p.x, p.y, p.z, f, X, Y, Z);
-                    zn[f] += mg_ldl(C.e + mg_parent(C, X, Y, Z));
+        for (int u = 0; u < U; u++) {
+            const int h = h0 + u * nt;
+            mk[u] = mo[u] = SOLID_BIT;
+            ii[u] = 0;
+            ri[u] = ro[u] = zo[u] = 0.f;
+            if (h >= np) continue;
+            const Pair p = mg_pair(h, hx, g.ny, c);
+            if (p.x < g.nx) {
+                // every load is issued before the link word is known (neighbour
+                // indices are always valid; closed faces are masked afterwards)
+                const int i = p.x + g.nx * p.row;
+                ii[u] = i;
+                int nb[6];
+                face_nbrs(g, p.x, p.y, p.z, i, nb);
+#pragma unroll
+                for (int f = 0; f < 6; f++) {
+                    zn[u][f] = mg_ldl(z + nb[f]);
+                    if (PRO) {
+                        int X, Y, Z;
+                        mg_face_coord(g.nx, g.ny, g.nz, p.x, p.y, p.z, f, X, Y, Z);
+                        zn[u][f] += mg_ldl(C.e + mg_parent(C, X, Y, Z));
+                    }
                 }
+                ri[u] = mg_ldl(r + i);
+                mk[u] = __ldg(mask + i);
             }
-            const float ri = mg_ldl(r + i);
-            const uint32_t m = __ldg(mask + i);
-            const unsigned o = mg_open(m);
-            if (!(m & SOLID_BIT) && o) {
-                float v = ri;
-#pragma unroll
-                for (int f = 0; f < 6; f++)
-                    if ((o >> f) & 1u) v += zn[f];
-                v *= mg_inv_deg(__popc(o));
-                __stcg(z + i, v);
-                if (RZ) rz += ri * v;
+            if (RZ && p.xo < g.nx) {
+                const int io = p.xo + g.nx * p.row;
+                ro[u] = mg_ldl(r + io);
+                zo[u] = mg_ldl(z + io);
+                mo[u] = __ldg(mask + io);
             }
         }
-        if (RZ && p.xo < g.nx) {
-            const int io = p.xo + g.nx * p.row;
-            const float ro = mg_ldl(r + io), zo = mg_ldl(z + io);
-            const uint32_t m = __ldg(mask + io);
-            if (!(m & SOLID_BIT) && mg_open(m)) rz += ro * zo;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const unsigned o = mg_open(mk[u]);
+            if (!(mk[u] & SOLID_BIT) && o) {
+                float v = ri[u];
+#pragma unroll
+                for (int f = 0; f < 6; f++)
+                    if ((o >> f) & 1u) v += zn[u][f];
+                v *= mg_inv_deg(__popc(o));
+                __stcg(z + ii[u], v);
+                if (RZ) rz += ri[u] * v;
+            }
+            if (RZ && !(mo[u] & SOLID_BIT) && mg_open(mo[u])) rz += ro[u] * zo[u];
         }
     }
 }
@@ -838,37 +856,55 @@ __device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const 
 
 // true residual r = b - A phi (exact in the potential type), as FP32, with
 // the first pre-smoothing half sweep (colour-0 z = r / deg); returns this
-// block's sum of r^2 (thread 0)
+// block's sum of r^2 (thread 0).  A thread takes MG_RES_U nodes per trip (one
+// per grid stride) with all their loads issued first; its nodes are still
+// summed in increasing order.
+constexpr int MG_RES_U = 2;
 template <typename PhiT>
 __device__ double mg_true_residual(const Grid3 &g, const uint32_t *__restrict__ mask, const PhiT *phi,
                                    const PhiT *b, float *r, float *z, int t0, int nt, double *sh)
 {
     float rr = 0.f;
     const int N = (int)g.N;
-    for (int i = t0; i < N; i += nt) {
-        const int x = i % g.nx, t = i / g.nx, y = t % g.ny, zz = t / g.ny;
-        int nb[6];
-        face_nbrs(g, x, y, zz, i, nb);
-        PhiT pn[6];
+    for (long long i0 = t0; i0 < N; i0 += (long long)MG_RES_U * nt) {
+        PhiT pn[MG_RES_U][6], bi[MG_RES_U], phii[MG_RES_U];
+        uint32_t mk[MG_RES_U];
+        int xyz[MG_RES_U];
 #pragma unroll
-        for (int f = 0; f < 6; f++) pn[f] = mg_ldl(phi + nb[f]);
-        const PhiT bi = mg_ldl(b + i), phii = mg_ldl(phi + i);
-        const uint32_t m = __ldg(mask + i);
-        if (m & SOLID_BIT) continue;
-        const unsigned o = mg_open(m);
-        float rv = 0.f;
-        if (o) {
-            PhiT acc = bi;
+        for (int k = 0; k < MG_RES_U; k++) {
+            const long long il = i0 + (long long)k * nt;
+            mk[k] = SOLID_BIT;
+            if (il >= N) continue;
+            const int i = (int)il;
+            const int x = i % g.nx, t = i / g.nx, y = t % g.ny, zz = t / g.ny;
+            xyz[k] = x + y + zz;
+            int nb[6];
+            face_nbrs(g, x, y, zz, i, nb);
 #pragma unroll
-            for (int f = 0; f < 6; f++)
-                if ((o >> f) & 1u) acc += pn[f];
-            acc -= (PhiT)__popc(o) * phii;
-            if constexpr (((PhiT)0.5) != 0) rv = (float)acc;
-            else rv = ll_to_float(acc) * (float)PHI_INV;
-            if (!((x + y + zz) & 1)) __stcg(z + i, rv * mg_inv_deg(__popc(o)));
+            for (int f = 0; f < 6; f++) pn[k][f] = mg_ldl(phi + nb[f]);
+            bi[k] = mg_ldl(b + i);
+            phii[k] = mg_ldl(phi + i);
+            mk[k] = __ldg(mask + i);
         }
-        __stcg(r + i, rv);
-        rr += rv * rv;
+#pragma unroll
+        for (int k = 0; k < MG_RES_U; k++) {
+            const int i = (int)(i0 + (long long)k * nt);
+            if (mk[k] & SOLID_BIT) continue;  // also every node past N
+            const unsigned o = mg_open(mk[k]);
+            float rv = 0.f;
+            if (o) {
+                PhiT acc = bi[k];
+#pragma unroll
+                for (int f = 0; f < 6; f++)
+                    if ((o >> f) & 1u) acc += pn[k][f];
+                acc -= (PhiT)__popc(o) * phii[k];
+                if constexpr (((PhiT)0.5) != 0) rv = (float)acc;
+                else rv = ll_to_float(acc) * (float)PHI_INV;
+                if (!(xyz[k] & 1)) __stcg(z + i, rv * mg_inv_deg(__popc(o)));
+            }
+            __stcg(r + i, rv);
+            rr += rv * rv;
+        }
     }
     return block_sum_lanes0(warp_sum_ff_lane0(rr), sh);
 }
@@ -977,6 +1013,58 @@ __device__ float mg_update_pass(const Grid3 &g, const uint32_t *__restrict__ mas
     return rr;
 }
 
+// Start of a solve, one pass: the starting guess phi <- 2 phi(t-1) - phi(t-2),
+// the linear extrapolation of the last two potentials (exact in the
+// fixed-point type; phi(t-1) is kept for the next step), and the source b.
+// A thread takes MG_START_U nodes per trip (one per grid stride) and issues
+// all their loads before it uses any, so their memory round trips overlap;
+// each thread still visits its nodes in increasing order, which keeps the
+// b^2 sum bit-identical to form_source's.  Returns the block's sum of b^2
+// (thread 0).
+constexpr int MG_START_U = 4;
+template <typename S, typename R, typename PhiT>
+__device__ double mg_start_pass(const StepArgs<S, R, PhiT> &a, const MgArgs &m, int tid, int nthr, double *sh,
+                                double *bc)
+{
+    const SrcMean sm = source_mean(a, bc);
+    const int N = (int)a.g.N;
+    PhiT *prev = (PhiT *)m.phi_prev;
+    const bool extrap = m.have_prev != 0;
+    double bl = 0.0;
+    float blf = 0.f;
+    for (long long i0 = tid; i0 < N; i0 += (long long)MG_START_U * nthr) {
+        uint32_t mk[MG_START_U];
+        PhiT cur[MG_START_U], pv[MG_START_U];
+        R rho[MG_START_U];
+#pragma unroll
+        for (int k = 0; k < MG_START_U; k++) {
+            const long long i = i0 + (long long)k * nthr;
+            mk[k] = SOLID_BIT;
+            cur[k] = pv[k] = (PhiT)0;
+            rho[k] = (R)0;
+            if (i < N) {
+                mk[k] = __ldg(a.mask + i);
+                cur[k] = __ldcg(a.phi + i);
+                if (extrap) pv[k] = __ldcg(prev + i);
+                rho[k] = __ldcg(a.rho + i);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < MG_START_U; k++) {
+            const long long i = i0 + (long long)k * nthr;
+            if (i >= N) continue;
+            PhiT bv = (PhiT)0;
+            if (!(mk[k] & SOLID_BIT)) {
+                if (extrap) __stcg(a.phi + i, (PhiT)2 * cur[k] - pv[k]);
+                __stcg(prev + i, cur[k]);
+                bv = source_value<R, PhiT>(rho[k], i, a.c4, sm, bl, blf);
+            }
+            __stcg(a.b + i, bv);
+        }
+    }
+    return source_norm<PhiT>(bl, blf, sh);
+}
+
 template <typename S, typename R, typename PhiT, bool TILES>
 __device__ void mg_solve(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const MgGrid &G, float *mg_sm, double *sh,
                          double *bc)
@@ -998,20 +1086,8 @@ __device__ void mg_solve(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const M
         return true;
     };
     if (G.blk == 0 && !m.dense) mg_cta_load(m, mg_sm);
-    // starting guess: the linear extrapolation 2 phi(t-1) - phi(t-2) of the
-    // last two potentials (exact in the fixed-point type); phi(t-1) is kept
-    // for the next step
-    {
-        PhiT *prev = (PhiT *)m.phi_prev;
-        for (int i = tid; i < N; i += nthr) {
-            if (__ldg(a.mask + i) & SOLID_BIT) continue;
-            const PhiT cur = __ldcg(a.phi + i);
-            if (m.have_prev) __stcg(a.phi + i, (PhiT)2 * cur - __ldcg(prev + i));
-            __stcg(prev + i, cur);
-        }
-    }
     double bb;
-    if (!reduce(form_source(a, tid, nthr, sh, bc), bb)) return;
+    if (!reduce(mg_start_pass(a, m, tid, nthr, sh, bc), bb)) return;
     if (a.fixed_iter <= 0 && bb == 0.0) {
         if (tid == 0) {
             *a.pois_iters = 0;
