@@ -77,6 +77,13 @@ __global__ void wait_selftest_kernel(unsigned *bar, int *status)
     grid_barrier(bar, gridDim.x, k, status);
 }
 
+// The multigrid lattice level's link byte of every node (see mg_link_of).
+__global__ void mg_link_kernel(const uint32_t *__restrict__ mask, uint8_t *__restrict__ link, long long N)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < N) link[i] = mg_link_of(mask[i]);
+}
+
 __global__ void mask_kernel(Grid3 g, int px, int py, int pz, const uint8_t *__restrict__ solid,
                             uint32_t *__restrict__ mask)
 {
@@ -153,11 +160,17 @@ void release(Ctx &c)
         dev_free(c, c.mg_lev[l].t, 0);
     }
     dev_free(c, c.mg_r, 0);
+    dev_free(c, c.mg_link, 0);
     dev_free(c, c.mg_z, 0);
     dev_free(c, c.mg_q, 0);
     dev_free(c, c.mg_p[0], 0);
     dev_free(c, c.mg_p[1], 0);
     dev_free(c, c.mg_part, 0);
+    dev_free(c, c.mgs_ctl, 0);
+    if (c.mgs_exec) cudaGraphExecDestroy(c.mgs_exec);
+    if (c.mgs_graph) cudaGraphDestroy(c.mgs_graph);
+    c.mgs_exec = nullptr;
+    c.mgs_graph = nullptr;
     dev_free(c, c.mg_dense, 0);
     dev_free(c, c.mg_phi_prev, 0);
     warmstart_free(c);
@@ -463,9 +476,11 @@ static void mg_pick_tile(const int ex[3], int H, int nblk, int tmax, size_t max_
 // (fluid to fluid, inside or across a periodic side); on level l+1, half the
 // sum of the level-l conductances crossing the aggregated face.  `tiles`:
 // smooth the grid-wide coarse levels of at most MG_TILE_CELLS_PER_BLOCK cells
-// per block in shared-memory tiles.  Returns an error message, or null.
+// per block in shared-memory tiles.  `split`: run the solve of a large
+// lattice in split form (ekl_mgs.cuh).  Returns an error message, or null.
 template <typename Alloc>
-static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long long coarsest_cells, bool tiles)
+static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long long coarsest_cells, bool tiles,
+                                   bool split)
 {
     int d[MG_MAXLEV][3];
     d[0][0] = c.nx;
@@ -611,13 +626,18 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long 
     // warps in flight (1024-thread blocks) then beat the 512-thread launch
     // that keeps 128 registers a thread for the latency-bound small solve
     c.mg_wide = N >= (long long)MG_WIDE_NODES_PER_SM * c.num_sms;  // (replicas use the batched kernel)
+    // the same lattices run the solve split into per-pass launches
+    c.mg_split = split && c.mg_wide;
+    c.mgs_iter_kernels = 2 * (2 * MG_NU - 1) + 8;
     if (ops(c.prec).mg_blocks(c.mg_smem, c.mg_wide) < 1) return "multigrid kernel cannot be resident";
     c.mg_r = (float *)A(N * sizeof(float));
+    c.mg_link = (uint8_t *)A(N);
     c.mg_z = (float *)A(N * sizeof(float));
     c.mg_q = (float *)A(N * sizeof(float));
     c.mg_p[0] = (float *)A(N * sizeof(float));
     c.mg_p[1] = (float *)A(N * sizeof(float));
-    c.mg_part = (double *)A((size_t)4 * c.pois_blocks * sizeof(double));
+    c.mg_part = (double *)A((size_t)8 * c.pois_blocks * sizeof(double));
+    c.mgs_ctl = A(sizeof(MgCtl));
     c.mg_phi_prev = A(N * phi_size(c.prec));
     c.mg_have_prev = 0;
     c.mg = 1;
@@ -856,7 +876,9 @@ static int create_handle(const ekl_params *P, void *stream, ekl_handle **out, bo
     }
     if (P->flags & EKL_POISSON_MG) {
         const bool tiles = !replica && !(P->flags & EKL_POISSON_GLOBAL);
-        const char *why = build_multigrid(c, solid, A, replica ? MG_COARSEST_CELLS_REPLICA : MG_COARSEST_CELLS, tiles);
+        const bool split = !replica && !(P->flags & EKL_POISSON_MG_SINGLE);
+        const char *why =
+            build_multigrid(c, solid, A, replica ? MG_COARSEST_CELLS_REPLICA : MG_COARSEST_CELLS, tiles, split);
         if (!why && !okall) why = "device allocation failed";
         if (why) {
             release(c);
@@ -877,6 +899,10 @@ static int create_handle(const ekl_params *P, void *stream, ekl_handle **out, bo
         if (e != cudaSuccess) { rc = fail_cuda(e, "upload solid"); break; }
         mask_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c.stream>>>(make_grid3(c.nx, c.ny, c.nz), c.per[0], c.per[1], c.per[2], d_solid, c.mask);
         c.launches++;
+        if (c.mg) {
+            mg_link_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c.stream>>>(c.mask, c.mg_link, N);
+            c.launches++;
+        }
         if (charged) {
             if (c.prec == EKL_F64) {
                 cudaMemcpyAsync(c.wall_share, share.data(), N * 8, cudaMemcpyHostToDevice, c.stream);
@@ -1155,7 +1181,8 @@ int ekl_get_stats(ekl_handle *h, ekl_stats *out)
     out->poisson_res = res;
     out->status = c.last_status;
     for (int k = 0; k < PH_COUNT; k++) out->ms_phase[k] = c.ms_phase[k];
-    out->launches = c.launches;
+    // a split multigrid solve launches its loop's kernels from the device
+    out->launches = c.launches + (c.mg_split ? (int64_t)c.mgs_iter_kernels * tot : 0);
     out->poisson_sweeps = tot;
     return EKL_OK;
 }

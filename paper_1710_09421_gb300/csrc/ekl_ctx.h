@@ -128,10 +128,16 @@ struct Ctx {
     size_t mg_smem;          // dynamic shared memory of the multigrid launch
     MgLevel mg_lev[MG_MAXLEV];
     float *mg_r, *mg_z, *mg_q, *mg_p[2];  // lattice-level CG vectors
+    uint8_t *mg_link;        // per-node link byte of the lattice level (wall bit, closed faces)
     float *mg_dense;         // pseudo-inverse of the coarsest operator, or null
     void *mg_phi_prev;       // potential of the step before the last (starting-guess extrapolation)
     int mg_have_prev;        // mg_phi_prev and phi hold two consecutive potentials
-    double *mg_part;         // [4][pois_blocks] reduction partials
+    double *mg_part;         // [8][pois_blocks] reduction partials
+    int mg_split;            // the split solve (ekl_mgs.cuh) instead of one cooperative launch
+    void *mgs_ctl;           // its scalar state (MgCtl)
+    cudaGraph_t mgs_graph;   // its CG loop, built at the first solve
+    cudaGraphExec_t mgs_exec;
+    int mgs_iter_kernels;    // kernels launched per CG iteration of the loop
 
     // learned warm start of the Poisson solve (ekl_net.cu)
     void *net;

@@ -41,6 +41,7 @@ struct MgArgs {
     float *r, *z, *q, *p[2];
     double *part;         // [4][gridDim.x]
     const float *dense;   // pseudo-inverse of the coarsest operator [N][N], or null
+    const uint8_t *link;  // per-node link byte of the lattice level (mg_link_of)
     void *phi_prev;       // potential of the step before the last (PhiT[N])
     int have_prev;        // phi_prev holds phi(t-2) and phi holds phi(t-1)
     int nlev, cta_from, nu, nu_c, coarse_sweeps;  // smoothing sweeps: lattice level, coarse levels
@@ -49,6 +50,17 @@ struct MgArgs {
     int tile_off;                 // tile region offset (floats) in the dynamic shared memory
     int tile[MG_MAXLEV][3];       // owned cells per tile, per level
     MgLevel lev[MG_MAXLEV];
+};
+
+// Scalar state of a split solve (ekl_mgs.cuh) in device memory: written by
+// its one-block control kernels, read by its lattice kernels.
+struct MgCtl {
+    double tol, bb, tol2, rr_true, rr_ref, rz_old;
+    int max_iter, fixed_iter, limit, it, pi;
+    int fresh;      // next search direction starts from z (beta = 0)
+    int current;    // rr_true belongs to the present phi
+    int converged, stop, need_true;
+    int skip;       // zero source: nothing to solve, nothing to report
 };
 
 // 4-byte words of shared memory for a tile region of Rx x Ry x Rz cells:
@@ -73,8 +85,24 @@ __device__ __forceinline__ float mg_inv_deg(int d)
 {
     return d == 6 ? (1.f / 6.f) : d == 5 ? 0.2f : d == 4 ? 0.25f : d == 3 ? (1.f / 3.f) : d == 2 ? 0.5f : 1.f;
 }
-// open faces of a fluid node, bit f in face order (-x, +x, -y, +y, -z, +z)
-__device__ __forceinline__ unsigned mg_open(uint32_t m) { return (~(m >> 1)) & 63u; }
+// The lattice-level passes read, per node, either the link word (bit 31 on
+// wall nodes, bit f + 1 when face f, in the order -x, +x, -y, +y, -z, +z,
+// is closed) or the link byte made from it (MgArgs::link: the same face bits,
+// the wall bit moved to bit 7), a quarter of the word's bytes.  L is the
+// type read.
+constexpr unsigned MG_LINK_SOLID = 0x80u;
+__device__ __forceinline__ uint8_t mg_link_of(uint32_t m)
+{
+    return (uint8_t)((m & 0x7Eu) | ((m & SOLID_BIT) ? MG_LINK_SOLID : 0u));
+}
+template <typename L> __device__ __forceinline__ bool mg_wall(unsigned m)
+{
+    if constexpr (sizeof(L) == 1) return (m & MG_LINK_SOLID) != 0;
+    else return (m & SOLID_BIT) != 0;
+}
+constexpr unsigned MG_NO_NODE = ~0u;  // a link value that reads as a wall in either type
+// open faces of a fluid node, bit f in face order
+__device__ __forceinline__ unsigned mg_open(unsigned m) { return (~(m >> 1)) & 63u; }
 
 // The pair h of a level's red-black iteration: the two nodes (2 xh, 2 xh + 1)
 // of one x-row; `x` takes colour c, `xo` the other colour.
@@ -170,25 +198,25 @@ __device__ __forceinline__ int mg_parent(const MgLevel &C, int x, int y, int z)
 // their memory round trips overlap; the updates, and the order of the r.z
 // sum, are those of one pair per trip.
 constexpr int MG_FINE_U = 1;
-template <bool RZ, bool PRO, int U = MG_FINE_U>
-static __device__ void fine_half(const Grid3 &g, const uint32_t *__restrict__ mask, const float *r, float *z,
+template <bool RZ, bool PRO, int U = MG_FINE_U, typename L>
+static __device__ void fine_half(const Grid3 &g, const L *__restrict__ link, const float *r, float *z,
                                  const MgLevel &C, int c, int t0, int nt, float &rz)
 {
     const int hx = (g.nx + 1) >> 1, np = hx * g.ny * g.nz;
     for (int h0 = t0; h0 < np; h0 += U * nt) {
         float zn[U][6], ri[U], ro[U], zo[U];
-        uint32_t mk[U], mo[U];
+        unsigned mk[U], mo[U];
         int ii[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const int h = h0 + u * nt;
-            mk[u] = mo[u] = SOLID_BIT;
+            mk[u] = mo[u] = MG_NO_NODE;
             ii[u] = 0;
             ri[u] = ro[u] = zo[u] = 0.f;
             if (h >= np) continue;
             const Pair p = mg_pair(h, hx, g.ny, c);
             if (p.x < g.nx) {
-                // every load is issued before the link word is known (neighbour
+                // every load is issued before the link byte is known (neighbour
                 // indices are always valid; closed faces are masked afterwards)
                 const int i = p.x + g.nx * p.row;
                 ii[u] = i;
@@ -204,19 +232,19 @@ static __device__ void fine_half(const Grid3 &g, const uint32_t *__restrict__ ma
                     }
                 }
                 ri[u] = mg_ldl(r + i);
-                mk[u] = __ldg(mask + i);
+                mk[u] = __ldg(link + i);
             }
             if (RZ && p.xo < g.nx) {
                 const int io = p.xo + g.nx * p.row;
                 ro[u] = mg_ldl(r + io);
                 zo[u] = mg_ldl(z + io);
-                mo[u] = __ldg(mask + io);
+                mo[u] = __ldg(link + io);
             }
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const unsigned o = mg_open(mk[u]);
-            if (!(mk[u] & SOLID_BIT) && o) {
+            if (!mg_wall<L>(mk[u]) && o) {
                 float v = ri[u];
 #pragma unroll
                 for (int f = 0; f < 6; f++)
@@ -225,7 +253,7 @@ static __device__ void fine_half(const Grid3 &g, const uint32_t *__restrict__ ma
                 __stcg(z + ii[u], v);
                 if (RZ) rz += ri[u] * v;
             }
-            if (RZ && !(mo[u] & SOLID_BIT) && mg_open(mo[u])) rz += ro[u] * zo[u];
+            if (RZ && !mg_wall<L>(mo[u]) && mg_open(mo[u])) rz += ro[u] * zo[u];
         }
     }
 }
@@ -242,7 +270,8 @@ __device__ __forceinline__ float mg_sum_rows(float v)
 }
 
 // residual r - A z of one fluid node of the lattice (0 elsewhere)
-__device__ __forceinline__ float fine_resid(const Grid3 &g, const uint32_t *__restrict__ mask, const float *r,
+template <typename L>
+__device__ __forceinline__ float fine_resid(const Grid3 &g, const L *__restrict__ link, const float *r,
                                             const float *z, int x, int y, int zz)
 {
     if (x >= g.nx || y >= g.ny || zz >= g.nz) return 0.f;
@@ -253,9 +282,9 @@ __device__ __forceinline__ float fine_resid(const Grid3 &g, const uint32_t *__re
 #pragma unroll
     for (int f = 0; f < 6; f++) zn[f] = mg_ldl(z + nb[f]);
     const float ri = mg_ldl(r + i), zi = mg_ldl(z + i);
-    const uint32_t m = __ldg(mask + i);
+    const unsigned m = __ldg(link + i);
     const unsigned o = mg_open(m);
-    if ((m & SOLID_BIT) || !o) return 0.f;
+    if (mg_wall<L>(m) || !o) return 0.f;
     float acc = ri - (float)__popc(o) * zi;
 #pragma unroll
     for (int f = 0; f < 6; f++)
@@ -265,8 +294,8 @@ __device__ __forceinline__ float fine_resid(const Grid3 &g, const uint32_t *__re
 
 // C.f = sum over the children of each level-1 cell of (r - A z); FIRST: also
 // start level 1's pre-smoothing (colour-0 cells take f / diag)
-template <bool FIRST>
-static __device__ void fine_restrict(const Grid3 &g, const uint32_t *__restrict__ mask, const float *r,
+template <bool FIRST, typename L>
+static __device__ void fine_restrict(const Grid3 &g, const L *__restrict__ link, const float *r,
                                      const float *z, const MgLevel &C, int t0, int nt)
 {
     const int lane = threadIdx.x & 31, total = ((C.N + 7) >> 3) * 32;
@@ -280,7 +309,7 @@ static __device__ void fine_restrict(const Grid3 &g, const uint32_t *__restrict_
             Y = t % C.ny;
             Z = t / C.ny;
             const int y0 = 2 * Y + (k & 1), z0 = 2 * Z + (k >> 1);
-            acc = fine_resid(g, mask, r, z, 2 * X, y0, z0) + fine_resid(g, mask, r, z, 2 * X + 1, y0, z0);
+            acc = fine_resid(g, link, r, z, 2 * X, y0, z0) + fine_resid(g, link, r, z, 2 * X + 1, y0, z0);
         }
         const float sum = mg_sum_rows(acc);
         if (I < C.N && k == 0) {
@@ -783,30 +812,20 @@ static __device__ void mg_dense_solve(const MgArgs &m, int t0, int nt)
     }
 }
 
-// One V-cycle z = M^-1 r over the grid, entered with z's colour-0 nodes
-// already set to r / deg; returns this block's partial of r.z in thread 0
-// (through rz_block), or false on a barrier abort.
-template <typename S, typename R, typename PhiT, bool TILES>
-__device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const MgGrid &G, unsigned &bar_k,
-                          float *sm, double *sh, double *bc, double &rz_block)
+// Coarse part of a V-cycle over the grid: entered with level 1's right-hand
+// side restricted (and, when level 1 is grid-wide and not block 0's, its
+// pre-smoothing started); leaves level 1's correction in lev[1].e for the
+// prolongating half sweep.  False on a barrier abort.
+template <bool TILES>
+__device__ bool mg_coarse_cycle(const MgArgs &m, const MgGrid &G, unsigned &bar_k, int *status, float *sm,
+                                double *sh, double *bc)
 {
-    const Grid3 g = a.g;
     const int t0 = G.t0, nt = G.nt;
-    float dummy = 0.f;
 #define MG_BAR()                                                          \
     do {                                                                  \
-        if (!grid_barrier(G.bar, (unsigned)G.nblk, bar_k, a.status)) return false; \
+        if (!grid_barrier(G.bar, (unsigned)G.nblk, bar_k, status)) return false; \
     } while (0)
     float *tsm = sm + m.tile_off;  // coarse tile regions
-    // lattice level: rest of the pre-smoothing, residual restricted to level 1
-    for (int s = 1; s < 2 * m.nu; s++) {
-        fine_half<false, false>(g, a.mask, m.r, m.z, m.lev[1], s & 1, t0, nt, dummy);
-        MG_BAR();
-    }
-    if (m.cta_from > 1) fine_restrict<true>(g, a.mask, m.r, m.z, m.lev[1], t0, nt);
-    else fine_restrict<false>(g, a.mask, m.r, m.z, m.lev[1], t0, nt);
-    MG_BAR();
-    // grid-wide coarse levels
     for (int l = 1; l < m.cta_from; l++) {
         if (TILES && l >= m.tile_from) {
             coarse_pre_tiles(m.lev[l], m.lev[l + 1], m.tile[l], 2 * m.nu_c, G.blk, G.nblk, tsm);
@@ -837,6 +856,33 @@ __device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const 
             MG_BAR();
         }
     }
+#undef MG_BAR
+    return true;
+}
+
+// One V-cycle z = M^-1 r over the grid, entered with z's colour-0 nodes
+// already set to r / deg; returns this block's partial of r.z in thread 0
+// (through rz_block), or false on a barrier abort.
+template <typename S, typename R, typename PhiT, bool TILES>
+__device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const MgGrid &G, unsigned &bar_k,
+                          float *sm, double *sh, double *bc, double &rz_block)
+{
+    const Grid3 g = a.g;
+    const int t0 = G.t0, nt = G.nt;
+    float dummy = 0.f;
+#define MG_BAR()                                                          \
+    do {                                                                  \
+        if (!grid_barrier(G.bar, (unsigned)G.nblk, bar_k, a.status)) return false; \
+    } while (0)
+    // lattice level: rest of the pre-smoothing, residual restricted to level 1
+    for (int s = 1; s < 2 * m.nu; s++) {
+        fine_half<false, false>(g, a.mask, m.r, m.z, m.lev[1], s & 1, t0, nt, dummy);
+        MG_BAR();
+    }
+    if (m.cta_from > 1) fine_restrict<true>(g, a.mask, m.r, m.z, m.lev[1], t0, nt);
+    else fine_restrict<false>(g, a.mask, m.r, m.z, m.lev[1], t0, nt);
+    MG_BAR();
+    if (!mg_coarse_cycle<TILES>(m, G, bar_k, a.status, sm, sh, bc)) return false;
     fine_half<false, true>(g, a.mask, m.r, m.z, m.lev[1], 1, t0, nt, dummy);
     MG_BAR();
     float rz = 0.f;
@@ -860,20 +906,20 @@ __device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const 
 // per grid stride) with all their loads issued first; its nodes are still
 // summed in increasing order.
 constexpr int MG_RES_U = 2;
-template <typename PhiT>
-__device__ double mg_true_residual(const Grid3 &g, const uint32_t *__restrict__ mask, const PhiT *phi,
+template <typename PhiT, typename L>
+__device__ double mg_true_residual(const Grid3 &g, const L *__restrict__ link, const PhiT *phi,
                                    const PhiT *b, float *r, float *z, int t0, int nt, double *sh)
 {
     float rr = 0.f;
     const int N = (int)g.N;
     for (long long i0 = t0; i0 < N; i0 += (long long)MG_RES_U * nt) {
         PhiT pn[MG_RES_U][6], bi[MG_RES_U], phii[MG_RES_U];
-        uint32_t mk[MG_RES_U];
+        unsigned mk[MG_RES_U];
         int xyz[MG_RES_U];
 #pragma unroll
         for (int k = 0; k < MG_RES_U; k++) {
             const long long il = i0 + (long long)k * nt;
-            mk[k] = SOLID_BIT;
+            mk[k] = MG_NO_NODE;
             if (il >= N) continue;
             const int i = (int)il;
             const int x = i % g.nx, t = i / g.nx, y = t % g.ny, zz = t / g.ny;
@@ -884,12 +930,12 @@ __device__ double mg_true_residual(const Grid3 &g, const uint32_t *__restrict__ 
             for (int f = 0; f < 6; f++) pn[k][f] = mg_ldl(phi + nb[f]);
             bi[k] = mg_ldl(b + i);
             phii[k] = mg_ldl(phi + i);
-            mk[k] = __ldg(mask + i);
+            mk[k] = __ldg(link + i);
         }
 #pragma unroll
         for (int k = 0; k < MG_RES_U; k++) {
             const int i = (int)(i0 + (long long)k * nt);
-            if (mk[k] & SOLID_BIT) continue;  // also every node past N
+            if (mg_wall<L>(mk[k])) continue;  // also every node past N
             const unsigned o = mg_open(mk[k]);
             float rv = 0.f;
             if (o) {
@@ -913,8 +959,8 @@ __device__ double mg_true_residual(const Grid3 &g, const uint32_t *__restrict__ 
 // division chain per two nodes and the loads of both issued together.
 
 // p = z + beta p_old and q = A p on the fluid nodes; returns sum p q
-template <bool FRESH>
-__device__ __forceinline__ void mg_pq_node(const Grid3 &g, const uint32_t *__restrict__ mask, const float *z,
+template <bool FRESH, typename L>
+__device__ __forceinline__ void mg_pq_node(const Grid3 &g, const L *__restrict__ link, const float *z,
                                            const float *pold, float beta, int x, int y, int zz, int i, float &pn,
                                            float &qv, bool &live)
 {
@@ -924,9 +970,9 @@ __device__ __forceinline__ void mg_pq_node(const Grid3 &g, const uint32_t *__res
 #pragma unroll
     for (int f = 0; f < 6; f++) pj[f] = FRESH ? mg_ldl(z + nb[f]) : mg_ldl(z + nb[f]) + beta * mg_ldl(pold + nb[f]);
     const float pi_ = FRESH ? mg_ldl(z + i) : mg_ldl(z + i) + beta * mg_ldl(pold + i);
-    const uint32_t mk = __ldg(mask + i);
+    const unsigned mk = __ldg(link + i);
     const unsigned o = mg_open(mk);
-    live = !(mk & SOLID_BIT);
+    live = !mg_wall<L>(mk);
     pn = 0.f;
     qv = 0.f;
     if (!live || !o) return;
@@ -938,8 +984,8 @@ __device__ __forceinline__ void mg_pq_node(const Grid3 &g, const uint32_t *__res
     qv = (float)__popc(o) * pn - acc;
 }
 
-template <bool FRESH>
-__device__ float mg_pq_pass(const Grid3 &g, const uint32_t *__restrict__ mask, const float *z, const float *pold,
+template <bool FRESH, typename L>
+__device__ float mg_pq_pass(const Grid3 &g, const L *__restrict__ link, const float *z, const float *pold,
                             float *pnew, float *q, float beta, int t0, int nt)
 {
     const int hx = (g.nx + 1) >> 1, np = hx * g.ny * g.nz;
@@ -951,8 +997,8 @@ __device__ float mg_pq_pass(const Grid3 &g, const uint32_t *__restrict__ mask, c
         const bool two = x0 + 1 < g.nx;
         float pn0, q0, pn1 = 0.f, q1 = 0.f;
         bool l0, l1 = false;
-        mg_pq_node<FRESH>(g, mask, z, pold, beta, x0, y, zz, i0, pn0, q0, l0);
-        if (two) mg_pq_node<FRESH>(g, mask, z, pold, beta, x0 + 1, y, zz, i0 + 1, pn1, q1, l1);
+        mg_pq_node<FRESH>(g, link, z, pold, beta, x0, y, zz, i0, pn0, q0, l0);
+        if (two) mg_pq_node<FRESH>(g, link, z, pold, beta, x0 + 1, y, zz, i0 + 1, pn1, q1, l1);
         if (l0) {
             __stcg(pnew + i0, pn0);
             __stcg(q + i0, q0);
@@ -968,8 +1014,8 @@ __device__ float mg_pq_pass(const Grid3 &g, const uint32_t *__restrict__ mask, c
 
 // phi += alpha p, r -= alpha q and colour-0 z = r / deg on the fluid nodes
 // with an open face; returns sum r^2
-template <typename PhiT>
-__device__ float mg_update_pass(const Grid3 &g, const uint32_t *__restrict__ mask, PhiT *phi, const float *p,
+template <typename PhiT, typename L>
+__device__ float mg_update_pass(const Grid3 &g, const L *__restrict__ link, PhiT *phi, const float *p,
                                 const float *q, float *r, float *z, double alpha, int t0, int nt)
 {
     const int hx = (g.nx + 1) >> 1, np = hx * g.ny * g.nz;
@@ -981,16 +1027,16 @@ __device__ float mg_update_pass(const Grid3 &g, const uint32_t *__restrict__ mas
         const int zz = row / g.ny, y = row - zz * g.ny;
         const int x0 = 2 * xh, i0 = x0 + g.nx * row;
         const int nk = x0 + 1 < g.nx ? 2 : 1;
-        uint32_t mk[2];
+        unsigned mk[2];
         float pv[2], qv[2], rv[2];
         PhiT ph[2];
 #pragma unroll
         for (int k = 0; k < 2; k++) {
-            mk[k] = SOLID_BIT;
+            mk[k] = MG_NO_NODE;
             pv[k] = qv[k] = rv[k] = 0.f;
             ph[k] = (PhiT)0;
             if (k < nk) {
-                mk[k] = __ldg(mask + i0 + k);
+                mk[k] = __ldg(link + i0 + k);
                 pv[k] = __ldcg(p + i0 + k);
                 qv[k] = __ldcg(q + i0 + k);
                 rv[k] = __ldcg(r + i0 + k);
@@ -1000,7 +1046,7 @@ __device__ float mg_update_pass(const Grid3 &g, const uint32_t *__restrict__ mas
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             const unsigned o = mg_open(mk[k]);
-            if ((mk[k] & SOLID_BIT) || !o) continue;
+            if (mg_wall<L>(mk[k]) || !o) continue;
             const int i = i0 + k;
             if constexpr (((PhiT)0.5) != 0) __stcg(phi + i, ph[k] + (double)af * (double)pv[k]);
             else __stcg(phi + i, ph[k] + float_to_ll(afx * pv[k]));
@@ -1022,9 +1068,9 @@ __device__ float mg_update_pass(const Grid3 &g, const uint32_t *__restrict__ mas
 // b^2 sum bit-identical to form_source's.  Returns the block's sum of b^2
 // (thread 0).
 constexpr int MG_START_U = 4;
-template <typename S, typename R, typename PhiT>
-__device__ double mg_start_pass(const StepArgs<S, R, PhiT> &a, const MgArgs &m, int tid, int nthr, double *sh,
-                                double *bc)
+template <typename S, typename R, typename PhiT, typename L>
+__device__ double mg_start_pass(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const L *__restrict__ link, int tid,
+                                int nthr, double *sh, double *bc)
 {
     const SrcMean sm = source_mean(a, bc);
     const int N = (int)a.g.N;
@@ -1033,17 +1079,17 @@ __device__ double mg_start_pass(const StepArgs<S, R, PhiT> &a, const MgArgs &m, 
     double bl = 0.0;
     float blf = 0.f;
     for (long long i0 = tid; i0 < N; i0 += (long long)MG_START_U * nthr) {
-        uint32_t mk[MG_START_U];
+        unsigned mk[MG_START_U];
         PhiT cur[MG_START_U], pv[MG_START_U];
         R rho[MG_START_U];
 #pragma unroll
         for (int k = 0; k < MG_START_U; k++) {
             const long long i = i0 + (long long)k * nthr;
-            mk[k] = SOLID_BIT;
+            mk[k] = MG_NO_NODE;
             cur[k] = pv[k] = (PhiT)0;
             rho[k] = (R)0;
             if (i < N) {
-                mk[k] = __ldg(a.mask + i);
+                mk[k] = __ldg(link + i);
                 cur[k] = __ldcg(a.phi + i);
                 if (extrap) pv[k] = __ldcg(prev + i);
                 rho[k] = __ldcg(a.rho + i);
@@ -1054,7 +1100,7 @@ __device__ double mg_start_pass(const StepArgs<S, R, PhiT> &a, const MgArgs &m, 
             const long long i = i0 + (long long)k * nthr;
             if (i >= N) continue;
             PhiT bv = (PhiT)0;
-            if (!(mk[k] & SOLID_BIT)) {
+            if (!mg_wall<L>(mk[k])) {
                 if (extrap) __stcg(a.phi + i, (PhiT)2 * cur[k] - pv[k]);
                 __stcg(prev + i, cur[k]);
                 bv = source_value<R, PhiT>(rho[k], i, a.c4, sm, bl, blf);
@@ -1087,7 +1133,7 @@ __device__ void mg_solve(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const M
     };
     if (G.blk == 0 && !m.dense) mg_cta_load(m, mg_sm);
     double bb;
-    if (!reduce(mg_start_pass(a, m, tid, nthr, sh, bc), bb)) return;
+    if (!reduce(mg_start_pass(a, m, a.mask, tid, nthr, sh, bc), bb)) return;
     if (a.fixed_iter <= 0 && bb == 0.0) {
         if (tid == 0) {
             *a.pois_iters = 0;

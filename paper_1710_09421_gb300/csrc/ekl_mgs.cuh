@@ -1,0 +1,237 @@
+// The multigrid-preconditioned CG solve of ekl_mg.cuh in split form, for
+// lattices whose passes are bound by memory: every lattice-level pass is its
+// own launch, the coarse levels of each V-cycle are one cooperative launch,
+// and the CG loop runs on the device as a CUDA graph with a conditional WHILE
+// node, so a step's solve needs no host round trip.
+//
+// Why split: inside the single cooperative launch every pass shares the
+// register budget of the whole solve (64 a thread at 1024 threads), and a
+// lattice pass cannot keep the loads of several nodes in flight; on its own
+// launch it can (MGS_U node pairs per thread and trip), and a lattice pass is
+// bound by memory latency at one pair.
+//
+// The passes, their thread-to-node maps and the block partials of every
+// reduction are those of the single-launch solve with the same grid
+// (nblk blocks of MGS_THREADS), and the partials are summed the same way, so
+// both forms return the same potential bit for bit.  The scalar recurrences
+// (beta, alpha, the convergence test, the restart from the true residual)
+// live in MgCtl in device memory: the lattice kernels read it, one-block
+// control kernels write it and set the loop's condition.
+#pragma once
+#include "ekl_mg.cuh"
+
+namespace ekl {
+
+constexpr int MGS_THREADS = 1024;
+constexpr int MGS_U = 2;  // node pairs per thread and trip in the lattice half sweeps
+
+// block-partial slots (nblk doubles each) in MgArgs::part
+enum { MGS_BB = 0, MGS_RES = 1, MGS_RZ = 2, MGS_PQ = 3, MGS_RR = 4, MGS_SLOTS = 5 };
+
+__device__ __forceinline__ double *mgs_slot(const MgArgs &m, int slot, int nblk) { return m.part + (size_t)slot * nblk; }
+
+// Start of the solve: guess, source and its block partials of b^2; block 0
+// records the step's solver settings.
+template <typename S, typename R, typename PhiT>
+__global__ void __launch_bounds__(MGS_THREADS, 1) mgs_start_kernel(StepArgs<S, R, PhiT> a, MgArgs m, MgCtl *ctl)
+{
+    __shared__ double sh[MGS_THREADS / 32];
+    __shared__ double bc[1];
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    const double t = mg_start_pass(a, m, m.link, tid, nthr, sh, bc);
+    if (threadIdx.x == 0) mgs_slot(m, MGS_BB, gridDim.x)[blockIdx.x] = t;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->tol = a.tol;
+        ctl->max_iter = a.max_iter;
+        ctl->fixed_iter = a.fixed_iter;
+    }
+}
+
+// True residual with its block partials of r^2.  when: 0 always, 1 when the
+// control state asks for one, 2 when phi moved since the last one.
+template <typename PhiT>
+__global__ void __launch_bounds__(MGS_THREADS, 1)
+    mgs_residual_kernel(Grid3 g, MgArgs m, const PhiT *phi, const PhiT *b, const MgCtl *ctl, int when)
+{
+    __shared__ double sh[MGS_THREADS / 32];
+    if (when == 1 && !ctl->need_true) return;
+    if (when == 2 && (ctl->current || ctl->skip)) return;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    const double t = mg_true_residual<PhiT>(g, m.link, phi, b, m.r, m.z, tid, nthr, sh);
+    if (threadIdx.x == 0) mgs_slot(m, MGS_RES, gridDim.x)[blockIdx.x] = t;
+}
+
+// Control kernels: one block of 32 threads.
+static __global__ void mgs_init_kernel(MgArgs m, MgCtl *ctl, int nblk, cudaGraphConditionalHandle loop,
+                                       int *pois_iters, double *pois_res)
+{
+    __shared__ double bc[1];
+    const double bb = sum_partials(mgs_slot(m, MGS_BB, nblk), nblk, bc);
+    const double rr = sum_partials(mgs_slot(m, MGS_RES, nblk), nblk, bc);
+    if (threadIdx.x != 0) return;
+    MgCtl c = *ctl;
+    c.bb = bb;
+    c.it = 0;
+    c.pi = 0;
+    c.fresh = 1;
+    c.current = 1;
+    c.stop = 0;
+    c.need_true = 0;
+    c.skip = 0;
+    c.rz_old = 1.0;
+    c.limit = c.fixed_iter > 0 ? c.fixed_iter : c.max_iter;
+    c.tol2 = c.tol * c.tol * bb;
+    c.rr_true = rr;
+    c.rr_ref = rr;
+    c.converged = c.fixed_iter <= 0 && rr <= c.tol2;
+    if (c.fixed_iter <= 0 && bb == 0.0) {
+        *pois_iters = 0;
+        *pois_res = 0.0;
+        c.skip = 1;
+        c.converged = 1;
+    }
+    *ctl = c;
+    cudaGraphSetConditional(loop, (!c.converged && c.it < c.limit) ? 1u : 0u);
+}
+
+// After the update pass: the CG scalars of the iteration, and whether the
+// true residual is due (the recurrence residual fell by inner_red, or under
+// a quarter of the tolerance, or the iteration limit is reached).
+static __global__ void mgs_mid_kernel(MgArgs m, MgCtl *ctl, int nblk)
+{
+    __shared__ double bc[1];
+    const double rz = sum_partials(mgs_slot(m, MGS_RZ, nblk), nblk, bc);
+    const double pq = sum_partials(mgs_slot(m, MGS_PQ, nblk), nblk, bc);
+    const double rr = sum_partials(mgs_slot(m, MGS_RR, nblk), nblk, bc);
+    if (threadIdx.x != 0) return;
+    MgCtl c = *ctl;
+    c.need_true = 0;
+    if (!(rz > 0.0) || !(pq > 0.0)) {
+        c.stop = 1;  // breakdown: phi was not moved in this iteration
+    } else {
+        c.rz_old = rz;
+        c.pi ^= 1;
+        c.it++;
+        c.fresh = 0;
+        c.current = 0;
+        if (c.fixed_iter <= 0 &&
+            (rr <= 0.25 * c.tol2 || rr <= (double)m.inner_red * m.inner_red * c.rr_ref || c.it == c.limit))
+            c.need_true = 1;
+    }
+    *ctl = c;
+}
+
+// After the (conditional) true residual: convergence test, restart, and the
+// loop's condition.
+static __global__ void mgs_end_kernel(MgArgs m, MgCtl *ctl, int nblk, cudaGraphConditionalHandle loop,
+                                      const int *status)
+{
+    __shared__ double bc[1];
+    const double rt = sum_partials(mgs_slot(m, MGS_RES, nblk), nblk, bc);
+    if (threadIdx.x != 0) return;
+    MgCtl c = *ctl;
+    if (c.need_true) {
+        c.rr_true = rt;
+        c.current = 1;
+        if (rt <= c.tol2) {
+            c.converged = 1;
+        } else {
+            c.rr_ref = rt;
+            c.fresh = 1;
+        }
+        c.need_true = 0;
+    }
+    *ctl = c;
+    const bool go = !c.stop && !c.converged && c.it < c.limit && !(*(volatile const int *)status & ST_TIMEOUT);
+    cudaGraphSetConditional(loop, go ? 1u : 0u);
+}
+
+// Iterations, final relative residual and the non-convergence flag.
+static __global__ void mgs_report_kernel(MgArgs m, const MgCtl *ctl, int nblk, int *pois_iters,
+                                         long long *pois_total, double *pois_res, int *status)
+{
+    __shared__ double bc[1];
+    const double rt = sum_partials(mgs_slot(m, MGS_RES, nblk), nblk, bc);
+    if (threadIdx.x != 0) return;
+    const MgCtl c = *ctl;
+    if (c.skip) return;
+    // a final true residual was formed exactly when phi moved after the last one
+    const double rr_true = c.current ? c.rr_true : rt;
+    *pois_iters = c.it;
+    pois_total[0] += c.it;
+    *pois_res = sqrt(rr_true / c.bb);
+    if (c.fixed_iter <= 0 && !(c.converged || rr_true <= c.tol2)) atomicOr(status, ST_NOCONV);
+}
+
+// V-cycle on the lattice level: one red-black half sweep (RZ: the last one,
+// with the block partials of r.z; PRO: the prolongating one)
+template <bool RZ, bool PRO>
+__global__ void __launch_bounds__(MGS_THREADS, 1) mgs_half_kernel(Grid3 g, MgArgs m, int c)
+{
+    __shared__ double sh[MGS_THREADS / 32];
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    float rz = 0.f;
+    fine_half<RZ, PRO, MGS_U>(g, m.link, m.r, m.z, m.lev[1], c, tid, nthr, rz);
+    if constexpr (RZ) {
+        const double t = block_sum_lanes0(warp_sum_ff_lane0(rz), sh);
+        if (threadIdx.x == 0) mgs_slot(m, MGS_RZ, gridDim.x)[blockIdx.x] = t;
+    }
+}
+
+template <bool FIRST> __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_restrict_kernel(Grid3 g, MgArgs m)
+{
+    fine_restrict<FIRST>(g, m.link, m.r, m.z, m.lev[1], (int)(blockIdx.x * blockDim.x + threadIdx.x),
+                         (int)(gridDim.x * blockDim.x));
+}
+
+// The coarse levels of one V-cycle (cooperative launch; `bar` zeroed before it)
+static __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_coarse_kernel(MgArgs m, unsigned *bar, int *status)
+{
+    __shared__ double sh[MGS_THREADS / 32];
+    __shared__ double bc[1];
+    extern __shared__ float mg_sm[];
+    const MgGrid G{(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x), (int)gridDim.x,
+                   (int)blockIdx.x, bar};
+    if (G.blk == 0 && !m.dense) mg_cta_load(m, mg_sm);
+    unsigned bar_k = 0;
+    mg_coarse_cycle<true>(m, G, bar_k, status, mg_sm, sh, bc);
+}
+
+// p = z + beta p_old, q = A p with the block partials of p.q
+static __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_pq_kernel(Grid3 g, MgArgs m, const MgCtl *ctl)
+{
+    __shared__ double sh[MGS_THREADS / 32];
+    __shared__ double bc[1];
+    const int nblk = gridDim.x;
+    const double rz = sum_partials(mgs_slot(m, MGS_RZ, nblk), nblk, bc);
+    if (!(rz > 0.0)) return;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    const int fresh = ctl->fresh, pi = ctl->pi;
+    const float beta = fresh ? 0.f : (float)(rz / ctl->rz_old);
+    const float *pold = m.p[pi];
+    float *pnew = m.p[pi ^ 1];
+    const float t = fresh ? mg_pq_pass<true>(g, m.link, m.z, pold, pnew, m.q, beta, tid, nthr)
+                          : mg_pq_pass<false>(g, m.link, m.z, pold, pnew, m.q, beta, tid, nthr);
+    const double pq = block_sum_lanes0(warp_sum_ff_lane0(t), sh);
+    if (threadIdx.x == 0) mgs_slot(m, MGS_PQ, nblk)[blockIdx.x] = pq;
+}
+
+// phi += alpha p, r -= alpha q (and the next V-cycle's first half sweep)
+// with the block partials of r^2
+template <typename PhiT>
+__global__ void __launch_bounds__(MGS_THREADS, 1) mgs_update_kernel(Grid3 g, MgArgs m, PhiT *phi, const MgCtl *ctl)
+{
+    __shared__ double sh[MGS_THREADS / 32];
+    __shared__ double bc[1];
+    const int nblk = gridDim.x;
+    const double rz = sum_partials(mgs_slot(m, MGS_RZ, nblk), nblk, bc);
+    const double pq = sum_partials(mgs_slot(m, MGS_PQ, nblk), nblk, bc);
+    if (!(rz > 0.0) || !(pq > 0.0)) return;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    const double alpha = rz / pq;
+    const float t = mg_update_pass<PhiT>(g, m.link, phi, m.p[ctl->pi ^ 1], m.q, m.r, m.z, alpha, tid, nthr);
+    const double rr = block_sum_lanes0(warp_sum_ff_lane0(t), sh);
+    if (threadIdx.x == 0) mgs_slot(m, MGS_RR, nblk)[blockIdx.x] = rr;
+}
+
+}  // namespace ekl

@@ -8,6 +8,7 @@
 
 #include "ekl_kernels.cuh"
 #include "ekl_mg.cuh"
+#include "ekl_mgs.cuh"
 
 namespace ekl {
 
@@ -141,6 +142,7 @@ static inline MgArgs make_mg_args(const Ctx &c)
     m.p[0] = c.mg_p[0];
     m.p[1] = c.mg_p[1];
     m.part = c.mg_part;
+    m.link = c.mg_link;
     m.dense = c.mg_dense;
     m.phi_prev = c.mg_phi_prev;
     // with a learned warm start installed the network supplies the guess
@@ -158,6 +160,110 @@ static inline MgArgs make_mg_args(const Ctx &c)
         for (int k = 0; k < 3; k++) m.tile[l][k] = c.mg_tile[l][k];
     }
     return m;
+}
+
+// Graph of a split multigrid solve (ekl_mgs.cuh), launched after the step's
+// start kernel:
+//   true residual -> init -> WHILE (condition set by init / end) {
+//     pre-smoothing half sweeps, restriction, coarse levels (cooperative),
+//     prolongating and post-smoothing half sweeps, p/q, update, mid,
+//     true residual when due, end }
+//   -> true residual when phi moved after the last one -> report.
+// Every argument is fixed for the life of the handle; the step's tolerance
+// and iteration limits reach the graph through MgCtl.
+template <typename PhiT> static cudaError_t mgs_build(Ctx &c, const MgArgs &m0, Grid3 g)
+{
+    MgArgs m = m0;
+    const int nb = c.pois_blocks;
+    MgCtl *ctl = (MgCtl *)c.mgs_ctl;
+    const PhiT *phi = (const PhiT *)c.phi, *b = (const PhiT *)c.b;
+    PhiT *phiw = (PhiT *)c.phi;
+    int when0 = 0, when2 = 2, nblk = nb;
+    cudaGraph_t G = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaGraphConditionalHandle loop;
+    cudaGraphNode_t nres0, ninit, nloop, nres2, nrep;
+    cudaError_t e = cudaGraphCreate(&G, 0);
+    auto kernel_node = [&](cudaGraphNode_t *out, cudaGraphNode_t *dep, const void *fn, int grid, int block,
+                           void **args) {
+        cudaKernelNodeParams kp = {};
+        kp.func = (void *)fn;
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(block);
+        kp.kernelParams = args;
+        return cudaGraphAddKernelNode(out, G, dep, dep ? 1 : 0, &kp);
+    };
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&loop, G, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        void *args[] = {&g, &m, &phi, &b, &ctl, &when0};
+        e = kernel_node(&nres0, nullptr, (const void *)mgs_residual_kernel<PhiT>, nb, MGS_THREADS, args);
+    }
+    if (e == cudaSuccess) {
+        void *args[] = {&m, &ctl, &nblk, &loop, &c.pois_iters, &c.pois_res};
+        e = kernel_node(&ninit, &nres0, (const void *)mgs_init_kernel, 1, 32, args);
+    }
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = loop;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&nloop, G, &ninit, nullptr, 1, &cp);
+        if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess && c.mg_smem > 48 * 1024)
+        e = cudaFuncSetAttribute(mgs_coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.mg_smem);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        for (int s = 1; s < 2 * MG_NU; s++) mgs_half_kernel<false, false><<<nb, MGS_THREADS, 0, cs>>>(g, m, s & 1);
+        if (m.cta_from > 1) mgs_restrict_kernel<true><<<nb, MGS_THREADS, 0, cs>>>(g, m);
+        else mgs_restrict_kernel<false><<<nb, MGS_THREADS, 0, cs>>>(g, m);
+        cudaMemsetAsync(c.barrier, 0, 4 * sizeof(unsigned), cs);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute coop[1];
+        coop[0].id = cudaLaunchAttributeCooperative;
+        coop[0].val.cooperative = 1;
+        cfg.gridDim = dim3(nb);
+        cfg.blockDim = dim3(MGS_THREADS);
+        cfg.dynamicSmemBytes = c.mg_smem;
+        cfg.stream = cs;
+        cfg.attrs = coop;
+        cfg.numAttrs = 1;
+        cudaError_t el = cudaLaunchKernelEx(&cfg, mgs_coarse_kernel, m, c.barrier, c.status);
+        mgs_half_kernel<false, true><<<nb, MGS_THREADS, 0, cs>>>(g, m, 1);
+        for (int s = 1; s < 2 * MG_NU; s++) {
+            const int col = (s & 1) ^ 1;
+            if (s == 2 * MG_NU - 1) mgs_half_kernel<true, false><<<nb, MGS_THREADS, 0, cs>>>(g, m, col);
+            else mgs_half_kernel<false, false><<<nb, MGS_THREADS, 0, cs>>>(g, m, col);
+        }
+        mgs_pq_kernel<<<nb, MGS_THREADS, 0, cs>>>(g, m, ctl);
+        mgs_update_kernel<PhiT><<<nb, MGS_THREADS, 0, cs>>>(g, m, phiw, ctl);
+        mgs_mid_kernel<<<1, 32, 0, cs>>>(m, ctl, nb);
+        mgs_residual_kernel<PhiT><<<nb, MGS_THREADS, 0, cs>>>(g, m, phi, b, ctl, 1);
+        mgs_end_kernel<<<1, 32, 0, cs>>>(m, ctl, nb, loop, c.status);
+        cudaError_t ek = cudaGetLastError();
+        cudaError_t ec = cudaStreamEndCapture(cs, &body);
+        e = el != cudaSuccess ? el : ek != cudaSuccess ? ek : ec;
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (e == cudaSuccess) {
+        void *args[] = {&g, &m, &phi, &b, &ctl, &when2};
+        e = kernel_node(&nres2, &nloop, (const void *)mgs_residual_kernel<PhiT>, nb, MGS_THREADS, args);
+    }
+    if (e == cudaSuccess) {
+        void *args[] = {&m, &ctl, &nblk, &c.pois_iters, &c.pois_total, &c.pois_res, &c.status};
+        e = kernel_node(&nrep, &nres2, (const void *)mgs_report_kernel, 1, 32, args);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c.mgs_exec, G, 0);
+    if (e != cudaSuccess) {
+        if (G) cudaGraphDestroy(G);
+        c.mgs_exec = nullptr;
+        return e;
+    }
+    c.mgs_graph = G;
+    return cudaSuccess;
 }
 
 static inline int cuda_ok(cudaError_t e) { return e == cudaSuccess ? EKL_OK : EKL_ERR_CUDA; }
@@ -208,7 +314,15 @@ template <typename S, typename R, typename PhiT, bool DEV> int steps_impl(Ctx &c
         }
         phase_begin(c, PH_POISSON);
         cudaMemsetAsync(c.barrier, 0, 4 * sizeof(unsigned), c.stream);
-        if (c.mg) {
+        if (c.mg && c.mg_split) {
+            MgArgs m = make_mg_args(c);
+            mgs_start_kernel<S, R, PhiT><<<c.pois_blocks, MGS_THREADS, 0, c.stream>>>(a, m, (MgCtl *)c.mgs_ctl);
+            c.launches++;
+            if (!c.mgs_exec && mgs_build<PhiT>(c, m, a.g) != cudaSuccess) return EKL_ERR_CUDA;
+            if (cudaGraphLaunch(c.mgs_exec, c.stream) != cudaSuccess) return EKL_ERR_CUDA;
+            c.launches += 4;  // the loop's kernels are counted from its iterations
+            c.mg_have_prev = 1;
+        } else if (c.mg) {
             MgArgs m = make_mg_args(c);
             void *args[] = {&a, &m};
             const void *kern = c.mg_wide ? (const void *)poisson_mg_wide_kernel<S, R, PhiT>

@@ -200,6 +200,46 @@ def test_mg_wide_launch_large_lattice_agrees_with_sor():
     sor.close()
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_mg_split_solve_equals_single_launch(prec):
+    """A lattice of at least 16 384 nodes per SM runs the solve split: every
+    lattice pass its own launch, the coarse levels of a V-cycle one
+    cooperative launch, the CG loop a CUDA graph with a conditional WHILE
+    node.  Same passes, thread-to-node maps and block partials, summed the
+    same way, as the single cooperative launch (EKL_POISSON_MG_SINGLE):
+    potentials, densities, iteration counts and residuals agree bit for bit,
+    with the tolerance stop and with a fixed iteration count.  The launch
+    counter includes the kernels the loop launches on the device (4 per solve
+    around the loop, 14 per CG iteration)."""
+    wl = W.translocation(nx=160, ny=160, nz=128, membrane=(60, 67), radius=5.0, salt=0.005, n_beads=16,
+                         precision=prec)
+    assert wl.n_nodes >= 16384 * 152
+    if prec == "f64":
+        wl = wl.replace(poisson_tol=1e-10)
+    for case in (wl, wl.replace(poisson_fixed_iter=3)):
+        out = []
+        for flags in (MG, MG | W.FLAG_POISSON_MG_SINGLE):
+            sim = E.Simulation(case.replace(flags=flags))
+            l0 = sim.stats()["launches"]
+            its = []
+            for _ in range(3):
+                rc = sim.step(1)
+                assert rc >= 0 and not (rc & E.EKL_WARN_NOCONV), rc
+                st = sim.stats()
+                its.append((st["poisson_iters"], st["poisson_res"]))
+            launches = sim.stats()["launches"] - l0
+            out.append((sim.fields(("n", "phi")), its, launches))
+            sim.close()
+        (fs, its_s, ls), (f1, its_1, l1) = out
+        print(prec, case.poisson_fixed_iter, its_s, ls, l1)
+        assert its_s == its_1
+        if case.poisson_fixed_iter:
+            assert all(it == 3 for it, _ in its_s)
+        for k in ("n", "phi"):
+            assert np.array_equal(fs[k], f1[k]), k
+        assert ls - l1 == sum(4 + 14 * it for it, _ in its_s)
+
+
 def _fp32_source_allowance(wl, f, rho_o, q_beads):
     """A priori bound, relative to ||b||, of how far the FP32 path's Poisson
     source may sit from the oracle's FP64 source formed from the same
