@@ -130,6 +130,9 @@ void release(Ctx &c)
     dev_free(c, c.phi, 0);
     dev_free(c, c.part_charge, 0);
     dev_free(c, c.part_charge_q, 0);
+    dev_free(c, c.charge_tot, 0);
+    dev_free(c, c.charge_tot_q, 0);
+    dev_free(c, c.charge_chunks, 0);
     dev_free(c, c.part_mass, 0);
     dev_free(c, c.part_pois, 0);
     dev_free(c, c.barrier, 0);
@@ -838,6 +841,9 @@ static int create_handle(const ekl_params *P, void *stream, ekl_handle **out, bo
     c.phi = A(N * ps);
     c.part_charge = (double *)A((size_t)c.charge_blocks * (CHARGE_THREADS / 32) * sizeof(double));
     c.part_charge_q = (long long *)A((size_t)c.charge_blocks * sizeof(long long));
+    c.charge_tot = (double *)A(sizeof(double));
+    c.charge_tot_q = (long long *)A(sizeof(long long));
+    c.charge_chunks = A(CHARGE_CHUNK_BYTES);
     c.part_mass = (double *)A((size_t)((N + 255) / 256) * NS * sizeof(double));
     c.part_pois = (double *)A((size_t)c.pois_blocks * sizeof(double));
     c.barrier = (unsigned *)A(4 * sizeof(unsigned));
@@ -897,6 +903,8 @@ static int create_handle(const ekl_params *P, void *stream, ekl_handle **out, bo
         if (!d_solid) { rc = fail(EKL_ERR_ALLOC, "device allocation failed"); break; }
         e = cudaMemcpyAsync(d_solid, solid, N, cudaMemcpyHostToDevice, c.stream);
         if (e != cudaSuccess) { rc = fail_cuda(e, "upload solid"); break; }
+        e = cudaMemsetAsync(c.charge_chunks, 0, CHARGE_CHUNK_BYTES, c.stream);
+        if (e != cudaSuccess) { rc = fail_cuda(e, "clear charge totals"); break; }
         mask_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c.stream>>>(make_grid3(c.nx, c.ny, c.nz), c.per[0], c.per[1], c.per[2], d_solid, c.mask);
         c.launches++;
         if (c.mg) {
@@ -1318,6 +1326,7 @@ void batch_release(Batch &B)
     dev_free(c0, B.barrier, 0);
     dev_free(c0, B.status, 0);
     dev_free(c0, B.d_mgargs, 0);
+    dev_free(c0, B.d_ctot, 0);
     dev_free(c0, B.mg_bars, 0);
 }
 
@@ -1381,6 +1390,7 @@ int ekl_batch_create(int32_t nrep, const ekl_params *params, void *stream, ekl_b
         B.d_block_rep = (int *)A(4 * (size_t)sms * 2);
         B.d_block_local = (int *)A(4 * (size_t)sms * 2);
         B.d_rep_blocks = (int *)A(4 * (size_t)nrep);
+        B.d_ctot = A(sizeof(ChargeTotals) * (size_t)nrep);
         B.barrier = (unsigned *)A(4 * sizeof(unsigned));
         B.status = (int *)A(sizeof(int));
         if (!ok) rc = fail(EKL_ERR_ALLOC, "device allocation failed");

@@ -87,6 +87,9 @@ struct Ctx {
     void *phi;         // PhiT[N]
     double *part_charge;  // [charge blocks]
     long long *part_charge_q;  // [charge blocks] fixed-point paths: exact sum of rho * 2^40
+    double *charge_tot;        // totals of the two (charge_total_kernel)
+    long long *charge_tot_q;
+    void *charge_chunks;       // its per-block chunk totals and arrival counter (zeroed)
     double *part_mass;    // [mass blocks][3] (filled on request)
     double *part_pois;    // [poisson blocks][2]
     unsigned *barrier;    // {count, generation, abort}
@@ -180,6 +183,7 @@ struct Batch {
     // blocks with its own barrier words
     int mg;
     void *d_mgargs;          // MgArgs per replica
+    void *d_ctot;            // ChargeTotals per replica
     unsigned *mg_bars;       // [4 * nrep]
     size_t mg_smem;          // largest replica's shared memory for its coarse levels
 };

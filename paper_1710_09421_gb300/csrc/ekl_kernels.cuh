@@ -51,6 +51,10 @@ template <typename S, typename R, typename PhiT> struct StepArgs {
     // reductions / status
     double *part_charge;
     long long *part_charge_q;  // fixed-point paths: exact sum of rho * 2^40 per block
+    // totals of those partials (charge_totals), or null: the solve then sums
+    // the partials itself
+    double *charge_tot;
+    long long *charge_tot_q;
     double *part_mass;
     double *part_pois;
     unsigned *barrier;
@@ -220,6 +224,92 @@ __device__ __forceinline__ void charge_body(const StepArgs<S, R, PhiT> &a, long 
     }
 }
 
+// Totals of the charge pass's block partials, for the Poisson solve, in a
+// fixed order, the same for a single run and for a batch replica: block b of
+// CHARGE_TOTAL_BLOCKS sums the partials of its contiguous chunk (thread t
+// keeps eight running sums, t + 1024 (8 j + u) going to sum u, added in a
+// fixed tree; then a fixed shuffle tree per warp and the warps in order); the
+// block that finishes last sums the chunk totals in chunk order and resets
+// the arrival counter.  FIXED: also the exact integer total of rho * 2^40.
+constexpr int CHARGE_TOTAL_BLOCKS = 64;
+constexpr size_t CHARGE_CHUNK_BYTES = CHARGE_TOTAL_BLOCKS * (sizeof(double) + sizeof(long long)) + 16;
+struct ChargeTotals {
+    const double *part;
+    const long long *part_q;
+    int n;
+    double *tot;
+    long long *tot_q;
+    double *chunk;         // [CHARGE_TOTAL_BLOCKS]
+    long long *chunk_q;    // [CHARGE_TOTAL_BLOCKS]
+    unsigned *arrived;     // zero between launches
+};
+
+template <bool FIXED> __device__ void charge_totals(const ChargeTotals &T)
+{
+    __shared__ double sh[32];
+    __shared__ long long shq[32];
+    __shared__ int last;
+    constexpr int U = 8;
+    const int per = (T.n + CHARGE_TOTAL_BLOCKS - 1) / CHARGE_TOTAL_BLOCKS;
+    const int k_beg = blockIdx.x * per, k_end = min(T.n, k_beg + per);
+    double v[U];
+    long long q = 0;
+#pragma unroll
+    for (int u = 0; u < U; u++) v[u] = 0.0;
+    for (int k0 = k_beg + threadIdx.x; k0 < k_end; k0 += U * blockDim.x) {
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int k = k0 + u * blockDim.x;
+            if (k < k_end) {
+                v[u] += __ldcg(T.part + k);
+                if (FIXED) q += __ldcg(T.part_q + k);
+            }
+        }
+    }
+    auto block_ll = [&](long long x) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) shq[threadIdx.x >> 5] = x;
+        __syncthreads();
+        long long r = 0;
+        if (threadIdx.x == 0)
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) r += shq[w];
+        return r;
+    };
+    const double t = block_sum(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])), sh);
+    const long long tq = FIXED ? block_ll(q) : 0;
+    if (threadIdx.x == 0) {
+        __stcg(T.chunk + blockIdx.x, t);
+        if (FIXED) __stcg(T.chunk_q + blockIdx.x, tq);
+        __threadfence();
+        last = atomicAdd(T.arrived, 1u) == CHARGE_TOTAL_BLOCKS - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const double c = threadIdx.x < CHARGE_TOTAL_BLOCKS ? __ldcg(T.chunk + threadIdx.x) : 0.0;
+    const long long cq = (FIXED && threadIdx.x < CHARGE_TOTAL_BLOCKS) ? __ldcg(T.chunk_q + threadIdx.x) : 0;
+    const double tt = block_sum(c, sh);
+    const long long ttq = FIXED ? block_ll(cq) : 0;
+    if (threadIdx.x == 0) {
+        *T.tot = tt;
+        if (FIXED) *T.tot_q = ttq;
+        *T.arrived = 0;
+    }
+}
+
+template <bool FIXED> __global__ void __launch_bounds__(1024) charge_total_kernel(ChargeTotals T)
+{
+    charge_totals<FIXED>(T);
+}
+
+// the same for every replica of a batch (blockIdx.y: replica)
+template <bool FIXED> __global__ void __launch_bounds__(1024) charge_total_batch_kernel(const ChargeTotals *T)
+{
+    charge_totals<FIXED>(T[blockIdx.y]);
+}
+
 template <typename S, typename R, typename PhiT, bool DEV>
 __global__ void __launch_bounds__(CHARGE_THREADS) charge_kernel(StepArgs<S, R, PhiT> a)
 {
@@ -323,14 +413,14 @@ template <typename S, typename R, typename PhiT>
 __device__ SrcMean source_mean(const StepArgs<S, R, PhiT> &a, double *bc)
 {
     SrcMean sm{0.0, 0, 0, 0.f};
-    const double csum = sum_partials(a.part_charge, a.nblocks_charge, bc);
+    const double csum = a.charge_tot ? __ldcg(a.charge_tot) : sum_partials(a.part_charge, a.nblocks_charge, bc);
     const double nfl = a.n_fluid;
     sm.mean = nfl > 0 ? csum / nfl : 0.0;
     // fixed point: the exact total S of rho * 2^40 over the fluid nodes,
     // S / n = mean_lo + frac with 0 <= frac < 1, and C = c4 frac split into
     // integer and fraction
     if constexpr (!(((PhiT)0.5) != 0)) {
-        const long long S = sum_partials_ll(a.part_charge_q, a.nblocks_charge);
+        const long long S = a.charge_tot ? __ldcg(a.charge_tot_q) : sum_partials_ll(a.part_charge_q, a.nblocks_charge);
         const long long n = (long long)nfl;
         if (n > 0) {
             long long mean_lo = S / n;

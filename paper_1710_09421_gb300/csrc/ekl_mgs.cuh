@@ -23,7 +23,7 @@
 namespace ekl {
 
 constexpr int MGS_THREADS = 1024;
-constexpr int MGS_U = 2;  // node pairs per thread and trip in the lattice half sweeps
+constexpr int MGS_U = 4;  // node pairs per thread and trip in the lattice half sweeps
 
 // block-partial slots (nblk doubles each) in MgArgs::part
 enum { MGS_BB = 0, MGS_RES = 1, MGS_RZ = 2, MGS_PQ = 3, MGS_RR = 4, MGS_SLOTS = 5 };

@@ -44,6 +44,8 @@ static StepArgs<S, R, PhiT> make_args(Ctx &c, int parity = -1)
     a.patch_f = (const R *)c.patch_f;
     a.part_charge = c.part_charge;
     a.part_charge_q = c.part_charge_q;
+    a.charge_tot = c.charge_tot;
+    a.charge_tot_q = c.charge_tot_q;
     a.part_mass = c.part_mass;
     a.part_pois = c.part_pois;
     a.barrier = c.barrier;
@@ -266,6 +268,20 @@ template <typename PhiT> static cudaError_t mgs_build(Ctx &c, const MgArgs &m0, 
     return cudaSuccess;
 }
 
+static inline ChargeTotals charge_totals_args(const Ctx &c)
+{
+    ChargeTotals T;
+    T.part = c.part_charge;
+    T.part_q = c.part_charge_q;
+    T.n = c.charge_blocks;
+    T.tot = c.charge_tot;
+    T.tot_q = c.charge_tot_q;
+    T.chunk = (double *)c.charge_chunks;
+    T.chunk_q = (long long *)(T.chunk + CHARGE_TOTAL_BLOCKS);
+    T.arrived = (unsigned *)(T.chunk_q + CHARGE_TOTAL_BLOCKS);
+    return T;
+}
+
 static inline int cuda_ok(cudaError_t e) { return e == cudaSuccess ? EKL_OK : EKL_ERR_CUDA; }
 
 static inline void phase_begin(Ctx &c, int ph)
@@ -302,7 +318,9 @@ template <typename S, typename R, typename PhiT, bool DEV> int steps_impl(Ctx &c
         // 2. charge density from the streamed ion densities
         phase_begin(c, PH_CHARGE);
         charge_kernel<S, R, PhiT, DEV><<<c.charge_blocks, CHARGE_THREADS, 0, c.stream>>>(a);
-        c.launches++;
+        charge_total_kernel<!(((PhiT)0.5) != 0)>
+            <<<CHARGE_TOTAL_BLOCKS, 1024, 0, c.stream>>>(charge_totals_args(c));
+        c.launches += 2;
         phase_end(c, PH_CHARGE);
         // 3. Poisson: one cooperative launch for all sweeps (after the learned
         //    warm start, when one is installed)
@@ -438,6 +456,16 @@ template <typename S, typename R, typename PhiT, bool DEV> int mass_impl(Ctx &c)
 }
 
 // ------------------------------------------------------------------ batch
+static inline int charge_batch_tables(Batch &B)
+{
+    std::vector<ChargeTotals> t(B.nrep);
+    for (int r = 0; r < B.nrep; r++) t[r] = charge_totals_args(*B.reps[r]);
+    if (cudaMemcpyAsync(B.d_ctot, t.data(), t.size() * sizeof(ChargeTotals), cudaMemcpyHostToDevice, B.stream) !=
+        cudaSuccess)
+        return EKL_ERR_CUDA;
+    return cudaStreamSynchronize(B.stream) == cudaSuccess ? EKL_OK : EKL_ERR_CUDA;
+}
+
 static inline int mg_batch_tables(Batch &B)
 {
     std::vector<MgArgs> t(B.nrep);
@@ -499,6 +527,7 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_tables(Batc
         cudaMemcpyAsync(B.d_rep_blocks, k.data(), n * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess)
         return EKL_ERR_CUDA;
     if (cudaStreamSynchronize(B.stream) != cudaSuccess) return EKL_ERR_CUDA;
+    if (charge_batch_tables(B) != EKL_OK) return EKL_ERR_CUDA;
     if (B.mg && mg_batch_tables(B) != EKL_OK) return EKL_ERR_CUDA;
     B.max_nb = 0;
     B.fluct = 0;
@@ -530,7 +559,9 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_impl(Batch 
         }
         charge_batch_kernel<S, R, PhiT, DEV><<<dim3(B.max_charge_blocks, n), CHARGE_THREADS, 0, B.stream>>>(
             (const StepArgs<S, R, PhiT> *)B.d_args[q]);
-        B.launches++;
+        charge_total_batch_kernel<!(((PhiT)0.5) != 0)>
+            <<<dim3(CHARGE_TOTAL_BLOCKS, n), 1024, 0, B.stream>>>((const ChargeTotals *)B.d_ctot);
+        B.launches += 2;
         cudaMemsetAsync(B.barrier, 0, 4 * sizeof(unsigned), B.stream);
         if (B.mg) {
             cudaMemsetAsync(B.mg_bars, 0, 4 * sizeof(unsigned) * (size_t)n, B.stream);

@@ -31,8 +31,11 @@ def test_bench_pore_lb_bytes():
 def test_multigrid_bytes_per_iteration_and_solve():
     wl = box(4, 4, 4)
     nf = 64
-    assert bench.MG_BYTES_PER_ITER == 172 and bench.MG_BYTES_PER_SOLVE == 68
+    assert bench.mg_bytes_per_iter(4) == 172 and bench.mg_bytes_per_solve(4) == 68
     assert bench.mg_algorithmic_bytes(wl, 5) == nf * (5 * 172 + 68)
+    # the split solve's 1-byte link array: 3 B less per lattice pass
+    assert bench.mg_bytes_per_iter(1) == 172 - 3 * 5.5 - 3 * 3 and bench.mg_bytes_per_solve(1) == 68 - 9
+    assert bench.mg_algorithmic_bytes(wl, 5, link_bytes=1) == nf * (5 * 146.5 + 59)
 
 
 def test_clock_summary():

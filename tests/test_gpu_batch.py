@@ -47,10 +47,11 @@ def test_batch_tolerance_and_autotune():
     for r in range(len(wls)):
         st = batch.reps[r].stats()
         assert st["poisson_res"] <= 1e-8 and st["poisson_iters"] > 0
-    # one launch per phase per step for the whole batch (5 phases)
+    # one launch per phase per step for the whole batch (5 phases), plus the
+    # charge totals
     l0 = batch.launches()
     batch.step(3)
-    assert batch.launches() - l0 == 3 * 5
+    assert batch.launches() - l0 == 3 * 6
     batch.close()
 
 
@@ -77,7 +78,7 @@ def test_batch_multigrid_replicas():
         assert ref.poisson_residual(ref.last_rho(), phi) <= tol * 1.001, r
     l0 = batch.launches()
     assert batch.step(9) >= 0
-    assert batch.launches() - l0 == 9 * 5
+    assert batch.launches() - l0 == 9 * 6
     for r, wl in enumerate(wls):
         st = batch.reps[r].stats()
         assert st["poisson_res"] <= tol and st["poisson_iters"] > 0, (r, st)
