@@ -258,15 +258,78 @@ static __device__ void fine_half(const Grid3 &g, const L *__restrict__ link, con
     }
 }
 
-// Restriction: a warp takes 8 consecutive coarse cells; lane = X + 8 k
-// computes the two x-children (dx = 0, 1) in the (dy, dz) = (k & 1, k >> 1)
-// row of cell X, so each quarter-warp reads 16 consecutive fine nodes; the
-// four rows of a cell are summed by shuffles.  The loop is warp-uniform.
+// Warp-shuffle restrictions (fine_restrict_warp, coarse_restrict): a warp
+// takes 8 consecutive coarse cells; lane = X + 8 k computes the two
+// x-children (dx = 0, 1) in the (dy, dz) = (k & 1, k >> 1) row of cell X;
+// the four rows of a cell are summed by shuffles.  The loops are
+// warp-uniform.
 __device__ __forceinline__ float mg_sum_rows(float v)
 {
     v += __shfl_xor_sync(0xffffffffu, v, 8);
     v += __shfl_xor_sync(0xffffffffu, v, 16);
     return v;
+}
+
+// The loads of one node's residual r - A z, issued before any is used
+template <typename L> struct ResidIn {
+    float zn[6], ri, zi;
+    unsigned m;
+};
+template <typename L>
+__device__ __forceinline__ void fine_resid_load(const Grid3 &g, const L *__restrict__ link, const float *r,
+                                                const float *z, int x, int y, int zz, ResidIn<L> &o)
+{
+    o.m = MG_NO_NODE;
+    if (x >= g.nx || y >= g.ny || zz >= g.nz) return;
+    const int i = x + g.nx * (y + g.ny * zz);
+    int nb[6];
+    face_nbrs(g, x, y, zz, i, nb);
+#pragma unroll
+    for (int f = 0; f < 6; f++) o.zn[f] = mg_ldl(z + nb[f]);
+    o.ri = mg_ldl(r + i);
+    o.zi = mg_ldl(z + i);
+    o.m = __ldg(link + i);
+}
+template <typename L> __device__ __forceinline__ float fine_resid_eval(const ResidIn<L> &o)
+{
+    const unsigned open = mg_open(o.m);
+    if (mg_wall<L>(o.m) || !open) return 0.f;
+    float acc = o.ri - (float)__popc(open) * o.zi;
+#pragma unroll
+    for (int f = 0; f < 6; f++)
+        if ((open >> f) & 1u) acc += o.zn[f];
+    return acc;
+}
+
+// C.f = sum over the children of each level-1 cell of (r - A z); FIRST: also
+// start level 1's pre-smoothing (colour-0 cells take f / diag).  A thread
+// takes whole cells (consecutive threads, consecutive cells of a row), so a
+// warp reads 64 consecutive nodes of a fine row per load; the children of a
+// cell are visited one z-plane at a time, the loads of its four nodes issued
+// before any is used.  The sum is formed as (row (0,0) + row (1,0)) +
+// (row (0,1) + row (1,1)) over the (dy, dz) rows, each row the x-pair's sum.
+template <bool FIRST, typename L>
+static __device__ void fine_restrict_cells(const Grid3 &g, const L *__restrict__ link, const float *r,
+                                     const float *z, const MgLevel &C, int t0, int nt)
+{
+    for (int I = t0; I < C.N; I += nt) {
+        const int X = I % C.nx, t = I / C.nx, Y = t % C.ny, Z = t / C.ny;
+        float row[2][2];
+#pragma unroll
+        for (int dz = 0; dz < 2; dz++) {
+            ResidIn<L> in[2][2];
+#pragma unroll
+            for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+                for (int dx = 0; dx < 2; dx++)
+                    fine_resid_load(g, link, r, z, 2 * X + dx, 2 * Y + dy, 2 * Z + dz, in[dy][dx]);
+#pragma unroll
+            for (int dy = 0; dy < 2; dy++) row[dy][dz] = fine_resid_eval(in[dy][0]) + fine_resid_eval(in[dy][1]);
+        }
+        const float f = (row[0][0] + row[1][0]) + (row[0][1] + row[1][1]);
+        __stcg(C.f + I, f);
+        if (FIRST && !((X + Y + Z) & 1)) __stcg(C.e + I, f * __ldg(&C.sig[I].w));
+    }
 }
 
 // residual r - A z of one fluid node of the lattice (0 elsewhere)
@@ -292,10 +355,13 @@ __device__ __forceinline__ float fine_resid(const Grid3 &g, const L *__restrict_
     return acc;
 }
 
-// C.f = sum over the children of each level-1 cell of (r - A z); FIRST: also
-// start level 1's pre-smoothing (colour-0 cells take f / diag)
+// The same restriction for the single cooperative launch (fewer registers):
+// a warp takes 8 consecutive coarse cells, lane = X + 8 k computes the two
+// x-children in the (dy, dz) = (k & 1, k >> 1) row of cell X, and the four
+// rows are summed by shuffles in the same order as fine_restrict_cells (same
+// result bit for bit).  The loop is warp-uniform.
 template <bool FIRST, typename L>
-static __device__ void fine_restrict(const Grid3 &g, const L *__restrict__ link, const float *r,
+static __device__ void fine_restrict_warp(const Grid3 &g, const L *__restrict__ link, const float *r,
                                      const float *z, const MgLevel &C, int t0, int nt)
 {
     const int lane = threadIdx.x & 31, total = ((C.N + 7) >> 3) * 32;
@@ -879,8 +945,8 @@ __device__ bool mg_vcycle(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const 
         fine_half<false, false>(g, a.mask, m.r, m.z, m.lev[1], s & 1, t0, nt, dummy);
         MG_BAR();
     }
-    if (m.cta_from > 1) fine_restrict<true>(g, a.mask, m.r, m.z, m.lev[1], t0, nt);
-    else fine_restrict<false>(g, a.mask, m.r, m.z, m.lev[1], t0, nt);
+    if (m.cta_from > 1) fine_restrict_warp<true>(g, a.mask, m.r, m.z, m.lev[1], t0, nt);
+    else fine_restrict_warp<false>(g, a.mask, m.r, m.z, m.lev[1], t0, nt);
     MG_BAR();
     if (!mg_coarse_cycle<TILES>(m, G, bar_k, a.status, sm, sh, bc)) return false;
     fine_half<false, true>(g, a.mask, m.r, m.z, m.lev[1], 1, t0, nt, dummy);
@@ -958,9 +1024,91 @@ __device__ double mg_true_residual(const Grid3 &g, const L *__restrict__ link, c
 // The CG passes walk the lattice by pairs (2 xh, 2 xh + 1) of one x-row: one
 // division chain per two nodes and the loads of both issued together.
 
-// p = z + beta p_old and q = A p on the fluid nodes; returns sum p q
+// p = z + beta p_old and q = A p on the fluid nodes: the loads of one node
+template <typename L> struct PqIn {
+    float zj[6], pj[6], zi, pi;
+    unsigned m;
+};
 template <bool FRESH, typename L>
-__device__ __forceinline__ void mg_pq_node(const Grid3 &g, const L *__restrict__ link, const float *z,
+__device__ __forceinline__ void mg_pq_load(const Grid3 &g, const L *__restrict__ link, const float *z,
+                                           const float *pold, int x, int y, int zz, int i, PqIn<L> &o)
+{
+    int nb[6];
+    face_nbrs(g, x, y, zz, i, nb);
+#pragma unroll
+    for (int f = 0; f < 6; f++) {
+        o.zj[f] = mg_ldl(z + nb[f]);
+        if (!FRESH) o.pj[f] = mg_ldl(pold + nb[f]);
+    }
+    o.zi = mg_ldl(z + i);
+    if (!FRESH) o.pi = mg_ldl(pold + i);
+    o.m = __ldg(link + i);
+}
+template <bool FRESH, typename L>
+__device__ __forceinline__ void mg_pq_eval(const PqIn<L> &o, float beta, float &pn, float &qv, bool &live)
+{
+    const unsigned open = mg_open(o.m);
+    live = !mg_wall<L>(o.m);
+    pn = 0.f;
+    qv = 0.f;
+    if (!live || !open) return;
+    pn = FRESH ? o.zi : o.zi + beta * o.pi;
+    float acc = 0.f;
+#pragma unroll
+    for (int f = 0; f < 6; f++)
+        if ((open >> f) & 1u) acc += FRESH ? o.zj[f] : o.zj[f] + beta * o.pj[f];
+    qv = (float)__popc(open) * pn - acc;
+}
+
+// U pairs per thread and trip (loads of all first); returns sum p q in the
+// order of one pair per trip
+template <bool FRESH, typename L, int U = 1>
+__device__ float mg_pq_pass(const Grid3 &g, const L *__restrict__ link, const float *z, const float *pold,
+                            float *pnew, float *q, float beta, int t0, int nt)
+{
+    const int hx = (g.nx + 1) >> 1, np = hx * g.ny * g.nz;
+    float pq = 0.f;
+    for (int h0 = t0; h0 < np; h0 += U * nt) {
+        PqIn<L> in[U][2];
+        int i0[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int h = h0 + u * nt;
+            in[u][0].m = in[u][1].m = MG_NO_NODE;
+            i0[u] = 0;
+            if (h >= np) continue;
+            const int row = h / hx, xh = h - row * hx;
+            const int zz = row / g.ny, y = row - zz * g.ny;
+            const int x0 = 2 * xh;
+            i0[u] = x0 + g.nx * row;
+            mg_pq_load<FRESH>(g, link, z, pold, x0, y, zz, i0[u], in[u][0]);
+            if (x0 + 1 < g.nx) mg_pq_load<FRESH>(g, link, z, pold, x0 + 1, y, zz, i0[u] + 1, in[u][1]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            float pn0, q0, pn1, q1;
+            bool l0, l1;
+            mg_pq_eval<FRESH>(in[u][0], beta, pn0, q0, l0);
+            mg_pq_eval<FRESH>(in[u][1], beta, pn1, q1, l1);
+            if (l0) {
+                __stcg(pnew + i0[u], pn0);
+                __stcg(q + i0[u], q0);
+            }
+            if (l1) {
+                __stcg(pnew + i0[u] + 1, pn1);
+                __stcg(q + i0[u] + 1, q1);
+            }
+            pq += pn0 * q0 + pn1 * q1;
+        }
+    }
+    return pq;
+}
+
+// The same p/q pass for the single cooperative launch, one pair per trip
+// with the neighbours' p formed as they arrive (fewer registers; the same
+// values and the same order of the p.q sum as mg_pq_pass)
+template <bool FRESH, typename L>
+__device__ __forceinline__ void mg_pq_node_lean(const Grid3 &g, const L *__restrict__ link, const float *z,
                                            const float *pold, float beta, int x, int y, int zz, int i, float &pn,
                                            float &qv, bool &live)
 {
@@ -985,7 +1133,7 @@ __device__ __forceinline__ void mg_pq_node(const Grid3 &g, const L *__restrict__
 }
 
 template <bool FRESH, typename L>
-__device__ float mg_pq_pass(const Grid3 &g, const L *__restrict__ link, const float *z, const float *pold,
+__device__ float mg_pq_pass_lean(const Grid3 &g, const L *__restrict__ link, const float *z, const float *pold,
                             float *pnew, float *q, float beta, int t0, int nt)
 {
     const int hx = (g.nx + 1) >> 1, np = hx * g.ny * g.nz;
@@ -997,8 +1145,8 @@ __device__ float mg_pq_pass(const Grid3 &g, const L *__restrict__ link, const fl
         const bool two = x0 + 1 < g.nx;
         float pn0, q0, pn1 = 0.f, q1 = 0.f;
         bool l0, l1 = false;
-        mg_pq_node<FRESH>(g, link, z, pold, beta, x0, y, zz, i0, pn0, q0, l0);
-        if (two) mg_pq_node<FRESH>(g, link, z, pold, beta, x0 + 1, y, zz, i0 + 1, pn1, q1, l1);
+        mg_pq_node_lean<FRESH>(g, link, z, pold, beta, x0, y, zz, i0, pn0, q0, l0);
+        if (two) mg_pq_node_lean<FRESH>(g, link, z, pold, beta, x0 + 1, y, zz, i0 + 1, pn1, q1, l1);
         if (l0) {
             __stcg(pnew + i0, pn0);
             __stcg(q + i0, q0);
@@ -1162,8 +1310,8 @@ __device__ void mg_solve(const StepArgs<S, R, PhiT> &a, const MgArgs &m, const M
         // formed from their z and p_old)
         const float *pold = m.p[pi];
         float *pnew = m.p[pi ^ 1];
-        float pq_t = fresh ? mg_pq_pass<true>(g, a.mask, m.z, pold, pnew, m.q, beta, tid, nthr)
-                           : mg_pq_pass<false>(g, a.mask, m.z, pold, pnew, m.q, beta, tid, nthr);
+        float pq_t = fresh ? mg_pq_pass_lean<true>(g, a.mask, m.z, pold, pnew, m.q, beta, tid, nthr)
+                           : mg_pq_pass_lean<false>(g, a.mask, m.z, pold, pnew, m.q, beta, tid, nthr);
         pi ^= 1;
         double pq;
         if (!reduce(block_sum_lanes0(warp_sum_ff_lane0(pq_t), sh), pq)) return;

@@ -23,7 +23,8 @@
 namespace ekl {
 
 constexpr int MGS_THREADS = 1024;
-constexpr int MGS_U = 4;  // node pairs per thread and trip in the lattice half sweeps
+constexpr int MGS_U = 4;   // node pairs per thread and trip in the lattice half sweeps
+constexpr int MGS_PQU = 1; // p/q pass node pairs per thread and trip
 
 // block-partial slots (nblk doubles each) in MgArgs::part
 enum { MGS_BB = 0, MGS_RES = 1, MGS_RZ = 2, MGS_PQ = 3, MGS_RR = 4, MGS_SLOTS = 5 };
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_half_kernel(Grid3 g, MgArg
 
 template <bool FIRST> __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_restrict_kernel(Grid3 g, MgArgs m)
 {
-    fine_restrict<FIRST>(g, m.link, m.r, m.z, m.lev[1], (int)(blockIdx.x * blockDim.x + threadIdx.x),
+    fine_restrict_cells<FIRST>(g, m.link, m.r, m.z, m.lev[1], (int)(blockIdx.x * blockDim.x + threadIdx.x),
                          (int)(gridDim.x * blockDim.x));
 }
 
@@ -210,8 +211,8 @@ static __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_pq_kernel(Grid3 g, 
     const float beta = fresh ? 0.f : (float)(rz / ctl->rz_old);
     const float *pold = m.p[pi];
     float *pnew = m.p[pi ^ 1];
-    const float t = fresh ? mg_pq_pass<true>(g, m.link, m.z, pold, pnew, m.q, beta, tid, nthr)
-                          : mg_pq_pass<false>(g, m.link, m.z, pold, pnew, m.q, beta, tid, nthr);
+    const float t = fresh ? mg_pq_pass<true, uint8_t, MGS_PQU>(g, m.link, m.z, pold, pnew, m.q, beta, tid, nthr)
+                          : mg_pq_pass<false, uint8_t, MGS_PQU>(g, m.link, m.z, pold, pnew, m.q, beta, tid, nthr);
     const double pq = block_sum_lanes0(warp_sum_ff_lane0(t), sh);
     if (threadIdx.x == 0) mgs_slot(m, MGS_PQ, nblk)[blockIdx.x] = pq;
 }
