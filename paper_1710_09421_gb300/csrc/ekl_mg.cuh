@@ -440,7 +440,9 @@ __device__ __forceinline__ float mg_cresid(float f, float e, float4 s, float sxm
 
 // Half sweep of colour c of e <- (f + sum sigma e_j) / diag.  Faces beyond a
 // closed side carry sigma = 0 and inactive cells keep e = 0, so wrapped or
-// inactive neighbours contribute nothing.
+// inactive neighbours contribute nothing.  Every load of a cell is issued
+// before its activity (1/diag = 0 on inactive cells) is known, so a cell
+// costs one memory round trip, not two.
 template <bool SH, bool PRO>
 static __device__ void coarse_half(const MgLevel &L, const MgLevel &C, int c, int t0, int nt)
 {
@@ -449,12 +451,11 @@ static __device__ void coarse_half(const MgLevel &L, const MgLevel &C, int c, in
         const Pair p = mg_pair(h, hx, L.ny, c);
         if (p.x >= L.nx) continue;
         const int i = p.x + L.nx * p.row;
-        const float4 s = mg_sig<SH>(L.sig + i);
-        if (s.w == 0.f) continue;
         const CNbr n = coarse_nbrs(L, p.x, p.y, p.z, i);
         const int xm = p.x == 0 ? L.nx - 1 : p.x - 1, xp = p.x == L.nx - 1 ? 0 : p.x + 1;
         const int ym = p.y == 0 ? L.ny - 1 : p.y - 1, yp = p.y == L.ny - 1 ? 0 : p.y + 1;
         const int zm = p.z == 0 ? L.nz - 1 : p.z - 1, zp = p.z == L.nz - 1 ? 0 : p.z + 1;
+        const float4 s = mg_sig<SH>(L.sig + i);
         const float v = mg_relax(mg_ld<SH>(L.f + i), s, mg_sx<SH>(L.sig + n.xm), mg_sy<SH>(L.sig + n.ym),
                                  mg_sz<SH>(L.sig + n.zm), coarse_val<SH, PRO>(L, C, n.xp, xp, p.y, p.z),
                                  coarse_val<SH, PRO>(L, C, n.xm, xm, p.y, p.z),
@@ -462,22 +463,23 @@ static __device__ void coarse_half(const MgLevel &L, const MgLevel &C, int c, in
                                  coarse_val<SH, PRO>(L, C, n.ym, p.x, ym, p.z),
                                  coarse_val<SH, PRO>(L, C, n.zp, p.x, p.y, zp),
                                  coarse_val<SH, PRO>(L, C, n.zm, p.x, p.y, zm));
-        mg_st<SH>(L.e + i, v);
+        if (s.w != 0.f) mg_st<SH>(L.e + i, v);
     }
 }
 
-// residual f - A e of one cell of a coarse level (0 outside or inactive)
 template <bool SH>
 __device__ __forceinline__ float coarse_resid(const MgLevel &L, int x, int y, int z)
 {
     if (x >= L.nx || y >= L.ny || z >= L.nz) return 0.f;
     const int i = x + L.nx * (y + L.ny * z);
     const float4 sg = mg_sig<SH>(L.sig + i);
-    if (sg.w == 0.f) return 0.f;
     const CNbr n = coarse_nbrs(L, x, y, z, i);
-    return mg_cresid(mg_ld<SH>(L.f + i), mg_ld<SH>(L.e + i), sg, mg_sx<SH>(L.sig + n.xm), mg_sy<SH>(L.sig + n.ym),
-                     mg_sz<SH>(L.sig + n.zm), mg_ld<SH>(L.e + n.xp), mg_ld<SH>(L.e + n.xm), mg_ld<SH>(L.e + n.yp),
-                     mg_ld<SH>(L.e + n.ym), mg_ld<SH>(L.e + n.zp), mg_ld<SH>(L.e + n.zm));
+    // formed before the activity test, so all its loads are in flight at once
+    const float res = mg_cresid(mg_ld<SH>(L.f + i), mg_ld<SH>(L.e + i), sg, mg_sx<SH>(L.sig + n.xm),
+                                mg_sy<SH>(L.sig + n.ym), mg_sz<SH>(L.sig + n.zm), mg_ld<SH>(L.e + n.xp),
+                                mg_ld<SH>(L.e + n.xm), mg_ld<SH>(L.e + n.yp), mg_ld<SH>(L.e + n.ym),
+                                mg_ld<SH>(L.e + n.zp), mg_ld<SH>(L.e + n.zm));
+    return sg.w == 0.f ? 0.f : res;
 }
 
 // C.f = sum over the children of each cell of level l+1 of (f - A e) on
