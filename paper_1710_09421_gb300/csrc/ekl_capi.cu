@@ -631,7 +631,8 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long 
     c.mg_wide = N >= (long long)MG_WIDE_NODES_PER_SM * c.num_sms;  // (replicas use the batched kernel)
     // the same lattices run the solve split into per-pass launches
     c.mg_split = split && c.mg_wide;
-    c.mgs_iter_kernels = 2 * (2 * MG_NU - 1) + 8;
+    c.mgs_l1 = c.mg_split && c.mg_cta_from > 1 && c.mg_tile_from > 1;
+    c.mgs_iter_kernels = 2 * (2 * MG_NU - 1) + 8 + (c.mgs_l1 ? 2 * (2 * MG_NU_COARSE - 1) + 2 : 0);
     if (ops(c.prec).mg_blocks(c.mg_smem, c.mg_wide) < 1) return "multigrid kernel cannot be resident";
     c.mg_r = (float *)A(N * sizeof(float));
     c.mg_link = (uint8_t *)A(N);

@@ -141,6 +141,7 @@ struct Ctx {
     cudaGraph_t mgs_graph;   // its CG loop, built at the first solve
     cudaGraphExec_t mgs_exec;
     int mgs_iter_kernels;    // kernels launched per CG iteration of the loop
+    int mgs_l1;              // level 1 grid-wide: smoothed by separate launches in the loop
 
     // learned warm start of the Poisson solve (ekl_net.cu)
     void *net;

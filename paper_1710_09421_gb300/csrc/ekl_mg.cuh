@@ -442,28 +442,43 @@ __device__ __forceinline__ float mg_cresid(float f, float e, float4 s, float sxm
 // closed side carry sigma = 0 and inactive cells keep e = 0, so wrapped or
 // inactive neighbours contribute nothing.  Every load of a cell is issued
 // before its activity (1/diag = 0 on inactive cells) is known, so a cell
-// costs one memory round trip, not two.
-template <bool SH, bool PRO>
+// costs one memory round trip, not two; a thread takes U cells per trip
+// (h, h + nt, ...) with all their loads issued first.
+template <bool SH, bool PRO, int U = 1>
 static __device__ void coarse_half(const MgLevel &L, const MgLevel &C, int c, int t0, int nt)
 {
     const int hx = (L.nx + 1) >> 1, np = hx * L.ny * L.nz;
-    for (int h = t0; h < np; h += nt) {
-        const Pair p = mg_pair(h, hx, L.ny, c);
-        if (p.x >= L.nx) continue;
-        const int i = p.x + L.nx * p.row;
-        const CNbr n = coarse_nbrs(L, p.x, p.y, p.z, i);
-        const int xm = p.x == 0 ? L.nx - 1 : p.x - 1, xp = p.x == L.nx - 1 ? 0 : p.x + 1;
-        const int ym = p.y == 0 ? L.ny - 1 : p.y - 1, yp = p.y == L.ny - 1 ? 0 : p.y + 1;
-        const int zm = p.z == 0 ? L.nz - 1 : p.z - 1, zp = p.z == L.nz - 1 ? 0 : p.z + 1;
-        const float4 s = mg_sig<SH>(L.sig + i);
-        const float v = mg_relax(mg_ld<SH>(L.f + i), s, mg_sx<SH>(L.sig + n.xm), mg_sy<SH>(L.sig + n.ym),
-                                 mg_sz<SH>(L.sig + n.zm), coarse_val<SH, PRO>(L, C, n.xp, xp, p.y, p.z),
-                                 coarse_val<SH, PRO>(L, C, n.xm, xm, p.y, p.z),
-                                 coarse_val<SH, PRO>(L, C, n.yp, p.x, yp, p.z),
-                                 coarse_val<SH, PRO>(L, C, n.ym, p.x, ym, p.z),
-                                 coarse_val<SH, PRO>(L, C, n.zp, p.x, p.y, zp),
-                                 coarse_val<SH, PRO>(L, C, n.zm, p.x, p.y, zm));
-        if (s.w != 0.f) mg_st<SH>(L.e + i, v);
+    for (int h0 = t0; h0 < np; h0 += U * nt) {
+        float v[U], w[U];
+        int ii[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int h = h0 + u * nt;
+            w[u] = 0.f;
+            v[u] = 0.f;
+            ii[u] = 0;
+            if (h >= np) continue;
+            const Pair p = mg_pair(h, hx, L.ny, c);
+            if (p.x >= L.nx) continue;
+            const int i = p.x + L.nx * p.row;
+            ii[u] = i;
+            const CNbr n = coarse_nbrs(L, p.x, p.y, p.z, i);
+            const int xm = p.x == 0 ? L.nx - 1 : p.x - 1, xp = p.x == L.nx - 1 ? 0 : p.x + 1;
+            const int ym = p.y == 0 ? L.ny - 1 : p.y - 1, yp = p.y == L.ny - 1 ? 0 : p.y + 1;
+            const int zm = p.z == 0 ? L.nz - 1 : p.z - 1, zp = p.z == L.nz - 1 ? 0 : p.z + 1;
+            const float4 s = mg_sig<SH>(L.sig + i);
+            w[u] = s.w;
+            v[u] = mg_relax(mg_ld<SH>(L.f + i), s, mg_sx<SH>(L.sig + n.xm), mg_sy<SH>(L.sig + n.ym),
+                            mg_sz<SH>(L.sig + n.zm), coarse_val<SH, PRO>(L, C, n.xp, xp, p.y, p.z),
+                            coarse_val<SH, PRO>(L, C, n.xm, xm, p.y, p.z),
+                            coarse_val<SH, PRO>(L, C, n.yp, p.x, yp, p.z),
+                            coarse_val<SH, PRO>(L, C, n.ym, p.x, ym, p.z),
+                            coarse_val<SH, PRO>(L, C, n.zp, p.x, p.y, zp),
+                            coarse_val<SH, PRO>(L, C, n.zm, p.x, p.y, zm));
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (w[u] != 0.f) mg_st<SH>(L.e + ii[u], v[u]);
     }
 }
 
@@ -880,13 +895,15 @@ static __device__ void mg_dense_solve(const MgArgs &m, int t0, int nt)
     }
 }
 
-// Coarse part of a V-cycle over the grid: entered with level 1's right-hand
-// side restricted (and, when level 1 is grid-wide and not block 0's, its
-// pre-smoothing started); leaves level 1's correction in lev[1].e for the
-// prolongating half sweep.  False on a barrier abort.
+// Coarse part of a V-cycle over the grid, from level `from` (1, or 2 when
+// level 1 is smoothed by separate launches): entered with level from's
+// right-hand side restricted (and, when that level is grid-wide and not
+// block 0's, its pre-smoothing started); leaves level from's correction in
+// lev[from].e for the prolongating half sweep of the level above.  False on
+// a barrier abort.
 template <bool TILES>
 __device__ bool mg_coarse_cycle(const MgArgs &m, const MgGrid &G, unsigned &bar_k, int *status, float *sm,
-                                double *sh, double *bc)
+                                double *sh, double *bc, int from = 1)
 {
     const int t0 = G.t0, nt = G.nt;
 #define MG_BAR()                                                          \
@@ -894,7 +911,7 @@ __device__ bool mg_coarse_cycle(const MgArgs &m, const MgGrid &G, unsigned &bar_
         if (!grid_barrier(G.bar, (unsigned)G.nblk, bar_k, status)) return false; \
     } while (0)
     float *tsm = sm + m.tile_off;  // coarse tile regions
-    for (int l = 1; l < m.cta_from; l++) {
+    for (int l = from; l < m.cta_from; l++) {
         if (TILES && l >= m.tile_from) {
             coarse_pre_tiles(m.lev[l], m.lev[l + 1], m.tile[l], 2 * m.nu_c, G.blk, G.nblk, tsm);
             MG_BAR();
@@ -911,7 +928,7 @@ __device__ bool mg_coarse_cycle(const MgArgs &m, const MgGrid &G, unsigned &bar_
     if (m.dense) mg_dense_solve(m, t0, nt);
     else if (G.blk == 0) mg_cta_cycle(m, sm, sh, bc);
     MG_BAR();
-    for (int l = m.cta_from - 1; l >= 1; l--) {
+    for (int l = m.cta_from - 1; l >= from; l--) {
         if (TILES && l >= m.tile_from) {
             coarse_post_tiles(m.lev[l], m.lev[l + 1], m.tile[l], 2 * m.nu_c, G.blk, G.nblk, tsm);
             MG_BAR();

@@ -25,6 +25,7 @@ namespace ekl {
 constexpr int MGS_THREADS = 1024;
 constexpr int MGS_U = 4;   // node pairs per thread and trip in the lattice half sweeps
 constexpr int MGS_PQU = 1; // p/q pass node pairs per thread and trip
+constexpr int MGS_CU = 1;  // level-1 cells per thread and trip in its half sweeps
 
 // block-partial slots (nblk doubles each) in MgArgs::part
 enum { MGS_BB = 0, MGS_RES = 1, MGS_RZ = 2, MGS_PQ = 3, MGS_RR = 4, MGS_SLOTS = 5 };
@@ -185,8 +186,24 @@ template <bool FIRST> __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_rest
                          (int)(gridDim.x * blockDim.x));
 }
 
-// The coarse levels of one V-cycle (cooperative launch; `bar` zeroed before it)
-static __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_coarse_kernel(MgArgs m, unsigned *bar, int *status)
+// Level 1, when grid-wide, in separate launches like the lattice: one
+// red-black half sweep (PRO: prolongating from level 2) ...
+template <bool PRO> __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_chalf_kernel(MgArgs m, int c)
+{
+    coarse_half<false, PRO, MGS_CU>(m.lev[1], m.lev[2], c, (int)(blockIdx.x * blockDim.x + threadIdx.x),
+                            (int)(gridDim.x * blockDim.x));
+}
+// ... and its restriction to level 2 (FIRST: level 2 is grid-wide or tiled)
+template <bool FIRST> __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_crestrict_kernel(MgArgs m)
+{
+    coarse_restrict<false, FIRST>(m.lev[1], m.lev[2], (int)(blockIdx.x * blockDim.x + threadIdx.x),
+                                  (int)(gridDim.x * blockDim.x));
+}
+
+// The coarse levels of one V-cycle from level `from` (cooperative launch;
+// `bar` zeroed before it)
+static __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_coarse_kernel(MgArgs m, unsigned *bar, int *status,
+                                                                          int from)
 {
     __shared__ double sh[MGS_THREADS / 32];
     __shared__ double bc[1];
@@ -195,7 +212,7 @@ static __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_coarse_kernel(MgArg
                    (int)blockIdx.x, bar};
     if (G.blk == 0 && !m.dense) mg_cta_load(m, mg_sm);
     unsigned bar_k = 0;
-    mg_coarse_cycle<true>(m, G, bar_k, status, mg_sm, sh, bc);
+    mg_coarse_cycle<true>(m, G, bar_k, status, mg_sm, sh, bc, from);
 }
 
 // p = z + beta p_old, q = A p with the block partials of p.q

@@ -167,9 +167,10 @@ static inline MgArgs make_mg_args(const Ctx &c)
 // Graph of a split multigrid solve (ekl_mgs.cuh), launched after the step's
 // start kernel:
 //   true residual -> init -> WHILE (condition set by init / end) {
-//     pre-smoothing half sweeps, restriction, coarse levels (cooperative),
-//     prolongating and post-smoothing half sweeps, p/q, update, mid,
-//     true residual when due, end }
+//     pre-smoothing half sweeps, restriction, [level 1: half sweeps and
+//     restriction], coarse levels (cooperative), [level 1: prolongating and
+//     post-smoothing half sweeps], lattice prolongating and post-smoothing
+//     half sweeps, p/q, update, mid, true residual when due, end }
 //   -> true residual when phi moved after the last one -> report.
 // Every argument is fixed for the life of the handle; the step's tolerance
 // and iteration limits reach the graph through MgCtl.
@@ -222,6 +223,13 @@ template <typename PhiT> static cudaError_t mgs_build(Ctx &c, const MgArgs &m0, 
         for (int s = 1; s < 2 * MG_NU; s++) mgs_half_kernel<false, false><<<nb, MGS_THREADS, 0, cs>>>(g, m, s & 1);
         if (m.cta_from > 1) mgs_restrict_kernel<true><<<nb, MGS_THREADS, 0, cs>>>(g, m);
         else mgs_restrict_kernel<false><<<nb, MGS_THREADS, 0, cs>>>(g, m);
+        // level 1 smoothed and restricted by separate launches when grid-wide
+        const int from = c.mgs_l1 ? 2 : 1;
+        if (c.mgs_l1) {
+            for (int s = 1; s < 2 * MG_NU_COARSE; s++) mgs_chalf_kernel<false><<<nb, MGS_THREADS, 0, cs>>>(m, s & 1);
+            if (m.cta_from > 2) mgs_crestrict_kernel<true><<<nb, MGS_THREADS, 0, cs>>>(m);
+            else mgs_crestrict_kernel<false><<<nb, MGS_THREADS, 0, cs>>>(m);
+        }
         cudaMemsetAsync(c.barrier, 0, 4 * sizeof(unsigned), cs);
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute coop[1];
@@ -233,7 +241,12 @@ template <typename PhiT> static cudaError_t mgs_build(Ctx &c, const MgArgs &m0, 
         cfg.stream = cs;
         cfg.attrs = coop;
         cfg.numAttrs = 1;
-        cudaError_t el = cudaLaunchKernelEx(&cfg, mgs_coarse_kernel, m, c.barrier, c.status);
+        cudaError_t el = cudaLaunchKernelEx(&cfg, mgs_coarse_kernel, m, c.barrier, c.status, from);
+        if (c.mgs_l1) {
+            mgs_chalf_kernel<true><<<nb, MGS_THREADS, 0, cs>>>(m, 1);
+            for (int s = 1; s < 2 * MG_NU_COARSE; s++)
+                mgs_chalf_kernel<false><<<nb, MGS_THREADS, 0, cs>>>(m, (s & 1) ^ 1);
+        }
         mgs_half_kernel<false, true><<<nb, MGS_THREADS, 0, cs>>>(g, m, 1);
         for (int s = 1; s < 2 * MG_NU; s++) {
             const int col = (s & 1) ^ 1;

@@ -436,11 +436,14 @@ def small_pore(nx=40, ny=24, nz=36, membrane=(16, 19), radius=4.0, n_beads=8,
 
 def replica_set(n_rep=96, seed=1000, sizes_xy=(48, 64, 96), sizes_z=(96, 128, 192),
                 radius=(3.0, 8.0), beads=(16, 128), salt=(0.002, 0.02), E_z=5e-3,
-                membrane_thickness=8, precision="f32"):
+                membrane_thickness=8, bead_charge=-0.1, precision="f32"):
     """Independent translocation pores of uneven size: each replica draws its
     box from sizes_xy^2 x sizes_z, a pore radius, a chain length and a salt
     concentration (seeded), with its own seeds; membrane of the given
-    thickness centred in z."""
+    thickness centred in z.  Beads carry the paper's 0.1 e (Sec. IV.A): with
+    one elementary charge per bead, a long chain in a narrow pore at the low
+    end of the salt range drives the ion densities negative within a few
+    dozen steps (the stability bound of Sec. III)."""
     rng = np.random.default_rng(seed)
     out = []
     for r in range(n_rep):
@@ -452,7 +455,7 @@ def replica_set(n_rep=96, seed=1000, sizes_xy=(48, 64, 96), sizes_z=(96, 128, 19
         zc = Lz // 2
         mem = (zc - membrane_thickness // 2, zc + membrane_thickness // 2 - 1)
         wl = translocation(nx=L, ny=L, nz=Lz, membrane=mem, radius=R, salt=c0, n_beads=nb,
-                           E=(0.0, 0.0, E_z), precision=precision, seed_init=seed + r,
+                           bead_charge=bead_charge, E=(0.0, 0.0, E_z), precision=precision, seed_init=seed + r,
                            seed_chain=seed + 5000 + r, seed_noise=seed + 10000 + r)
         wl.name = f"rep{r}_{L}x{L}x{Lz}_r{R:.1f}_N{nb}"
         out.append(wl)

@@ -209,8 +209,9 @@ def test_mg_split_solve_equals_single_launch(prec):
     same way, as the single cooperative launch (EKL_POISSON_MG_SINGLE):
     potentials, densities, iteration counts and residuals agree bit for bit,
     with the tolerance stop and with a fixed iteration count.  The launch
-    counter includes the kernels the loop launches on the device (4 per solve
-    around the loop, 14 per CG iteration)."""
+    counter includes the kernels the loop launches on the device: 4 per solve
+    around the loop, and per CG iteration 14, plus 8 when level 1 is too
+    large for shared-memory tiles and is smoothed by separate launches."""
     wl = W.translocation(nx=160, ny=160, nz=128, membrane=(60, 67), radius=5.0, salt=0.005, n_beads=16,
                          precision=prec)
     assert wl.n_nodes >= 16384 * 152
@@ -237,7 +238,9 @@ def test_mg_split_solve_equals_single_launch(prec):
             assert all(it == 3 for it, _ in its_s)
         for k in ("n", "phi"):
             assert np.array_equal(fs[k], f1[k]), k
-        assert ls - l1 == sum(4 + 14 * it for it, _ in its_s)
+        level1 = (wl.nx // 2) * (wl.ny // 2) * (wl.nz // 2)
+        per_it = 14 + (8 if level1 > 1024 * 152 else 0)
+        assert ls - l1 == sum(4 + per_it * it for it, _ in its_s)
 
 
 def _fp32_source_allowance(wl, f, rho_o, q_beads):
