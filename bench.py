@@ -40,13 +40,14 @@ FALLBACK_HBM_GBS = 6800.0
 # keyed by kernel and workload, each valid only while the source files it was
 # taken on are unchanged
 PROFILED = {
-    # (kernel, workload): (sha256 prefix of its source files, dram read + write bytes per launch)
-    ("lb_fused_kernel", "pore_64x64x128_r4_N32"): ("64c6980a96cc13dc", 119372032 + 65814272),
-    ("poisson_mg_kernel", "pore_64x64x128_r4_N32"): ("18df217dc0e82b21", 20447744 + 888320),
-    ("lb_fused_kernel", "pore_256x256x512_r8_N128"): ("64c6980a96cc13dc", 7823804928 + 7367143680),
-    ("poisson_mg_wide_kernel", "pore_256x256x512_r8_N128"): ("18df217dc0e82b21", 33757597440 + 12620104960),
-    ("lb_fused_kernel", "pore_128x128x256_r6_N64"): ("64c6980a96cc13dc", 978504960 + 877521408),
-    ("poisson_mg_wide_kernel", "pore_128x128x256_r6_N64"): ("18df217dc0e82b21", 1022712832 + 978288384),
+    # (kernel, workload): (sha256 prefix of its source files, dram read + write bytes per launch), from one
+    # ncu pass over the benchmark command (--graph-profiling graph; the split solve's figure is its start
+    # kernel plus its graph, for a 6.0-iteration solve)
+    ("lb_fused_kernel", "pore_256x256x512_r8_N128"): ("5cdb2b8298eba70c", 7824103381 + 7365439744),
+    ("multigrid_split_solve", "pore_256x256x512_r8_N128"): ("0e9ebb7da074a8db",
+                                                         674907107 + 696883569 + 29051280995 + 12443790165),
+    ("lb_fused_kernel", "pore_64x64x128_r4_N32"): ("5cdb2b8298eba70c", 119390582 + 63535832),
+    ("poisson_mg_kernel", "pore_64x64x128_r4_N32"): ("83191a6862e35346", 21422828 + 2023640),
 }
 KERNEL_SOURCES = {
     "lb_fused_kernel": ("ekl_kernels.cuh", "ekl_dev.cuh"),
@@ -162,7 +163,7 @@ def mg_bytes_per_solve(L):
 
 
 MG_SPLIT_NODES_PER_SM = 16384  # lattices at least this large per SM run the split solve
-MG_SPLIT_KERNELS_PER_ITER = 14  # launches per CG iteration of the split solve's graph
+MG_SPLIT_KERNELS_PER_ITER = 22  # launches per CG iteration of the split solve's graph (level 1 grid-wide)
 MG_SPLIT_KERNELS_PER_SOLVE = 5  # start, first true residual, init, final residual, report
 
 
@@ -551,6 +552,8 @@ def rooflines(W, wl, m, store):
     pois = {"kernel": pk, "bound": "hbm", "achieved": round(pa, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(pa / hbm, 4), "peak_kind": peak_kind, "traffic": profiled_traffic(pk, wl.name),
             "algorithmic_bytes_per_launch": int(pb), "avg_launch_ms": round(ph["poisson"], 5)}
+    if split and pois["traffic"] is not None:
+        pois["traffic_note"] = "ncu, one pass: the start kernel plus the solve's graph, for a 6.0-iteration solve"
     if split:
         pois["launches_per_solve"] = round(MG_SPLIT_KERNELS_PER_SOLVE + MG_SPLIT_KERNELS_PER_ITER * m["phase_iters"], 1)
         pois["unit_measured"] = ("the whole solve, timed with CUDA events on its stream: a start kernel and one graph "
