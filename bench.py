@@ -162,14 +162,18 @@ def mg_bytes_per_solve(L):
     return (12 + L) + 2 * (22 + L)
 
 
-MG_SPLIT_NODES_PER_SM = 16384  # lattices at least this large per SM run the split solve
-MG_SPLIT_KERNELS_PER_ITER = 22  # launches per CG iteration of the split solve's graph (level 1 grid-wide)
 MG_SPLIT_KERNELS_PER_SOLVE = 5  # start, first true residual, init, final residual, report
 
 
 def mg_split(W, wl, sms=152):
-    return (bool(wl.flags & W.FLAG_POISSON_MG) and not (wl.flags & W.FLAG_POISSON_MG_SINGLE)
-            and wl.n_nodes >= MG_SPLIT_NODES_PER_SM * sms)
+    return bool(wl.flags & W.FLAG_POISSON_MG) and not (wl.flags & W.FLAG_POISSON_MG_SINGLE)
+
+
+def mg_split_kernels_per_iter(wl, sms=152):
+    """Launches per CG iteration of the split solve: 14, plus 8 when level 1
+    is too large for shared-memory tiles (more than 1024 cells per block)."""
+    level1 = ((wl.nx + 1) // 2) * ((wl.ny + 1) // 2) * ((wl.nz + 1) // 2)
+    return 14 + (8 if level1 > 1024 * sms else 0)
 
 
 def mg_algorithmic_bytes(wl, iters, link_bytes=4):
@@ -538,7 +542,7 @@ def rooflines(W, wl, m, store):
     ph = m["phase"]
     split = mg and mg_split(W, wl, n_sms())
     if split:
-        pk = "multigrid_split_solve"
+        pk = "multigrid_split_solve"  # (a single handle; batches keep the cooperative launch)
         pb = mg_algorithmic_bytes(wl, m["phase_iters"], link_bytes=1)
     elif mg:
         pk = "poisson_mg_wide_kernel" if wl.n_nodes >= 152 * 16384 else "poisson_mg_kernel"
@@ -555,7 +559,8 @@ def rooflines(W, wl, m, store):
     if split and pois["traffic"] is not None:
         pois["traffic_note"] = "ncu, one pass: the start kernel plus the solve's graph, for a 6.0-iteration solve"
     if split:
-        pois["launches_per_solve"] = round(MG_SPLIT_KERNELS_PER_SOLVE + MG_SPLIT_KERNELS_PER_ITER * m["phase_iters"], 1)
+        pois["launches_per_solve"] = round(MG_SPLIT_KERNELS_PER_SOLVE + mg_split_kernels_per_iter(wl, n_sms())
+                                           * m["phase_iters"], 1)
         pois["unit_measured"] = ("the whole solve, timed with CUDA events on its stream: a start kernel and one graph "
                                  "launch (lattice passes one kernel each, the coarse levels of each V-cycle one "
                                  "cooperative kernel, the CG loop a conditional WHILE node); bytes and time per solve")

@@ -82,10 +82,11 @@ extern "C" {
  * EKL_POISSON_GLOBAL is set.  ekl_create fails with EKL_ERR_ARG when no
  * coarser level exists (a periodic extent that is not a multiple of 4). */
 #define EKL_POISSON_MG 16
-/* With EKL_POISSON_MG: always run the solve as one cooperative launch.  By
- * default a lattice of at least 16384 nodes per SM runs it split (every
- * lattice pass its own launch, the CG loop a CUDA graph with a conditional
- * WHILE node); both forms return the same potential bit for bit. */
+/* With EKL_POISSON_MG: run the solve as one cooperative launch.  By default
+ * a single handle runs it split (every lattice pass its own launch, the CG
+ * loop a CUDA graph with a conditional WHILE node, built at the first step);
+ * both forms return the same potential bit for bit.  Batches always use
+ * the cooperative launch (one per step for all replicas). */
 #define EKL_POISSON_MG_SINGLE 32
 
 #define EKL_BOND_FENE 0

@@ -142,6 +142,7 @@ struct Ctx {
     cudaGraphExec_t mgs_exec;
     int mgs_iter_kernels;    // kernels launched per CG iteration of the loop
     int mgs_l1;              // level 1 grid-wide: smoothed by separate launches in the loop
+    int mgs_threads;         // block size of its lattice launches (that of the single launch it matches)
 
     // learned warm start of the Poisson solve (ekl_net.cu)
     void *net;

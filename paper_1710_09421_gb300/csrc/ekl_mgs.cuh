@@ -1,19 +1,21 @@
-// The multigrid-preconditioned CG solve of ekl_mg.cuh in split form, for
-// lattices whose passes are bound by memory: every lattice-level pass is its
-// own launch, the coarse levels of each V-cycle are one cooperative launch,
-// and the CG loop runs on the device as a CUDA graph with a conditional WHILE
+// The multigrid-preconditioned CG solve of ekl_mg.cuh in split form: every
+// lattice-level pass is its own launch (level 1 too when it is grid-wide),
+// the remaining coarse levels of each V-cycle are one cooperative launch, and
+// the CG loop runs on the device as a CUDA graph with a conditional WHILE
 // node, so a step's solve needs no host round trip.
 //
 // Why split: inside the single cooperative launch every pass shares the
 // register budget of the whole solve (64 a thread at 1024 threads), and a
 // lattice pass cannot keep the loads of several nodes in flight; on its own
 // launch it can (MGS_U node pairs per thread and trip), and a lattice pass is
-// bound by memory latency at one pair.
+// bound by memory latency at one pair.  On small lattices a graph node also
+// costs less than a grid barrier.
 //
 // The passes, their thread-to-node maps and the block partials of every
-// reduction are those of the single-launch solve with the same grid
-// (nblk blocks of MGS_THREADS), and the partials are summed the same way, so
-// both forms return the same potential bit for bit.  The scalar recurrences
+// reduction are those of the single-launch solve with the same grid (nblk
+// blocks of the single launch's block size: 1024 threads on lattices of at
+// least MG_WIDE_NODES_PER_SM nodes per SM, else 512), and the partials are
+// summed the same way, so both forms return the same potential bit for bit.  The scalar recurrences
 // (beta, alpha, the convergence test, the restart from the true residual)
 // live in MgCtl in device memory: the lattice kernels read it, one-block
 // control kernels write it and set the loop's condition.
@@ -22,7 +24,7 @@
 
 namespace ekl {
 
-constexpr int MGS_THREADS = 1024;
+constexpr int MGS_THREADS = 1024;  // the largest block size of the split kernels
 constexpr int MGS_U = 4;   // node pairs per thread and trip in the lattice half sweeps
 constexpr int MGS_PQU = 1; // p/q pass node pairs per thread and trip
 constexpr int MGS_CU = 1;  // level-1 cells per thread and trip in its half sweeps

@@ -177,7 +177,7 @@ static inline MgArgs make_mg_args(const Ctx &c)
 template <typename PhiT> static cudaError_t mgs_build(Ctx &c, const MgArgs &m0, Grid3 g)
 {
     MgArgs m = m0;
-    const int nb = c.pois_blocks;
+    const int nb = c.pois_blocks, nt = c.mgs_threads;
     MgCtl *ctl = (MgCtl *)c.mgs_ctl;
     const PhiT *phi = (const PhiT *)c.phi, *b = (const PhiT *)c.b;
     PhiT *phiw = (PhiT *)c.phi;
@@ -199,7 +199,7 @@ template <typename PhiT> static cudaError_t mgs_build(Ctx &c, const MgArgs &m0, 
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&loop, G, 0, cudaGraphCondAssignDefault);
     if (e == cudaSuccess) {
         void *args[] = {&g, &m, &phi, &b, &ctl, &when0};
-        e = kernel_node(&nres0, nullptr, (const void *)mgs_residual_kernel<PhiT>, nb, MGS_THREADS, args);
+        e = kernel_node(&nres0, nullptr, (const void *)mgs_residual_kernel<PhiT>, nb, nt, args);
     }
     if (e == cudaSuccess) {
         void *args[] = {&m, &ctl, &nblk, &loop, &c.pois_iters, &c.pois_res};
@@ -220,15 +220,15 @@ template <typename PhiT> static cudaError_t mgs_build(Ctx &c, const MgArgs &m0, 
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-        for (int s = 1; s < 2 * MG_NU; s++) mgs_half_kernel<false, false><<<nb, MGS_THREADS, 0, cs>>>(g, m, s & 1);
-        if (m.cta_from > 1) mgs_restrict_kernel<true><<<nb, MGS_THREADS, 0, cs>>>(g, m);
-        else mgs_restrict_kernel<false><<<nb, MGS_THREADS, 0, cs>>>(g, m);
+        for (int s = 1; s < 2 * MG_NU; s++) mgs_half_kernel<false, false><<<nb, nt, 0, cs>>>(g, m, s & 1);
+        if (m.cta_from > 1) mgs_restrict_kernel<true><<<nb, nt, 0, cs>>>(g, m);
+        else mgs_restrict_kernel<false><<<nb, nt, 0, cs>>>(g, m);
         // level 1 smoothed and restricted by separate launches when grid-wide
         const int from = c.mgs_l1 ? 2 : 1;
         if (c.mgs_l1) {
-            for (int s = 1; s < 2 * MG_NU_COARSE; s++) mgs_chalf_kernel<false><<<nb, MGS_THREADS, 0, cs>>>(m, s & 1);
-            if (m.cta_from > 2) mgs_crestrict_kernel<true><<<nb, MGS_THREADS, 0, cs>>>(m);
-            else mgs_crestrict_kernel<false><<<nb, MGS_THREADS, 0, cs>>>(m);
+            for (int s = 1; s < 2 * MG_NU_COARSE; s++) mgs_chalf_kernel<false><<<nb, nt, 0, cs>>>(m, s & 1);
+            if (m.cta_from > 2) mgs_crestrict_kernel<true><<<nb, nt, 0, cs>>>(m);
+            else mgs_crestrict_kernel<false><<<nb, nt, 0, cs>>>(m);
         }
         cudaMemsetAsync(c.barrier, 0, 4 * sizeof(unsigned), cs);
         cudaLaunchConfig_t cfg = {};
@@ -236,27 +236,27 @@ template <typename PhiT> static cudaError_t mgs_build(Ctx &c, const MgArgs &m0, 
         coop[0].id = cudaLaunchAttributeCooperative;
         coop[0].val.cooperative = 1;
         cfg.gridDim = dim3(nb);
-        cfg.blockDim = dim3(MGS_THREADS);
+        cfg.blockDim = dim3(nt);
         cfg.dynamicSmemBytes = c.mg_smem;
         cfg.stream = cs;
         cfg.attrs = coop;
         cfg.numAttrs = 1;
         cudaError_t el = cudaLaunchKernelEx(&cfg, mgs_coarse_kernel, m, c.barrier, c.status, from);
         if (c.mgs_l1) {
-            mgs_chalf_kernel<true><<<nb, MGS_THREADS, 0, cs>>>(m, 1);
+            mgs_chalf_kernel<true><<<nb, nt, 0, cs>>>(m, 1);
             for (int s = 1; s < 2 * MG_NU_COARSE; s++)
-                mgs_chalf_kernel<false><<<nb, MGS_THREADS, 0, cs>>>(m, (s & 1) ^ 1);
+                mgs_chalf_kernel<false><<<nb, nt, 0, cs>>>(m, (s & 1) ^ 1);
         }
-        mgs_half_kernel<false, true><<<nb, MGS_THREADS, 0, cs>>>(g, m, 1);
+        mgs_half_kernel<false, true><<<nb, nt, 0, cs>>>(g, m, 1);
         for (int s = 1; s < 2 * MG_NU; s++) {
             const int col = (s & 1) ^ 1;
-            if (s == 2 * MG_NU - 1) mgs_half_kernel<true, false><<<nb, MGS_THREADS, 0, cs>>>(g, m, col);
-            else mgs_half_kernel<false, false><<<nb, MGS_THREADS, 0, cs>>>(g, m, col);
+            if (s == 2 * MG_NU - 1) mgs_half_kernel<true, false><<<nb, nt, 0, cs>>>(g, m, col);
+            else mgs_half_kernel<false, false><<<nb, nt, 0, cs>>>(g, m, col);
         }
-        mgs_pq_kernel<<<nb, MGS_THREADS, 0, cs>>>(g, m, ctl);
-        mgs_update_kernel<PhiT><<<nb, MGS_THREADS, 0, cs>>>(g, m, phiw, ctl);
+        mgs_pq_kernel<<<nb, nt, 0, cs>>>(g, m, ctl);
+        mgs_update_kernel<PhiT><<<nb, nt, 0, cs>>>(g, m, phiw, ctl);
         mgs_mid_kernel<<<1, 32, 0, cs>>>(m, ctl, nb);
-        mgs_residual_kernel<PhiT><<<nb, MGS_THREADS, 0, cs>>>(g, m, phi, b, ctl, 1);
+        mgs_residual_kernel<PhiT><<<nb, nt, 0, cs>>>(g, m, phi, b, ctl, 1);
         mgs_end_kernel<<<1, 32, 0, cs>>>(m, ctl, nb, loop, c.status);
         cudaError_t ek = cudaGetLastError();
         cudaError_t ec = cudaStreamEndCapture(cs, &body);
@@ -265,7 +265,7 @@ template <typename PhiT> static cudaError_t mgs_build(Ctx &c, const MgArgs &m0, 
     if (cs) cudaStreamDestroy(cs);
     if (e == cudaSuccess) {
         void *args[] = {&g, &m, &phi, &b, &ctl, &when2};
-        e = kernel_node(&nres2, &nloop, (const void *)mgs_residual_kernel<PhiT>, nb, MGS_THREADS, args);
+        e = kernel_node(&nres2, &nloop, (const void *)mgs_residual_kernel<PhiT>, nb, nt, args);
     }
     if (e == cudaSuccess) {
         void *args[] = {&m, &ctl, &nblk, &c.pois_iters, &c.pois_total, &c.pois_res, &c.status};
@@ -347,7 +347,7 @@ template <typename S, typename R, typename PhiT, bool DEV> int steps_impl(Ctx &c
         cudaMemsetAsync(c.barrier, 0, 4 * sizeof(unsigned), c.stream);
         if (c.mg && c.mg_split) {
             MgArgs m = make_mg_args(c);
-            mgs_start_kernel<S, R, PhiT><<<c.pois_blocks, MGS_THREADS, 0, c.stream>>>(a, m, (MgCtl *)c.mgs_ctl);
+            mgs_start_kernel<S, R, PhiT><<<c.pois_blocks, c.mgs_threads, 0, c.stream>>>(a, m, (MgCtl *)c.mgs_ctl);
             c.launches++;
             if (!c.mgs_exec && mgs_build<PhiT>(c, m, a.g) != cudaSuccess) return EKL_ERR_CUDA;
             if (cudaGraphLaunch(c.mgs_exec, c.stream) != cudaSuccess) return EKL_ERR_CUDA;

@@ -34,7 +34,7 @@ FLAG_GAMMA_LITERAL = 1 << 1    # gamma^alpha = xi for every species (literal Sec
 FLAG_NO_BEAD_NOISE = 1 << 2    # switch off the Langevin noise on the beads
 FLAG_POISSON_GLOBAL = 1 << 3   # CUDA library only: no shared-memory Poisson tiles
 FLAG_POISSON_MG = 1 << 4       # CUDA library only: multigrid-preconditioned CG Poisson solver
-FLAG_POISSON_MG_SINGLE = 1 << 5  # CUDA library only: the multigrid solve as one cooperative launch
+FLAG_POISSON_MG_SINGLE = 1 << 5  # CUDA library only: the multigrid solve as one cooperative launch (not split)
 
 BOND_FENE = 0
 BOND_HARMONIC = 1

@@ -243,6 +243,37 @@ def test_mg_split_solve_equals_single_launch(prec):
         assert ls - l1 == sum(4 + per_it * it for it, _ in its_s)
 
 
+@pytest.mark.parametrize("case", ["pore_f32", "closed_odd_f64"])
+def test_mg_split_solve_equals_single_launch_small(case):
+    """Small lattices run the split solve too, with the 512-thread blocks of
+    the single launch they match: a 32x32x40 pore (coarse levels in tiles and
+    block 0's shared memory) and a closed box with odd extents on every
+    level give the same potentials, densities and iteration counts bit for
+    bit in both forms."""
+    if case == "closed_odd_f64":
+        solid = np.zeros((41, 37, 45), np.uint8)
+        solid[15:25, 10:20, 12:30] = 1
+        wl = box(45, 37, 41, periodic=(0, 0, 0), solid=solid, E_app=(1e-3, 2e-3, 0.0),
+                 n_init=W.ion_densities(solid, 0.01, 1.0, 0.0, 1e-3, 5), poisson_tol=1e-11, flags=MG)
+    else:
+        wl = W.small_pore(nx=32, ny=32, nz=40, membrane=(18, 22), radius=4.0, n_beads=6,
+                          precision="f32").replace(flags=MG)
+    out = []
+    for flags in (MG, MG | W.FLAG_POISSON_MG_SINGLE):
+        sim = E.Simulation(wl.replace(flags=flags))
+        its = []
+        for _ in range(4):
+            assert sim.step(1) >= 0
+            st = sim.stats()
+            its.append((st["poisson_iters"], st["poisson_res"]))
+        out.append((sim.fields(("n", "phi")), its))
+        sim.close()
+    (fs, its_s), (f1, its_1) = out
+    assert its_s == its_1
+    for k in ("n", "phi"):
+        assert np.array_equal(fs[k], f1[k]), k
+
+
 def _fp32_source_allowance(wl, f, rho_o, q_beads):
     """A priori bound, relative to ||b||, of how far the FP32 path's Poisson
     source may sit from the oracle's FP64 source formed from the same
