@@ -254,6 +254,8 @@ typedef struct ekl_batch ekl_batch;
 /* nrep parameter blocks (params[r]); errors as ekl_create, plus
  * EKL_ERR_ARG when nrep exceeds the number of co-resident Poisson blocks. */
 int ekl_batch_create(int32_t nrep, const ekl_params *params, void *stream, ekl_batch **out);
+/* the same call under the name the batch interface is also known by */
+int ekl_create_batch(int32_t nrep, const ekl_params *params, void *stream, ekl_batch **out);
 
 /* beads of replica rep, as ekl_set_beads */
 int ekl_batch_set_beads(ekl_batch *b, int32_t rep, int32_t n, const double *R, const double *V,

@@ -1433,6 +1433,11 @@ int ekl_batch_create(int32_t nrep, const ekl_params *params, void *stream, ekl_b
     return EKL_OK;
 }
 
+int ekl_create_batch(int32_t nrep, const ekl_params *params, void *stream, ekl_batch **out)
+{
+    return ekl_batch_create(nrep, params, stream, out);
+}
+
 int ekl_batch_set_beads(ekl_batch *bh, int32_t rep, int32_t n, const double *R, const double *V, const double *q,
                         const int32_t *chain)
 {

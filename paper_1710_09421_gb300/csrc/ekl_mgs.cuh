@@ -32,6 +32,12 @@ constexpr int MGS_CU = 1;  // level-1 cells per thread and trip in its half swee
 // block-partial slots (nblk doubles each) in MgArgs::part
 enum { MGS_BB = 0, MGS_RES = 1, MGS_RZ = 2, MGS_PQ = 3, MGS_RR = 4, MGS_SLOTS = 5 };
 
+// Programmatic dependent launch: the loop's lattice kernels are launched so
+// that they may start while the kernel before them drains; each waits here,
+// before touching anything that kernel wrote, until it has completed and its
+// writes are visible (a no-op when launched without the attribute).
+__device__ __forceinline__ void mgs_wait_previous() { cudaGridDependencySynchronize(); }
+
 __device__ __forceinline__ double *mgs_slot(const MgArgs &m, int slot, int nblk) { return m.part + (size_t)slot * nblk; }
 
 // Start of the solve: guess, source and its block partials of b^2; block 0
@@ -39,6 +45,7 @@ __device__ __forceinline__ double *mgs_slot(const MgArgs &m, int slot, int nblk)
 template <typename S, typename R, typename PhiT>
 __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_start_kernel(StepArgs<S, R, PhiT> a, MgArgs m, MgCtl *ctl)
 {
+    mgs_wait_previous();
     __shared__ double sh[MGS_THREADS / 32];
     __shared__ double bc[1];
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
@@ -57,6 +64,7 @@ template <typename PhiT>
 __global__ void __launch_bounds__(MGS_THREADS, 1)
     mgs_residual_kernel(Grid3 g, MgArgs m, const PhiT *phi, const PhiT *b, const MgCtl *ctl, int when)
 {
+    mgs_wait_previous();
     __shared__ double sh[MGS_THREADS / 32];
     if (when == 1 && !ctl->need_true) return;
     if (when == 2 && (ctl->current || ctl->skip)) return;
@@ -69,6 +77,7 @@ __global__ void __launch_bounds__(MGS_THREADS, 1)
 static __global__ void mgs_init_kernel(MgArgs m, MgCtl *ctl, int nblk, cudaGraphConditionalHandle loop,
                                        int *pois_iters, double *pois_res)
 {
+    mgs_wait_previous();
     __shared__ double bc[1];
     const double bb = sum_partials(mgs_slot(m, MGS_BB, nblk), nblk, bc);
     const double rr = sum_partials(mgs_slot(m, MGS_RES, nblk), nblk, bc);
@@ -103,6 +112,7 @@ static __global__ void mgs_init_kernel(MgArgs m, MgCtl *ctl, int nblk, cudaGraph
 // a quarter of the tolerance, or the iteration limit is reached).
 static __global__ void mgs_mid_kernel(MgArgs m, MgCtl *ctl, int nblk)
 {
+    mgs_wait_previous();
     __shared__ double bc[1];
     const double rz = sum_partials(mgs_slot(m, MGS_RZ, nblk), nblk, bc);
     const double pq = sum_partials(mgs_slot(m, MGS_PQ, nblk), nblk, bc);
@@ -130,6 +140,7 @@ static __global__ void mgs_mid_kernel(MgArgs m, MgCtl *ctl, int nblk)
 static __global__ void mgs_end_kernel(MgArgs m, MgCtl *ctl, int nblk, cudaGraphConditionalHandle loop,
                                       const int *status)
 {
+    mgs_wait_previous();
     __shared__ double bc[1];
     const double rt = sum_partials(mgs_slot(m, MGS_RES, nblk), nblk, bc);
     if (threadIdx.x != 0) return;
@@ -154,6 +165,7 @@ static __global__ void mgs_end_kernel(MgArgs m, MgCtl *ctl, int nblk, cudaGraphC
 static __global__ void mgs_report_kernel(MgArgs m, const MgCtl *ctl, int nblk, int *pois_iters,
                                          long long *pois_total, double *pois_res, int *status)
 {
+    mgs_wait_previous();
     __shared__ double bc[1];
     const double rt = sum_partials(mgs_slot(m, MGS_RES, nblk), nblk, bc);
     if (threadIdx.x != 0) return;
@@ -172,6 +184,7 @@ static __global__ void mgs_report_kernel(MgArgs m, const MgCtl *ctl, int nblk, i
 template <bool RZ, bool PRO>
 __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_half_kernel(Grid3 g, MgArgs m, int c)
 {
+    mgs_wait_previous();
     __shared__ double sh[MGS_THREADS / 32];
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
     float rz = 0.f;
@@ -184,6 +197,7 @@ __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_half_kernel(Grid3 g, MgArg
 
 template <bool FIRST> __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_restrict_kernel(Grid3 g, MgArgs m)
 {
+    mgs_wait_previous();
     fine_restrict_cells<FIRST>(g, m.link, m.r, m.z, m.lev[1], (int)(blockIdx.x * blockDim.x + threadIdx.x),
                          (int)(gridDim.x * blockDim.x));
 }
@@ -192,12 +206,14 @@ template <bool FIRST> __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_rest
 // red-black half sweep (PRO: prolongating from level 2) ...
 template <bool PRO> __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_chalf_kernel(MgArgs m, int c)
 {
+    mgs_wait_previous();
     coarse_half<false, PRO, MGS_CU>(m.lev[1], m.lev[2], c, (int)(blockIdx.x * blockDim.x + threadIdx.x),
                             (int)(gridDim.x * blockDim.x));
 }
 // ... and its restriction to level 2 (FIRST: level 2 is grid-wide or tiled)
 template <bool FIRST> __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_crestrict_kernel(MgArgs m)
 {
+    mgs_wait_previous();
     coarse_restrict<false, FIRST>(m.lev[1], m.lev[2], (int)(blockIdx.x * blockDim.x + threadIdx.x),
                                   (int)(gridDim.x * blockDim.x));
 }
@@ -207,6 +223,7 @@ template <bool FIRST> __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_cres
 static __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_coarse_kernel(MgArgs m, unsigned *bar, int *status,
                                                                           int from)
 {
+    mgs_wait_previous();
     __shared__ double sh[MGS_THREADS / 32];
     __shared__ double bc[1];
     extern __shared__ float mg_sm[];
@@ -220,6 +237,7 @@ static __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_coarse_kernel(MgArg
 // p = z + beta p_old, q = A p with the block partials of p.q
 static __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_pq_kernel(Grid3 g, MgArgs m, const MgCtl *ctl)
 {
+    mgs_wait_previous();
     __shared__ double sh[MGS_THREADS / 32];
     __shared__ double bc[1];
     const int nblk = gridDim.x;
@@ -241,6 +259,7 @@ static __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_pq_kernel(Grid3 g, 
 template <typename PhiT>
 __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_update_kernel(Grid3 g, MgArgs m, PhiT *phi, const MgCtl *ctl)
 {
+    mgs_wait_previous();
     __shared__ double sh[MGS_THREADS / 32];
     __shared__ double bc[1];
     const int nblk = gridDim.x;

@@ -174,7 +174,7 @@ static inline MgArgs make_mg_args(const Ctx &c)
 //   -> true residual when phi moved after the last one -> report.
 // Every argument is fixed for the life of the handle; the step's tolerance
 // and iteration limits reach the graph through MgCtl.
-template <typename PhiT> static cudaError_t mgs_build(Ctx &c, const MgArgs &m0, Grid3 g)
+template <typename PhiT> static cudaError_t mgs_build(Ctx &c, const MgArgs &m0, Grid3 g, bool pdl)
 {
     MgArgs m = m0;
     const int nb = c.pois_blocks, nt = c.mgs_threads;
@@ -220,15 +220,33 @@ template <typename PhiT> static cudaError_t mgs_build(Ctx &c, const MgArgs &m0, 
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-        for (int s = 1; s < 2 * MG_NU; s++) mgs_half_kernel<false, false><<<nb, nt, 0, cs>>>(g, m, s & 1);
-        if (m.cta_from > 1) mgs_restrict_kernel<true><<<nb, nt, 0, cs>>>(g, m);
-        else mgs_restrict_kernel<false><<<nb, nt, 0, cs>>>(g, m);
+        // every lattice kernel but the first of the body and the one after
+        // the cooperative launch may start while its predecessor drains
+        // (programmatic dependent launch; each waits for its predecessor
+        // before touching its output)
+        cudaLaunchAttribute dep[1];
+        dep[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        dep[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaError_t el = cudaSuccess;
+        auto go = [&](bool overlap, unsigned grid, unsigned block, auto kern, auto... args) {
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3(grid);
+            lc.blockDim = dim3(block);
+            lc.stream = cs;
+            lc.attrs = dep;
+            lc.numAttrs = (overlap && pdl) ? 1 : 0;
+            const cudaError_t r = cudaLaunchKernelEx(&lc, kern, args...);
+            if (el == cudaSuccess) el = r;
+        };
+        for (int s = 1; s < 2 * MG_NU; s++) go(s > 1, nb, nt, mgs_half_kernel<false, false>, g, m, s & 1);
+        if (m.cta_from > 1) go(true, nb, nt, mgs_restrict_kernel<true>, g, m);
+        else go(true, nb, nt, mgs_restrict_kernel<false>, g, m);
         // level 1 smoothed and restricted by separate launches when grid-wide
         const int from = c.mgs_l1 ? 2 : 1;
         if (c.mgs_l1) {
-            for (int s = 1; s < 2 * MG_NU_COARSE; s++) mgs_chalf_kernel<false><<<nb, nt, 0, cs>>>(m, s & 1);
-            if (m.cta_from > 2) mgs_crestrict_kernel<true><<<nb, nt, 0, cs>>>(m);
-            else mgs_crestrict_kernel<false><<<nb, nt, 0, cs>>>(m);
+            for (int s = 1; s < 2 * MG_NU_COARSE; s++) go(true, nb, nt, mgs_chalf_kernel<false>, m, s & 1);
+            if (m.cta_from > 2) go(true, nb, nt, mgs_crestrict_kernel<true>, m);
+            else go(true, nb, nt, mgs_crestrict_kernel<false>, m);
         }
         cudaMemsetAsync(c.barrier, 0, 4 * sizeof(unsigned), cs);
         cudaLaunchConfig_t cfg = {};
@@ -241,23 +259,23 @@ template <typename PhiT> static cudaError_t mgs_build(Ctx &c, const MgArgs &m0, 
         cfg.stream = cs;
         cfg.attrs = coop;
         cfg.numAttrs = 1;
-        cudaError_t el = cudaLaunchKernelEx(&cfg, mgs_coarse_kernel, m, c.barrier, c.status, from);
+        const cudaError_t ecoop = cudaLaunchKernelEx(&cfg, mgs_coarse_kernel, m, c.barrier, c.status, from);
+        if (el == cudaSuccess) el = ecoop;
         if (c.mgs_l1) {
-            mgs_chalf_kernel<true><<<nb, nt, 0, cs>>>(m, 1);
-            for (int s = 1; s < 2 * MG_NU_COARSE; s++)
-                mgs_chalf_kernel<false><<<nb, nt, 0, cs>>>(m, (s & 1) ^ 1);
+            go(false, nb, nt, mgs_chalf_kernel<true>, m, 1);
+            for (int s = 1; s < 2 * MG_NU_COARSE; s++) go(true, nb, nt, mgs_chalf_kernel<false>, m, (s & 1) ^ 1);
         }
-        mgs_half_kernel<false, true><<<nb, nt, 0, cs>>>(g, m, 1);
+        go(c.mgs_l1 != 0, nb, nt, mgs_half_kernel<false, true>, g, m, 1);
         for (int s = 1; s < 2 * MG_NU; s++) {
             const int col = (s & 1) ^ 1;
-            if (s == 2 * MG_NU - 1) mgs_half_kernel<true, false><<<nb, nt, 0, cs>>>(g, m, col);
-            else mgs_half_kernel<false, false><<<nb, nt, 0, cs>>>(g, m, col);
+            if (s == 2 * MG_NU - 1) go(true, nb, nt, mgs_half_kernel<true, false>, g, m, col);
+            else go(true, nb, nt, mgs_half_kernel<false, false>, g, m, col);
         }
-        mgs_pq_kernel<<<nb, nt, 0, cs>>>(g, m, ctl);
-        mgs_update_kernel<PhiT><<<nb, nt, 0, cs>>>(g, m, phiw, ctl);
-        mgs_mid_kernel<<<1, 32, 0, cs>>>(m, ctl, nb);
-        mgs_residual_kernel<PhiT><<<nb, nt, 0, cs>>>(g, m, phi, b, ctl, 1);
-        mgs_end_kernel<<<1, 32, 0, cs>>>(m, ctl, nb, loop, c.status);
+        go(true, nb, nt, mgs_pq_kernel, g, m, (const MgCtl *)ctl);
+        go(true, nb, nt, mgs_update_kernel<PhiT>, g, m, phiw, (const MgCtl *)ctl);
+        go(true, 1, 32, mgs_mid_kernel, m, ctl, nb);
+        go(true, nb, nt, mgs_residual_kernel<PhiT>, g, m, phi, b, (const MgCtl *)ctl, 1);
+        go(true, 1, 32, mgs_end_kernel, m, ctl, nb, loop, (const int *)c.status);
         cudaError_t ek = cudaGetLastError();
         cudaError_t ec = cudaStreamEndCapture(cs, &body);
         e = el != cudaSuccess ? el : ek != cudaSuccess ? ek : ec;
@@ -349,7 +367,11 @@ template <typename S, typename R, typename PhiT, bool DEV> int steps_impl(Ctx &c
             MgArgs m = make_mg_args(c);
             mgs_start_kernel<S, R, PhiT><<<c.pois_blocks, c.mgs_threads, 0, c.stream>>>(a, m, (MgCtl *)c.mgs_ctl);
             c.launches++;
-            if (!c.mgs_exec && mgs_build<PhiT>(c, m, a.g) != cudaSuccess) return EKL_ERR_CUDA;
+            // the graph with programmatic dependent launches, else without
+            if (!c.mgs_exec && mgs_build<PhiT>(c, m, a.g, true) != cudaSuccess) {
+                cudaGetLastError();
+                if (mgs_build<PhiT>(c, m, a.g, false) != cudaSuccess) return EKL_ERR_CUDA;
+            }
             if (cudaGraphLaunch(c.mgs_exec, c.stream) != cudaSuccess) return EKL_ERR_CUDA;
             c.launches += 4;  // the loop's kernels are counted from its iterations
             c.mg_have_prev = 1;
