@@ -420,11 +420,11 @@ __device__ SrcMean source_mean(const StepArgs<S, R, PhiT> &a, double *bc)
     // S / n = mean_lo + frac with 0 <= frac < 1, and C = c4 frac split into
     // integer and fraction
     if constexpr (!(((PhiT)0.5) != 0)) {
-        const long long S = a.charge_tot ? __ldcg(a.charge_tot_q) : sum_partials_ll(a.part_charge_q, a.nblocks_charge);
+        const long long Sq = a.charge_tot ? __ldcg(a.charge_tot_q) : sum_partials_ll(a.part_charge_q, a.nblocks_charge);
         const long long n = (long long)nfl;
         if (n > 0) {
-            long long mean_lo = S / n;
-            long long rem = S - mean_lo * n;
+            long long mean_lo = Sq / n;
+            long long rem = Sq - mean_lo * n;
             if (rem < 0) {
                 mean_lo -= 1;
                 rem += n;
