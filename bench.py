@@ -42,12 +42,13 @@ FALLBACK_HBM_GBS = 6800.0
 PROFILED = {
     # (kernel, workload): (sha256 prefix of its source files, dram read + write bytes per launch), from one
     # ncu pass over the benchmark command (--graph-profiling graph; the split solve's figure is its start
-    # kernel plus its graph, for a 6.0-iteration solve)
-    ("lb_fused_kernel", "pore_256x256x512_r8_N128"): ("5cdb2b8298eba70c", 7824103381 + 7365439744),
-    ("multigrid_split_solve", "pore_256x256x512_r8_N128"): ("0e9ebb7da074a8db",
-                                                         674907107 + 696883569 + 29051280995 + 12443790165),
-    ("lb_fused_kernel", "pore_64x64x128_r4_N32"): ("5cdb2b8298eba70c", 119390582 + 63535832),
-    ("poisson_mg_kernel", "pore_64x64x128_r4_N32"): ("83191a6862e35346", 21422828 + 2023640),
+    # kernel plus its graph, the mean over the capture's solves: 6.4 CG iterations on 256x256x512, 5.2 on
+    # 64x64x128)
+    ("lb_fused_kernel", "pore_256x256x512_r8_N128"): ("3748fc75630d6ab3", 7824183011 + 7365414755),
+    ("multigrid_split_solve", "pore_256x256x512_r8_N128"): ("5732002be10a0027",
+                                                         674898887 + 696782876 + 30350284629 + 13197447296),
+    ("lb_fused_kernel", "pore_64x64x128_r4_N32"): ("3748fc75630d6ab3", 119387372 + 63406887),
+    ("multigrid_split_solve", "pore_64x64x128_r4_N32"): ("5732002be10a0027", 10720177 + 0 + 17262237 + 57698),
 }
 KERNEL_SOURCES = {
     "lb_fused_kernel": ("ekl_kernels.cuh", "ekl_dev.cuh"),
@@ -557,7 +558,8 @@ def rooflines(W, wl, m, store):
             "frac": round(pa / hbm, 4), "peak_kind": peak_kind, "traffic": profiled_traffic(pk, wl.name),
             "algorithmic_bytes_per_launch": int(pb), "avg_launch_ms": round(ph["poisson"], 5)}
     if split and pois["traffic"] is not None:
-        pois["traffic_note"] = "ncu, one pass: the start kernel plus the solve's graph, for a 6.0-iteration solve"
+        pois["traffic_note"] = ("ncu, one pass: the start kernel plus the solve's graph, mean over the capture's "
+                                "solves (6.4 CG iterations on 256x256x512, 5.2 on 64x64x128)")
     if split:
         pois["launches_per_solve"] = round(MG_SPLIT_KERNELS_PER_SOLVE + mg_split_kernels_per_iter(wl, n_sms())
                                            * m["phase_iters"], 1)
