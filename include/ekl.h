@@ -174,7 +174,12 @@ int ekl_step(ekl_handle *h, int32_t nsteps);
  * ekl_step / ekl_get_stats). */
 int ekl_step_async(ekl_handle *h, int32_t nsteps);
 
-/* Copy fields to host memory (any pointer may be NULL):
+/* Copy fields to host memory (any pointer may be NULL).  Arrays of 8 MB and
+ * more move through two 64 MB pinned staging buffers that the library
+ * allocates at the first such transfer and keeps for the life of the
+ * process (the same for ekl_create's initial densities and for
+ * ekl_get_state / ekl_set_state); without pinned memory they are plain
+ * copies.
  *   n_out[3][N]     species densities n^a of the current populations (Eq. 15)
  *   j_out[3][3][N]  bare currents sum_p c_p f_p (Eq. 16)
  *   phi_out[N]      potential of the last step, fluid mean removed, 0 on walls

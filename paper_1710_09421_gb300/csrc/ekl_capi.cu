@@ -345,11 +345,12 @@ static void par_memcpy(void *dst, const void *src, size_t n)
 static cudaError_t staged_copy(cudaStream_t stream, int device, void *dst, const void *src, size_t bytes,
                                bool to_host)
 {
-    if (bytes < ((size_t)8 << 20)) {  // small: one plain copy
+    auto plain = [&]() {  // one pageable copy
         cudaError_t e = cudaMemcpyAsync(dst, src, bytes, to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice,
                                         stream);
         return e == cudaSuccess ? cudaStreamSynchronize(stream) : e;
-    }
+    };
+    if (bytes < ((size_t)8 << 20)) return plain();
     std::lock_guard<std::mutex> lock(g_stage_lock);
     cudaError_t e = cudaSuccess;
     if (g_stage_dev != device) {
@@ -359,11 +360,23 @@ static cudaError_t staged_copy(cudaStream_t stream, int device, void *dst, const
                 cudaEventDestroy(g_stage_ev[b]);
                 g_stage[b] = nullptr;
             }
+        g_stage_dev = -1;
+        bool ev_made[2] = {false, false};
         for (int b = 0; b < 2 && e == cudaSuccess; b++) {
             e = cudaMallocHost(&g_stage[b], STAGE_BYTES);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g_stage_ev[b], cudaEventDisableTiming);
+            if (e != cudaSuccess) g_stage[b] = nullptr;
+            else if ((e = cudaEventCreateWithFlags(&g_stage_ev[b], cudaEventDisableTiming)) == cudaSuccess)
+                ev_made[b] = true;
         }
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) {  // no pinned memory to be had: the plain copy
+            for (int b = 0; b < 2; b++) {
+                if (g_stage[b]) cudaFreeHost(g_stage[b]);
+                if (ev_made[b]) cudaEventDestroy(g_stage_ev[b]);
+                g_stage[b] = nullptr;
+            }
+            cudaGetLastError();
+            return plain();
+        }
         g_stage_dev = device;
     }
     const size_t nch = (bytes + STAGE_BYTES - 1) / STAGE_BYTES;
