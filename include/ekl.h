@@ -83,10 +83,12 @@ extern "C" {
  * coarser level exists (a periodic extent that is not a multiple of 4). */
 #define EKL_POISSON_MG 16
 /* With EKL_POISSON_MG: run the solve as one cooperative launch.  By default
- * a single handle runs it split (every lattice pass its own launch, the CG
- * loop a CUDA graph with a conditional WHILE node, built at the first step);
- * both forms return the same potential bit for bit.  Batches always use
- * the cooperative launch (one per step for all replicas). */
+ * the solve runs split (every lattice pass its own launch, the CG loop a
+ * CUDA graph with a conditional WHILE node, built at the first step); both
+ * forms return the same potential bit for bit.  A batch takes the flag of
+ * replica 0: split, each launch serves every replica and the loop runs
+ * while any replica is iterating; cooperative, one launch per step for all
+ * replicas. */
 #define EKL_POISSON_MG_SINGLE 32
 
 #define EKL_BOND_FENE 0
@@ -282,7 +284,9 @@ ekl_handle *ekl_batch_replica(ekl_batch *b, int32_t rep);
  * tunes the weighting only. */
 int ekl_batch_autotune(ekl_batch *b, int32_t trial_steps, int32_t *choice_out);
 
-/* kernels launched by the batch itself since creation */
+/* kernels launched by the batch itself since creation (a split multigrid
+ * solve launches its loop from the device: this then reads the device's
+ * loop count and waits for the batch's stream; -1 on a CUDA error) */
 int64_t ekl_batch_launches(ekl_batch *b);
 
 void ekl_batch_destroy(ekl_batch *b);

@@ -1431,6 +1431,13 @@ void batch_release(Batch &B)
     dev_free(c0, B.d_mgargs, 0);
     dev_free(c0, B.d_ctot, 0);
     dev_free(c0, B.mg_bars, 0);
+    if (B.mgs_exec) cudaGraphExecDestroy(B.mgs_exec);
+    if (B.mgs_graph) cudaGraphDestroy(B.mgs_graph);
+    B.mgs_exec = nullptr;
+    B.mgs_graph = nullptr;
+    dev_free(c0, B.d_ctl, 0);
+    dev_free(c0, B.d_grids, 0);
+    dev_free(c0, B.d_loops, 0);
 }
 
 }  // namespace
@@ -1514,6 +1521,11 @@ int ekl_batch_create(int32_t nrep, const ekl_params *params, void *stream, ekl_b
             for (int r = 0; r < nrep; r++) B.mg_smem = std::max(B.mg_smem, B.reps[r]->mg_smem);
             B.d_mgargs = A(nrep * sizeof(MgArgs));
             B.mg_bars = (unsigned *)A(4 * sizeof(unsigned) * (size_t)nrep);
+            B.mgs_split = !(params[0].flags & EKL_POISSON_MG_SINGLE);
+            B.d_ctl = A(nrep * sizeof(MgCtl));
+            B.d_grids = A(nrep * sizeof(Grid3));
+            B.d_loops = (int *)A(sizeof(int));
+            if (ok) cudaMemsetAsync(B.d_loops, 0, sizeof(int), B.stream);
             if (!ok) rc = fail(EKL_ERR_ALLOC, "device allocation failed");
             else if (ops(B.prec).mg_batch_blocks(B.mg_smem) < 1)
                 rc = fail(EKL_ERR_CUDA, "batched multigrid kernel cannot be resident");
@@ -1618,7 +1630,19 @@ int ekl_batch_autotune(ekl_batch *bh, int32_t trial_steps, int32_t *choice_out)
     return EKL_OK;
 }
 
-int64_t ekl_batch_launches(ekl_batch *bh) { return bh ? bh->b.launches : 0; }
+int64_t ekl_batch_launches(ekl_batch *bh)
+{
+    if (!bh) return 0;
+    Batch &B = bh->b;
+    if (!B.mgs_exec) return B.launches;
+    // a split solve launches its loop's kernels from the device
+    DeviceScope dscope(B.reps[0]->device);
+    int loops = 0;
+    if (!dscope.ok() || cudaMemcpyAsync(&loops, B.d_loops, sizeof(int), cudaMemcpyDeviceToHost, B.stream) != cudaSuccess ||
+        cudaStreamSynchronize(B.stream) != cudaSuccess)
+        return -1;
+    return B.launches + (int64_t)B.mgs_iter_kernels * loops;
+}
 
 void ekl_batch_destroy(ekl_batch *bh)
 {

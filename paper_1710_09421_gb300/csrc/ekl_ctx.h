@@ -188,6 +188,16 @@ struct Batch {
     void *d_ctot;            // ChargeTotals per replica
     unsigned *mg_bars;       // [4 * nrep]
     size_t mg_smem;          // largest replica's shared memory for its coarse levels
+    // split form of the batched solve (ekl_mgs.cuh): per-pass launches over
+    // all replicas, the CG loop a graph with a conditional WHILE node
+    int mgs_split;
+    void *d_ctl;             // MgCtl per replica
+    void *d_grids;           // Grid3 per replica
+    int *d_loops;            // loop iterations run (launch accounting)
+    cudaGraph_t mgs_graph;
+    cudaGraphExec_t mgs_exec;
+    int mgs_blocks;          // grid the graph was built for
+    int mgs_iter_kernels;    // kernels of one loop iteration
 };
 int run_batch_f64(Batch &b, int nsteps);
 int run_batch_f32(Batch &b, int nsteps);

@@ -61,6 +61,7 @@ struct MgCtl {
     int current;    // rr_true belongs to the present phi
     int converged, stop, need_true;
     int skip;       // zero source: nothing to solve, nothing to report
+    int done;       // batches: this replica's loop has ended
 };
 
 // 4-byte words of shared memory for a tile region of Rx x Ry x Rz cells:

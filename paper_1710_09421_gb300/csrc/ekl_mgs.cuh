@@ -274,3 +274,285 @@ __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_update_kernel(Grid3 g, MgA
 }
 
 }  // namespace ekl
+
+// ------------------------------------------------------------------ batches
+// The split solve for a batch of replicas: every kernel runs over all
+// replicas at once, block b working for replica block_rep[b] as its block
+// block_local[b] of rep_blocks[r] (the tables of the batch's cooperative
+// launch, so thread maps and partials are those of that launch), with one
+// MgCtl per replica; a replica that has converged skips its work, and the
+// loop runs while any replica has not.  Replicas do not tile their coarse
+// levels.
+namespace ekl {
+
+struct MgsBatch {
+    const MgArgs *mg;  // [nrep]
+    const Grid3 *grid; // [nrep] lattice of each replica
+    MgCtl *ctl;        // [nrep]
+    PoisBatch pb;
+    int *loops;        // iterations the batch loop has run (launch accounting)
+};
+
+struct BRep {
+    int r, lb, nb, t0, nt;
+};
+__device__ __forceinline__ BRep mgsb_rep(const PoisBatch &pb)
+{
+    BRep x;
+    x.r = pb.block_rep[blockIdx.x];
+    x.lb = pb.block_local[blockIdx.x];
+    x.nb = pb.rep_blocks[x.r];
+    x.t0 = x.lb * blockDim.x + threadIdx.x;
+    x.nt = x.nb * blockDim.x;
+    return x;
+}
+
+template <typename S, typename R, typename PhiT>
+__global__ void __launch_bounds__(MGS_THREADS, 1)
+    mgsb_start_kernel(const StepArgs<S, R, PhiT> *reps, MgsBatch B)
+{
+    mgs_wait_previous();
+    __shared__ double sh[MGS_THREADS / 32];
+    __shared__ double bc[1];
+    const BRep x = mgsb_rep(B.pb);
+    const StepArgs<S, R, PhiT> &a = reps[x.r];
+    const MgArgs &m = B.mg[x.r];
+    const double t = mg_start_pass(a, m, m.link, x.t0, x.nt, sh, bc);
+    if (threadIdx.x == 0) mgs_slot(m, MGS_BB, x.nb)[x.lb] = t;
+    if (x.lb == 0 && threadIdx.x == 0) {
+        MgCtl &c = B.ctl[x.r];
+        c.tol = a.tol;
+        c.max_iter = a.max_iter;
+        c.fixed_iter = a.fixed_iter;
+    }
+}
+
+template <typename S, typename R, typename PhiT>
+__global__ void __launch_bounds__(MGS_THREADS, 1)
+    mgsb_residual_kernel(const StepArgs<S, R, PhiT> *reps, MgsBatch B, int when)
+{
+    mgs_wait_previous();
+    __shared__ double sh[MGS_THREADS / 32];
+    const BRep x = mgsb_rep(B.pb);
+    const MgCtl &c = B.ctl[x.r];
+    if (when == 1 && (c.done || !c.need_true)) return;
+    if (when == 2 && (c.current || c.skip)) return;
+    const StepArgs<S, R, PhiT> &a = reps[x.r];
+    const MgArgs &m = B.mg[x.r];
+    const double t = mg_true_residual<PhiT>(a.g, m.link, a.phi, a.b, m.r, m.z, x.t0, x.nt, sh);
+    if (threadIdx.x == 0) mgs_slot(m, MGS_RES, x.nb)[x.lb] = t;
+}
+
+// one block of 32 threads per replica
+template <typename S, typename R, typename PhiT>
+__global__ void mgsb_init_kernel(const StepArgs<S, R, PhiT> *reps, MgsBatch B)
+{
+    mgs_wait_previous();
+    __shared__ double bc[1];
+    const int r = blockIdx.x, nb = B.pb.rep_blocks[r];
+    const MgArgs &m = B.mg[r];
+    const double bb = sum_partials(mgs_slot(m, MGS_BB, nb), nb, bc);
+    const double rr = sum_partials(mgs_slot(m, MGS_RES, nb), nb, bc);
+    if (threadIdx.x != 0) return;
+    MgCtl c = B.ctl[r];
+    c.bb = bb;
+    c.it = 0;
+    c.pi = 0;
+    c.fresh = 1;
+    c.current = 1;
+    c.stop = 0;
+    c.need_true = 0;
+    c.skip = 0;
+    c.rz_old = 1.0;
+    c.limit = c.fixed_iter > 0 ? c.fixed_iter : c.max_iter;
+    c.tol2 = c.tol * c.tol * bb;
+    c.rr_true = rr;
+    c.rr_ref = rr;
+    c.converged = c.fixed_iter <= 0 && rr <= c.tol2;
+    if (c.fixed_iter <= 0 && bb == 0.0) {
+        *reps[r].pois_iters = 0;
+        *reps[r].pois_res = 0.0;
+        c.skip = 1;
+        c.converged = 1;
+    }
+    c.done = c.converged || c.it >= c.limit;
+    B.ctl[r] = c;
+}
+
+// one block: the loop goes on while any replica is not done
+__global__ static void mgsb_cond_kernel(MgsBatch B, cudaGraphConditionalHandle loop, int count)
+{
+    mgs_wait_previous();
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int r = threadIdx.x; r < B.pb.nrep; r += blockDim.x) mine |= !B.ctl[r].done;
+    if (mine) atomicOr(&any, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cudaGraphSetConditional(loop, any ? 1u : 0u);
+        if (count && any) *B.loops += 1;
+    }
+}
+
+template <bool RZ, bool PRO>
+__global__ void __launch_bounds__(MGS_THREADS, 1) mgsb_half_kernel(MgsBatch B, int c)
+{
+    mgs_wait_previous();
+    __shared__ double sh[MGS_THREADS / 32];
+    const BRep x = mgsb_rep(B.pb);
+    if (B.ctl[x.r].done) return;
+    const MgArgs &m = B.mg[x.r];
+    float rz = 0.f;
+    fine_half<RZ, PRO, MGS_U>(B.grid[x.r], m.link, m.r, m.z, m.lev[1], c, x.t0, x.nt, rz);
+    if constexpr (RZ) {
+        const double t = block_sum_lanes0(warp_sum_ff_lane0(rz), sh);
+        if (threadIdx.x == 0) mgs_slot(m, MGS_RZ, x.nb)[x.lb] = t;
+    }
+}
+
+__global__ static void __launch_bounds__(MGS_THREADS, 1) mgsb_restrict_kernel(MgsBatch B)
+{
+    mgs_wait_previous();
+    const BRep x = mgsb_rep(B.pb);
+    if (B.ctl[x.r].done) return;
+    const MgArgs &m = B.mg[x.r];
+    if (m.cta_from > 1) fine_restrict_cells<true>(B.grid[x.r], m.link, m.r, m.z, m.lev[1], x.t0, x.nt);
+    else fine_restrict_cells<false>(B.grid[x.r], m.link, m.r, m.z, m.lev[1], x.t0, x.nt);
+}
+
+// the coarse levels of every active replica (cooperative; `bars` zeroed)
+template <typename S, typename R, typename PhiT>
+__global__ void __launch_bounds__(MGS_THREADS, 1)
+    mgsb_coarse_kernel(const StepArgs<S, R, PhiT> *reps, MgsBatch B, unsigned *bars)
+{
+    mgs_wait_previous();
+    __shared__ double sh[MGS_THREADS / 32];
+    __shared__ double bc[1];
+    extern __shared__ float mg_sm[];
+    const BRep x = mgsb_rep(B.pb);
+    if (B.ctl[x.r].done) return;  // every block of that replica
+    const MgArgs &m = B.mg[x.r];
+    const MgGrid G{x.t0, x.nt, x.nb, x.lb, bars + 4 * x.r};
+    if (G.blk == 0 && !m.dense) mg_cta_load(m, mg_sm);
+    unsigned bar_k = 0;
+    mg_coarse_cycle<false>(m, G, bar_k, reps[x.r].status, mg_sm, sh, bc, 1);
+}
+
+__global__ static void __launch_bounds__(MGS_THREADS, 1) mgsb_pq_kernel(MgsBatch B)
+{
+    mgs_wait_previous();
+    __shared__ double sh[MGS_THREADS / 32];
+    __shared__ double bc[1];
+    const BRep x = mgsb_rep(B.pb);
+    const MgCtl &c = B.ctl[x.r];
+    if (c.done) return;
+    const MgArgs &m = B.mg[x.r];
+    const double rz = sum_partials(mgs_slot(m, MGS_RZ, x.nb), x.nb, bc);
+    if (!(rz > 0.0)) return;
+    const int fresh = c.fresh, pi = c.pi;
+    const float beta = fresh ? 0.f : (float)(rz / c.rz_old);
+    const float *pold = m.p[pi];
+    float *pnew = m.p[pi ^ 1];
+    const float t = fresh ? mg_pq_pass<true, uint8_t, MGS_PQU>(B.grid[x.r], m.link, m.z, pold, pnew, m.q, beta, x.t0, x.nt)
+                          : mg_pq_pass<false, uint8_t, MGS_PQU>(B.grid[x.r], m.link, m.z, pold, pnew, m.q, beta, x.t0, x.nt);
+    const double pq = block_sum_lanes0(warp_sum_ff_lane0(t), sh);
+    if (threadIdx.x == 0) mgs_slot(m, MGS_PQ, x.nb)[x.lb] = pq;
+}
+
+template <typename S, typename R, typename PhiT>
+__global__ void __launch_bounds__(MGS_THREADS, 1) mgsb_update_kernel(const StepArgs<S, R, PhiT> *reps, MgsBatch B)
+{
+    mgs_wait_previous();
+    __shared__ double sh[MGS_THREADS / 32];
+    __shared__ double bc[1];
+    const BRep x = mgsb_rep(B.pb);
+    const MgCtl &c = B.ctl[x.r];
+    if (c.done) return;
+    const MgArgs &m = B.mg[x.r];
+    const double rz = sum_partials(mgs_slot(m, MGS_RZ, x.nb), x.nb, bc);
+    const double pq = sum_partials(mgs_slot(m, MGS_PQ, x.nb), x.nb, bc);
+    if (!(rz > 0.0) || !(pq > 0.0)) return;
+    const double alpha = rz / pq;
+    const float t = mg_update_pass<PhiT>(reps[x.r].g, m.link, reps[x.r].phi, m.p[c.pi ^ 1], m.q, m.r, m.z, alpha,
+                                         x.t0, x.nt);
+    const double rr = block_sum_lanes0(warp_sum_ff_lane0(t), sh);
+    if (threadIdx.x == 0) mgs_slot(m, MGS_RR, x.nb)[x.lb] = rr;
+}
+
+// one block of 32 threads per replica (active replicas only)
+__global__ static void mgsb_mid_kernel(MgsBatch B)
+{
+    mgs_wait_previous();
+    __shared__ double bc[1];
+    const int r = blockIdx.x, nb = B.pb.rep_blocks[r];
+    if (B.ctl[r].done) return;
+    const MgArgs &m = B.mg[r];
+    const double rz = sum_partials(mgs_slot(m, MGS_RZ, nb), nb, bc);
+    const double pq = sum_partials(mgs_slot(m, MGS_PQ, nb), nb, bc);
+    const double rr = sum_partials(mgs_slot(m, MGS_RR, nb), nb, bc);
+    if (threadIdx.x != 0) return;
+    MgCtl c = B.ctl[r];
+    c.need_true = 0;
+    if (!(rz > 0.0) || !(pq > 0.0)) {
+        c.stop = 1;
+    } else {
+        c.rz_old = rz;
+        c.pi ^= 1;
+        c.it++;
+        c.fresh = 0;
+        c.current = 0;
+        if (c.fixed_iter <= 0 &&
+            (rr <= 0.25 * c.tol2 || rr <= (double)m.inner_red * m.inner_red * c.rr_ref || c.it == c.limit))
+            c.need_true = 1;
+    }
+    B.ctl[r] = c;
+}
+
+template <typename S, typename R, typename PhiT>
+__global__ void mgsb_end_kernel(const StepArgs<S, R, PhiT> *reps, MgsBatch B)
+{
+    mgs_wait_previous();
+    __shared__ double bc[1];
+    const int r = blockIdx.x, nb = B.pb.rep_blocks[r];
+    if (B.ctl[r].done) return;
+    const MgArgs &m = B.mg[r];
+    const double rt = sum_partials(mgs_slot(m, MGS_RES, nb), nb, bc);
+    if (threadIdx.x != 0) return;
+    MgCtl c = B.ctl[r];
+    if (c.need_true) {
+        c.rr_true = rt;
+        c.current = 1;
+        if (rt <= c.tol2) {
+            c.converged = 1;
+        } else {
+            c.rr_ref = rt;
+            c.fresh = 1;
+        }
+        c.need_true = 0;
+    }
+    c.done = c.stop || c.converged || c.it >= c.limit || (*(volatile const int *)reps[r].status & ST_TIMEOUT);
+    B.ctl[r] = c;
+}
+
+template <typename S, typename R, typename PhiT>
+__global__ void mgsb_report_kernel(const StepArgs<S, R, PhiT> *reps, MgsBatch B)
+{
+    mgs_wait_previous();
+    __shared__ double bc[1];
+    const int r = blockIdx.x, nb = B.pb.rep_blocks[r];
+    const MgArgs &m = B.mg[r];
+    const double rt = sum_partials(mgs_slot(m, MGS_RES, nb), nb, bc);
+    if (threadIdx.x != 0) return;
+    const MgCtl c = B.ctl[r];
+    if (c.skip) return;
+    const double rr_true = c.current ? c.rr_true : rt;
+    const StepArgs<S, R, PhiT> &a = reps[r];
+    *a.pois_iters = c.it;
+    a.pois_total[0] += c.it;
+    *a.pois_res = sqrt(rr_true / c.bb);
+    if (c.fixed_iter <= 0 && !(c.converged || rr_true <= c.tol2)) atomicOr(a.status, ST_NOCONV);
+}
+
+}  // namespace ekl

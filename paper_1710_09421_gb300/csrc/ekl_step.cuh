@@ -504,9 +504,15 @@ static inline int charge_batch_tables(Batch &B)
 static inline int mg_batch_tables(Batch &B)
 {
     std::vector<MgArgs> t(B.nrep);
-    for (int r = 0; r < B.nrep; r++) t[r] = make_mg_args(*B.reps[r]);
+    std::vector<Grid3> g(B.nrep);
+    for (int r = 0; r < B.nrep; r++) {
+        t[r] = make_mg_args(*B.reps[r]);
+        g[r] = make_grid3(B.reps[r]->nx, B.reps[r]->ny, B.reps[r]->nz);
+    }
     if (cudaMemcpyAsync(B.d_mgargs, t.data(), t.size() * sizeof(MgArgs), cudaMemcpyHostToDevice, B.stream) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaMemcpyAsync(B.d_grids, g.data(), g.size() * sizeof(Grid3), cudaMemcpyHostToDevice, B.stream) !=
+            cudaSuccess)
         return EKL_ERR_CUDA;
     return cudaStreamSynchronize(B.stream) == cudaSuccess ? EKL_OK : EKL_ERR_CUDA;
 }
@@ -578,6 +584,131 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_tables(Batc
     return EKL_OK;
 }
 
+// Graph of the batched split solve (ekl_mgs.cuh), launched after the step's
+// start kernel: true residuals -> init -> loop condition -> WHILE (any
+// replica not done) { the passes of one CG iteration over every replica,
+// a replica that is done skipping them; loop condition } -> final true
+// residuals -> report.  The descriptors it reads (parity 0: the solve does
+// not touch the populations) keep their addresses for the batch's life; the
+// graph is rebuilt when the Poisson grid changes.
+template <typename S, typename R, typename PhiT> static cudaError_t mgsb_build(Batch &B, bool pdl)
+{
+    const int n = B.nrep, nb = B.pois_blocks, nt = MGS_THREADS;
+    const StepArgs<S, R, PhiT> *reps = (const StepArgs<S, R, PhiT> *)B.d_args[0];
+    MgsBatch mb{(const MgArgs *)B.d_mgargs, (const Grid3 *)B.d_grids, (MgCtl *)B.d_ctl,
+                PoisBatch{n, B.d_block_rep, B.d_block_local, B.d_rep_blocks, B.barrier, B.status}, B.d_loops};
+    unsigned *bars = B.mg_bars;
+    int when0 = 0, when2 = 2, one = 1;
+    cudaGraph_t G = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaGraphConditionalHandle loop;
+    cudaGraphNode_t nres0, ninit, ncond, nloop, nres2, nrep;
+    cudaError_t e = cudaGraphCreate(&G, 0);
+    auto kernel_node = [&](cudaGraphNode_t *out, cudaGraphNode_t *dep, const void *fn, int grid, int block,
+                           void **args) {
+        cudaKernelNodeParams kp = {};
+        kp.func = (void *)fn;
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(block);
+        kp.kernelParams = args;
+        return cudaGraphAddKernelNode(out, G, dep, dep ? 1 : 0, &kp);
+    };
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&loop, G, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        void *args[] = {&reps, &mb, &when0};
+        e = kernel_node(&nres0, nullptr, (const void *)mgsb_residual_kernel<S, R, PhiT>, nb, nt, args);
+    }
+    if (e == cudaSuccess) {
+        void *args[] = {&reps, &mb};
+        e = kernel_node(&ninit, &nres0, (const void *)mgsb_init_kernel<S, R, PhiT>, n, 32, args);
+    }
+    if (e == cudaSuccess) {
+        void *args[] = {&mb, &loop, &one};
+        e = kernel_node(&ncond, &ninit, (const void *)mgsb_cond_kernel, 1, 256, args);
+    }
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = loop;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&nloop, G, &ncond, nullptr, 1, &cp);
+        if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess && B.mg_smem > 48 * 1024)
+        e = cudaFuncSetAttribute(mgsb_coarse_kernel<S, R, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)B.mg_smem);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        cudaLaunchAttribute dep[1];
+        dep[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        dep[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaError_t el = cudaSuccess;
+        auto go = [&](bool overlap, unsigned grid, unsigned block, auto kern, auto... args) {
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3(grid);
+            lc.blockDim = dim3(block);
+            lc.stream = cs;
+            lc.attrs = dep;
+            lc.numAttrs = (overlap && pdl) ? 1 : 0;
+            const cudaError_t r = cudaLaunchKernelEx(&lc, kern, args...);
+            if (el == cudaSuccess) el = r;
+        };
+        for (int s = 1; s < 2 * MG_NU; s++) go(s > 1, nb, nt, mgsb_half_kernel<false, false>, mb, s & 1);
+        go(true, nb, nt, mgsb_restrict_kernel, mb);
+        cudaMemsetAsync(bars, 0, 4 * sizeof(unsigned) * (size_t)n, cs);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute coop[1];
+        coop[0].id = cudaLaunchAttributeCooperative;
+        coop[0].val.cooperative = 1;
+        cfg.gridDim = dim3(nb);
+        cfg.blockDim = dim3(nt);
+        cfg.dynamicSmemBytes = B.mg_smem;
+        cfg.stream = cs;
+        cfg.attrs = coop;
+        cfg.numAttrs = 1;
+        const cudaError_t ecoop = cudaLaunchKernelEx(&cfg, mgsb_coarse_kernel<S, R, PhiT>, reps, mb, bars);
+        if (el == cudaSuccess) el = ecoop;
+        go(false, nb, nt, mgsb_half_kernel<false, true>, mb, 1);
+        for (int s = 1; s < 2 * MG_NU; s++) {
+            const int col = (s & 1) ^ 1;
+            if (s == 2 * MG_NU - 1) go(true, nb, nt, mgsb_half_kernel<true, false>, mb, col);
+            else go(true, nb, nt, mgsb_half_kernel<false, false>, mb, col);
+        }
+        go(true, nb, nt, mgsb_pq_kernel, mb);
+        go(true, nb, nt, mgsb_update_kernel<S, R, PhiT>, reps, mb);
+        go(true, n, 32, mgsb_mid_kernel, mb);
+        go(true, nb, nt, mgsb_residual_kernel<S, R, PhiT>, reps, mb, 1);
+        go(true, n, 32, mgsb_end_kernel<S, R, PhiT>, reps, mb);
+        go(true, 1, 256, mgsb_cond_kernel, mb, loop, 1);
+        cudaError_t ek = cudaGetLastError();
+        cudaError_t ec = cudaStreamEndCapture(cs, &body);
+        e = el != cudaSuccess ? el : ek != cudaSuccess ? ek : ec;
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (e == cudaSuccess) {
+        void *args[] = {&reps, &mb, &when2};
+        e = kernel_node(&nres2, &nloop, (const void *)mgsb_residual_kernel<S, R, PhiT>, nb, nt, args);
+    }
+    if (e == cudaSuccess) {
+        void *args[] = {&reps, &mb};
+        e = kernel_node(&nrep, &nres2, (const void *)mgsb_report_kernel<S, R, PhiT>, n, 32, args);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&B.mgs_exec, G, 0);
+    if (e != cudaSuccess) {
+        if (G) cudaGraphDestroy(G);
+        B.mgs_exec = nullptr;
+        return e;
+    }
+    B.mgs_graph = G;
+    B.mgs_blocks = nb;
+    // half sweeps, restriction, coarse, p/q, update, mid, residual, end, condition
+    B.mgs_iter_kernels = 2 * (2 * MG_NU - 1) + 1 + 1 + 1 + 6;
+    return cudaSuccess;
+}
+
 template <typename S, typename R, typename PhiT, bool DEV> int batch_impl(Batch &B, int nsteps)
 {
     if (!B.ready) {
@@ -610,12 +741,31 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_impl(Batch 
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.mg_smem);
                 attr_bytes = B.mg_smem;
             }
-            void *args[] = {&reps, &mgs, &pb, &bars};
-            cudaError_t e = cudaLaunchCooperativeKernel((const void *)poisson_mg_batch_kernel<S, R, PhiT>,
-                                                        dim3(B.pois_blocks), dim3(MG_BATCH_THREADS), args, B.mg_smem,
-                                                        B.stream);
-            B.launches++;
-            if (e != cudaSuccess) return EKL_ERR_CUDA;
+            if (B.mgs_split) {
+                static_assert(MGS_THREADS == MG_BATCH_THREADS, "split and cooperative batch solves share the grid");
+                if (B.mgs_exec && B.mgs_blocks != B.pois_blocks) {
+                    cudaGraphExecDestroy(B.mgs_exec);
+                    cudaGraphDestroy(B.mgs_graph);
+                    B.mgs_exec = nullptr;
+                    B.mgs_graph = nullptr;
+                }
+                // the graph with programmatic dependent launches, else without
+                if (!B.mgs_exec && mgsb_build<S, R, PhiT>(B, true) != cudaSuccess) {
+                    cudaGetLastError();
+                    if (mgsb_build<S, R, PhiT>(B, false) != cudaSuccess) return EKL_ERR_CUDA;
+                }
+                const MgsBatch mb{mgs, (const Grid3 *)B.d_grids, (MgCtl *)B.d_ctl, pb, B.d_loops};
+                mgsb_start_kernel<S, R, PhiT><<<B.pois_blocks, MGS_THREADS, 0, B.stream>>>(reps, mb);
+                if (cudaGraphLaunch(B.mgs_exec, B.stream) != cudaSuccess) return EKL_ERR_CUDA;
+                B.launches += 6;  // start, residual, init, condition, final residual, report
+            } else {
+                void *args[] = {&reps, &mgs, &pb, &bars};
+                cudaError_t e = cudaLaunchCooperativeKernel((const void *)poisson_mg_batch_kernel<S, R, PhiT>,
+                                                            dim3(B.pois_blocks), dim3(MG_BATCH_THREADS), args,
+                                                            B.mg_smem, B.stream);
+                B.launches++;
+                if (e != cudaSuccess) return EKL_ERR_CUDA;
+            }
             // from now on every replica extrapolates its starting guess
             bool changed = false;
             for (int r = 0; r < n; r++)

@@ -76,9 +76,15 @@ def test_batch_multigrid_replicas():
         assert ref.step(1) >= 0
         _, phi, _ = batch.reps[r].get_state()
         assert ref.poisson_residual(ref.last_rho(), phi) <= tol * 1.001, r
+    tot0 = [batch.reps[r].stats()["poisson_sweeps"] for r in range(len(wls))]
     l0 = batch.launches()
     assert batch.step(9) >= 0
-    assert batch.launches() - l0 == 9 * 6
+    # per step: bin, charge, charge totals, MD, LB and the split solve's six
+    # host launches; the loop's 15 kernels once per iteration, an iteration
+    # running while any replica is still iterating
+    extra = batch.launches() - l0 - 9 * 11
+    its = [batch.reps[r].stats()["poisson_sweeps"] - tot0[r] for r in range(len(wls))]
+    assert extra % 15 == 0 and max(its) <= extra // 15 <= sum(its), (extra, its)
     for r, wl in enumerate(wls):
         st = batch.reps[r].stats()
         assert st["poisson_res"] <= tol and st["poisson_iters"] > 0, (r, st)
@@ -111,3 +117,30 @@ def test_batch_replica_field_change_matches_single_run():
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), r
         sim.close()
     batch.close()
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_batch_split_solve_equals_cooperative(precision):
+    """The batched multigrid solve split into per-pass launches over all
+    replicas (the default) and the single cooperative launch return the same
+    states bit for bit, with the same iteration counts, on replicas of three
+    sizes that converge after different numbers of iterations."""
+    wls = _uneven(0)
+    wls[2] = W.small_pore(nx=16, ny=16, nz=20, membrane=(8, 11), radius=3.0, n_beads=3, seed_init=9)
+    wls = [w.replace(poisson_tol=1e-8, flags=W.FLAG_POISSON_MG, precision=precision) for w in wls]
+    coop = [w.replace(flags=W.FLAG_POISSON_MG | W.FLAG_POISSON_MG_SINGLE) for w in wls]
+    a, b = E.Batch(wls, precision=precision), E.Batch(coop, precision=precision)
+    iters = [[], []]
+    for _ in range(4):
+        assert a.step(2) >= 0 and b.step(2) >= 0
+        for k, bt in enumerate((a, b)):
+            iters[k].append([bt.reps[r].stats()["poisson_iters"] for r in range(len(wls))])
+    assert iters[0] == iters[1]
+    assert len({tuple(x) for x in iters[0]}) > 0 and any(len(set(x)) > 1 for x in iters[0]), iters[0]
+    for r in range(len(wls)):
+        sa, sb = a.reps[r].get_state(), b.reps[r].get_state()
+        assert np.array_equal(sa[0], sb[0]) and np.array_equal(sa[1], sb[1]), r
+        fa, fb = a.reps[r].fields(("R",)), b.reps[r].fields(("R",))
+        assert np.array_equal(fa["R"], fb["R"]), r
+    a.close()
+    b.close()
