@@ -135,6 +135,7 @@ def load(build_if_missing: bool = True):
         L.ekl_batch_replica.argtypes = [vp, C.c_int32]
         L.ekl_batch_replica.restype = vp
         L.ekl_batch_autotune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
+        L.ekl_batch_set_schedule.argtypes = [vp, C.c_int32]
         L.ekl_batch_launches.argtypes = [vp]
         L.ekl_batch_launches.restype = C.c_int64
         L.ekl_batch_destroy.argtypes = [vp]
@@ -446,6 +447,10 @@ def ekl_batch_replica(b, rep):
     return C.c_void_p(load().ekl_batch_replica(b, int(rep)))
 
 
+def ekl_batch_set_schedule(b, choice):
+    return _check(load().ekl_batch_set_schedule(b, int(choice)), "ekl_batch_set_schedule")
+
+
 def ekl_batch_autotune(b, trial_steps):
     c = C.c_int32(0)
     _check(load().ekl_batch_autotune(b, int(trial_steps), C.byref(c)), "ekl_batch_autotune")
@@ -500,6 +505,9 @@ class Batch:
 
     def autotune(self, trial_steps=2):
         return ekl_batch_autotune(self.h, trial_steps)
+
+    def set_schedule(self, choice):
+        return ekl_batch_set_schedule(self.h, choice)
 
     def launches(self):
         return load().ekl_batch_launches(self.h)

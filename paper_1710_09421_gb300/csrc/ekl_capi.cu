@@ -1414,6 +1414,29 @@ int batch_run(Batch &B, int nsteps)
     }
 }
 
+// Poisson schedule `choice` (bit 1: blocks shared by fluid nodes, else by
+// all nodes; bit 0: SOR on 512-thread blocks two per SM, or the split
+// multigrid solve's lattice passes on MGS_MAX_FACTOR times the blocks)
+int batch_schedule(Batch &B, int choice)
+{
+    const int sms = B.reps[0]->num_sms;
+    if (choice < 0 || choice > 3) return EKL_ERR_ARG;
+    if (B.mg) {
+        // the cooperative multigrid launch keeps one 1024-thread block per SM
+        if ((choice & 1) && !B.mgs_split) return EKL_ERR_ARG;
+        B.pois_threads = MG_BATCH_THREADS;
+        B.pois_blocks = sms;
+        B.mgs_factor = (choice & 1) ? MGS_MAX_FACTOR : 1;
+    } else {
+        B.pois_threads = (choice & 1) ? 512 : 1024;
+        B.pois_blocks = (choice & 1) ? 2 * sms : sms;
+    }
+    if (B.nrep > B.pois_blocks) return EKL_ERR_ARG;
+    B.weight_fluid = (choice >> 1) & 1;
+    B.ready = 0;
+    return EKL_OK;
+}
+
 void batch_release(Batch &B)
 {
     if (!B.reps) return;
@@ -1438,6 +1461,10 @@ void batch_release(Batch &B)
     dev_free(c0, B.d_ctl, 0);
     dev_free(c0, B.d_grids, 0);
     dev_free(c0, B.d_loops, 0);
+    dev_free(c0, B.d_lrep, 0);
+    dev_free(c0, B.d_lloc, 0);
+    dev_free(c0, B.d_lrb, 0);
+    dev_free(c0, B.d_mgs_part, 0);
 }
 
 }  // namespace
@@ -1525,6 +1552,12 @@ int ekl_batch_create(int32_t nrep, const ekl_params *params, void *stream, ekl_b
             B.d_ctl = A(nrep * sizeof(MgCtl));
             B.d_grids = A(nrep * sizeof(Grid3));
             B.d_loops = (int *)A(sizeof(int));
+            B.mgs_factor = MGS_MAX_FACTOR;  // schedule bit 0 (the faster on uneven replicas)
+            B.mgs_part_stride = MGS_MAX_FACTOR * sms;
+            B.d_lrep = (int *)A(4 * (size_t)MGS_MAX_FACTOR * sms);
+            B.d_lloc = (int *)A(4 * (size_t)MGS_MAX_FACTOR * sms);
+            B.d_lrb = (int *)A(4 * (size_t)nrep);
+            B.d_mgs_part = (double *)A(sizeof(double) * MGS_PART_SLOTS * (size_t)nrep * B.mgs_part_stride);
             if (ok) cudaMemsetAsync(B.d_loops, 0, sizeof(int), B.stream);
             if (!ok) rc = fail(EKL_ERR_ALLOC, "device allocation failed");
             else if (ops(B.prec).mg_batch_blocks(B.mg_smem) < 1)
@@ -1592,19 +1625,13 @@ int ekl_batch_autotune(ekl_batch *bh, int32_t trial_steps, int32_t *choice_out)
     DeviceScope dscope(bh->b.reps[0]->device);
     if (!dscope.ok()) return fail(EKL_ERR_ARG, "the batch's device cannot be made current");
     Batch &B = bh->b;
-    const int sms = B.reps[0]->num_sms;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bestc = 0;
+    int bestc = -1;
     for (int choice = 0; choice < 4; choice++) {
-        if (B.mg && (choice & 1)) continue;  // the multigrid launch keeps one 1024-thread block per SM
-        B.pois_threads = (choice & 1) ? 512 : 1024;
-        B.pois_blocks = (choice & 1) ? 2 * sms : sms;
-        B.weight_fluid = (choice >> 1) & 1;
-        B.ready = 0;
-        if (B.nrep > B.pois_blocks) continue;
+        if (batch_schedule(B, choice) != EKL_OK) continue;
         cudaEventRecord(e0, B.stream);
         int rc = batch_run(B, trial_steps);
         cudaEventRecord(e1, B.stream);
@@ -1622,11 +1649,15 @@ int ekl_batch_autotune(ekl_batch *bh, int32_t trial_steps, int32_t *choice_out)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    B.pois_threads = (bestc & 1) ? 512 : 1024;
-    B.pois_blocks = (bestc & 1) ? 2 * sms : sms;
-    B.weight_fluid = (bestc >> 1) & 1;
-    B.ready = 0;
+    if (bestc < 0 || batch_schedule(B, bestc) != EKL_OK) return fail(EKL_ERR_CUDA, "no Poisson schedule could run");
     if (choice_out) *choice_out = bestc;
+    return EKL_OK;
+}
+
+int ekl_batch_set_schedule(ekl_batch *bh, int32_t choice)
+{
+    if (!bh) return fail(EKL_ERR_ARG, "batch is null");
+    if (batch_schedule(bh->b, choice) != EKL_OK) return fail(EKL_ERR_ARG, "schedule not available for this batch");
     return EKL_OK;
 }
 

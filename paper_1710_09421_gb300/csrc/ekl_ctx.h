@@ -196,9 +196,19 @@ struct Batch {
     int *d_loops;            // loop iterations run (launch accounting)
     cudaGraph_t mgs_graph;
     cudaGraphExec_t mgs_exec;
-    int mgs_blocks;          // grid the graph was built for
+    int mgs_blocks, mgs_cblocks;  // lattice and coarse grids the graph was built for
     int mgs_iter_kernels;    // kernels of one loop iteration
+    // the lattice passes may split replicas into more blocks than the
+    // cooperative coarse launch (mgs_factor times as many; 1: the same
+    // blocks, and the same results bit for bit as the cooperative form)
+    int mgs_factor;
+    int mgs_lblocks;
+    int *d_lrep, *d_lloc, *d_lrb;  // block tables of the lattice passes
+    double *d_mgs_part;      // block partials: per replica MGS_SLOTS x mgs_part_stride
+    int mgs_part_stride;
 };
+constexpr int MGS_MAX_FACTOR = 4;
+constexpr int MGS_PART_SLOTS = 5;  // block-partial slots of a split solve (ekl_mgs.cuh)
 int run_batch_f64(Batch &b, int nsteps);
 int run_batch_f32(Batch &b, int nsteps);
 int run_batch_bf16(Batch &b, int nsteps);

@@ -31,6 +31,7 @@ constexpr int MGS_CU = 1;  // level-1 cells per thread and trip in its half swee
 
 // block-partial slots (nblk doubles each) in MgArgs::part
 enum { MGS_BB = 0, MGS_RES = 1, MGS_RZ = 2, MGS_PQ = 3, MGS_RR = 4, MGS_SLOTS = 5 };
+static_assert(MGS_SLOTS == MGS_PART_SLOTS, "batch partial buffers are sized by MGS_PART_SLOTS");
 
 // Programmatic dependent launch: the loop's lattice kernels are launched so
 // that they may start while the kernel before them drains; each waits here,
@@ -289,9 +290,17 @@ struct MgsBatch {
     const MgArgs *mg;  // [nrep]
     const Grid3 *grid; // [nrep] lattice of each replica
     MgCtl *ctl;        // [nrep]
-    PoisBatch pb;
+    PoisBatch pb;      // blocks of the lattice passes
+    PoisBatch cpb;     // blocks of the cooperative coarse launch
+    double *part;      // block partials: replica r, slot s at part + (r MGS_SLOTS + s) stride
+    int stride;
     int *loops;        // iterations the batch loop has run (launch accounting)
 };
+
+__device__ __forceinline__ double *mgsb_slot(const MgsBatch &B, int r, int slot)
+{
+    return B.part + ((size_t)r * MGS_SLOTS + slot) * B.stride;
+}
 
 struct BRep {
     int r, lb, nb, t0, nt;
@@ -318,7 +327,7 @@ __global__ void __launch_bounds__(MGS_THREADS, 1)
     const StepArgs<S, R, PhiT> &a = reps[x.r];
     const MgArgs &m = B.mg[x.r];
     const double t = mg_start_pass(a, m, m.link, x.t0, x.nt, sh, bc);
-    if (threadIdx.x == 0) mgs_slot(m, MGS_BB, x.nb)[x.lb] = t;
+    if (threadIdx.x == 0) mgsb_slot(B, x.r, MGS_BB)[x.lb] = t;
     if (x.lb == 0 && threadIdx.x == 0) {
         MgCtl &c = B.ctl[x.r];
         c.tol = a.tol;
@@ -340,7 +349,7 @@ __global__ void __launch_bounds__(MGS_THREADS, 1)
     const StepArgs<S, R, PhiT> &a = reps[x.r];
     const MgArgs &m = B.mg[x.r];
     const double t = mg_true_residual<PhiT>(a.g, m.link, a.phi, a.b, m.r, m.z, x.t0, x.nt, sh);
-    if (threadIdx.x == 0) mgs_slot(m, MGS_RES, x.nb)[x.lb] = t;
+    if (threadIdx.x == 0) mgsb_slot(B, x.r, MGS_RES)[x.lb] = t;
 }
 
 // one block of 32 threads per replica
@@ -351,8 +360,8 @@ __global__ void mgsb_init_kernel(const StepArgs<S, R, PhiT> *reps, MgsBatch B)
     __shared__ double bc[1];
     const int r = blockIdx.x, nb = B.pb.rep_blocks[r];
     const MgArgs &m = B.mg[r];
-    const double bb = sum_partials(mgs_slot(m, MGS_BB, nb), nb, bc);
-    const double rr = sum_partials(mgs_slot(m, MGS_RES, nb), nb, bc);
+    const double bb = sum_partials(mgsb_slot(B, r, MGS_BB), nb, bc);
+    const double rr = sum_partials(mgsb_slot(B, r, MGS_RES), nb, bc);
     if (threadIdx.x != 0) return;
     MgCtl c = B.ctl[r];
     c.bb = bb;
@@ -408,7 +417,7 @@ __global__ void __launch_bounds__(MGS_THREADS, 1) mgsb_half_kernel(MgsBatch B, i
     fine_half<RZ, PRO, MGS_U>(B.grid[x.r], m.link, m.r, m.z, m.lev[1], c, x.t0, x.nt, rz);
     if constexpr (RZ) {
         const double t = block_sum_lanes0(warp_sum_ff_lane0(rz), sh);
-        if (threadIdx.x == 0) mgs_slot(m, MGS_RZ, x.nb)[x.lb] = t;
+        if (threadIdx.x == 0) mgsb_slot(B, x.r, MGS_RZ)[x.lb] = t;
     }
 }
 
@@ -431,7 +440,7 @@ __global__ void __launch_bounds__(MGS_THREADS, 1)
     __shared__ double sh[MGS_THREADS / 32];
     __shared__ double bc[1];
     extern __shared__ float mg_sm[];
-    const BRep x = mgsb_rep(B.pb);
+    const BRep x = mgsb_rep(B.cpb);
     if (B.ctl[x.r].done) return;  // every block of that replica
     const MgArgs &m = B.mg[x.r];
     const MgGrid G{x.t0, x.nt, x.nb, x.lb, bars + 4 * x.r};
@@ -449,7 +458,7 @@ __global__ static void __launch_bounds__(MGS_THREADS, 1) mgsb_pq_kernel(MgsBatch
     const MgCtl &c = B.ctl[x.r];
     if (c.done) return;
     const MgArgs &m = B.mg[x.r];
-    const double rz = sum_partials(mgs_slot(m, MGS_RZ, x.nb), x.nb, bc);
+    const double rz = sum_partials(mgsb_slot(B, x.r, MGS_RZ), x.nb, bc);
     if (!(rz > 0.0)) return;
     const int fresh = c.fresh, pi = c.pi;
     const float beta = fresh ? 0.f : (float)(rz / c.rz_old);
@@ -458,7 +467,7 @@ __global__ static void __launch_bounds__(MGS_THREADS, 1) mgsb_pq_kernel(MgsBatch
     const float t = fresh ? mg_pq_pass<true, uint8_t, MGS_PQU>(B.grid[x.r], m.link, m.z, pold, pnew, m.q, beta, x.t0, x.nt)
                           : mg_pq_pass<false, uint8_t, MGS_PQU>(B.grid[x.r], m.link, m.z, pold, pnew, m.q, beta, x.t0, x.nt);
     const double pq = block_sum_lanes0(warp_sum_ff_lane0(t), sh);
-    if (threadIdx.x == 0) mgs_slot(m, MGS_PQ, x.nb)[x.lb] = pq;
+    if (threadIdx.x == 0) mgsb_slot(B, x.r, MGS_PQ)[x.lb] = pq;
 }
 
 template <typename S, typename R, typename PhiT>
@@ -471,14 +480,14 @@ __global__ void __launch_bounds__(MGS_THREADS, 1) mgsb_update_kernel(const StepA
     const MgCtl &c = B.ctl[x.r];
     if (c.done) return;
     const MgArgs &m = B.mg[x.r];
-    const double rz = sum_partials(mgs_slot(m, MGS_RZ, x.nb), x.nb, bc);
-    const double pq = sum_partials(mgs_slot(m, MGS_PQ, x.nb), x.nb, bc);
+    const double rz = sum_partials(mgsb_slot(B, x.r, MGS_RZ), x.nb, bc);
+    const double pq = sum_partials(mgsb_slot(B, x.r, MGS_PQ), x.nb, bc);
     if (!(rz > 0.0) || !(pq > 0.0)) return;
     const double alpha = rz / pq;
     const float t = mg_update_pass<PhiT>(reps[x.r].g, m.link, reps[x.r].phi, m.p[c.pi ^ 1], m.q, m.r, m.z, alpha,
                                          x.t0, x.nt);
     const double rr = block_sum_lanes0(warp_sum_ff_lane0(t), sh);
-    if (threadIdx.x == 0) mgs_slot(m, MGS_RR, x.nb)[x.lb] = rr;
+    if (threadIdx.x == 0) mgsb_slot(B, x.r, MGS_RR)[x.lb] = rr;
 }
 
 // one block of 32 threads per replica (active replicas only)
@@ -489,9 +498,9 @@ __global__ static void mgsb_mid_kernel(MgsBatch B)
     const int r = blockIdx.x, nb = B.pb.rep_blocks[r];
     if (B.ctl[r].done) return;
     const MgArgs &m = B.mg[r];
-    const double rz = sum_partials(mgs_slot(m, MGS_RZ, nb), nb, bc);
-    const double pq = sum_partials(mgs_slot(m, MGS_PQ, nb), nb, bc);
-    const double rr = sum_partials(mgs_slot(m, MGS_RR, nb), nb, bc);
+    const double rz = sum_partials(mgsb_slot(B, r, MGS_RZ), nb, bc);
+    const double pq = sum_partials(mgsb_slot(B, r, MGS_PQ), nb, bc);
+    const double rr = sum_partials(mgsb_slot(B, r, MGS_RR), nb, bc);
     if (threadIdx.x != 0) return;
     MgCtl c = B.ctl[r];
     c.need_true = 0;
@@ -518,7 +527,7 @@ __global__ void mgsb_end_kernel(const StepArgs<S, R, PhiT> *reps, MgsBatch B)
     const int r = blockIdx.x, nb = B.pb.rep_blocks[r];
     if (B.ctl[r].done) return;
     const MgArgs &m = B.mg[r];
-    const double rt = sum_partials(mgs_slot(m, MGS_RES, nb), nb, bc);
+    const double rt = sum_partials(mgsb_slot(B, r, MGS_RES), nb, bc);
     if (threadIdx.x != 0) return;
     MgCtl c = B.ctl[r];
     if (c.need_true) {
@@ -543,7 +552,7 @@ __global__ void mgsb_report_kernel(const StepArgs<S, R, PhiT> *reps, MgsBatch B)
     __shared__ double bc[1];
     const int r = blockIdx.x, nb = B.pb.rep_blocks[r];
     const MgArgs &m = B.mg[r];
-    const double rt = sum_partials(mgs_slot(m, MGS_RES, nb), nb, bc);
+    const double rt = sum_partials(mgsb_slot(B, r, MGS_RES), nb, bc);
     if (threadIdx.x != 0) return;
     const MgCtl c = B.ctl[r];
     if (c.skip) return;

@@ -537,36 +537,49 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_tables(Batc
     }
     // Poisson blocks: at least one per replica, the rest in proportion to
     // the replica's (fluid) node count, largest remainders first
-    const int total = B.pois_blocks;
     std::vector<double> w(n);
     double W = 0.0;
     for (int r = 0; r < n; r++) {
         w[r] = (double)(B.weight_fluid ? B.reps[r]->n_fluid : B.reps[r]->N);
         W += w[r];
     }
-    std::vector<int> k(n, 1);
-    int used = n;
-    std::vector<std::pair<double, int>> frac;
-    for (int r = 0; r < n; r++) {
-        double share = (total - n) * w[r] / W;
-        int extra = (int)share;
-        k[r] += extra;
-        used += extra;
-        frac.push_back({share - extra, r});
-    }
-    std::sort(frac.begin(), frac.end(), [](auto &x, auto &y) { return x.first > y.first || (x.first == y.first && x.second < y.second); });
-    for (int t = 0; used < total && t < n; t++, used++) k[frac[t].second]++;
-    std::vector<int> brep, bloc;
-    for (int r = 0; r < n; r++)
-        for (int j = 0; j < k[r]; j++) {
-            brep.push_back(r);
-            bloc.push_back(j);
+    std::vector<int> k, brep, bloc, lk, lrep, lloc;
+    auto share_out = [&](int total, std::vector<int> &k, std::vector<int> &brep, std::vector<int> &bloc) {
+        k.assign(n, 1);
+        int used = n;
+        std::vector<std::pair<double, int>> frac;
+        for (int r = 0; r < n; r++) {
+            double share = (total - n) * w[r] / W;
+            int extra = (int)share;
+            k[r] += extra;
+            used += extra;
+            frac.push_back({share - extra, r});
         }
+        std::sort(frac.begin(), frac.end(),
+                  [](auto &x, auto &y) { return x.first > y.first || (x.first == y.first && x.second < y.second); });
+        for (int t = 0; used < total && t < n; t++, used++) k[frac[t].second]++;
+        for (int r = 0; r < n; r++)
+            for (int j = 0; j < k[r]; j++) {
+                brep.push_back(r);
+                bloc.push_back(j);
+            }
+    };
+    share_out(B.pois_blocks, k, brep, bloc);
     B.pois_blocks = (int)brep.size();
     if (cudaMemcpyAsync(B.d_block_rep, brep.data(), brep.size() * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess ||
         cudaMemcpyAsync(B.d_block_local, bloc.data(), bloc.size() * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess ||
         cudaMemcpyAsync(B.d_rep_blocks, k.data(), n * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess)
         return EKL_ERR_CUDA;
+    if (B.mg && B.mgs_split) {
+        // the split solve's lattice passes: mgs_factor times the blocks
+        // (factor 1: the same tables)
+        share_out(B.pois_blocks * B.mgs_factor, lk, lrep, lloc);
+        B.mgs_lblocks = (int)lrep.size();
+        if (cudaMemcpyAsync(B.d_lrep, lrep.data(), lrep.size() * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess ||
+            cudaMemcpyAsync(B.d_lloc, lloc.data(), lloc.size() * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess ||
+            cudaMemcpyAsync(B.d_lrb, lk.data(), n * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess)
+            return EKL_ERR_CUDA;
+    }
     if (cudaStreamSynchronize(B.stream) != cudaSuccess) return EKL_ERR_CUDA;
     if (charge_batch_tables(B) != EKL_OK) return EKL_ERR_CUDA;
     if (B.mg && mg_batch_tables(B) != EKL_OK) return EKL_ERR_CUDA;
@@ -591,12 +604,23 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_tables(Batc
 // residuals -> report.  The descriptors it reads (parity 0: the solve does
 // not touch the populations) keep their addresses for the batch's life; the
 // graph is rebuilt when the Poisson grid changes.
+static inline MgsBatch mgsb_args(const Batch &B)
+{
+    return MgsBatch{(const MgArgs *)B.d_mgargs,
+                    (const Grid3 *)B.d_grids,
+                    (MgCtl *)B.d_ctl,
+                    PoisBatch{B.nrep, B.d_lrep, B.d_lloc, B.d_lrb, B.barrier, B.status},
+                    PoisBatch{B.nrep, B.d_block_rep, B.d_block_local, B.d_rep_blocks, B.barrier, B.status},
+                    B.d_mgs_part,
+                    B.mgs_part_stride,
+                    B.d_loops};
+}
+
 template <typename S, typename R, typename PhiT> static cudaError_t mgsb_build(Batch &B, bool pdl)
 {
-    const int n = B.nrep, nb = B.pois_blocks, nt = MGS_THREADS;
+    const int n = B.nrep, nb = B.mgs_lblocks, ncb = B.pois_blocks, nt = MGS_THREADS;
     const StepArgs<S, R, PhiT> *reps = (const StepArgs<S, R, PhiT> *)B.d_args[0];
-    MgsBatch mb{(const MgArgs *)B.d_mgargs, (const Grid3 *)B.d_grids, (MgCtl *)B.d_ctl,
-                PoisBatch{n, B.d_block_rep, B.d_block_local, B.d_rep_blocks, B.barrier, B.status}, B.d_loops};
+    MgsBatch mb = mgsb_args(B);
     unsigned *bars = B.mg_bars;
     int when0 = 0, when2 = 2, one = 1;
     cudaGraph_t G = nullptr;
@@ -663,7 +687,7 @@ template <typename S, typename R, typename PhiT> static cudaError_t mgsb_build(B
         cudaLaunchAttribute coop[1];
         coop[0].id = cudaLaunchAttributeCooperative;
         coop[0].val.cooperative = 1;
-        cfg.gridDim = dim3(nb);
+        cfg.gridDim = dim3(ncb);
         cfg.blockDim = dim3(nt);
         cfg.dynamicSmemBytes = B.mg_smem;
         cfg.stream = cs;
@@ -704,6 +728,7 @@ template <typename S, typename R, typename PhiT> static cudaError_t mgsb_build(B
     }
     B.mgs_graph = G;
     B.mgs_blocks = nb;
+    B.mgs_cblocks = ncb;
     // half sweeps, restriction, coarse, p/q, update, mid, residual, end, condition
     B.mgs_iter_kernels = 2 * (2 * MG_NU - 1) + 1 + 1 + 1 + 6;
     return cudaSuccess;
@@ -743,7 +768,7 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_impl(Batch 
             }
             if (B.mgs_split) {
                 static_assert(MGS_THREADS == MG_BATCH_THREADS, "split and cooperative batch solves share the grid");
-                if (B.mgs_exec && B.mgs_blocks != B.pois_blocks) {
+                if (B.mgs_exec && (B.mgs_blocks != B.mgs_lblocks || B.mgs_cblocks != B.pois_blocks)) {
                     cudaGraphExecDestroy(B.mgs_exec);
                     cudaGraphDestroy(B.mgs_graph);
                     B.mgs_exec = nullptr;
@@ -754,8 +779,7 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_impl(Batch 
                     cudaGetLastError();
                     if (mgsb_build<S, R, PhiT>(B, false) != cudaSuccess) return EKL_ERR_CUDA;
                 }
-                const MgsBatch mb{mgs, (const Grid3 *)B.d_grids, (MgCtl *)B.d_ctl, pb, B.d_loops};
-                mgsb_start_kernel<S, R, PhiT><<<B.pois_blocks, MGS_THREADS, 0, B.stream>>>(reps, mb);
+                mgsb_start_kernel<S, R, PhiT><<<B.mgs_lblocks, MGS_THREADS, 0, B.stream>>>(reps, mgsb_args(B));
                 if (cudaGraphLaunch(B.mgs_exec, B.stream) != cudaSuccess) return EKL_ERR_CUDA;
                 B.launches += 6;  // start, residual, init, condition, final residual, report
             } else {
