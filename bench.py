@@ -543,7 +543,7 @@ def rooflines(W, wl, m, store):
     ph = m["phase"]
     split = mg and mg_split(W, wl, n_sms())
     if split:
-        pk = "multigrid_split_solve"  # (a single handle; batches keep the cooperative launch)
+        pk = "multigrid_split_solve"
         pb = mg_algorithmic_bytes(wl, m["phase_iters"], link_bytes=1)
     elif mg:
         pk = "poisson_mg_wide_kernel" if wl.n_nodes >= 152 * 16384 else "poisson_mg_kernel"

@@ -279,11 +279,15 @@ __global__ void __launch_bounds__(MGS_THREADS, 1) mgs_update_kernel(Grid3 g, MgA
 // ------------------------------------------------------------------ batches
 // The split solve for a batch of replicas: every kernel runs over all
 // replicas at once, block b working for replica block_rep[b] as its block
-// block_local[b] of rep_blocks[r] (the tables of the batch's cooperative
-// launch, so thread maps and partials are those of that launch), with one
-// MgCtl per replica; a replica that has converged skips its work, and the
-// loop runs while any replica has not.  Replicas do not tile their coarse
-// levels.
+// block_local[b] of rep_blocks[r], with one MgCtl per replica; a replica
+// that has converged skips its work, and the loop runs while any replica
+// has not.  The lattice passes and the coarse launch have tables of their
+// own: the coarse launch is cooperative (the cooperative batch solve's
+// blocks, one per SM), while the lattice passes may take several times as
+// many blocks, which evens out the load of replicas of uneven size.  With
+// the same tables for both, thread maps and partials are those of the
+// cooperative batch solve and the results are the same bit for bit.
+// Replicas do not tile their coarse levels.
 namespace ekl {
 
 struct MgsBatch {
