@@ -727,7 +727,7 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long 
     // large lattices per SM make the lattice passes bandwidth-bound: twice the
     // warps in flight (1024-thread blocks) then beat the 512-thread launch
     // that keeps 128 registers a thread for the latency-bound small solve
-    c.mg_wide = N >= (long long)MG_WIDE_NODES_PER_SM * c.num_sms;  // (replicas use the batched kernel)
+    c.mg_wide = N >= (long long)MG_WIDE_NODES_PER_SM * c.num_sms;  // (replicas use the batched solve)
     // the solve runs split into per-pass launches (measured faster on every
     // lattice size tried: 64x64x128 0.53 against 0.57 ms, 256x256x512 8.3
     // against 14.4 ms), with the block size of the single launch it matches
