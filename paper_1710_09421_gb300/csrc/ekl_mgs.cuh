@@ -306,6 +306,20 @@ __device__ __forceinline__ double *mgsb_slot(const MgsBatch &B, int r, int slot)
     return B.part + ((size_t)r * MGS_SLOTS + slot) * B.stride;
 }
 
+// A replica's descriptors live in global memory, where the passes' own
+// stores could alias them as far as the compiler knows: read through a
+// reference there, a field would be loaded again after every store.  The
+// kernels therefore take value copies (the lattice and level 1 in
+// registers) or, for the whole descriptor, a copy in shared memory.
+template <typename T> __device__ __forceinline__ void mgsb_copy(const T *src, T &dst)
+{
+    static_assert(sizeof(T) % sizeof(int) == 0, "descriptor copied as 4-byte words");
+    const int *s = (const int *)src;
+    int *d = (int *)&dst;
+    for (int i = threadIdx.x; i < (int)(sizeof(T) / sizeof(int)); i += blockDim.x) d[i] = __ldg(s + i);
+    __syncthreads();
+}
+
 struct BRep {
     int r, lb, nb, t0, nt;
 };
@@ -327,9 +341,13 @@ __global__ void __launch_bounds__(MGS_THREADS, 1)
     mgs_wait_previous();
     __shared__ double sh[MGS_THREADS / 32];
     __shared__ double bc[1];
+    __shared__ StepArgs<S, R, PhiT> s_a;
+    __shared__ MgArgs s_m;
     const BRep x = mgsb_rep(B.pb);
-    const StepArgs<S, R, PhiT> &a = reps[x.r];
-    const MgArgs &m = B.mg[x.r];
+    mgsb_copy(reps + x.r, s_a);
+    mgsb_copy(B.mg + x.r, s_m);
+    const StepArgs<S, R, PhiT> &a = s_a;
+    const MgArgs &m = s_m;
     const double t = mg_start_pass(a, m, m.link, x.t0, x.nt, sh, bc);
     if (threadIdx.x == 0) mgsb_slot(B, x.r, MGS_BB)[x.lb] = t;
     if (x.lb == 0 && threadIdx.x == 0) {
@@ -350,9 +368,9 @@ __global__ void __launch_bounds__(MGS_THREADS, 1)
     const MgCtl &c = B.ctl[x.r];
     if (when == 1 && (c.done || !c.need_true)) return;
     if (when == 2 && (c.current || c.skip)) return;
-    const StepArgs<S, R, PhiT> &a = reps[x.r];
+    const Grid3 g = B.grid[x.r];
     const MgArgs &m = B.mg[x.r];
-    const double t = mg_true_residual<PhiT>(a.g, m.link, a.phi, a.b, m.r, m.z, x.t0, x.nt, sh);
+    const double t = mg_true_residual<PhiT>(g, m.link, reps[x.r].phi, reps[x.r].b, m.r, m.z, x.t0, x.nt, sh);
     if (threadIdx.x == 0) mgsb_slot(B, x.r, MGS_RES)[x.lb] = t;
 }
 
@@ -418,7 +436,9 @@ __global__ void __launch_bounds__(MGS_THREADS, 1) mgsb_half_kernel(MgsBatch B, i
     if (B.ctl[x.r].done) return;
     const MgArgs &m = B.mg[x.r];
     float rz = 0.f;
-    fine_half<RZ, PRO, MGS_U>(B.grid[x.r], m.link, m.r, m.z, m.lev[1], c, x.t0, x.nt, rz);
+    const Grid3 g = B.grid[x.r];
+    const MgLevel l1 = m.lev[1];
+    fine_half<RZ, PRO, MGS_U>(g, m.link, m.r, m.z, l1, c, x.t0, x.nt, rz);
     if constexpr (RZ) {
         const double t = block_sum_lanes0(warp_sum_ff_lane0(rz), sh);
         if (threadIdx.x == 0) mgsb_slot(B, x.r, MGS_RZ)[x.lb] = t;
@@ -431,8 +451,10 @@ __global__ static void __launch_bounds__(MGS_THREADS, 1) mgsb_restrict_kernel(Mg
     const BRep x = mgsb_rep(B.pb);
     if (B.ctl[x.r].done) return;
     const MgArgs &m = B.mg[x.r];
-    if (m.cta_from > 1) fine_restrict_cells<true>(B.grid[x.r], m.link, m.r, m.z, m.lev[1], x.t0, x.nt);
-    else fine_restrict_cells<false>(B.grid[x.r], m.link, m.r, m.z, m.lev[1], x.t0, x.nt);
+    const Grid3 g = B.grid[x.r];
+    const MgLevel l1 = m.lev[1];
+    if (m.cta_from > 1) fine_restrict_cells<true>(g, m.link, m.r, m.z, l1, x.t0, x.nt);
+    else fine_restrict_cells<false>(g, m.link, m.r, m.z, l1, x.t0, x.nt);
 }
 
 // the coarse levels of every active replica (cooperative; `bars` zeroed)
@@ -446,7 +468,9 @@ __global__ void __launch_bounds__(MGS_THREADS, 1)
     extern __shared__ float mg_sm[];
     const BRep x = mgsb_rep(B.cpb);
     if (B.ctl[x.r].done) return;  // every block of that replica
-    const MgArgs &m = B.mg[x.r];
+    __shared__ MgArgs s_m;
+    mgsb_copy(B.mg + x.r, s_m);
+    const MgArgs &m = s_m;
     const MgGrid G{x.t0, x.nt, x.nb, x.lb, bars + 4 * x.r};
     if (G.blk == 0 && !m.dense) mg_cta_load(m, mg_sm);
     unsigned bar_k = 0;
@@ -468,8 +492,9 @@ __global__ static void __launch_bounds__(MGS_THREADS, 1) mgsb_pq_kernel(MgsBatch
     const float beta = fresh ? 0.f : (float)(rz / c.rz_old);
     const float *pold = m.p[pi];
     float *pnew = m.p[pi ^ 1];
-    const float t = fresh ? mg_pq_pass<true, uint8_t, MGS_PQU>(B.grid[x.r], m.link, m.z, pold, pnew, m.q, beta, x.t0, x.nt)
-                          : mg_pq_pass<false, uint8_t, MGS_PQU>(B.grid[x.r], m.link, m.z, pold, pnew, m.q, beta, x.t0, x.nt);
+    const Grid3 g = B.grid[x.r];
+    const float t = fresh ? mg_pq_pass<true, uint8_t, MGS_PQU>(g, m.link, m.z, pold, pnew, m.q, beta, x.t0, x.nt)
+                          : mg_pq_pass<false, uint8_t, MGS_PQU>(g, m.link, m.z, pold, pnew, m.q, beta, x.t0, x.nt);
     const double pq = block_sum_lanes0(warp_sum_ff_lane0(t), sh);
     if (threadIdx.x == 0) mgsb_slot(B, x.r, MGS_PQ)[x.lb] = pq;
 }
@@ -488,7 +513,8 @@ __global__ void __launch_bounds__(MGS_THREADS, 1) mgsb_update_kernel(const StepA
     const double pq = sum_partials(mgsb_slot(B, x.r, MGS_PQ), x.nb, bc);
     if (!(rz > 0.0) || !(pq > 0.0)) return;
     const double alpha = rz / pq;
-    const float t = mg_update_pass<PhiT>(reps[x.r].g, m.link, reps[x.r].phi, m.p[c.pi ^ 1], m.q, m.r, m.z, alpha,
+    const Grid3 g = B.grid[x.r];
+    const float t = mg_update_pass<PhiT>(g, m.link, reps[x.r].phi, m.p[c.pi ^ 1], m.q, m.r, m.z, alpha,
                                          x.t0, x.nt);
     const double rr = block_sum_lanes0(warp_sum_ff_lane0(t), sh);
     if (threadIdx.x == 0) mgsb_slot(B, x.r, MGS_RR)[x.lb] = rr;
