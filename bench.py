@@ -45,10 +45,10 @@ PROFILED = {
     # kernel plus its graph, the mean over the capture's solves: 6.4 CG iterations on 256x256x512, 5.2 on
     # 64x64x128)
     ("lb_fused_kernel", "pore_256x256x512_r8_N128"): ("3748fc75630d6ab3", 7824183011 + 7365414755),
-    ("multigrid_split_solve", "pore_256x256x512_r8_N128"): ("5732002be10a0027",
-                                                         674898887 + 696782876 + 30350284629 + 13197447296),
+    ("multigrid_split_solve", "pore_256x256x512_r8_N128"): ("b54e3161bf0d0b0c",
+                                                         674939861 + 696828516 + 30335018012 + 13175362446),
     ("lb_fused_kernel", "pore_64x64x128_r4_N32"): ("3748fc75630d6ab3", 119387372 + 63406887),
-    ("multigrid_split_solve", "pore_64x64x128_r4_N32"): ("5732002be10a0027", 10720177 + 0 + 17262237 + 57698),
+    ("multigrid_split_solve", "pore_64x64x128_r4_N32"): ("b54e3161bf0d0b0c", 10722363 + 0 + 17252569 + 42673),
 }
 KERNEL_SOURCES = {
     "lb_fused_kernel": ("ekl_kernels.cuh", "ekl_dev.cuh"),
