@@ -378,13 +378,14 @@ int ekl_net_train_grid(int32_t nsamples, const int32_t dims[3], const int32_t pe
  * running between capture and replay of a CUDA graph on a pool-allocated
  * stream, a real-time loop that reserved all device memory up front, a host
  * framework whose allocator is locked during a solver callback).  It returns
- * the fields of ekl_get_fields (n, j, R and V bit for bit; phi to the
- * round-off of its mean subtraction, which sums in another order), staged
+ * the fields of ekl_get_fields bit for bit (both remove phi's fluid mean
+ * with the same deterministic device sum), staged
  * through one fixed device array of
  * EKL_NOALLOC_MAX_DOUBLES doubles (16 MiB) that the library reserves on every
  * GPU that loads it, instead of per-call device buffers; it calls no
  * cudaMalloc/cudaFree and no allocator.  A request needing more staging than
- * that (3N + 9N + N doubles for n_out/j_out/phi_out, 6 per bead for R/V) is
+ * that (3N + 9N + N + 512 doubles for n_out/j_out/phi_out, 6 per bead for
+ * R/V) is
  * rejected with EKL_ERR_ARG.  All calls share the array: calls whose GPU work
  * overlaps race and must be serialised by the caller.  The first call on a
  * device looks up the array's device address (once per device); make it

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "ekl_kernels.cuh"
+#include "ekl_gauge.cuh"
 #include "ekl_mg.cuh"
 
 using namespace ekl;
@@ -1159,7 +1160,8 @@ int ekl_get_fields(ekl_handle *h, double *n_out, double *j_out, double *phi_out,
     const long long N = c.N;
     double *dn = n_out ? (double *)dev_alloc(c, (size_t)NS * N * 8) : nullptr;
     double *dj = j_out ? (double *)dev_alloc(c, (size_t)NS * 3 * N * 8) : nullptr;
-    double *dp = phi_out ? (double *)dev_alloc(c, (size_t)N * 8) : nullptr;
+    // the potential, then the gauge's block partials
+    double *dp = phi_out ? (double *)dev_alloc(c, ((size_t)N + 2 * GAUGE_BLOCKS) * 8) : nullptr;
     if ((n_out && !dn) || (j_out && !dj) || (phi_out && !dp)) {
         dev_free(c, dn, 0);
         dev_free(c, dj, 0);
@@ -1168,7 +1170,14 @@ int ekl_get_fields(ekl_handle *h, double *n_out, double *j_out, double *phi_out,
     }
     int rc = ops(c.prec).fields(c, dn, dj, dp);
     cudaError_t e = cudaSuccess;
-    if (rc == EKL_OK) {
+    if (rc == EKL_OK && dp) {
+        // gauge on the device: remove the fluid mean (deterministic sum)
+        gauge_partials_kernel<<<GAUGE_BLOCKS, GAUGE_THREADS, 0, c.stream>>>(dp, c.mask, N, dp + N);
+        gauge_apply_kernel<<<c.num_sms * 2, GAUGE_THREADS, 0, c.stream>>>(c.mask, N, dp, dp + N);
+        c.launches += 2;
+        e = cudaGetLastError();
+    }
+    if (rc == EKL_OK && e == cudaSuccess) {
         if (dn) e = staged_copy(c.stream, c.device, n_out, dn, (size_t)NS * N * 8, true);
         if (e == cudaSuccess && dj) e = staged_copy(c.stream, c.device, j_out, dj, (size_t)NS * 3 * N * 8, true);
         if (e == cudaSuccess && dp) e = staged_copy(c.stream, c.device, phi_out, dp, (size_t)N * 8, true);
@@ -1192,21 +1201,6 @@ int ekl_get_fields(ekl_handle *h, double *n_out, double *j_out, double *phi_out,
     dev_free(c, dp, 0);
     if (rc != EKL_OK) return fail(rc, "fields kernel failed");
     if (e != cudaSuccess) return fail_cuda(e, "get_fields");
-    if (phi_out) {
-        // gauge: remove the fluid mean, summed in node order
-        std::vector<uint32_t> m(N);
-        e = cudaMemcpy(m.data(), c.mask, N * 4, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return fail_cuda(e, "get_fields mask");
-        double sum = 0.0;
-        long long nf = 0;
-        for (long long i = 0; i < N; i++)
-            if (!(m[i] & SOLID_BIT)) {
-                sum += phi_out[i];
-                nf++;
-            }
-        double mean = nf ? sum / nf : 0.0;
-        for (long long i = 0; i < N; i++) phi_out[i] = (m[i] & SOLID_BIT) ? 0.0 : phi_out[i] - mean;
-    }
     return EKL_OK;
 }
 

@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "ekl_step.cuh"
+#include "ekl_gauge.cuh"
 
 struct ekl_handle {
     ekl::Ctx c;
@@ -71,26 +72,6 @@ int stage_address(int dev, double **out)
 
 // potential of the last step with the fluid mean removed, wall nodes zero;
 // one block, fixed reduction order
-__global__ void gauge_kernel(const uint32_t *__restrict__ mask, long long N, double *phi)
-{
-    __shared__ double sh[32];
-    __shared__ double tot[2];
-    double s = 0.0, c = 0.0;
-    for (long long i = threadIdx.x; i < N; i += blockDim.x)
-        if (!(mask[i] & ekl::SOLID_BIT)) {
-            s += phi[i];
-            c += 1.0;
-        }
-    double ts = ekl::block_sum(s, sh);
-    if (threadIdx.x == 0) tot[0] = ts;
-    double tc = ekl::block_sum(c, sh);
-    if (threadIdx.x == 0) tot[1] = tc;
-    __syncthreads();
-    const double mean = tot[1] > 0.0 ? tot[0] / tot[1] : 0.0;
-    for (long long i = threadIdx.x; i < N; i += blockDim.x)
-        phi[i] = (mask[i] & ekl::SOLID_BIT) ? 0.0 : phi[i] - mean;
-}
-
 template <typename R> __global__ void beads_kernel(const double *Rb, const R *Vb, int n3, double *out)
 {
     for (int k = threadIdx.x; k < n3; k += blockDim.x) {
@@ -129,7 +110,7 @@ extern "C" int ekl_get_fields_noalloc(ekl_handle *h, double *n_out, double *j_ou
     const long long N = c.N;
     const bool beads = c.nb > 0 && (R_out || V_out);
     size_t need = (n_out ? 3 * (size_t)N : 0) + (j_out ? 9 * (size_t)N : 0) +
-                  (phi_out ? (size_t)N : 0) + (beads ? 6 * (size_t)c.nb : 0);
+                  (phi_out ? (size_t)N + 2 * ekl::GAUGE_BLOCKS : 0) + (beads ? 6 * (size_t)c.nb : 0);
     if (need > NOALLOC_DOUBLES) {
         char msg[256];
         snprintf(msg, sizeof msg,
@@ -153,8 +134,11 @@ extern "C" int ekl_get_fields_noalloc(ekl_handle *h, double *n_out, double *j_ou
     }
     if (rc != EKL_OK) return rc;
     if (dp) {
-        gauge_kernel<<<1, 1024, 0, c.stream>>>(c.mask, N, dp);
-        c.launches++;
+        // the gauge's block partials after the bead block
+        double *gp = db + (beads ? 6 * c.nb : 0);
+        ekl::gauge_partials_kernel<<<ekl::GAUGE_BLOCKS, ekl::GAUGE_THREADS, 0, c.stream>>>(dp, c.mask, N, gp);
+        ekl::gauge_apply_kernel<<<c.num_sms * 2, ekl::GAUGE_THREADS, 0, c.stream>>>(c.mask, N, dp, gp);
+        c.launches += 2;
     }
     if (beads) {
         if (c.prec == EKL_F64) beads_kernel<double><<<1, 256, 0, c.stream>>>((const double *)c.R, (const double *)c.V, 3 * c.nb, db);
