@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <new>
+#include <condition_variable>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -323,23 +324,77 @@ static void *g_stage[2] = {nullptr, nullptr};
 static cudaEvent_t g_stage_ev[2];
 static int g_stage_dev = -1;
 
-static void par_memcpy(void *dst, const void *src, size_t n)
-{
-    const int hw = (int)std::thread::hardware_concurrency();
-    const int T = (int)std::max<size_t>(1, std::min<size_t>({(size_t)std::max(1, hw), 16, n >> 22}));
-    if (T <= 1) {
-        memcpy(dst, src, n);
-        return;
+// Host copies of a staged transfer: a crew of threads, made once per
+// transfer, copies each chunk in equal slices (one per thread) while the
+// transfer's next DMA runs.
+class CopyCrew {
+  public:
+    explicit CopyCrew(size_t bytes)
+    {
+        const int hw = (int)std::thread::hardware_concurrency();
+        T_ = (int)std::max<size_t>(1, std::min<size_t>({(size_t)std::max(1, hw), 16, bytes >> 22}));
+        for (int t = 1; t < T_; t++) th_.emplace_back([this, t]() { work(t); });
     }
-    const size_t part = (n + T - 1) / T;
-    std::vector<std::thread> pool;
-    for (int t = 0; t < T; t++) {
-        const size_t off = part * t;
-        if (off >= n) break;
-        pool.emplace_back([=]() { memcpy((char *)dst + off, (const char *)src + off, std::min(part, n - off)); });
+    ~CopyCrew()
+    {
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            stop_ = true;
+        }
+        go_.notify_all();
+        for (auto &t : th_) t.join();
     }
-    for (auto &th : pool) th.join();
-}
+    // dst <- src (n bytes), the calling thread taking slice 0
+    void copy(void *dst, const void *src, size_t n)
+    {
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            dst_ = (char *)dst;
+            src_ = (const char *)src;
+            n_ = n;
+            pending_ = T_ - 1;
+            gen_++;
+        }
+        go_.notify_all();
+        slice(0, (char *)dst, (const char *)src, n);
+        std::unique_lock<std::mutex> lk(m_);
+        done_.wait(lk, [this]() { return pending_ == 0; });
+    }
+
+  private:
+    void slice(int t, char *dst, const char *src, size_t n) const
+    {
+        const size_t part = (n + T_ - 1) / T_, off = part * t;
+        if (off < n) memcpy(dst + off, src + off, std::min(part, n - off));
+    }
+    void work(int t)
+    {
+        long seen = 0;
+        for (;;) {
+            std::unique_lock<std::mutex> lk(m_);
+            go_.wait(lk, [&]() { return stop_ || gen_ != seen; });
+            if (stop_) return;
+            seen = gen_;
+            char *d = dst_;
+            const char *s = src_;
+            const size_t n = n_;
+            lk.unlock();
+            slice(t, d, s, n);
+            lk.lock();
+            if (--pending_ == 0) done_.notify_one();
+        }
+    }
+    int T_ = 1;
+    std::vector<std::thread> th_;
+    std::mutex m_;
+    std::condition_variable go_, done_;
+    long gen_ = 0;
+    int pending_ = 0;
+    bool stop_ = false;
+    char *dst_ = nullptr;
+    const char *src_ = nullptr;
+    size_t n_ = 0;
+};
 
 // dst <- src, bytes long, one side on the device (to_host: src is device
 // memory); ordered on the stream and complete on return
@@ -382,6 +437,7 @@ static cudaError_t staged_copy(cudaStream_t stream, int device, void *dst, const
     }
     const size_t nch = (bytes + STAGE_BYTES - 1) / STAGE_BYTES;
     auto len = [&](size_t k) { return std::min(STAGE_BYTES, bytes - k * STAGE_BYTES); };
+    CopyCrew crew(std::min(bytes, STAGE_BYTES));
     if (to_host) {
         // DMA of chunk k into buffer k % 2 while the host copies chunk k - 1 out
         for (size_t k = 0; k <= nch && e == cudaSuccess; k++) {
@@ -392,7 +448,7 @@ static cudaError_t staged_copy(cudaStream_t stream, int device, void *dst, const
             }
             if (k >= 1 && e == cudaSuccess) {
                 e = cudaEventSynchronize(g_stage_ev[(k - 1) & 1]);
-                if (e == cudaSuccess) par_memcpy((char *)dst + (k - 1) * STAGE_BYTES, g_stage[(k - 1) & 1], len(k - 1));
+                if (e == cudaSuccess) crew.copy((char *)dst + (k - 1) * STAGE_BYTES, g_stage[(k - 1) & 1], len(k - 1));
             }
         }
     } else {
@@ -401,7 +457,7 @@ static cudaError_t staged_copy(cudaStream_t stream, int device, void *dst, const
         for (size_t k = 0; k < nch && e == cudaSuccess; k++) {
             if (k >= 2) e = cudaEventSynchronize(g_stage_ev[k & 1]);
             if (e != cudaSuccess) break;
-            par_memcpy(g_stage[k & 1], (const char *)src + k * STAGE_BYTES, len(k));
+            crew.copy(g_stage[k & 1], (const char *)src + k * STAGE_BYTES, len(k));
             e = cudaMemcpyAsync((char *)dst + k * STAGE_BYTES, g_stage[k & 1], len(k), cudaMemcpyHostToDevice, stream);
             if (e == cudaSuccess) e = cudaEventRecord(g_stage_ev[k & 1], stream);
         }
