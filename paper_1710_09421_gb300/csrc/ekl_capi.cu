@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <new>
 #include <condition_variable>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -655,14 +656,17 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long 
         nlev++;
     }
     if (nlev < 2) return "multigrid needs a coarser level: periodic extents must be multiples of 4";
-    // lattice conductances of the +x, +y, +z faces
+    // lattice conductances of the +x, +y, +z faces (every entry written by
+    // the plane loops: the arrays are not cleared first)
     const long long N = c.N;
-    std::vector<float> sg[3];
-    for (int a = 0; a < 3; a++) sg[a].assign(N, 0.f);
+    std::unique_ptr<float[]> sg[3];
+    for (int a = 0; a < 3; a++) sg[a].reset(new (std::nothrow) float[N]);
+    if (!sg[0] || !sg[1] || !sg[2]) return "host allocation failed";
     host_parallel(c.nz, [&](int z) {  // planes on the host's cores (disjoint writes)
         for (int y = 0; y < c.ny; y++)
             for (int x = 0; x < c.nx; x++) {
                 const long long i = x + (long long)c.nx * (y + (long long)c.ny * z);
+                for (int a = 0; a < 3; a++) sg[a][i] = 0.f;
                 if (solid[i]) continue;
                 const int q[3] = {x, y, z}, L[3] = {c.nx, c.ny, c.nz};
                 for (int a = 0; a < 3; a++) {
@@ -680,8 +684,9 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long 
     for (int l = 1; l < nlev; l++) {
         const int *F = d[l - 1], *C = d[l];
         const long long NC = (long long)C[0] * C[1] * C[2];
-        std::vector<float> cs[3];
-        for (int a = 0; a < 3; a++) cs[a].assign(NC, 0.f);
+        std::unique_ptr<float[]> cs[3];  // every entry written below
+        for (int a = 0; a < 3; a++) cs[a].reset(new (std::nothrow) float[NC]);
+        if (!cs[0] || !cs[1] || !cs[2]) return "host allocation failed";
         host_parallel(C[2], [&](int Z) {
             for (int Y = 0; Y < C[1]; Y++)
                 for (int X = 0; X < C[0]; X++) {
@@ -705,7 +710,7 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long 
                 }
         });
         std::vector<float4> h4(NC);
-        for (int Z = 0; Z < C[2]; Z++)
+        host_parallel(C[2], [&](int Z) {
             for (int Y = 0; Y < C[1]; Y++)
                 for (int X = 0; X < C[0]; X++) {
                     const long long I = X + (long long)C[0] * (Y + (long long)C[1] * Z);
@@ -715,6 +720,7 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long 
                     const double diag = (double)cs[0][I] + cs[1][I] + cs[2][I] + cs[0][xm] + cs[1][ym] + cs[2][zm];
                     h4[I] = make_float4(cs[0][I], cs[1][I], cs[2][I], diag > 0.0 ? (float)(1.0 / diag) : 0.f);
                 }
+        });
         MgLevel &ml = c.mg_lev[l];
         ml.nx = C[0];
         ml.ny = C[1];
@@ -729,7 +735,7 @@ static const char *build_multigrid(Ctx &c, const uint8_t *solid, Alloc &A, long 
         if (cudaMemset(ml.e, 0, NC * sizeof(float)) != cudaSuccess ||
             cudaMemset(ml.t, 0, NC * sizeof(float)) != cudaSuccess)
             return "multigrid setup failed";
-        if (cudaMemcpy(ml.sig, h4.data(), NC * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (staged_copy(c.stream, c.device, ml.sig, h4.data(), NC * sizeof(float4), false) != cudaSuccess)
             return "multigrid upload failed";
         if (l == nlev - 1 && NC <= MG_DENSE_CELLS) {
             const std::vector<float> M = coarse_pinv(C[0], C[1], C[2], h4);
@@ -898,7 +904,16 @@ static int create_handle(const ekl_params *P, void *stream, ekl_handle **out, bo
     // geometry on the host: fluid count, wall charge shares
     const uint8_t *solid = P->solid;
     long long nf = 0;
-    for (long long i = 0; i < N; i++) nf += solid[i] ? 0 : 1;
+    {
+        const long long plane = (long long)c.nx * c.ny;
+        std::vector<long long> nfz(c.nz, 0);
+        host_parallel(c.nz, [&](int z) {
+            long long k = 0;
+            for (long long i = z * plane; i < (z + 1) * plane; i++) k += solid[i] ? 0 : 1;
+            nfz[z] = k;
+        });
+        for (int z = 0; z < c.nz; z++) nf += nfz[z];
+    }
     c.n_fluid = nf;
     bool charged = false;
     if (P->surface_charge)
