@@ -473,6 +473,23 @@ static cudaError_t staged_copy(cudaStream_t stream, int device, void *dst, const
 //   A^+ = (A + sum_parts 1_p 1_p^T / n_p)^-1 - sum_parts 1_p 1_p^T / n_p,
 // the bracket being positive definite (Cholesky, FP64).  Returns row-major
 // FP32 [n][n] with zero rows and columns on inactive cells.
+// sum of a[k] b[k] over k0 <= k < k1 in four interleaved partial sums (a
+// fixed order: the same on every host), so that the products' additions
+// need not wait on one another
+static inline double dot4(const double *a, const double *b, int k0, int k1)
+{
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = k0;
+    for (; k + 4 <= k1; k += 4) {
+        s0 += a[k] * b[k];
+        s1 += a[k + 1] * b[k + 1];
+        s2 += a[k + 2] * b[k + 2];
+        s3 += a[k + 3] * b[k + 3];
+    }
+    for (; k < k1; k++) s0 += a[k] * b[k];
+    return (s0 + s1) + (s2 + s3);
+}
+
 static std::vector<float> coarse_pinv(int nx, int ny, int nz, const std::vector<float4> &sig)
 {
     const int n = nx * ny * nz;
@@ -553,20 +570,13 @@ static std::vector<float> coarse_pinv(int nx, int ny, int nz, const std::vector<
             double *ri = &B[(size_t)i * n];
             for (int j = kb; j < e; j++) {
                 const double *rj = &B[(size_t)j * n];
-                double v = ri[j];
-                for (int k = kb; k < j; k++) v -= ri[k] * rj[k];
-                ri[j] = v / rj[j];
+                ri[j] = (ri[j] - dot4(ri, rj, kb, j)) / rj[j];
             }
         });
         host_parallel(n - e, [&](int t) {
             const int i = e + t;
             double *ri = &B[(size_t)i * n];
-            for (int j = e; j <= i; j++) {
-                const double *rj = &B[(size_t)j * n];
-                double v = 0.0;
-                for (int k = kb; k < e; k++) v += ri[k] * rj[k];
-                ri[j] -= v;
-            }
+            for (int j = e; j <= i; j++) ri[j] -= dot4(ri, &B[(size_t)j * n], kb, e);
         });
     }
     if (!spd) return {};
@@ -577,9 +587,7 @@ static std::vector<float> coarse_pinv(int nx, int ny, int nz, const std::vector<
         w[j] = 1.0 / at(j, j);
         for (int i = j + 1; i < n; i++) {
             const double *ri = &B[(size_t)i * n];
-            double v = 0.0;
-            for (int k = j; k < i; k++) v -= ri[k] * w[k];
-            w[i] = v / ri[i];
+            w[i] = -dot4(ri, w, j, i) / ri[i];
         }
     });
     std::vector<float> M((size_t)n * n, 0.f);
@@ -588,9 +596,7 @@ static std::vector<float> coarse_pinv(int nx, int ny, int nz, const std::vector<
         const double *wi = &Wt[(size_t)i * n];
         for (int j = 0; j <= i; j++) {
             if (!act[j]) continue;
-            const double *wj = &Wt[(size_t)j * n];
-            double v = 0.0;
-            for (int k = i; k < n; k++) v += wi[k] * wj[k];
+            double v = dot4(wi, &Wt[(size_t)j * n], i, n);
             if (part[i] == part[j]) v -= 1.0 / count[part[i]];
             M[(size_t)i * n + j] = M[(size_t)j * n + i] = (float)v;
         }
