@@ -1535,6 +1535,9 @@ void batch_release(Batch &B)
     dev_free(c0, B.d_lrep, 0);
     dev_free(c0, B.d_lloc, 0);
     dev_free(c0, B.d_lrb, 0);
+    dev_free(c0, B.d_crep, 0);
+    dev_free(c0, B.d_cloc, 0);
+    dev_free(c0, B.d_crb, 0);
     dev_free(c0, B.d_mgs_part, 0);
 }
 
@@ -1628,6 +1631,9 @@ int ekl_batch_create(int32_t nrep, const ekl_params *params, void *stream, ekl_b
             B.d_lrep = (int *)A(4 * (size_t)MGS_MAX_FACTOR * sms);
             B.d_lloc = (int *)A(4 * (size_t)MGS_MAX_FACTOR * sms);
             B.d_lrb = (int *)A(4 * (size_t)nrep);
+            B.d_crep = (int *)A(4 * (size_t)2 * sms);
+            B.d_cloc = (int *)A(4 * (size_t)2 * sms);
+            B.d_crb = (int *)A(4 * (size_t)nrep);
             B.d_mgs_part = (double *)A(sizeof(double) * MGS_PART_SLOTS * (size_t)nrep * B.mgs_part_stride);
             if (ok) cudaMemsetAsync(B.d_loops, 0, sizeof(int), B.stream);
             if (!ok) rc = fail(EKL_ERR_ALLOC, "device allocation failed");

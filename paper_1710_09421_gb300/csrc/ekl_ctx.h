@@ -204,6 +204,11 @@ struct Batch {
     int mgs_factor;
     int mgs_lblocks;
     int *d_lrep, *d_lloc, *d_lrb;  // block tables of the lattice passes
+    // block tables of the cooperative coarse launch: two 512-thread blocks
+    // per SM where they fit, so that a replica's coarse levels spread over
+    // more SMs (else one 1024-thread block per SM)
+    int *d_crep, *d_cloc, *d_crb;
+    int mgs_cgrid, mgs_cthreads;
     double *d_mgs_part;      // block partials: per replica MGS_SLOTS x mgs_part_stride
     int mgs_part_stride;
 };

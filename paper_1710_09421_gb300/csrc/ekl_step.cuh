@@ -579,6 +579,27 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_tables(Batc
             cudaMemcpyAsync(B.d_lloc, lloc.data(), lloc.size() * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess ||
             cudaMemcpyAsync(B.d_lrb, lk.data(), n * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess)
             return EKL_ERR_CUDA;
+        // the coarse launch: with the finer lattice tables, two 512-thread
+        // blocks per SM when both are resident (its block-wide sums then run
+        // over 512 threads; factor 1 keeps the cooperative solve's blocks and
+        // results)
+        int occ = 0;
+        if (B.mg_smem > 48 * 1024)
+            cudaFuncSetAttribute(mgsb_coarse_kernel<S, R, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)B.mg_smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mgsb_coarse_kernel<S, R, PhiT>, MGS_THREADS / 2,
+                                                          B.mg_smem) != cudaSuccess)
+            occ = 0;
+        cudaGetLastError();
+        const int per_sm = (B.mgs_factor > 1 && occ >= 2) ? 2 : 1;
+        B.mgs_cthreads = MGS_THREADS / per_sm;
+        std::vector<int> ck, crep, cloc;
+        share_out(B.pois_blocks * per_sm, ck, crep, cloc);
+        B.mgs_cgrid = (int)crep.size();
+        if (cudaMemcpyAsync(B.d_crep, crep.data(), crep.size() * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess ||
+            cudaMemcpyAsync(B.d_cloc, cloc.data(), cloc.size() * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess ||
+            cudaMemcpyAsync(B.d_crb, ck.data(), n * 4, cudaMemcpyHostToDevice, B.stream) != cudaSuccess)
+            return EKL_ERR_CUDA;
     }
     if (cudaStreamSynchronize(B.stream) != cudaSuccess) return EKL_ERR_CUDA;
     if (charge_batch_tables(B) != EKL_OK) return EKL_ERR_CUDA;
@@ -610,7 +631,7 @@ static inline MgsBatch mgsb_args(const Batch &B)
                     (const Grid3 *)B.d_grids,
                     (MgCtl *)B.d_ctl,
                     PoisBatch{B.nrep, B.d_lrep, B.d_lloc, B.d_lrb, B.barrier, B.status},
-                    PoisBatch{B.nrep, B.d_block_rep, B.d_block_local, B.d_rep_blocks, B.barrier, B.status},
+                    PoisBatch{B.nrep, B.d_crep, B.d_cloc, B.d_crb, B.barrier, B.status},
                     B.d_mgs_part,
                     B.mgs_part_stride,
                     B.d_loops};
@@ -618,7 +639,7 @@ static inline MgsBatch mgsb_args(const Batch &B)
 
 template <typename S, typename R, typename PhiT> static cudaError_t mgsb_build(Batch &B, bool pdl)
 {
-    const int n = B.nrep, nb = B.mgs_lblocks, ncb = B.pois_blocks, nt = MGS_THREADS;
+    const int n = B.nrep, nb = B.mgs_lblocks, ncb = B.mgs_cgrid, nt = MGS_THREADS;
     const StepArgs<S, R, PhiT> *reps = (const StepArgs<S, R, PhiT> *)B.d_args[0];
     MgsBatch mb = mgsb_args(B);
     unsigned *bars = B.mg_bars;
@@ -688,7 +709,7 @@ template <typename S, typename R, typename PhiT> static cudaError_t mgsb_build(B
         coop[0].id = cudaLaunchAttributeCooperative;
         coop[0].val.cooperative = 1;
         cfg.gridDim = dim3(ncb);
-        cfg.blockDim = dim3(nt);
+        cfg.blockDim = dim3(B.mgs_cthreads);
         cfg.dynamicSmemBytes = B.mg_smem;
         cfg.stream = cs;
         cfg.attrs = coop;
@@ -768,7 +789,7 @@ template <typename S, typename R, typename PhiT, bool DEV> int batch_impl(Batch 
             }
             if (B.mgs_split) {
                 static_assert(MGS_THREADS == MG_BATCH_THREADS, "split and cooperative batch solves share the grid");
-                if (B.mgs_exec && (B.mgs_blocks != B.mgs_lblocks || B.mgs_cblocks != B.pois_blocks)) {
+                if (B.mgs_exec && (B.mgs_blocks != B.mgs_lblocks || B.mgs_cblocks != B.mgs_cgrid)) {
                     cudaGraphExecDestroy(B.mgs_exec);
                     cudaGraphDestroy(B.mgs_graph);
                     B.mgs_exec = nullptr;
