@@ -282,15 +282,16 @@ ekl_handle *ekl_batch_replica(ekl_batch *b, int32_t rep);
  * *choice_out gets its index (bit 0: 512-thread blocks, bit 1: fluid
  * weighting).  A multigrid batch keeps one 1024-thread block per SM for its
  * coarse levels; bit 0 then puts the split solve's lattice passes on four
- * times the blocks (not available to the cooperative form). */
+ * times the blocks and its coarse launch on two 512-thread blocks per SM
+ * (not available to the cooperative form). */
 int ekl_batch_autotune(ekl_batch *b, int32_t trial_steps, int32_t *choice_out);
 
 /* Set the Poisson schedule the autotuner would pick as `choice` (0..3; bit 1:
  * blocks shared by fluid nodes, else by all nodes; bit 0: SOR on 512-thread
  * blocks two per SM, or for a split multigrid batch its lattice passes on
- * four times the blocks of the coarse launch, whose block partials then
- * differ from the cooperative form's, so the potentials agree to rounding
- * instead of bit for bit).  Takes effect at the next step.  EKL_ERR_ARG for
+ * four times as many blocks and its coarse launch on two 512-thread blocks
+ * per SM, whose sums then run in another order than the cooperative
+ * form's, so the potentials agree to rounding instead of bit for bit).  Takes effect at the next step.  EKL_ERR_ARG for
  * a choice out of range or not available (bit 0 on a cooperative multigrid
  * batch). */
 int ekl_batch_set_schedule(ekl_batch *b, int32_t choice);
