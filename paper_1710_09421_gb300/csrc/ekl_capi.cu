@@ -333,8 +333,17 @@ class CopyCrew {
     explicit CopyCrew(size_t bytes)
     {
         const int hw = (int)std::thread::hardware_concurrency();
-        T_ = (int)std::max<size_t>(1, std::min<size_t>({(size_t)std::max(1, hw), 16, bytes >> 22}));
-        for (int t = 1; t < T_; t++) th_.emplace_back([this, t]() { work(t); });
+        const int T = (int)std::max<size_t>(1, std::min<size_t>({(size_t)std::max(1, hw), 16, bytes >> 22}));
+        // slices are set by the threads actually made (T_ is read by the
+        // workers only after the first copy() publishes a job under m_)
+        for (int t = 1; t < T; t++) {
+            try {
+                th_.emplace_back([this, t]() { work(t); });
+            } catch (...) {
+                break;
+            }
+        }
+        T_ = (int)th_.size() + 1;
     }
     ~CopyCrew()
     {
