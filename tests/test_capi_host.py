@@ -47,3 +47,19 @@ def test_no_cpu_fallback_in_binding():
     assert "oracle" not in src.replace("# ", "")
     for name in ("stream(", "collide", "poisson_solve"):
         assert name not in src
+
+
+def test_batch_entry_points_reject_a_null_batch():
+    """The batch calls check their handle before any CUDA work: a null batch
+    is refused with EKL_ERR_ARG and a message (and has made no launches)."""
+    import ctypes as C
+
+    L = E.load()
+    L.ekl_batch_set_schedule.argtypes = [C.c_void_p, C.c_int32]
+    L.ekl_batch_step.argtypes = [C.c_void_p, C.c_int32]
+    L.ekl_batch_launches.argtypes = [C.c_void_p]
+    L.ekl_batch_launches.restype = C.c_int64
+    assert L.ekl_batch_set_schedule(None, 1) == E.EKL_ERR_ARG
+    assert b"batch" in L.ekl_last_error()
+    assert L.ekl_batch_step(None, 1) == E.EKL_ERR_ARG
+    assert L.ekl_batch_launches(None) == 0
